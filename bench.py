@@ -1,0 +1,300 @@
+#!/usr/bin/env python
+"""Throughput of BSGD-TV epochs on one GB300 (or N independent ones).
+
+A step is one epoch of Algorithm 1 (fused block products, reductions, step and
+the FGP TV prox) on the 512x512 workload: 30-ellipse phantom, parallel beam
+with 360 angles x 727 bins (A has 1.2e8 nonzeros, 0.96 GB as FP32 values +
+int32 indices), M = N = 8 blocks, lambda = 0.02, 50 FGP iterations.  The
+inputs (A) are larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  With torchrun (N > 1) every rank reconstructs its own
+slice (weak scaling, no data exchange); the elapsed time is the max over
+ranks.  --impl reference times the FP64 CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "BSGD-TV epochs/s + HBM GB/s (fused Ax,Aᵀr,TV-prox); served p50/p99 latency"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "products_ellipse512.json")
+TRAFFIC_SOURCES = ["paper_1812_01307_gb300/csrc/products.cu", "paper_1812_01307_gb300/csrc/layout.cpp",
+                   "paper_1812_01307_gb300/csrc/bsgdtv_internal.h"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="ellipse512")
+    ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(wl):
+    return (f"{wl.name}: {wl.n}x{wl.n} image, {wl.n_ellipses} ellipses, parallel beam "
+            f"{wl.n_angles} angles x {wl.n_bins} bins, M=N={wl.M}, lambda={wl.lam}, "
+            f"{wl.fgp_iters} FGP iterations per epoch, x0=0")
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, flags in rows for k, fl in enumerate(flags)
+                          if fl.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the product kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    try:
+        with open(PROFILE_TRAFFIC) as f:
+            prof = json.load(f)
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for p in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    if prof.get("source_sha256") != h.hexdigest():
+        return None
+    return prof.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_epochs_per_s(P, mu, seconds, min_epochs=2, max_epochs=10 ** 9):
+    """Times the FP64 oracle's epochs (block-by-block Algorithm 1 + FGP) on the
+    host; returns (epochs/s, epochs timed, seconds)."""
+    import numpy as np
+    import oracle
+    wl = P.wl
+    A = oracle.to_scipy(P.A)
+    rb, cb = oracle.partition(A.shape[0], A.shape[1], wl.M, wl.N, wl.n_bins, wl.n)
+    blocks = oracle.split_blocks(A, rb, cb)
+    y = P.y.astype(np.float32).astype(np.float64)
+    x = np.zeros(A.shape[1])
+    r = y.copy()
+    rng = np.random.default_rng(0)
+    done = 0
+    t0 = time.perf_counter()
+    while done < max_epochs and (done < min_epochs or time.perf_counter() - t0 < seconds):
+        x, r, _ = oracle.epoch(blocks, rb, cb, y, x, r, mu, wl.lam, wl.fgp_iters, (wl.n, wl.n), rng)
+        done += 1
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args):
+    from paper_1812_01307_gb300 import dist as D
+    rank, _, world = D.env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1812_01307_gb300 import synth
+    wl = synth.WORKLOADS[args.workload]
+    P = synth.make_problem(wl)
+    u, _ = oracle.power_iteration(P.A, 1000, 1e-10)
+    mu = 0.9 / (2 * u)
+    # warm-up (one epoch at most) and a bounded timed sample of the K steps
+    oracle_epochs_per_s(P, mu, 0.0, min_epochs=min(args.warmup, 1), max_epochs=min(args.warmup, 1))
+    budget = 120.0
+    v, done, dt = oracle_epochs_per_s(P, mu, budget, min_epochs=1, max_epochs=max(args.steps, 1))
+    sample = (f"{done} of the {args.steps} requested epochs of {wl.name} (time-bounded, "
+              f"{dt:.1f} s), FP64 numpy/scipy, block by block")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "epochs/s", "n_gpus": args.gpus,
+            "steps": done, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_desc(wl)},
+            "cpu_baseline": {"value": v, "unit": "epochs/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "epochs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1812_01307_gb300 import dist as D
+    from paper_1812_01307_gb300 import synth
+    rank, local, world = D.env_rank()
+    if world != args.gpus:
+        print(f"warning: WORLD_SIZE={world} but --gpus {args.gpus}", file=sys.stderr)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    D.barrier()
+    from paper_1812_01307_gb300 import bsgdtv as B
+    B.load()
+
+    base = synth.WORKLOADS[args.workload]
+    import dataclasses
+    wl = dataclasses.replace(base, seed=base.seed + rank)   # each rank its own slice
+    P = synth.make_problem(wl)
+    rec = B.Reconstructor(P.A, (wl.n, wl.n), wl.M, wl.N, row_unit=wl.n_bins, col_unit=wl.n)
+    u, _ = rec.estimate_umax(1000, 1e-10)
+    mu = 0.9 / (2 * u)
+    y_dev = torch.tensor(P.y, dtype=torch.float32, device=dev)
+    rec.set_data(y_dev, wl.lam, mu)
+    info = rec.info()
+    K, W = args.steps, args.warmup
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    rec.run(W, wl.fgp_iters)
+    torch.cuda.synchronize()
+    launches0 = B.bsgdtv_launch_count()
+    D.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    prod_ms, epoch_ms = B.bsgdtv_run_timed(rec.h, K, wl.fgp_iters)
+    ev1.record()
+    torch.cuda.synchronize()
+    D.barrier()
+    clocks = sampler.stop()
+    launches = B.bsgdtv_launch_count() - launches0
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    elapsed_max = D.max_over_ranks(elapsed, dev)
+    value = world * K / elapsed_max
+
+    # end to end through the public API: y from pinned host memory in, x out, every step
+    E = max(1, min(args.e2e_steps, K))
+    y_pin = torch.empty(P.A.rows, dtype=torch.float32).pin_memory()
+    y_pin.copy_(torch.from_numpy(P.y.astype(np.float32)))
+    x_pin = torch.empty(P.A.cols_n, dtype=torch.float32).pin_memory()
+    y_np, x_np = y_pin.numpy(), x_pin.numpy()
+    torch.cuda.synchronize()
+    D.barrier()
+    t0 = time.perf_counter()
+    for _ in range(E):
+        B.bsgdtv_set_data(rec.h, y_np, wl.lam, mu)
+        rec.run(1, wl.fgp_iters)
+        B.bsgdtv_get_x(rec.h, x_np)
+    torch.cuda.synchronize()
+    e2e_dt = D.max_over_ranks(time.perf_counter() - t0, dev)
+    e2e = {"value": world * E / e2e_dt, "unit": "epochs/s", "h2d_bytes_per_step": 4 * P.A.rows,
+           "d2h_bytes_per_step": 4 * P.A.cols_n, "steps": E,
+           "note": "per step: bsgdtv_set_data(host y) + bsgdtv_run(1 epoch) + bsgdtv_get_x(host x)"}
+    rec.close()
+
+    peak, peak_kind = hbm_peak()
+    prod_avg_s = prod_ms / 1e3 / K
+    per_launch = info["min_bytes_per_pass"]
+    achieved = per_launch / prod_avg_s / 1e9
+    R, c, nnz = P.A.rows, P.A.cols_n, info["nnz"]
+    epoch_bytes = 8 * nnz + 4 * (3 * R + 2 * c) + 8 * c
+    line = {"metric": METRIC, "value": value, "unit": "epochs/s", "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": 1e3 * elapsed_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(wl), "parallelism": f"independent slices x{world}",
+                       "l2": "inputs larger than L2 (A = %.2f GB), no flush" % (8 * nnz / 1e9),
+                       "nnz": nnz, "segments": info["segments"], "work_items": info["work_items"]},
+            "hbm_gbs_epoch": epoch_bytes * K / (elapsed / 1.0) / 1e9 if world == 1 else None,
+            "products_per_s": 2 * value,
+            "roofline": {"bound": "hbm", "kernel": "products_kernel (fused Ax, 2A^T r)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": profiled_traffic(), "bytes_per_launch": per_launch,
+                         "avg_launch_ms": prod_avg_s * 1e3,
+                         "share_of_epoch": prod_ms / epoch_ms if epoch_ms > 0 else None},
+            "gpu_launches": launches, "clocks": clocks, "e2e": e2e}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, done, dt = oracle_epochs_per_s(P, mu, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "epochs/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{done} epochs of {wl.name} from x=0 ({dt:.1f} s, FP64 numpy/scipy, one thread)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,177 @@
+/*
+ * bsgdtv.h -- C ABI of the GB300 (sm_103a) BSGD-TV library.
+ *
+ * BSGD-TV (Gao & Blumensath, arXiv 1812.01307) reconstructs an image x from
+ * projections y ~ A x by repeating one epoch of Algorithm 1:
+ *   lines 2-5  block products  z^j_{I_i} = A_{I_i}^{J_j} x_{J_j}  and
+ *              g^i_{J_j} = 2 (A_{I_i}^{J_j})^T r_{I_i}   (r from the previous epoch)
+ *   line 6     r = y - sum_j z^j
+ *   line 7     g = sum_i g^i
+ *   line 8     x = x + mu g
+ *   line 9     x = argmin_t ||t - x||^2 + 2 mu lambda TV(t), solved by Beck &
+ *              Teboulle's fast gradient projection (FGP) with tau = mu*lambda.
+ * A is divided into M row blocks I_i and N column blocks J_j (Sec. 2.1).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: BSGDTV_OK (0) or a negative BSGDTV_ERR_* code.  Nothing
+ *     throws across this boundary.  bsgdtv_last_error() gives a message for
+ *     the calling thread's most recent failure.
+ *   - Host arrays passed in are copied; the caller keeps ownership.  A handle
+ *     owns all the device memory it allocates and frees it in bsgdtv_destroy.
+ *   - `*_on_device` flags say whether a pointer is device memory (1) or host
+ *     memory (0).  Device pointers must be on the handle's device.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
+ *     call enqueues its work on the handle's stream; calls that return data to
+ *     the host (get_x to host, objective, estimate_umax, ...) synchronise it.
+ *   - The image is img_h x img_w, row-major (pixel (s,t) is column s*img_w+t
+ *     of A).  TV is isotropic with forward differences and a zero-difference
+ *     (Neumann) border, the discretisation FGP is defined on.
+ *   - Floating point: A values, x, y, r are FP32 with FP32 accumulation on the
+ *     hot path; u_max and the objective are computed in FP64.
+ */
+#ifndef BSGDTV_H
+#define BSGDTV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bsgdtv_ctx *bsgdtv_t;
+
+enum {
+    BSGDTV_OK = 0,
+    BSGDTV_ERR_INVALID_ARG = -1, /* bad size, pointer, bound or flag */
+    BSGDTV_ERR_OOM = -2,         /* device or host allocation failed */
+    BSGDTV_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    BSGDTV_ERR_STATE = -4,       /* call out of order (e.g. run before set_data) */
+    BSGDTV_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    BSGDTV_ERR_NONFINITE = -6,   /* NaN/Inf in an input */
+    BSGDTV_ERR_UNSUPPORTED = -7  /* valid request this build does not handle */
+};
+
+/* Creates a handle from a host CSR matrix A (rows = rays, cols = pixels).
+ *   rows, cols          size of A; cols must equal img_h*img_w.
+ *   row_ptr [rows+1]    int64 offsets, row_ptr[0] = 0, non-decreasing.
+ *   col_idx [nnz]       int32 column indices in [0, cols), ascending in a row.
+ *   vals    [nnz]       float64 weights (stored on the device as FP32).
+ *   M, N                number of row / column blocks (Sec. 2.1).
+ *   row_bounds [M+1]    optional explicit I_i bounds (NULL: numpy.array_split of
+ *                       rows/row_unit units into M groups, times row_unit).
+ *   col_bounds [N+1]    optional explicit J_j bounds (NULL: the same with
+ *                       cols/col_unit and N).  Every J_j bound must be a multiple
+ *                       of img_w: column blocks are bands of whole image rows.
+ *   row_unit, col_unit  grouping units for the default bounds (e.g. n_bins and
+ *                       img_w so that I_i are whole angles, J_j whole rows).
+ *   stream              cudaStream_t for all of this handle's work.
+ * Validates the CSR (sorted, in range, finite) and fails with
+ * BSGDTV_ERR_INVALID_ARG / BSGDTV_ERR_NONFINITE otherwise. */
+int bsgdtv_create_csr(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, int img_w,
+                      const int64_t *row_ptr, const int32_t *col_idx, const double *vals,
+                      int M, int N, int64_t row_unit, int64_t col_unit,
+                      const int64_t *row_bounds, const int64_t *col_bounds, void *stream);
+
+/* Releases every resource of the handle.  NULL is ignored. */
+void bsgdtv_destroy(bsgdtv_t h);
+
+/* Copies the partition bounds I_i [M+1] and J_j [N+1] (host arrays). */
+int bsgdtv_get_partition(bsgdtv_t h, int64_t *row_bounds, int64_t *col_bounds);
+
+/* Sets the projections y [rows] (FP32), the TV weight lambda >= 0 and the step
+ * mu.  mu <= 0 selects mu = 0.9/(2 u_max) (Theorem 1 requires mu < 1/(2 u_max)),
+ * estimating u_max first if no estimate exists.  Resets the iteration:
+ * x^0 = 0, r^{-1} = y - A x^0 = y, epoch counter 0.  Rejects NaN/Inf in y
+ * (BSGDTV_ERR_NONFINITE). */
+int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, double mu);
+
+/* Largest eigenvalue u_max of A^T A by power iteration in FP64 on the device
+ * (A as stored, i.e. FP32 weights widened to FP64), from the all-ones vector,
+ * stopping when the Rayleigh quotient changes by <= rel_tol relatively or after
+ * max_iters iterations.  Writes u_max and the iteration count (may be NULL). */
+int bsgdtv_estimate_umax(bsgdtv_t h, int max_iters, double rel_tol, double *u_max, int *iters);
+
+/* Current step mu (after set_data) and the stored u_max estimate (0 if none). */
+int bsgdtv_get_params(bsgdtv_t h, double *mu, double *lambda, double *u_max);
+
+/* Runs `epochs` epochs of Algorithm 1 with `fgp_iters` FGP iterations for
+ * line 9 (lambda = 0 or fgp_iters = 0 makes line 9 the identity).  Asynchronous
+ * on the handle's stream; resumes from the current state. */
+int bsgdtv_run(bsgdtv_t h, int epochs, int fgp_iters);
+
+/* bsgdtv_run that also times, with CUDA events recorded on the handle's
+ * stream inside the epoch graphs, every launch of the fused product kernel
+ * (lines 2-5) and every whole epoch.  Synchronises.  products_ms / epoch_ms
+ * (may be NULL) receive the sums over the `epochs` epochs. */
+int bsgdtv_run_timed(bsgdtv_t h, int epochs, int fgp_iters, double *products_ms,
+                     double *epoch_ms);
+
+/* Copies x [cols] (FP32).  To the host: synchronises the stream. */
+int bsgdtv_get_x(bsgdtv_t h, float *out, int out_on_device);
+
+/* Checkpoint: x^k [cols], r^{k-1} [rows] (the residual the next epoch's
+ * gradient uses) and k.  set_state restores them (requires set_data first). */
+int bsgdtv_get_state(bsgdtv_t h, float *x, float *r, int64_t *epoch, int on_device);
+int bsgdtv_set_state(bsgdtv_t h, const float *x, const float *r, int64_t epoch, int on_device);
+
+/* FP64 monitoring of the current x: data term ||y - A x||^2 and TV(x)
+ * (Eq. 1; the function line 9 as printed minimises is data + lambda*TV).
+ * Synchronises. */
+int bsgdtv_objective(bsgdtv_t h, double *data_term, double *tv);
+
+/* Test hook: the block products of lines 3-4 for given x [cols] and r [rows]
+ * (device pointers), computed by the same fused kernel the epoch uses.
+ *   z_blocks [N*rows]:  z_blocks[j*rows + k] = (A_{I_i}^{J_j} x_{J_j})_k for row
+ *                       k of block I_i (i.e. z^j stacked over i).
+ *   g_blocks [M*cols]:  g_blocks[i*cols + c] = (2 (A_{I_i}^{J_j})^T r_{I_i})_c
+ *                       for column c of block J_j.
+ * Does not touch the iteration state. */
+int bsgdtv_block_products(bsgdtv_t h, const float *x, const float *r, float *z_blocks,
+                          float *g_blocks);
+
+/* Sizes of the stored operator: nnz of A, number of row segments in the tiled
+ * layout, work items per product pass, and the bytes one product pass must
+ * move at minimum (8 B per nonzero + x, r, z, g once). */
+int bsgdtv_get_info(bsgdtv_t h, int64_t *nnz, int64_t *segments, int64_t *work_items,
+                    int64_t *min_bytes_per_pass);
+
+/* Line 9 alone: x = FGP(b, tau, iters) for one img_h x img_w image (device
+ * pointers b, x; may not alias).  Beck-Teboulle FGP, cold start, isotropic TV,
+ * P_C = identity; tau <= 0 or iters <= 0 copies b.  Allocates its scratch (the
+ * dual fields) from the device heap for the duration of the call and
+ * synchronises `stream` before returning. */
+int bsgdtv_tv_prox(const float *b, float *x, int img_h, int img_w, double tau, int iters,
+                   void *stream);
+
+/* Host only (no GPU needed): the partition bounds bsgdtv_create_csr uses when
+ * row_bounds / col_bounds are NULL, written to row_bounds [M+1] and
+ * col_bounds [N+1]. */
+int bsgdtv_partition_bounds(int64_t rows, int64_t cols, int M, int N, int64_t row_unit,
+                            int64_t col_unit, int64_t *row_bounds, int64_t *col_bounds);
+
+/* Host only (no GPU needed): validates a CSR exactly as bsgdtv_create_csr
+ * does, builds the tiled device layout in host memory and checks that decoding
+ * it gives back A (columns exact, values equal to the FP32-rounded input).
+ * stats [6] (may be NULL) receives {nnz, segments, slabs, work items, row
+ * groups, pixel tiles}.  Returns BSGDTV_ERR_INVALID_ARG / _NONFINITE for a bad
+ * CSR and BSGDTV_ERR_STATE if the layout does not reproduce A. */
+int bsgdtv_layout_check(int64_t rows, int64_t cols, int img_h, int img_w, const int64_t *row_ptr,
+                        const int32_t *col_idx, const double *vals, int M, int N,
+                        int64_t row_unit, int64_t col_unit, const int64_t *row_bounds,
+                        const int64_t *col_bounds, int target_items, int64_t *stats);
+
+/* Number of kernels this library has launched in the calling process
+ * (graph replays count every kernel node). */
+int64_t bsgdtv_launch_count(void);
+
+/* Message for the calling thread's most recent failure ("" if none). */
+const char *bsgdtv_last_error(void);
+
+/* Static description of an error code. */
+const char *bsgdtv_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSGDTV_H */

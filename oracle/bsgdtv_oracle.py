@@ -235,12 +235,17 @@ def epoch(blocks, rb, cb, y, x, r_prev, mu, lam, fgp_iters, img_shape, rng=None)
 
 
 def run(A, y, img_shape, M, N, lam, mu, epochs, fgp_iters, row_unit=1, col_unit=1,
-        x0=None, r0=None, seed=0, callback=None):
+        x0=None, r0=None, seed=0, callback=None, row_bounds=None, col_bounds=None):
     """Algorithm 1 for `epochs` epochs from x^0 (default 0) and r^{-1} (default
-    y - A x^0, R3).  Returns (x, r) after the last epoch."""
+    y - A x^0, R3).  Explicit block bounds override the unit split.  Returns
+    (x, r) after the last epoch."""
     A = to_scipy(A)
     rows, cols = A.shape
     rb, cb = partition(rows, cols, M, N, row_unit, col_unit)
+    if row_bounds is not None:
+        rb = np.asarray(row_bounds, dtype=np.int64)
+    if col_bounds is not None:
+        cb = np.asarray(col_bounds, dtype=np.int64)
     blocks = split_blocks(A, rb, cb)
     y = np.asarray(y, dtype=np.float64)
     x = np.zeros(cols) if x0 is None else np.asarray(x0, dtype=np.float64).copy()

@@ -1,0 +1,363 @@
+"""Python binding of the BSGD-TV C ABI (``include/bsgdtv.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``libbsgdtv.so``.  The functions carry the C names.  Device buffers
+are passed as CUDA ``torch.Tensor`` objects (PyTorch supplies device memory
+and the stream); host buffers as numpy arrays.  There is no fallback: if the
+library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+_lib = None
+
+
+class BsgdtvError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Loads libbsgdtv.so (built by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"BSGD-TV CUDA library not built: {path} is missing "
+                           "(run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "bsgdtv_create_csr": (I32, [ctypes.POINTER(P), I64, I64, I32, I32, P, P, P, I32, I32, I64, I64, P, P, P]),
+        "bsgdtv_destroy": (None, [P]),
+        "bsgdtv_get_partition": (I32, [P, P, P]),
+        "bsgdtv_set_data": (I32, [P, P, I32, D, D]),
+        "bsgdtv_estimate_umax": (I32, [P, I32, D, ctypes.POINTER(D), ctypes.POINTER(I32)]),
+        "bsgdtv_get_params": (I32, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "bsgdtv_run": (I32, [P, I32, I32]),
+        "bsgdtv_run_timed": (I32, [P, I32, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "bsgdtv_get_x": (I32, [P, P, I32]),
+        "bsgdtv_get_state": (I32, [P, P, P, ctypes.POINTER(I64), I32]),
+        "bsgdtv_set_state": (I32, [P, P, P, I64, I32]),
+        "bsgdtv_objective": (I32, [P, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "bsgdtv_block_products": (I32, [P, P, P, P, P]),
+        "bsgdtv_get_info": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "bsgdtv_tv_prox": (I32, [P, P, I32, I32, D, I32, P]),
+        "bsgdtv_partition_bounds": (I32, [I64, I64, I32, I32, I64, I64, P, P]),
+        "bsgdtv_layout_check": (I32, [I64, I64, I32, I32, P, P, P, I32, I32, I64, I64, P, P, I32, P]),
+        "bsgdtv_launch_count": (I64, []),
+        "bsgdtv_last_error": (ctypes.c_char_p, []),
+        "bsgdtv_strerror": (ctypes.c_char_p, [I32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names the binding expects the library to export."""
+    return ["bsgdtv_create_csr", "bsgdtv_destroy", "bsgdtv_get_partition", "bsgdtv_set_data",
+            "bsgdtv_estimate_umax", "bsgdtv_get_params", "bsgdtv_run", "bsgdtv_run_timed", "bsgdtv_get_x",
+            "bsgdtv_get_state", "bsgdtv_set_state", "bsgdtv_objective", "bsgdtv_block_products",
+            "bsgdtv_get_info", "bsgdtv_tv_prox", "bsgdtv_partition_bounds", "bsgdtv_layout_check",
+            "bsgdtv_launch_count", "bsgdtv_last_error", "bsgdtv_strerror"]
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        lib = load()
+        msg = lib.bsgdtv_last_error().decode() or lib.bsgdtv_strerror(rc).decode()
+        raise BsgdtvError(rc, where, msg)
+
+
+def _dev_ptr(t, dtype=None, numel=None):
+    """Pointer of a contiguous CUDA tensor (checked)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch.Tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a, dtype, numel=None):
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a C-contiguous numpy array of {np.dtype(dtype)}")
+    if numel is not None and a.size != numel:
+        raise ValueError(f"expected {numel} elements, got {a.size}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _is_tensor(a) -> bool:
+    try:
+        import torch
+        return isinstance(a, torch.Tensor)
+    except ImportError:
+        return False
+
+
+def current_stream():
+    """cudaStream_t of torch's current stream (None if CUDA is unavailable)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ C names
+def bsgdtv_create_csr(rows, cols, img_h, img_w, row_ptr, col_idx, vals, M, N, row_unit=1,
+                      col_unit=1, row_bounds=None, col_bounds=None, stream=None):
+    lib = load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    vals = np.ascontiguousarray(vals, dtype=np.float64)
+    if row_ptr.size != rows + 1:
+        raise ValueError("row_ptr must have rows+1 entries")
+    rb = None if row_bounds is None else np.ascontiguousarray(row_bounds, dtype=np.int64)
+    cb = None if col_bounds is None else np.ascontiguousarray(col_bounds, dtype=np.int64)
+    h = ctypes.c_void_p()
+    rc = lib.bsgdtv_create_csr(ctypes.byref(h), int(rows), int(cols), int(img_h), int(img_w),
+                               _host_ptr(row_ptr, np.int64), _host_ptr(col_idx, np.int32),
+                               _host_ptr(vals, np.float64), int(M), int(N), int(row_unit),
+                               int(col_unit), None if rb is None else _host_ptr(rb, np.int64),
+                               None if cb is None else _host_ptr(cb, np.int64),
+                               stream if stream is not None else current_stream())
+    _check(rc, "bsgdtv_create_csr")
+    return h
+
+
+def bsgdtv_destroy(h):
+    load().bsgdtv_destroy(h)
+
+
+def bsgdtv_get_partition(h, M, N):
+    rb = np.zeros(M + 1, dtype=np.int64)
+    cb = np.zeros(N + 1, dtype=np.int64)
+    _check(load().bsgdtv_get_partition(h, _host_ptr(rb, np.int64), _host_ptr(cb, np.int64)),
+           "bsgdtv_get_partition")
+    return rb, cb
+
+
+def bsgdtv_set_data(h, y, lam, mu=0.0):
+    lib = load()
+    if _is_tensor(y):
+        import torch
+        rc = lib.bsgdtv_set_data(h, _dev_ptr(y, torch.float32), 1, float(lam), float(mu))
+    else:
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        rc = lib.bsgdtv_set_data(h, _host_ptr(y, np.float32), 0, float(lam), float(mu))
+    _check(rc, "bsgdtv_set_data")
+
+
+def bsgdtv_estimate_umax(h, max_iters=5000, rel_tol=1e-12):
+    u = ctypes.c_double()
+    it = ctypes.c_int()
+    _check(load().bsgdtv_estimate_umax(h, int(max_iters), float(rel_tol), ctypes.byref(u),
+                                       ctypes.byref(it)), "bsgdtv_estimate_umax")
+    return u.value, it.value
+
+
+def bsgdtv_get_params(h):
+    mu, lam, u = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().bsgdtv_get_params(h, ctypes.byref(mu), ctypes.byref(lam), ctypes.byref(u)),
+           "bsgdtv_get_params")
+    return mu.value, lam.value, u.value
+
+
+def bsgdtv_run(h, epochs, fgp_iters):
+    _check(load().bsgdtv_run(h, int(epochs), int(fgp_iters)), "bsgdtv_run")
+
+
+def bsgdtv_run_timed(h, epochs, fgp_iters):
+    """Runs epochs and returns (sum of product-kernel ms, sum of epoch ms)."""
+    pk, ep = ctypes.c_double(), ctypes.c_double()
+    _check(load().bsgdtv_run_timed(h, int(epochs), int(fgp_iters), ctypes.byref(pk),
+                                   ctypes.byref(ep)), "bsgdtv_run_timed")
+    return pk.value, ep.value
+
+
+def bsgdtv_get_info(h):
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(load().bsgdtv_get_info(h, *[ctypes.byref(a) for a in v]), "bsgdtv_get_info")
+    return {"nnz": v[0].value, "segments": v[1].value, "work_items": v[2].value,
+            "min_bytes_per_pass": v[3].value}
+
+
+def bsgdtv_get_x(h, out):
+    """Copies x into `out` (CUDA float32 tensor or float32 numpy array)."""
+    lib = load()
+    if _is_tensor(out):
+        import torch
+        rc = lib.bsgdtv_get_x(h, _dev_ptr(out, torch.float32), 1)
+    else:
+        rc = lib.bsgdtv_get_x(h, _host_ptr(out, np.float32), 0)
+    _check(rc, "bsgdtv_get_x")
+    return out
+
+
+def bsgdtv_get_state(h, x, r):
+    lib = load()
+    ep = ctypes.c_int64()
+    if _is_tensor(x):
+        import torch
+        rc = lib.bsgdtv_get_state(h, _dev_ptr(x, torch.float32), _dev_ptr(r, torch.float32),
+                                  ctypes.byref(ep), 1)
+    else:
+        rc = lib.bsgdtv_get_state(h, _host_ptr(x, np.float32), _host_ptr(r, np.float32),
+                                  ctypes.byref(ep), 0)
+    _check(rc, "bsgdtv_get_state")
+    return ep.value
+
+
+def bsgdtv_set_state(h, x, r, epoch):
+    lib = load()
+    if _is_tensor(x):
+        import torch
+        rc = lib.bsgdtv_set_state(h, _dev_ptr(x, torch.float32), _dev_ptr(r, torch.float32),
+                                  int(epoch), 1)
+    else:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        r = np.ascontiguousarray(r, dtype=np.float32)
+        rc = lib.bsgdtv_set_state(h, _host_ptr(x, np.float32), _host_ptr(r, np.float32),
+                                  int(epoch), 0)
+    _check(rc, "bsgdtv_set_state")
+
+
+def bsgdtv_objective(h):
+    f, tv = ctypes.c_double(), ctypes.c_double()
+    _check(load().bsgdtv_objective(h, ctypes.byref(f), ctypes.byref(tv)), "bsgdtv_objective")
+    return f.value, tv.value
+
+
+def bsgdtv_block_products(h, x, r, z_blocks, g_blocks):
+    import torch
+    _check(load().bsgdtv_block_products(h, _dev_ptr(x, torch.float32), _dev_ptr(r, torch.float32),
+                                        _dev_ptr(z_blocks, torch.float32),
+                                        _dev_ptr(g_blocks, torch.float32)),
+           "bsgdtv_block_products")
+
+
+def bsgdtv_tv_prox(b, x, tau, iters, stream=None):
+    import torch
+    if b.dim() != 2 or x.shape != b.shape:
+        raise ValueError("b and x must be matching 2-D tensors")
+    _check(load().bsgdtv_tv_prox(_dev_ptr(b, torch.float32), _dev_ptr(x, torch.float32),
+                                 int(b.shape[0]), int(b.shape[1]), float(tau), int(iters),
+                                 stream if stream is not None else current_stream()),
+           "bsgdtv_tv_prox")
+
+
+def bsgdtv_partition_bounds(rows, cols, M, N, row_unit=1, col_unit=1):
+    """Host only: default I_i / J_j bounds."""
+    rb = np.zeros(M + 1, dtype=np.int64)
+    cb = np.zeros(N + 1, dtype=np.int64)
+    _check(load().bsgdtv_partition_bounds(int(rows), int(cols), int(M), int(N), int(row_unit),
+                                          int(col_unit), _host_ptr(rb, np.int64),
+                                          _host_ptr(cb, np.int64)), "bsgdtv_partition_bounds")
+    return rb, cb
+
+
+def bsgdtv_layout_check(rows, cols, img_h, img_w, row_ptr, col_idx, vals, M, N, row_unit=1,
+                        col_unit=1, row_bounds=None, col_bounds=None, target_items=608):
+    """Host only: builds the device layout in host memory and checks it decodes
+    back to A.  Returns the layout statistics (raises on failure)."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    vals = np.ascontiguousarray(vals, dtype=np.float64)
+    rb = None if row_bounds is None else np.ascontiguousarray(row_bounds, dtype=np.int64)
+    cb = None if col_bounds is None else np.ascontiguousarray(col_bounds, dtype=np.int64)
+    stats = np.zeros(6, dtype=np.int64)
+    rc = load().bsgdtv_layout_check(int(rows), int(cols), int(img_h), int(img_w),
+                                    _host_ptr(row_ptr, np.int64), _host_ptr(col_idx, np.int32),
+                                    _host_ptr(vals, np.float64), int(M), int(N), int(row_unit),
+                                    int(col_unit), None if rb is None else _host_ptr(rb, np.int64),
+                                    None if cb is None else _host_ptr(cb, np.int64),
+                                    int(target_items), _host_ptr(stats, np.int64))
+    _check(rc, "bsgdtv_layout_check")
+    keys = ["nnz", "segments", "slabs", "work_items", "groups", "tiles"]
+    return dict(zip(keys, (int(v) for v in stats)))
+
+
+def bsgdtv_launch_count() -> int:
+    return int(load().bsgdtv_launch_count())
+
+
+def bsgdtv_strerror(code: int) -> str:
+    return load().bsgdtv_strerror(int(code)).decode()
+
+
+# ------------------------------------------------------------- convenience
+class Reconstructor:
+    """Owns one handle: ``Reconstructor(A, img_shape, M, N, ...)`` then
+    ``set_data`` / ``run`` / ``x()``.  `A` is any host CSR with row_ptr, cols,
+    vals, rows and cols_n attributes."""
+
+    def __init__(self, A, img_shape, M, N, row_unit=1, col_unit=1, row_bounds=None,
+                 col_bounds=None, stream=None):
+        self.img_shape = tuple(img_shape)
+        self.rows, self.cols = int(A.rows), int(A.cols_n)
+        self.M, self.N = int(M), int(N)
+        self.h = bsgdtv_create_csr(self.rows, self.cols, img_shape[0], img_shape[1], A.row_ptr,
+                                   A.cols, A.vals, M, N, row_unit, col_unit, row_bounds,
+                                   col_bounds, stream)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            bsgdtv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def partition(self):
+        return bsgdtv_get_partition(self.h, self.M, self.N)
+
+    def info(self):
+        return bsgdtv_get_info(self.h)
+
+    def estimate_umax(self, max_iters=5000, rel_tol=1e-12):
+        return bsgdtv_estimate_umax(self.h, max_iters, rel_tol)
+
+    def set_data(self, y, lam, mu=0.0):
+        bsgdtv_set_data(self.h, y, lam, mu)
+
+    def params(self):
+        return bsgdtv_get_params(self.h)
+
+    def run(self, epochs, fgp_iters):
+        bsgdtv_run(self.h, epochs, fgp_iters)
+
+    def x(self, out=None):
+        if out is None:
+            out = np.empty(self.cols, dtype=np.float32)
+        return bsgdtv_get_x(self.h, out)
+
+    def objective(self):
+        return bsgdtv_objective(self.h)

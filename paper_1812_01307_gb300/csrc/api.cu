@@ -1,0 +1,694 @@
+// C ABI of the BSGD-TV library: handle lifetime, data, the epoch loop of
+// Algorithm 1 (captured once per configuration into CUDA graphs), the FP64
+// step-size estimate (Theorem 1) and monitoring (Eq. 1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "bsgdtv_internal.h"
+
+namespace bsgdtv {
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches(0);
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int resolve_bounds(int64_t rows, int64_t cols, int M, int N, int64_t row_unit, int64_t col_unit,
+                   const int64_t *row_bounds, const int64_t *col_bounds, std::vector<int64_t> &rb,
+                   std::vector<int64_t> &cb) {
+    if (rows < 1 || cols < 1 || M < 1 || N < 1)
+        return fail(BSGDTV_ERR_INVALID_ARG, "rows, cols, M, N must be >= 1");
+    if (!row_bounds && (row_unit < 1 || rows % row_unit || rows / row_unit < M))
+        return fail(BSGDTV_ERR_INVALID_ARG, "row_unit must divide rows into at least M units");
+    if (!col_bounds && (col_unit < 1 || cols % col_unit || cols / col_unit < N))
+        return fail(BSGDTV_ERR_INVALID_ARG, "col_unit must divide cols into at least N units");
+    rb = row_bounds ? std::vector<int64_t>(row_bounds, row_bounds + M + 1)
+                    : default_bounds(rows, M, row_unit);
+    cb = col_bounds ? std::vector<int64_t>(col_bounds, col_bounds + N + 1)
+                    : default_bounds(cols, N, col_unit);
+    return BSGDTV_OK;
+}
+
+}  // namespace bsgdtv
+
+using namespace bsgdtv;
+
+struct bsgdtv_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;     // caller's stream (may be the legacy default)
+    cudaStream_t cap_stream = nullptr; // private stream used only for graph capture
+    HostLayout host;                   // layout metadata (bulk arrays released after upload)
+    DevLayout dl;
+    std::vector<void *> allocs;
+
+    float *y = nullptr, *r[2] = {nullptr, nullptr}, *x = nullptr, *xhat = nullptr;
+    float *z_part = nullptr, *g_part = nullptr;
+    float *fp = nullptr, *fq = nullptr, *fpp = nullptr, *fqp = nullptr;
+    float *mom = nullptr;
+    int mom_len = 0;
+    int *flag = nullptr;
+    int cur = 0;   // r[cur] holds r^{k-1}
+    bool has_data = false;
+    double lambda = 0.0, mu = 0.0, u_max = 0.0;
+    int64_t epoch = 0;
+    int64_t seg_count = 0;
+
+    // FP64 scratch (allocated on first use)
+    double *v64 = nullptr, *w64 = nullptr, *g64 = nullptr, *z64 = nullptr, *gp64 = nullptr,
+           *y64 = nullptr, *x64 = nullptr, *partials = nullptr, *scal = nullptr;
+
+    // graphs: one per parity of the r double buffer
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    // timed variant: event-record nodes around the product kernel and at the
+    // end of the epoch, re-pointed to fresh events before every replay
+    cudaGraph_t tgraph[2] = {nullptr, nullptr};
+    cudaGraphExec_t texec[2] = {nullptr, nullptr};
+    cudaGraphNode_t tnode[2][3] = {};
+    cudaEvent_t tmark[3] = {nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> tevents;
+    int graph_fgp_iters = -1;
+    bool graph_prox = false;
+    double graph_mu = 0.0, graph_lambda = 0.0;
+    int64_t graph_kernels = 0;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(bsgdtv_ctx *h, T **out, size_t count) {
+    void *p = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BSGDTV_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) +
+                                        "): " + cudaGetErrorString(e));
+    }
+    h->allocs.push_back(p);
+    *out = static_cast<T *>(p);
+    return BSGDTV_OK;
+}
+
+template <typename T>
+int upload(bsgdtv_ctx *h, T **out, const std::vector<T> &v) {
+    BSG_CHECK(dalloc(h, out, v.size()));
+    if (!v.empty())
+        BSG_CUDA(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice,
+                                 h->stream));
+    return BSGDTV_OK;
+}
+
+void drop_graphs(bsgdtv_ctx *h) {
+    for (auto &g : h->gexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    for (auto &g : h->texec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    for (auto &g : h->tgraph)
+        if (g) {
+            cudaGraphDestroy(g);
+            g = nullptr;
+        }
+    for (auto &row : h->tnode)
+        for (auto &nd : row) nd = nullptr;
+    h->graph_fgp_iters = -1;
+}
+
+int ensure_mom(bsgdtv_ctx *h, int iters) {
+    if (iters <= h->mom_len) {
+        // coefficients are a prefix-stable sequence: reuse
+        return BSGDTV_OK;
+    }
+    std::vector<float> m;
+    fgp_momentum_host(iters, m);
+    float *d = nullptr;
+    BSG_CHECK(dalloc(h, &d, m.size()));
+    BSG_CUDA(cudaMemcpy(d, m.data(), m.size() * sizeof(float), cudaMemcpyHostToDevice));
+    h->mom = d;
+    h->mom_len = iters;
+    return BSGDTV_OK;
+}
+
+// Enqueues one epoch (lines 2-9) reading r[par] and writing r[1-par].  With
+// `marks`, records marks[0] / marks[1] around the product kernel and marks[2]
+// at the end of the epoch.
+int enqueue_epoch(bsgdtv_ctx *h, int par, int fgp_iters, cudaStream_t s,
+                  cudaEvent_t *marks = nullptr) {
+    const bool prox = h->lambda > 0.0 && fgp_iters > 0;
+    if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[0], s, cudaEventRecordExternal));
+    BSG_CUDA(launch_products<float>(h->dl, h->x, h->r[par], h->z_part, h->g_part, s));
+    if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[1], s, cudaEventRecordExternal));
+    float *xdst = prox ? h->xhat : h->x;
+    BSG_CUDA(launch_reduce_update<float>(h->dl, h->z_part, h->g_part, h->y, h->r[1 - par], h->x,
+                                         xdst, (float)h->mu, s));
+    if (prox) {
+        FgpScratch sc{h->fp, h->fq, h->fpp, h->fqp};
+        BSG_CUDA(launch_fgp(h->xhat, h->x, h->dl.img_h, h->dl.img_w, (float)(h->mu * h->lambda),
+                            fgp_iters, h->mom, sc, s));
+    }
+    if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[2], s, cudaEventRecordExternal));
+    return BSGDTV_OK;
+}
+
+int build_timed_graphs(bsgdtv_ctx *h, int fgp_iters) {
+    for (int k = 0; k < 3; ++k)
+        if (!h->tmark[k]) BSG_CUDA(cudaEventCreate(&h->tmark[k]));
+    const int64_t before = g_launches.load();
+    for (int par = 0; par < 2; ++par) {
+        cudaGraph_t g = nullptr;
+        BSG_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_epoch(h, par, fgp_iters, h->cap_stream, h->tmark);
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (rc != BSGDTV_OK) {
+            if (g) cudaGraphDestroy(g);
+            g_launches.fetch_sub(g_launches.load() - before);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(BSGDTV_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        h->tgraph[par] = g;
+        size_t n = 0;
+        BSG_CUDA(cudaGraphGetNodes(g, nullptr, &n));
+        std::vector<cudaGraphNode_t> nodes(n);
+        BSG_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            BSG_CUDA(cudaGraphNodeGetType(nd, &t));
+            if (t != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev;
+            BSG_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+            for (int k = 0; k < 3; ++k)
+                if (ev == h->tmark[k]) h->tnode[par][k] = nd;
+        }
+        for (int k = 0; k < 3; ++k)
+            if (!h->tnode[par][k]) return fail(BSGDTV_ERR_CUDA, "timed graph: event node not found");
+        BSG_CUDA(cudaGraphInstantiate(&h->texec[par], g, 0));
+    }
+    g_launches.fetch_sub(g_launches.load() - before);
+    return BSGDTV_OK;
+}
+
+int build_graphs(bsgdtv_ctx *h, int fgp_iters) {
+    drop_graphs(h);
+    BSG_CHECK(ensure_mom(h, std::max(fgp_iters, 1)));
+    const int64_t before = g_launches.load();
+    for (int par = 0; par < 2; ++par) {
+        cudaGraph_t g = nullptr;
+        BSG_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_epoch(h, par, fgp_iters, h->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (rc != BSGDTV_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(BSGDTV_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&h->gexec[par], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(BSGDTV_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    // capture counted the kernels once per parity; replays are counted in run
+    const int64_t per_epoch = (g_launches.load() - before) / 2;
+    g_launches.fetch_sub(g_launches.load() - before);
+    h->graph_kernels = per_epoch;
+    h->graph_fgp_iters = fgp_iters;
+    h->graph_prox = h->lambda > 0.0 && fgp_iters > 0;
+    h->graph_mu = h->mu;
+    h->graph_lambda = h->lambda;
+    return BSGDTV_OK;
+}
+
+int ensure_fp64(bsgdtv_ctx *h) {
+    if (h->v64) return BSGDTV_OK;
+    const int64_t c = h->dl.cols, R = h->dl.rows;
+    BSG_CHECK(dalloc(h, &h->v64, c));
+    BSG_CHECK(dalloc(h, &h->g64, c));
+    BSG_CHECK(dalloc(h, &h->x64, c));
+    BSG_CHECK(dalloc(h, &h->w64, R));
+    BSG_CHECK(dalloc(h, &h->y64, R));
+    BSG_CHECK(dalloc(h, &h->z64, h->dl.n_slabs * kSlab));
+    BSG_CHECK(dalloc(h, &h->gp64, (size_t)h->dl.n_groups * c));
+    BSG_CHECK(dalloc(h, &h->partials, kDotPartials));
+    BSG_CHECK(dalloc(h, &h->scal, 8));
+    return BSGDTV_OK;
+}
+
+int prepare_kernels() {
+    BSG_CUDA(prepare_products_kernels());
+    return BSGDTV_OK;
+}
+
+int set_device(bsgdtv_ctx *h) {
+    BSG_CUDA(cudaSetDevice(h->device));
+    return BSGDTV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bsgdtv_last_error(void) { return g_last_error.c_str(); }
+
+const char *bsgdtv_strerror(int code) {
+    switch (code) {
+        case BSGDTV_OK: return "ok";
+        case BSGDTV_ERR_INVALID_ARG: return "invalid argument";
+        case BSGDTV_ERR_OOM: return "out of memory";
+        case BSGDTV_ERR_CUDA: return "CUDA error";
+        case BSGDTV_ERR_STATE: return "call out of order";
+        case BSGDTV_ERR_TIMEOUT: return "device wait timed out";
+        case BSGDTV_ERR_NONFINITE: return "non-finite input";
+        case BSGDTV_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown error";
+    }
+}
+
+int64_t bsgdtv_launch_count(void) { return g_launches.load(); }
+
+int bsgdtv_partition_bounds(int64_t rows, int64_t cols, int M, int N, int64_t row_unit,
+                            int64_t col_unit, int64_t *row_bounds, int64_t *col_bounds) {
+    if (!row_bounds || !col_bounds) return fail(BSGDTV_ERR_INVALID_ARG, "null output");
+    std::vector<int64_t> rb, cb;
+    BSG_CHECK(resolve_bounds(rows, cols, M, N, row_unit, col_unit, nullptr, nullptr, rb, cb));
+    std::copy(rb.begin(), rb.end(), row_bounds);
+    std::copy(cb.begin(), cb.end(), col_bounds);
+    return BSGDTV_OK;
+}
+
+int bsgdtv_layout_check(int64_t rows, int64_t cols, int img_h, int img_w, const int64_t *row_ptr,
+                        const int32_t *col_idx, const double *vals, int M, int N,
+                        int64_t row_unit, int64_t col_unit, const int64_t *row_bounds,
+                        const int64_t *col_bounds, int target_items, int64_t *stats) {
+    std::vector<int64_t> rb, cb;
+    BSG_CHECK(resolve_bounds(rows, cols, M, N, row_unit, col_unit, row_bounds, col_bounds, rb, cb));
+    try {
+        HostLayout L;
+        BSG_CHECK(build_layout(L, rows, cols, img_h, img_w, row_ptr, col_idx, vals, M, N,
+                               rb.data(), cb.data(), target_items));
+        BSG_CHECK(verify_layout(L, row_ptr, col_idx, vals));
+        if (stats) {
+            stats[0] = L.nnz;
+            stats[1] = (int64_t)L.ray_seg_pos.size();
+            stats[2] = L.n_slabs();
+            stats[3] = (int64_t)L.items.size();
+            stats[4] = L.n_groups();
+            stats[5] = (int64_t)L.tiles.size();
+        }
+    } catch (const std::bad_alloc &) {
+        return fail(BSGDTV_ERR_OOM, "host allocation while building the layout");
+    }
+    return BSGDTV_OK;
+}
+
+int bsgdtv_create_csr(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, int img_w,
+                      const int64_t *row_ptr, const int32_t *col_idx, const double *vals, int M,
+                      int N, int64_t row_unit, int64_t col_unit, const int64_t *row_bounds,
+                      const int64_t *col_bounds, void *stream) {
+    if (!out) return fail(BSGDTV_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    std::vector<int64_t> rb, cb;
+    BSG_CHECK(resolve_bounds(rows, cols, M, N, row_unit, col_unit, row_bounds, col_bounds, rb, cb));
+    std::unique_ptr<bsgdtv_ctx> h(new (std::nothrow) bsgdtv_ctx());
+    if (!h) return fail(BSGDTV_ERR_OOM, "host allocation");
+    // the layout is validated and built on the host before any CUDA call
+    int sms = 152;
+    if (cudaGetDevice(&h->device) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    cudaGetLastError();
+    try {
+        BSG_CHECK(build_layout(h->host, rows, cols, img_h, img_w, row_ptr, col_idx, vals, M, N,
+                               rb.data(), cb.data(), 4 * sms));
+    } catch (const std::bad_alloc &) {
+        return fail(BSGDTV_ERR_OOM, "host allocation while building the layout");
+    }
+    BSG_CUDA(cudaGetDevice(&h->device));
+    h->stream = (cudaStream_t)stream;
+    HostLayout &L = h->host;
+    BSG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    bsgdtv_ctx *hp = h.get();
+    DevLayout &d = h->dl;
+    {
+        float *v = nullptr;
+        int32_t *ix = nullptr, *sr = nullptr, *sln = nullptr, *rsp = nullptr, *rsq = nullptr,
+                *si = nullptr, *gb = nullptr;
+        int64_t *so = nullptr;
+        WorkItem *it = nullptr;
+        Tile *tl = nullptr;
+        int rc = BSGDTV_OK;
+        if ((rc = upload(hp, &v, L.vals)) || (rc = upload(hp, &ix, L.idx)) ||
+            (rc = upload(hp, &so, L.slab_off)) || (rc = upload(hp, &sr, L.seg_ray)) ||
+            (rc = upload(hp, &sln, L.seg_len)) || (rc = upload(hp, &it, L.items)) ||
+            (rc = upload(hp, &tl, L.tiles)) || (rc = upload(hp, &rsp, L.ray_seg_ptr)) ||
+            (rc = upload(hp, &rsq, L.ray_seg_pos)) || (rc = upload(hp, &si, L.slab_item)) ||
+            (rc = upload(hp, &gb, L.group_block)) || (rc = prepare_kernels())) {
+            bsgdtv_destroy(h.release());
+            return rc;
+        }
+        d.vals = v;
+        d.idx = ix;
+        d.slab_off = so;
+        d.seg_ray = sr;
+        d.seg_len = sln;
+        d.items = it;
+        d.tiles = tl;
+        d.ray_seg_ptr = rsp;
+        d.ray_seg_pos = rsq;
+        d.slab_item = si;
+        d.group_block = gb;
+    }
+    d.n_items = (int)L.items.size();
+    d.n_groups = (int)L.n_groups();
+    d.n_tiles = (int)L.tiles.size();
+    d.M = M;
+    d.N = N;
+    d.n_slabs = L.n_slabs();
+    d.rows = rows;
+    d.cols = cols;
+    d.img_h = img_h;
+    d.img_w = img_w;
+    h->seg_count = (int64_t)L.ray_seg_pos.size();
+    int rc = BSGDTV_OK;
+    if ((rc = dalloc(hp, &h->y, rows)) || (rc = dalloc(hp, &h->r[0], rows)) ||
+        (rc = dalloc(hp, &h->r[1], rows)) || (rc = dalloc(hp, &h->x, cols)) ||
+        (rc = dalloc(hp, &h->xhat, cols)) || (rc = dalloc(hp, &h->z_part, d.n_slabs * kSlab)) ||
+        (rc = dalloc(hp, &h->g_part, (size_t)d.n_groups * cols)) || (rc = dalloc(hp, &h->fp, cols)) ||
+        (rc = dalloc(hp, &h->fq, cols)) || (rc = dalloc(hp, &h->fpp, cols)) ||
+        (rc = dalloc(hp, &h->fqp, cols)) || (rc = dalloc(hp, &h->flag, 1))) {
+        bsgdtv_destroy(h.release());
+        return rc;
+    }
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        bsgdtv_destroy(h.release());
+        return fail(BSGDTV_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    }
+    // bulk host arrays are no longer needed
+    std::vector<float>().swap(L.vals);
+    std::vector<int32_t>().swap(L.idx);
+    std::vector<int32_t>().swap(L.seg_ray);
+    std::vector<int32_t>().swap(L.ray_seg_pos);
+    *out = h.release();
+    return BSGDTV_OK;
+}
+
+void bsgdtv_destroy(bsgdtv_t h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    for (cudaEvent_t ev : h->tevents) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : h->tmark)
+        if (ev) cudaEventDestroy(ev);
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+}
+
+int bsgdtv_get_partition(bsgdtv_t h, int64_t *row_bounds, int64_t *col_bounds) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (row_bounds) std::memcpy(row_bounds, h->host.row_bounds.data(), (h->host.M + 1) * sizeof(int64_t));
+    if (col_bounds) std::memcpy(col_bounds, h->host.col_bounds.data(), (h->host.N + 1) * sizeof(int64_t));
+    return BSGDTV_OK;
+}
+
+int bsgdtv_get_info(bsgdtv_t h, int64_t *nnz, int64_t *segments, int64_t *work_items,
+                    int64_t *min_bytes_per_pass) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (nnz) *nnz = h->host.nnz;
+    if (segments) *segments = h->seg_count;
+    if (work_items) *work_items = h->dl.n_items;
+    if (min_bytes_per_pass)
+        *min_bytes_per_pass = 8 * h->host.nnz + 4 * (2 * h->dl.rows + 2 * h->dl.cols);
+    return BSGDTV_OK;
+}
+
+int bsgdtv_estimate_umax(bsgdtv_t h, int max_iters, double rel_tol, double *u_max, int *iters) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (max_iters < 1 || !(rel_tol >= 0.0)) return fail(BSGDTV_ERR_INVALID_ARG, "bad max_iters / rel_tol");
+    BSG_CHECK(set_device(h));
+    BSG_CHECK(ensure_fp64(h));
+    cudaStream_t s = h->stream;
+    const int64_t c = h->dl.cols, R = h->dl.rows;
+    // v = 1 / ||1||
+    BSG_CUDA(launch_fill64(h->v64, 1.0 / std::sqrt((double)c), c, s));
+    BSG_CUDA(launch_fill64(h->w64, 0.0, R, s));
+    double u = 0.0, u_new = 0.0;
+    int it = 0;
+    for (it = 1; it <= max_iters; ++it) {
+        // w = A v
+        BSG_CUDA(launch_products<double>(h->dl, h->v64, h->w64, h->z64, h->gp64, s));
+        BSG_CUDA(launch_reduce_update<double>(h->dl, h->z64, h->gp64, nullptr, h->w64, nullptr,
+                                              h->g64, 0.0, s));
+        // g = 2 A^T w  (the product kernel carries line 3's factor 2)
+        BSG_CUDA(launch_products<double>(h->dl, h->v64, h->w64, h->z64, h->gp64, s));
+        BSG_CUDA(launch_reduce_update<double>(h->dl, h->z64, h->gp64, nullptr, h->w64, nullptr,
+                                              h->g64, 0.0, s));
+        BSG_CUDA(launch_dot(h->v64, h->g64, c, h->partials, h->scal + 0, s));
+        BSG_CUDA(launch_dot(h->g64, nullptr, c, h->partials, h->scal + 1, s));
+        double sc[2];
+        BSG_CUDA(cudaMemcpyAsync(sc, h->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        BSG_CUDA(cudaStreamSynchronize(s));
+        u_new = 0.5 * sc[0];   // v . (A^T A v), ||v|| = 1
+        if (sc[1] == 0.0) {
+            u = 0.0;
+            break;
+        }
+        BSG_CUDA(launch_scale64(h->g64, h->scal + 1, h->v64, c, s));
+        if (it > 1 && std::fabs(u_new - u) <= rel_tol * std::fabs(u_new)) {
+            u = u_new;
+            break;
+        }
+        u = u_new;
+    }
+    if (it > max_iters) it = max_iters;
+    BSG_CUDA(cudaStreamSynchronize(s));
+    h->u_max = u;
+    if (u_max) *u_max = u;
+    if (iters) *iters = it;
+    return BSGDTV_OK;
+}
+
+int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, double mu) {
+    if (!h || !y) return fail(BSGDTV_ERR_INVALID_ARG, "null handle or y");
+    if (!(lambda >= 0.0) || !std::isfinite(lambda) || !std::isfinite(mu))
+        return fail(BSGDTV_ERR_INVALID_ARG, "lambda must be finite and >= 0, mu finite");
+    BSG_CHECK(set_device(h));
+    cudaStream_t s = h->stream;
+    const int64_t R = h->dl.rows, c = h->dl.cols;
+    if (!y_on_device) {
+        for (int64_t i = 0; i < R; ++i)
+            if (!std::isfinite(y[i])) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+        BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float), cudaMemcpyHostToDevice, s));
+    } else {
+        BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        int flag = 0;
+        BSG_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+        BSG_CUDA(launch_check_finite(h->y, R, h->flag, s));
+        BSG_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BSG_CUDA(cudaStreamSynchronize(s));
+        if (flag) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+    }
+    // x^0 = 0, r^{-1} = y - A x^0 = y
+    BSG_CUDA(cudaMemsetAsync(h->x, 0, c * sizeof(float), s));
+    h->cur = 0;
+    BSG_CUDA(cudaMemcpyAsync(h->r[0], h->y, R * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (mu <= 0.0) {
+        if (h->u_max <= 0.0) {
+            double u;
+            BSG_CHECK(bsgdtv_estimate_umax(h, 5000, 1e-12, &u, nullptr));
+        }
+        if (h->u_max <= 0.0) return fail(BSGDTV_ERR_INVALID_ARG, "A is zero: u_max = 0");
+        mu = 0.9 / (2.0 * h->u_max);
+    }
+    if (h->mu != mu || h->lambda != lambda) drop_graphs(h);
+    h->lambda = lambda;
+    h->mu = mu;
+    h->epoch = 0;
+    h->has_data = true;
+    return BSGDTV_OK;
+}
+
+int bsgdtv_get_params(bsgdtv_t h, double *mu, double *lambda, double *u_max) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (mu) *mu = h->mu;
+    if (lambda) *lambda = h->lambda;
+    if (u_max) *u_max = h->u_max;
+    return BSGDTV_OK;
+}
+
+int bsgdtv_run(bsgdtv_t h, int epochs, int fgp_iters) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (!h->has_data) return fail(BSGDTV_ERR_STATE, "bsgdtv_run before bsgdtv_set_data");
+    if (epochs < 0 || fgp_iters < 0) return fail(BSGDTV_ERR_INVALID_ARG, "negative epochs / fgp_iters");
+    if (epochs == 0) return BSGDTV_OK;
+    BSG_CHECK(set_device(h));
+    if (!h->gexec[0] || h->graph_fgp_iters != fgp_iters || h->graph_mu != h->mu ||
+        h->graph_lambda != h->lambda)
+        BSG_CHECK(build_graphs(h, fgp_iters));
+    for (int e = 0; e < epochs; ++e) {
+        BSG_CUDA(cudaGraphLaunch(h->gexec[h->cur], h->stream));
+        add_launches(h->graph_kernels);
+        h->cur ^= 1;
+        h->epoch++;
+    }
+    return BSGDTV_OK;
+}
+
+int bsgdtv_run_timed(bsgdtv_t h, int epochs, int fgp_iters, double *products_ms,
+                     double *epoch_ms) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (!h->has_data) return fail(BSGDTV_ERR_STATE, "bsgdtv_run_timed before bsgdtv_set_data");
+    if (epochs < 0 || fgp_iters < 0) return fail(BSGDTV_ERR_INVALID_ARG, "negative epochs / fgp_iters");
+    BSG_CHECK(set_device(h));
+    if (!h->gexec[0] || h->graph_fgp_iters != fgp_iters || h->graph_mu != h->mu ||
+        h->graph_lambda != h->lambda)
+        BSG_CHECK(build_graphs(h, fgp_iters));
+    if (!h->texec[0]) BSG_CHECK(build_timed_graphs(h, fgp_iters));
+    const size_t need = (size_t)3 * epochs;
+    while (h->tevents.size() < need) {
+        cudaEvent_t ev;
+        BSG_CUDA(cudaEventCreate(&ev));
+        h->tevents.push_back(ev);
+    }
+    for (int e = 0; e < epochs; ++e) {
+        cudaGraphExec_t ex = h->texec[h->cur];
+        for (int k = 0; k < 3; ++k)
+            BSG_CUDA(cudaGraphExecEventRecordNodeSetEvent(ex, h->tnode[h->cur][k], h->tevents[3 * e + k]));
+        BSG_CUDA(cudaGraphLaunch(ex, h->stream));
+        add_launches(h->graph_kernels);
+        h->cur ^= 1;
+        h->epoch++;
+    }
+    BSG_CUDA(cudaStreamSynchronize(h->stream));
+    double pk = 0.0, ep = 0.0;
+    for (int e = 0; e < epochs; ++e) {
+        float a = 0.f, b = 0.f;
+        BSG_CUDA(cudaEventElapsedTime(&a, h->tevents[3 * e], h->tevents[3 * e + 1]));
+        BSG_CUDA(cudaEventElapsedTime(&b, h->tevents[3 * e], h->tevents[3 * e + 2]));
+        pk += a;
+        ep += b;
+    }
+    if (products_ms) *products_ms = pk;
+    if (epoch_ms) *epoch_ms = ep;
+    return BSGDTV_OK;
+}
+
+int bsgdtv_get_x(bsgdtv_t h, float *out, int out_on_device) {
+    if (!h || !out) return fail(BSGDTV_ERR_INVALID_ARG, "null handle or out");
+    BSG_CHECK(set_device(h));
+    const size_t bytes = h->dl.cols * sizeof(float);
+    BSG_CUDA(cudaMemcpyAsync(out, h->x, bytes,
+                             out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             h->stream));
+    if (!out_on_device) BSG_CUDA(cudaStreamSynchronize(h->stream));
+    return BSGDTV_OK;
+}
+
+int bsgdtv_get_state(bsgdtv_t h, float *x, float *r, int64_t *epoch, int on_device) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (!h->has_data) return fail(BSGDTV_ERR_STATE, "no data set");
+    BSG_CHECK(set_device(h));
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (x) BSG_CUDA(cudaMemcpyAsync(x, h->x, h->dl.cols * sizeof(float), k, h->stream));
+    if (r) BSG_CUDA(cudaMemcpyAsync(r, h->r[h->cur], h->dl.rows * sizeof(float), k, h->stream));
+    if (epoch) *epoch = h->epoch;
+    if (!on_device) BSG_CUDA(cudaStreamSynchronize(h->stream));
+    return BSGDTV_OK;
+}
+
+int bsgdtv_set_state(bsgdtv_t h, const float *x, const float *r, int64_t epoch, int on_device) {
+    if (!h || !x || !r) return fail(BSGDTV_ERR_INVALID_ARG, "null handle, x or r");
+    if (!h->has_data) return fail(BSGDTV_ERR_STATE, "set_state before set_data");
+    if (epoch < 0) return fail(BSGDTV_ERR_INVALID_ARG, "negative epoch");
+    BSG_CHECK(set_device(h));
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    BSG_CUDA(cudaMemcpyAsync(h->x, x, h->dl.cols * sizeof(float), k, h->stream));
+    BSG_CUDA(cudaMemcpyAsync(h->r[h->cur], r, h->dl.rows * sizeof(float), k, h->stream));
+    if (!on_device) BSG_CUDA(cudaStreamSynchronize(h->stream));
+    h->epoch = epoch;
+    return BSGDTV_OK;
+}
+
+int bsgdtv_objective(bsgdtv_t h, double *data_term, double *tv) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (!h->has_data) return fail(BSGDTV_ERR_STATE, "no data set");
+    BSG_CHECK(set_device(h));
+    BSG_CHECK(ensure_fp64(h));
+    cudaStream_t s = h->stream;
+    const int64_t c = h->dl.cols, R = h->dl.rows;
+    BSG_CUDA(launch_f32_to_f64(h->x, h->x64, c, s));
+    BSG_CUDA(launch_f32_to_f64(h->y, h->y64, R, s));
+    BSG_CUDA(launch_fill64(h->w64, 0.0, R, s));
+    BSG_CUDA(launch_products<double>(h->dl, h->x64, h->w64, h->z64, h->gp64, s));
+    // w = y - A x (FP64)
+    BSG_CUDA(launch_reduce_update<double>(h->dl, h->z64, h->gp64, h->y64, h->w64, nullptr, h->g64,
+                                          0.0, s));
+    BSG_CUDA(launch_dot(h->w64, nullptr, R, h->partials, h->scal + 2, s));
+    BSG_CUDA(launch_tv64(h->x, h->dl.img_h, h->dl.img_w, h->partials, h->scal + 3, s));
+    double sc[2];
+    BSG_CUDA(cudaMemcpyAsync(sc, h->scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BSG_CUDA(cudaStreamSynchronize(s));
+    if (data_term) *data_term = sc[0];
+    if (tv) *tv = sc[1];
+    return BSGDTV_OK;
+}
+
+int bsgdtv_block_products(bsgdtv_t h, const float *x, const float *r, float *z_blocks,
+                          float *g_blocks) {
+    if (!h || !x || !r || !z_blocks || !g_blocks)
+        return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    BSG_CHECK(set_device(h));
+    cudaStream_t s = h->stream;
+    BSG_CUDA(launch_products<float>(h->dl, x, r, h->z_part, h->g_part, s));
+    BSG_CUDA(launch_block_sums(h->dl, h->z_part, h->g_part, z_blocks, g_blocks, s));
+    BSG_CUDA(cudaStreamSynchronize(s));
+    return BSGDTV_OK;
+}
+
+int bsgdtv_tv_prox(const float *b, float *x, int img_h, int img_w, double tau, int iters,
+                   void *stream) {
+    if (!b || !x || img_h < 1 || img_w < 1 || iters < 0 || !std::isfinite(tau))
+        return fail(BSGDTV_ERR_INVALID_ARG, "bad argument");
+    if (b == x) return fail(BSGDTV_ERR_INVALID_ARG, "b and x may not alias");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = (int64_t)img_h * img_w;
+    if (tau <= 0.0 || iters == 0) {
+        BSG_CUDA(cudaMemcpyAsync(x, b, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        BSG_CUDA(cudaStreamSynchronize(s));
+        return BSGDTV_OK;
+    }
+    std::vector<float> m;
+    fgp_momentum_host(iters, m);
+    float *scratch = nullptr;
+    const size_t bytes = (4 * n + m.size()) * sizeof(float);
+    BSG_CUDA(cudaMallocAsync((void **)&scratch, bytes, s));
+    float *mom = scratch + 4 * n;
+    cudaError_t e = cudaMemcpyAsync(mom, m.data(), m.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        FgpScratch sc{scratch, scratch + n, scratch + 2 * n, scratch + 3 * n};
+        e = launch_fgp(b, x, img_h, img_w, (float)tau, iters, mom, sc, s);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s);   // keeps m alive until the copy is done
+    cudaFreeAsync(scratch, s);
+    cudaError_t e3 = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(BSGDTV_ERR_CUDA, std::string("tv_prox: ") + cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return fail(BSGDTV_ERR_CUDA, std::string("tv_prox: ") + cudaGetErrorString(e2));
+    if (e3 != cudaSuccess) return fail(BSGDTV_ERR_CUDA, std::string("tv_prox: ") + cudaGetErrorString(e3));
+    return BSGDTV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// Internal declarations of the BSGD-TV library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bsgdtv.h"
+
+namespace bsgdtv {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+#define BSG_CUDA(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return ::bsgdtv::fail(BSGDTV_ERR_CUDA, std::string(#call) + ": " +               \
+                                                       cudaGetErrorString(e_));              \
+    } while (0)
+#define BSG_CHECK(expr)                \
+    do {                               \
+        int rc_ = (expr);              \
+        if (rc_ != BSGDTV_OK) return rc_; \
+    } while (0)
+
+void add_launches(int64_t n);
+
+// ------------------------------------------------------- tiled operator layout
+// The image is cut into pixel tiles (at most kTileH x kTileW, never crossing a
+// column-block band J_j) and the rows into groups (sub-ranges of the row blocks
+// I_i).  A work item is one (group, tile) pair.  Inside a work item every row
+// that touches the tile contributes one segment (its nonzeros in that tile).
+// Segments are packed 32 to a slab; a slab is stored column by column (element
+// k of every segment longer than k, in lane order), so that a warp reads it
+// with coalesced loads, one lane per segment.
+constexpr int kTileH = 64;
+constexpr int kTileW = 64;
+constexpr int kTileStride = kTileW + 1;   // padded shared-memory row stride (floats)
+constexpr int kSlab = 32;
+
+struct Tile {
+    int32_t r0, c0, h, w;   // image rows [r0, r0+h), cols [c0, c0+w)
+    int32_t band;           // column block j containing the tile
+    int32_t pad_;
+};
+
+struct WorkItem {
+    int32_t tile;
+    int32_t group;
+    int32_t slab_begin;
+    int32_t slab_end;
+};
+
+struct HostLayout {
+    int img_h = 0, img_w = 0;
+    int64_t rows = 0, cols = 0, nnz = 0;
+    int M = 0, N = 0;
+    std::vector<int64_t> row_bounds, col_bounds;   // I_i, J_j
+    std::vector<Tile> tiles;
+    std::vector<int64_t> group_bounds;              // [n_groups+1] row ranges
+    std::vector<int32_t> group_block;               // block i of each group
+    std::vector<WorkItem> items;                    // launch order (nnz descending)
+    std::vector<int64_t> item_nnz;
+    std::vector<int64_t> slab_off;                  // [n_slabs+1]
+    std::vector<int32_t> slab_item;                 // [n_slabs] item index (storage order)
+    std::vector<int32_t> seg_ray, seg_len;          // [n_slabs*32]
+    std::vector<float> vals;                        // [nnz] slab-ordered
+    std::vector<int32_t> idx;                       // [nnz] tile-local shared-memory word
+    std::vector<int32_t> ray_seg_ptr;               // [rows+1]
+    std::vector<int32_t> ray_seg_pos;               // [n_segments] segment slots, ascending tile
+    int64_t n_groups() const { return (int64_t)group_block.size(); }
+    int64_t n_slabs() const { return (int64_t)slab_item.size(); }
+};
+
+// Validates the CSR and builds the layout (host, multithreaded).  Returns a
+// BSGDTV_* code; on failure set_error has the reason.
+int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w,
+                 const int64_t *row_ptr, const int32_t *col_idx, const double *vals, int M, int N,
+                 const int64_t *row_bounds, const int64_t *col_bounds, int target_items);
+
+// Decodes the layout back into CSR and compares with the input (host check).
+int verify_layout(const HostLayout &L, const int64_t *row_ptr, const int32_t *col_idx,
+                  const double *vals);
+std::vector<int64_t> default_bounds(int64_t length, int parts, int64_t unit);
+int resolve_bounds(int64_t rows, int64_t cols, int M, int N, int64_t row_unit, int64_t col_unit,
+                   const int64_t *row_bounds, const int64_t *col_bounds, std::vector<int64_t> &rb,
+                   std::vector<int64_t> &cb);
+
+// ------------------------------------------------------------ device views
+struct DevLayout {
+    const float *vals = nullptr;
+    const int32_t *idx = nullptr;
+    const int64_t *slab_off = nullptr;
+    const int32_t *seg_ray = nullptr;
+    const int32_t *seg_len = nullptr;
+    const WorkItem *items = nullptr;
+    const Tile *tiles = nullptr;
+    const int32_t *ray_seg_ptr = nullptr;
+    const int32_t *ray_seg_pos = nullptr;
+    const int32_t *slab_item = nullptr;
+    const int32_t *group_block = nullptr;
+    int n_items = 0;
+    int n_groups = 0;
+    int n_tiles = 0;
+    int M = 0, N = 0;
+    int64_t n_slabs = 0;
+    int64_t rows = 0, cols = 0;
+    int img_h = 0, img_w = 0;
+};
+
+// products.cu: one pass over A.  z_part[slot] = sum over the segment of a*x,
+// g_part[group*cols + pixel] = sum over the group's rows of 2*a*r.
+cudaError_t prepare_products_kernels();   // sets shared-memory limits (call before capture)
+template <typename T>
+cudaError_t launch_products(const DevLayout &d, const T *x, const T *r, T *z_part, T *g_part,
+                            cudaStream_t s);
+
+// reduce.cu
+// r_out = y - sum of each row's segment partials; x_out = x + mu * sum_g g_part
+// (x_out may equal x).  y may be null (then r_out = +sum, used for A v).
+template <typename T>
+cudaError_t launch_reduce_update(const DevLayout &d, const T *z_part, const T *g_part, const T *y,
+                                 T *r_out, const T *x, T *x_out, T mu, cudaStream_t s);
+cudaError_t launch_block_sums(const DevLayout &d, const float *z_part, const float *g_part,
+                              float *z_blocks, float *g_blocks, cudaStream_t s);
+// Deterministic FP64 reductions: out[0] = sum a*b (b null: sum a*a) over n.
+cudaError_t launch_dot(const double *a, const double *b, int64_t n, double *partials,
+                       double *out, cudaStream_t s);
+cudaError_t launch_tv64(const float *x, int h, int w, double *partials, double *out,
+                        cudaStream_t s);
+cudaError_t launch_f32_to_f64(const float *in, double *out, int64_t n, cudaStream_t s);
+cudaError_t launch_fill64(double *out, double v, int64_t n, cudaStream_t s);
+cudaError_t launch_scale64(const double *in, const double *nrm2, double *out, int64_t n,
+                           cudaStream_t s);
+cudaError_t launch_check_finite(const float *v, int64_t n, int *flag, cudaStream_t s);
+constexpr int kDotPartials = 1024;
+
+// fgp.cu: K FGP iterations on an h x w image.  `mom` holds the K momentum
+// coefficients (iteration k uses mom[k-1]); p,q,pp,qp are h*w scratch fields.
+struct FgpScratch {
+    float *p, *q, *pp, *qp;
+};
+int fgp_plan_launches(int h, int w, int iters);
+cudaError_t launch_fgp(const float *b, float *x, int h, int w, float tau, int iters,
+                       const float *mom, FgpScratch sc, cudaStream_t s);
+void fgp_momentum_host(int iters, std::vector<float> &mom);
+
+}  // namespace bsgdtv

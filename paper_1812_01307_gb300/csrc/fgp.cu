@@ -1,0 +1,202 @@
+// Line 9 of Algorithm 1: x = argmin_t ||t - b||^2 + 2 tau TV(t), tau = mu*lambda,
+// by Beck & Teboulle's fast gradient projection (FGP, IEEE TIP 18(11), 2009).
+//
+// One FGP iteration on the dual pair (p, q) (p: (h-1) x w, q: h x (w-1)):
+//   u        = b - tau L(r, s)              L(p,q)_{i,j} = p_{i,j}+q_{i,j}-p_{i-1,j}-q_{i,j-1}
+//   (P, Q)   = L^T(u)                       P_{i,j} = u_{i,j}-u_{i+1,j}, Q_{i,j} = u_{i,j}-u_{i,j+1}
+//   (p, q)   = Proj[(r, s) + (P, Q)/(8 tau)]  per pixel onto the unit l2 ball
+//                                            (border p_{i,w-1}, q_{h-1,j} clipped alone)
+//   (r, s)   = (p, q) + beta_k (p - p_prev, q - q_prev)
+// and finally x = b - tau L(p, q).
+//
+// GPU mapping: each CTA owns a 64 x 64 pixel region; every thread keeps a
+// vertical strip of 8 pixels' fields (b, p, q, p_prev, q_prev, r, s, u) in
+// registers for all the iterations of one launch.  Only the values a
+// neighbour needs (s to the right neighbour, r across strip boundaries, u to
+// the left / upper neighbour) pass through shared memory, two barriers per
+// iteration.  When the image fits one region the whole FGP is one launch;
+// otherwise regions overlap by a halo of (iterations per launch + 1) pixels
+// (temporal blocking), so each launch runs several iterations with no global
+// synchronisation, and the dual fields persist in global memory (L2) between
+// launches.  Pixels outside the image hold exact zeros (b = p = q = 0), which
+// is the operator's own boundary condition, so no halo is needed there.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "bsgdtv_internal.h"
+
+namespace bsgdtv {
+
+namespace {
+
+constexpr int RW = 64;      // region width  = threads in x
+constexpr int TY = 8;       // threads in y
+constexpr int V = 8;        // pixels per thread (vertical strip)
+constexpr int RH = TY * V;  // region height
+constexpr int kMaxChunk = 8;  // iterations per launch when tiled (halo = chunk + 1)
+
+__global__ void __launch_bounds__(RW *TY)
+    fgp_kernel(const float *__restrict__ b, float *__restrict__ x_out, int H, int W, float tau,
+               float c8, const float *__restrict__ mom, int k0, int iters, int HL, int IH, int IW,
+               int first, int last, float *__restrict__ p_g, float *__restrict__ q_g,
+               float *__restrict__ pp_g, float *__restrict__ qp_g) {
+    __shared__ float s_buf[RH][RW + 1];
+    __shared__ float u_buf[RH][RW + 1];
+    __shared__ float r_edge[TY][RW];
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int R0 = blockIdx.y * IH - HL, C0 = blockIdx.x * IW - HL;
+    const int j = C0 + tx;
+    const bool col_in = (j >= 0 && j < W);
+
+    float bb[V], p[V], q[V], pp[V], qp[V], rr[V], ss[V], uu[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int i = R0 + ty * V + v;
+        const bool in = col_in && i >= 0 && i < H;
+        const int64_t o = (int64_t)i * W + j;
+        bb[v] = in ? b[o] : 0.f;
+        if (first || !in) {
+            p[v] = q[v] = pp[v] = qp[v] = 0.f;
+        } else {
+            p[v] = p_g[o];
+            q[v] = q_g[o];
+            pp[v] = pp_g[o];
+            qp[v] = qp_g[o];
+        }
+    }
+
+    for (int it = 0; it < iters; ++it) {
+        const float beta = mom[k0 + it];
+        // momentum point (r, s) from the last two iterates
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            rr[v] = p[v] + beta * (p[v] - pp[v]);
+            ss[v] = q[v] + beta * (q[v] - qp[v]);
+            s_buf[ty * V + v][tx] = ss[v];
+        }
+        r_edge[ty][tx] = rr[V - 1];
+        __syncthreads();
+        // u = b - tau L(r, s)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float r_up = (v > 0) ? rr[v - 1] : (ty > 0 ? r_edge[ty - 1][tx] : 0.f);
+            const float s_left = (tx > 0) ? s_buf[ty * V + v][tx - 1] : 0.f;
+            uu[v] = bb[v] - tau * (rr[v] + ss[v] - r_up - s_left);
+            u_buf[ty * V + v][tx] = uu[v];
+        }
+        __syncthreads();
+        // gradient step on the dual and projection
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int i = R0 + ty * V + v;
+            const bool in = col_in && i >= 0 && i < H;
+            const float u_down =
+                (v < V - 1) ? uu[v + 1] : (ty < TY - 1 ? u_buf[ty * V + v + 1][tx] : 0.f);
+            const float u_right = (tx < RW - 1) ? u_buf[ty * V + v][tx + 1] : 0.f;
+            const float pt = rr[v] + (uu[v] - u_down) * c8;
+            const float qt = ss[v] + (uu[v] - u_right) * c8;
+            const bool pm = in && (i < H - 1);
+            const bool qm = in && (j < W - 1);
+            float pn = 0.f, qn = 0.f;
+            if (pm && qm) {
+                const float den = fmaxf(1.f, sqrtf(pt * pt + qt * qt));
+                pn = pt / den;
+                qn = qt / den;
+            } else if (pm) {
+                pn = pt / fmaxf(1.f, fabsf(pt));
+            } else if (qm) {
+                qn = qt / fmaxf(1.f, fabsf(qt));
+            }
+            pp[v] = p[v];
+            qp[v] = q[v];
+            p[v] = pn;
+            q[v] = qn;
+        }
+    }
+
+    if (last) {
+        // x = b - tau L(p, q) with the final iterate
+        __syncthreads();
+#pragma unroll
+        for (int v = 0; v < V; ++v) s_buf[ty * V + v][tx] = q[v];
+        r_edge[ty][tx] = p[V - 1];
+        __syncthreads();
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int rr_ = ty * V + v;
+            const int i = R0 + rr_;
+            const bool interior = rr_ >= HL && rr_ < HL + IH && tx >= HL && tx < HL + IW;
+            if (!(interior && col_in && i >= 0 && i < H)) continue;
+            const float p_up = (v > 0) ? p[v - 1] : (ty > 0 ? r_edge[ty - 1][tx] : 0.f);
+            const float q_left = (tx > 0) ? s_buf[rr_][tx - 1] : 0.f;
+            x_out[(int64_t)i * W + j] = bb[v] - tau * (p[v] + q[v] - p_up - q_left);
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int rr_ = ty * V + v;
+            const int i = R0 + rr_;
+            const bool interior = rr_ >= HL && rr_ < HL + IH && tx >= HL && tx < HL + IW;
+            if (!(interior && col_in && i >= 0 && i < H)) continue;
+            const int64_t o = (int64_t)i * W + j;
+            p_g[o] = p[v];
+            q_g[o] = q[v];
+            pp_g[o] = pp[v];
+            qp_g[o] = qp[v];
+        }
+    }
+}
+
+}  // namespace
+
+void fgp_momentum_host(int iters, std::vector<float> &mom) {
+    // iteration 1 starts from (r_1, s_1) = (p_0, q_0) = 0; iteration k >= 2 uses
+    // (t_{k-1} - 1) / t_k with t_1 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
+    mom.assign(std::max(iters, 1), 0.f);
+    double t = 1.0;
+    for (int k = 1; k < iters; ++k) {
+        const double tn = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
+        mom[k] = (float)((t - 1.0) / tn);
+        t = tn;
+    }
+}
+
+static bool fits_one_region(int h, int w) { return h <= RH && w <= RW; }
+
+int fgp_plan_launches(int h, int w, int iters) {
+    if (iters <= 0) return 0;
+    if (fits_one_region(h, w)) return 1;
+    return (iters + kMaxChunk - 1) / kMaxChunk;
+}
+
+cudaError_t launch_fgp(const float *b, float *x, int h, int w, float tau, int iters,
+                       const float *mom, FgpScratch sc, cudaStream_t s) {
+    const dim3 block(RW, TY);
+    const float c8 = 1.0f / (8.0f * tau);
+    if (fits_one_region(h, w)) {
+        fgp_kernel<<<dim3(1, 1), block, 0, s>>>(b, x, h, w, tau, c8, mom, 0, iters, 0, RH, RW, 1, 1,
+                                                sc.p, sc.q, sc.pp, sc.qp);
+        add_launches(1);
+        return cudaGetLastError();
+    }
+    int done = 0;
+    while (done < iters) {
+        const int chunk = std::min(kMaxChunk, iters - done);
+        const int HL = chunk + 1;
+        const int IH = RH - 2 * HL, IW = RW - 2 * HL;
+        const dim3 grid((w + IW - 1) / IW, (h + IH - 1) / IH);
+        const int first = (done == 0), last = (done + chunk == iters);
+        fgp_kernel<<<grid, block, 0, s>>>(b, x, h, w, tau, c8, mom, done, chunk, HL, IH, IW, first,
+                                          last, sc.p, sc.q, sc.pp, sc.qp);
+        add_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        done += chunk;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace bsgdtv

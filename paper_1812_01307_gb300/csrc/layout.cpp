@@ -1,0 +1,357 @@
+// Host construction of the tiled, slab-packed operator layout.
+//
+// Partition (Sec. 2.1 of the paper): rows of A are split into M row blocks
+// I_i, columns into N column blocks J_j.  Default bounds follow
+// numpy.array_split over whole units (an angle's rays, an image row).
+// The GPU layout refines that partition: pixel tiles never cross a J_j band
+// and row groups never cross an I_i block, so every block product of lines
+// 3-4 of Algorithm 1 is a sum of work-item partials.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <numeric>
+#include <thread>
+
+#include "bsgdtv_internal.h"
+
+namespace bsgdtv {
+
+static std::vector<int64_t> split_units(int64_t units, int parts, int64_t unit) {
+    std::vector<int64_t> b(parts + 1, 0);
+    int64_t q = units / parts, rem = units % parts;
+    for (int k = 0; k < parts; ++k) b[k + 1] = b[k] + q + (k < rem ? 1 : 0);
+    for (auto &v : b) v *= unit;
+    return b;
+}
+
+std::vector<int64_t> default_bounds(int64_t length, int parts, int64_t unit) {
+    return split_units(length / unit, parts, unit);
+}
+
+template <typename F>
+static void parallel_for(int64_t n, F &&f) {
+    unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    int64_t nt = std::min<int64_t>(n, std::min<unsigned>(hw, 32u));
+    if (nt <= 1) {
+        for (int64_t i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::vector<std::thread> th;
+    std::atomic<int64_t> next(0);
+    for (int64_t t = 0; t < nt; ++t)
+        th.emplace_back([&]() {
+            for (;;) {
+                int64_t i = next.fetch_add(1);
+                if (i >= n) break;
+                f(i);
+            }
+        });
+    for (auto &t : th) t.join();
+}
+
+int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w,
+                 const int64_t *row_ptr, const int32_t *col_idx, const double *vals, int M, int N,
+                 const int64_t *row_bounds, const int64_t *col_bounds, int target_items) {
+    // ---------------------------------------------------------- validation
+    if (rows < 1 || cols < 1 || img_h < 1 || img_w < 1 || (int64_t)img_h * img_w != cols)
+        return fail(BSGDTV_ERR_INVALID_ARG, "bad sizes: need rows>=1 and cols == img_h*img_w");
+    if (rows >= (int64_t)1 << 31 || cols >= (int64_t)1 << 31)
+        return fail(BSGDTV_ERR_INVALID_ARG, "rows and cols must be < 2^31");
+    if (M < 1 || N < 1 || M > rows || N > img_h)
+        return fail(BSGDTV_ERR_INVALID_ARG, "need 1 <= M <= rows and 1 <= N <= img_h");
+    if (!row_ptr || (!col_idx && row_ptr[rows] > 0) || (!vals && row_ptr[rows] > 0))
+        return fail(BSGDTV_ERR_INVALID_ARG, "null CSR array");
+    if (row_ptr[0] != 0) return fail(BSGDTV_ERR_INVALID_ARG, "row_ptr[0] != 0");
+    for (int64_t r = 0; r < rows; ++r)
+        if (row_ptr[r + 1] < row_ptr[r]) return fail(BSGDTV_ERR_INVALID_ARG, "row_ptr decreasing");
+    const int64_t nnz = row_ptr[rows];
+    {
+        std::atomic<int> bad(0);
+        parallel_for(rows, [&](int64_t r) {
+            int64_t prev = -1;
+            for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+                int64_t c = col_idx[e];
+                if (c < 0 || c >= cols || c <= prev) bad.store(1);
+                if (!std::isfinite(vals[e])) bad.store(2);
+                prev = c;
+            }
+        });
+        if (bad.load() == 1)
+            return fail(BSGDTV_ERR_INVALID_ARG, "column index out of range or not ascending in a row");
+        if (bad.load() == 2) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in A");
+    }
+    L.img_h = img_h;
+    L.img_w = img_w;
+    L.rows = rows;
+    L.cols = cols;
+    L.nnz = nnz;
+    L.M = M;
+    L.N = N;
+    L.row_bounds.assign(row_bounds, row_bounds + M + 1);
+    L.col_bounds.assign(col_bounds, col_bounds + N + 1);
+    if (L.row_bounds[0] != 0 || L.row_bounds[M] != rows || L.col_bounds[0] != 0 ||
+        L.col_bounds[N] != cols)
+        return fail(BSGDTV_ERR_INVALID_ARG, "bounds must start at 0 and end at rows / cols");
+    for (int i = 0; i < M; ++i)
+        if (L.row_bounds[i + 1] < L.row_bounds[i]) return fail(BSGDTV_ERR_INVALID_ARG, "row bounds decreasing");
+    for (int j = 0; j < N; ++j) {
+        if (L.col_bounds[j + 1] < L.col_bounds[j]) return fail(BSGDTV_ERR_INVALID_ARG, "col bounds decreasing");
+        if (L.col_bounds[j] % img_w) return fail(BSGDTV_ERR_INVALID_ARG, "column blocks must be bands of whole image rows");
+    }
+
+    // ------------------------------------------------------------- tiles
+    // tile rows never cross a band J_j; tiles are stored row-major over
+    // (tile row, tile column)
+    std::vector<int32_t> tile_row_of(img_h);
+    struct TileRow { int32_t r0, h, band; };
+    std::vector<TileRow> trows;
+    for (int j = 0; j < N; ++j) {
+        int b0 = (int)(L.col_bounds[j] / img_w), b1 = (int)(L.col_bounds[j + 1] / img_w);
+        for (int r0 = b0; r0 < b1; r0 += kTileH) {
+            int h = std::min(kTileH, b1 - r0);
+            for (int rr = r0; rr < r0 + h; ++rr) tile_row_of[rr] = (int32_t)trows.size();
+            trows.push_back({r0, h, j});
+        }
+    }
+    const int n_tc = (img_w + kTileW - 1) / kTileW;
+    L.tiles.clear();
+    for (const TileRow &tr : trows) {
+        for (int tc = 0; tc < n_tc; ++tc) {
+            Tile t;
+            t.r0 = tr.r0;
+            t.c0 = tc * kTileW;
+            t.h = tr.h;
+            t.w = std::min(kTileW, img_w - t.c0);
+            t.band = tr.band;
+            t.pad_ = 0;
+            L.tiles.push_back(t);
+        }
+    }
+    const int n_tiles = (int)L.tiles.size();
+
+    // ------------------------------------------------------------ groups
+    int64_t pairs = (int64_t)M * n_tiles;
+    int n_sub = (int)std::max<int64_t>(1, (target_items + pairs / 2) / std::max<int64_t>(pairs, 1));
+    L.group_bounds.assign(1, 0);
+    L.group_block.clear();
+    for (int i = 0; i < M; ++i) {
+        int64_t len = L.row_bounds[i + 1] - L.row_bounds[i];
+        int sub = (int)std::min<int64_t>(n_sub, std::max<int64_t>(len, 1));
+        std::vector<int64_t> b = split_units(len, sub, 1);
+        for (int k = 0; k < sub; ++k) {
+            L.group_bounds.push_back(L.row_bounds[i] + b[k + 1]);
+            L.group_block.push_back(i);
+        }
+    }
+    const int n_groups = (int)L.group_block.size();
+    const int64_t n_pairs = (int64_t)n_groups * n_tiles;
+
+    auto tile_of = [&](int32_t c, int32_t &local) -> int32_t {
+        int32_t s = c / img_w, t = c % img_w;
+        int32_t tr = tile_row_of[s], tc = t / kTileW;
+        int32_t tid = tr * n_tc + tc;
+        const Tile &T = L.tiles[tid];
+        local = (s - T.r0) * kTileStride + (t - T.c0);
+        return tid;
+    };
+
+    // ---------------------------------------------- pass 1: counts per pair
+    std::vector<int64_t> pair_nnz(n_pairs, 0), pair_seg(n_pairs, 0);
+    parallel_for(n_groups, [&](int64_t g) {
+        std::vector<int64_t> last(n_tiles, -1);
+        int64_t *pn = &pair_nnz[g * n_tiles], *ps = &pair_seg[g * n_tiles];
+        for (int64_t r = L.group_bounds[g]; r < L.group_bounds[g + 1]; ++r) {
+            for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+                int32_t loc;
+                int32_t t = tile_of(col_idx[e], loc);
+                pn[t]++;
+                if (last[t] != r) {
+                    last[t] = r;
+                    ps[t]++;
+                }
+            }
+        }
+    });
+
+    // storage order of pairs: group-major, tile ascending
+    std::vector<int64_t> pair_slab0(n_pairs + 1, 0), pair_nnz0(n_pairs + 1, 0);
+    for (int64_t p = 0; p < n_pairs; ++p) {
+        pair_slab0[p + 1] = pair_slab0[p] + (pair_seg[p] + kSlab - 1) / kSlab;
+        pair_nnz0[p + 1] = pair_nnz0[p] + pair_nnz[p];
+    }
+    const int64_t n_slabs = pair_slab0[n_pairs];
+    if (n_slabs * kSlab >= ((int64_t)1 << 31))
+        return fail(BSGDTV_ERR_UNSUPPORTED, "too many row segments for 32-bit slots");
+    L.slab_off.assign(n_slabs + 1, 0);
+    L.slab_item.assign(n_slabs, 0);
+    L.seg_ray.assign(n_slabs * kSlab, 0);
+    L.seg_len.assign(n_slabs * kSlab, 0);
+    L.vals.assign(nnz, 0.0f);
+    L.idx.assign(nnz, 0);
+
+    // ------------------------------------- pass 2: segments, slab packing
+    parallel_for(n_groups, [&](int64_t g) {
+        // per pair of this group: segment starts (in a row-ordered scratch copy)
+        std::vector<int64_t> cursor_nnz(n_tiles, 0);
+        const int64_t nnz0 = pair_nnz0[g * n_tiles];
+        const int64_t nnz1 = pair_nnz0[(g + 1) * n_tiles];
+        std::vector<float> tv(nnz1 - nnz0);
+        std::vector<int32_t> ti(nnz1 - nnz0);
+        // segments of pair (g,t): row, start (in tv/ti), length
+        std::vector<std::vector<int64_t>> srow(n_tiles), sstart(n_tiles), slen(n_tiles);
+        for (int t = 0; t < n_tiles; ++t) {
+            srow[t].reserve(pair_seg[g * n_tiles + t]);
+            sstart[t].reserve(pair_seg[g * n_tiles + t]);
+            slen[t].reserve(pair_seg[g * n_tiles + t]);
+            cursor_nnz[t] = pair_nnz0[g * n_tiles + t] - nnz0;
+        }
+        std::vector<int64_t> last(n_tiles, -1);
+        for (int64_t r = L.group_bounds[g]; r < L.group_bounds[g + 1]; ++r) {
+            // first sweep: open one segment per tile touched (in order of first touch)
+            for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+                int32_t loc;
+                int32_t t = tile_of(col_idx[e], loc);
+                if (last[t] != r) {
+                    last[t] = r;
+                    srow[t].push_back(r);
+                    sstart[t].push_back(cursor_nnz[t]);
+                    slen[t].push_back(0);
+                }
+                int64_t pos = cursor_nnz[t]++;
+                tv[pos] = (float)vals[e];
+                ti[pos] = loc;
+                slen[t].back()++;
+            }
+        }
+        // Entries of one segment are contiguous in tv/ti only if no other
+        // segment of the same pair was opened in between, which holds because
+        // a row is finished before the next row starts.
+        for (int t = 0; t < n_tiles; ++t) {
+            const int64_t pair = g * n_tiles + t;
+            const int64_t nseg = (int64_t)srow[t].size();
+            int64_t out = pair_nnz0[pair];
+            for (int64_t s0 = 0, sl = pair_slab0[pair]; s0 < nseg; s0 += kSlab, ++sl) {
+                int lanes = (int)std::min<int64_t>(kSlab, nseg - s0);
+                L.slab_off[sl] = out;
+                int maxlen = 0;
+                for (int l = 0; l < lanes; ++l) {
+                    L.seg_ray[sl * kSlab + l] = (int32_t)srow[t][s0 + l];
+                    L.seg_len[sl * kSlab + l] = (int32_t)slen[t][s0 + l];
+                    maxlen = std::max<int>(maxlen, (int)slen[t][s0 + l]);
+                }
+                for (int k = 0; k < maxlen; ++k)
+                    for (int l = 0; l < lanes; ++l)
+                        if (slen[t][s0 + l] > k) {
+                            int64_t src = sstart[t][s0 + l] + k;
+                            L.vals[out] = tv[src];
+                            L.idx[out] = ti[src];
+                            ++out;
+                        }
+            }
+            for (int64_t sl = pair_slab0[pair]; sl < pair_slab0[pair + 1]; ++sl)
+                L.slab_item[sl] = (int32_t)pair;
+        }
+    });
+    L.slab_off[n_slabs] = nnz;
+
+    // --------------------------------------- per-ray segment slots (z reduce)
+    L.ray_seg_ptr.assign(rows + 1, 0);
+    for (int64_t sl = 0; sl < n_slabs; ++sl)
+        for (int l = 0; l < kSlab; ++l)
+            if (L.seg_len[sl * kSlab + l] > 0) L.ray_seg_ptr[L.seg_ray[sl * kSlab + l] + 1]++;
+    for (int64_t r = 0; r < rows; ++r) L.ray_seg_ptr[r + 1] += L.ray_seg_ptr[r];
+    L.ray_seg_pos.assign(L.ray_seg_ptr[rows], 0);
+    {
+        std::vector<int32_t> cur(L.ray_seg_ptr.begin(), L.ray_seg_ptr.end() - 1);
+        // slabs are stored group-major with tiles ascending, so each ray meets
+        // its segments in ascending tile order
+        for (int64_t sl = 0; sl < n_slabs; ++sl)
+            for (int l = 0; l < kSlab; ++l)
+                if (L.seg_len[sl * kSlab + l] > 0)
+                    L.ray_seg_pos[cur[L.seg_ray[sl * kSlab + l]]++] = (int32_t)(sl * kSlab + l);
+    }
+
+    // ------------------------------------------------- work items (launch order)
+    L.items.resize(n_pairs);
+    L.item_nnz.resize(n_pairs);
+    std::vector<int64_t> order(n_pairs);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t a, int64_t b) { return pair_nnz[a] > pair_nnz[b]; });
+    for (int64_t k = 0; k < n_pairs; ++k) {
+        int64_t p = order[k];
+        WorkItem w;
+        w.group = (int32_t)(p / n_tiles);
+        w.tile = (int32_t)(p % n_tiles);
+        w.slab_begin = (int32_t)pair_slab0[p];
+        w.slab_end = (int32_t)pair_slab0[p + 1];
+        L.items[k] = w;
+        L.item_nnz[k] = pair_nnz[p];
+    }
+    return BSGDTV_OK;
+}
+
+int verify_layout(const HostLayout &L, const int64_t *row_ptr, const int32_t *col_idx,
+                  const double *vals) {
+    const int n_tiles = (int)L.tiles.size();
+    std::vector<std::vector<std::pair<int32_t, float>>> per_row(L.rows);
+    std::vector<std::vector<int32_t>> slots_of_row(L.rows);
+    for (int64_t sl = 0; sl < L.n_slabs(); ++sl) {
+        const int pair = L.slab_item[sl];
+        const int g = pair / n_tiles, t = pair % n_tiles;
+        const Tile &T = L.tiles[t];
+        int maxlen = 0;
+        for (int l = 0; l < kSlab; ++l) {
+            const int len = L.seg_len[sl * kSlab + l];
+            const int ray = L.seg_ray[sl * kSlab + l];
+            if (len < 0) return fail(BSGDTV_ERR_STATE, "negative segment length");
+            if (len > 0) {
+                if (ray < L.group_bounds[g] || ray >= L.group_bounds[g + 1])
+                    return fail(BSGDTV_ERR_STATE, "segment row outside its group");
+                slots_of_row[ray].push_back((int32_t)(sl * kSlab + l));
+            }
+            maxlen = std::max(maxlen, len);
+        }
+        int64_t pos = L.slab_off[sl];
+        for (int k = 0; k < maxlen; ++k)
+            for (int l = 0; l < kSlab; ++l)
+                if (L.seg_len[sl * kSlab + l] > k) {
+                    const int32_t loc = L.idx[pos];
+                    const int lr = loc / kTileStride, lc = loc % kTileStride;
+                    if (lr >= T.h || lc >= T.w) return fail(BSGDTV_ERR_STATE, "local index outside tile");
+                    const int32_t col = (T.r0 + lr) * L.img_w + T.c0 + lc;
+                    per_row[L.seg_ray[sl * kSlab + l]].push_back({col, L.vals[pos]});
+                    ++pos;
+                }
+        if (pos != L.slab_off[sl + 1]) return fail(BSGDTV_ERR_STATE, "slab size mismatch");
+    }
+    for (int64_t r = 0; r < L.rows; ++r) {
+        auto &v = per_row[r];
+        std::sort(v.begin(), v.end());
+        if ((int64_t)v.size() != row_ptr[r + 1] - row_ptr[r]) return fail(BSGDTV_ERR_STATE, "row nnz mismatch");
+        for (size_t k = 0; k < v.size(); ++k) {
+            const int64_t e = row_ptr[r] + (int64_t)k;
+            if (v[k].first != col_idx[e] || v[k].second != (float)vals[e])
+                return fail(BSGDTV_ERR_STATE, "entry mismatch");
+        }
+        // the reduction visits exactly this row's segments, tiles ascending
+        const int32_t b0 = L.ray_seg_ptr[r], b1 = L.ray_seg_ptr[r + 1];
+        if (b1 - b0 != (int32_t)slots_of_row[r].size()) return fail(BSGDTV_ERR_STATE, "segment list size");
+        int prev_tile = -1;
+        for (int32_t e = b0; e < b1; ++e) {
+            const int32_t slot = L.ray_seg_pos[e];
+            if (L.seg_ray[slot] != r || L.seg_len[slot] <= 0) return fail(BSGDTV_ERR_STATE, "segment list entry");
+            const int tile = L.slab_item[slot / kSlab] % n_tiles;
+            if (tile <= prev_tile) return fail(BSGDTV_ERR_STATE, "segment list order");
+            prev_tile = tile;
+        }
+    }
+    // every (group, tile) pair is exactly one work item
+    std::vector<int> seen((size_t)L.n_groups() * n_tiles, 0);
+    for (const WorkItem &w : L.items) seen[(size_t)w.group * n_tiles + w.tile]++;
+    for (int v : seen)
+        if (v != 1) return fail(BSGDTV_ERR_STATE, "work items do not cover the pairs once");
+    return BSGDTV_OK;
+}
+
+}  // namespace bsgdtv

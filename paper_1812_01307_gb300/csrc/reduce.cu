@@ -1,0 +1,238 @@
+// Reductions and the gradient step of Algorithm 1 (lines 6-8), plus the
+// deterministic FP64 reductions used for u_max (Theorem 1) and the objective
+// (Eq. 1).  Every sum runs in a fixed order, so results do not depend on
+// scheduling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "bsgdtv_internal.h"
+
+namespace bsgdtv {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// blocks [0, nb_rows): one thread per row,  r = y - sum_j z   (line 6)
+// blocks [nb_rows, ..): one thread per pixel, x' = x + mu sum_i g (lines 7-8)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    reduce_update_kernel(const DevLayout d, const T *__restrict__ z_part,
+                         const T *__restrict__ g_part, const T *__restrict__ y, T *r_out,
+                         const T *x, T *x_out, T mu, int nb_rows) {
+    if ((int)blockIdx.x < nb_rows) {
+        const int64_t ray = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+        if (ray >= d.rows) return;
+        const int e0 = d.ray_seg_ptr[ray], e1 = d.ray_seg_ptr[ray + 1];
+        T acc = T(0);
+        for (int e = e0; e < e1; ++e) acc += z_part[d.ray_seg_pos[e]];
+        r_out[ray] = y ? (y[ray] - acc) : acc;
+    } else {
+        const int64_t p = (int64_t)(blockIdx.x - nb_rows) * kThreads + threadIdx.x;
+        if (p >= d.cols) return;
+        T acc = T(0);
+        for (int g = 0; g < d.n_groups; ++g) acc += g_part[(int64_t)g * d.cols + p];
+        x_out[p] = x ? (x[p] + mu * acc) : acc;
+    }
+}
+
+// Per-block sums of lines 3-4 for the test hook.
+__global__ void block_sums_kernel(const DevLayout d, const float *__restrict__ z_part,
+                                  const float *__restrict__ g_part, float *z_blocks,
+                                  float *g_blocks, int N, int M, int nb_rows) {
+    if ((int)blockIdx.x < nb_rows) {
+        const int64_t ray = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+        if (ray >= d.rows) return;
+        for (int j = 0; j < N; ++j) z_blocks[(int64_t)j * d.rows + ray] = 0.f;
+        const int e0 = d.ray_seg_ptr[ray], e1 = d.ray_seg_ptr[ray + 1];
+        int band = -1;
+        float acc = 0.f;
+        for (int e = e0; e < e1; ++e) {
+            const int slot = d.ray_seg_pos[e];
+            const int pair = d.slab_item[slot / kSlab];
+            const int b = d.tiles[pair % d.n_tiles].band;
+            if (b != band) {
+                if (band >= 0) z_blocks[(int64_t)band * d.rows + ray] = acc;
+                band = b;
+                acc = 0.f;
+            }
+            acc += z_part[slot];
+        }
+        if (band >= 0) z_blocks[(int64_t)band * d.rows + ray] = acc;
+    } else {
+        const int64_t p = (int64_t)(blockIdx.x - nb_rows) * kThreads + threadIdx.x;
+        if (p >= d.cols) return;
+        for (int i = 0; i < M; ++i) g_blocks[(int64_t)i * d.cols + p] = 0.f;
+        int blk = -1;
+        float acc = 0.f;
+        for (int g = 0; g < d.n_groups; ++g) {
+            const int b = d.group_block[g];
+            if (b != blk) {
+                if (blk >= 0) g_blocks[(int64_t)blk * d.cols + p] = acc;
+                blk = b;
+                acc = 0.f;
+            }
+            acc += g_part[(int64_t)g * d.cols + p];
+        }
+        if (blk >= 0) g_blocks[(int64_t)blk * d.cols + p] = acc;
+    }
+}
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (w == 0) {
+        v = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    dot_partial_kernel(const double *__restrict__ a, const double *__restrict__ b, int64_t n,
+                       double *partials) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kThreads)
+        acc += b ? a[i] * b[i] : a[i] * a[i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kThreads) final_sum_kernel(const double *partials, int n,
+                                                             double *out) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += kThreads) acc += partials[i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[0] = acc;
+}
+
+// TV_I of an h x w FP32 image in FP64: sum of sqrt(dv^2 + dh^2) with forward
+// differences, zero across the last row / column (Neumann border).
+__global__ void __launch_bounds__(kThreads)
+    tv_partial_kernel(const float *__restrict__ x, int h, int w, double *partials) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    const int64_t n = (int64_t)h * w;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kThreads) {
+        const int s = (int)(i / w), t = (int)(i % w);
+        const double v = x[i];
+        const double dv = (s + 1 < h) ? v - (double)x[i + w] : 0.0;
+        const double dh = (t + 1 < w) ? v - (double)x[i + 1] : 0.0;
+        acc += sqrt(dv * dv + dh * dh);
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void f32_to_f64_kernel(const float *in, double *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+__global__ void fill64_kernel(double *out, double v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = v;
+}
+
+// out = in / sqrt(nrm2[0])
+__global__ void scale64_kernel(const double *in, const double *nrm2, double *out, int64_t n) {
+    const double inv = 1.0 / sqrt(nrm2[0]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[i] * inv;
+}
+
+__global__ void check_finite_kernel(const float *v, int64_t n, int *flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(v[i])) atomicOr(flag, 1);
+}
+
+int grid_for(int64_t n) {
+    int64_t b = (n + kThreads - 1) / kThreads;
+    return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_reduce_update(const DevLayout &d, const T *z_part, const T *g_part, const T *y,
+                                 T *r_out, const T *x, T *x_out, T mu, cudaStream_t s) {
+    const int nb_rows = (int)((d.rows + kThreads - 1) / kThreads);
+    const int nb_cols = (int)((d.cols + kThreads - 1) / kThreads);
+    reduce_update_kernel<T><<<nb_rows + nb_cols, kThreads, 0, s>>>(d, z_part, g_part, y, r_out, x,
+                                                                   x_out, mu, nb_rows);
+    add_launches(1);
+    return cudaGetLastError();
+}
+template cudaError_t launch_reduce_update<float>(const DevLayout &, const float *, const float *,
+                                                 const float *, float *, const float *, float *,
+                                                 float, cudaStream_t);
+template cudaError_t launch_reduce_update<double>(const DevLayout &, const double *,
+                                                  const double *, const double *, double *,
+                                                  const double *, double *, double, cudaStream_t);
+
+cudaError_t launch_block_sums(const DevLayout &d, const float *z_part, const float *g_part,
+                              float *z_blocks, float *g_blocks, cudaStream_t s) {
+    const int nb_rows = (int)((d.rows + kThreads - 1) / kThreads);
+    const int nb_cols = (int)((d.cols + kThreads - 1) / kThreads);
+    block_sums_kernel<<<nb_rows + nb_cols, kThreads, 0, s>>>(d, z_part, g_part, z_blocks, g_blocks,
+                                                             d.N, d.M, nb_rows);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const double *a, const double *b, int64_t n, double *partials, double *out,
+                       cudaStream_t s) {
+    const int g = std::min(grid_for(n), kDotPartials);
+    dot_partial_kernel<<<g, kThreads, 0, s>>>(a, b, n, partials);
+    final_sum_kernel<<<1, kThreads, 0, s>>>(partials, g, out);
+    add_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tv64(const float *x, int h, int w, double *partials, double *out,
+                        cudaStream_t s) {
+    const int g = std::min(grid_for((int64_t)h * w), kDotPartials);
+    tv_partial_kernel<<<g, kThreads, 0, s>>>(x, h, w, partials);
+    final_sum_kernel<<<1, kThreads, 0, s>>>(partials, g, out);
+    add_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_f64(const float *in, double *out, int64_t n, cudaStream_t s) {
+    f32_to_f64_kernel<<<grid_for(n), kThreads, 0, s>>>(in, out, n);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill64(double *out, double v, int64_t n, cudaStream_t s) {
+    fill64_kernel<<<grid_for(n), kThreads, 0, s>>>(out, v, n);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale64(const double *in, const double *nrm2, double *out, int64_t n,
+                           cudaStream_t s) {
+    scale64_kernel<<<grid_for(n), kThreads, 0, s>>>(in, nrm2, out, n);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const float *v, int64_t n, int *flag, cudaStream_t s) {
+    check_finite_kernel<<<grid_for(n), kThreads, 0, s>>>(v, n, flag);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace bsgdtv
