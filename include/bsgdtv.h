@@ -143,6 +143,25 @@ int bsgdtv_get_info(bsgdtv_t h, int64_t *nnz, int64_t *segments, int64_t *work_i
 int bsgdtv_tv_prox(const float *b, float *x, int img_h, int img_w, double tau, int iters,
                    void *stream);
 
+/* bsgdtv_tv_prox for callers that cannot allocate device memory at call
+ * time (the paper has no counterpart; this is a deployment variant).  Such
+ * callers include processes whose device budget is fully claimed by their own
+ * pool allocator, latency-critical loops that cannot afford the device-wide
+ * synchronisation of cudaMalloc/cudaFree, and host runtimes that forbid
+ * plugins from allocating.  Same arguments, same result as bsgdtv_tv_prox;
+ * it calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
+ * (FGP dual fields and momentum table) is one file-scope device array of
+ * about 4 MiB that every GPU which loads the library keeps until the process
+ * exits.  Limits: img_h*img_w <= 262144 (e.g. 512 x 512) and iters <= 4096;
+ * larger requests fail with BSGDTV_ERR_INVALID_ARG.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * in the process share the one array and it keeps the last call's contents
+ * (nothing in it needs to start at zero): calls that overlap on the GPU, e.g.
+ * on two streams or from two threads, race.  Synchronises `stream`. */
+int bsgdtv_tv_prox_static(const float *b, float *x, int img_h, int img_w, double tau, int iters,
+                          void *stream);
+
 /* Host only (no GPU needed): the partition bounds bsgdtv_create_csr uses when
  * row_bounds / col_bounds are NULL, written to row_bounds [M+1] and
  * col_bounds [N+1]. */

@@ -51,6 +51,7 @@ def load(path: str | None = None):
         "bsgdtv_block_products": (I32, [P, P, P, P, P]),
         "bsgdtv_get_info": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "bsgdtv_tv_prox": (I32, [P, P, I32, I32, D, I32, P]),
+        "bsgdtv_tv_prox_static": (I32, [P, P, I32, I32, D, I32, P]),
         "bsgdtv_partition_bounds": (I32, [I64, I64, I32, I32, I64, I64, P, P]),
         "bsgdtv_layout_check": (I32, [I64, I64, I32, I32, P, P, P, I32, I32, I64, I64, P, P, I32, P]),
         "bsgdtv_launch_count": (I64, []),
@@ -70,7 +71,8 @@ def exported_symbols():
     return ["bsgdtv_create_csr", "bsgdtv_destroy", "bsgdtv_get_partition", "bsgdtv_set_data",
             "bsgdtv_estimate_umax", "bsgdtv_get_params", "bsgdtv_run", "bsgdtv_run_timed", "bsgdtv_get_x",
             "bsgdtv_get_state", "bsgdtv_set_state", "bsgdtv_objective", "bsgdtv_block_products",
-            "bsgdtv_get_info", "bsgdtv_tv_prox", "bsgdtv_partition_bounds", "bsgdtv_layout_check",
+            "bsgdtv_get_info", "bsgdtv_tv_prox", "bsgdtv_tv_prox_static", "bsgdtv_partition_bounds",
+            "bsgdtv_layout_check",
             "bsgdtv_launch_count", "bsgdtv_last_error", "bsgdtv_strerror"]
 
 
@@ -263,6 +265,19 @@ def bsgdtv_tv_prox(b, x, tau, iters, stream=None):
                                  int(b.shape[0]), int(b.shape[1]), float(tau), int(iters),
                                  stream if stream is not None else current_stream()),
            "bsgdtv_tv_prox")
+
+
+def bsgdtv_tv_prox_static(b, x, tau, iters, stream=None):
+    """TV prox with no allocation: scratch in a fixed device array inside the
+    library (for callers that cannot allocate device memory; at most 262144
+    pixels and 4096 iterations; concurrent calls race on the shared array)."""
+    import torch
+    if b.dim() != 2 or x.shape != b.shape:
+        raise ValueError("b and x must be matching 2-D tensors")
+    _check(load().bsgdtv_tv_prox_static(_dev_ptr(b, torch.float32), _dev_ptr(x, torch.float32),
+                                        int(b.shape[0]), int(b.shape[1]), float(tau), int(iters),
+                                        stream if stream is not None else current_stream()),
+           "bsgdtv_tv_prox_static")
 
 
 def bsgdtv_partition_bounds(rows, cols, M, N, row_unit=1, col_unit=1):
