@@ -370,6 +370,7 @@ int bsgdtv_create_csr(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, int 
         d.slab_item = si;
         d.group_block = gb;
     }
+    d.n_sms = sms;
     d.n_items = (int)L.items.size();
     d.n_groups = (int)L.n_groups();
     d.n_tiles = (int)L.tiles.size();
@@ -387,11 +388,13 @@ int bsgdtv_create_csr(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, int 
         (rc = dalloc(hp, &h->xhat, cols)) || (rc = dalloc(hp, &h->z_part, d.n_slabs * kSlab)) ||
         (rc = dalloc(hp, &h->g_part, (size_t)d.n_groups * cols)) || (rc = dalloc(hp, &h->fp, cols)) ||
         (rc = dalloc(hp, &h->fq, cols)) || (rc = dalloc(hp, &h->fpp, cols)) ||
-        (rc = dalloc(hp, &h->fqp, cols)) || (rc = dalloc(hp, &h->flag, 1))) {
+        (rc = dalloc(hp, &h->fqp, cols)) || (rc = dalloc(hp, &h->flag, 1)) ||
+        (rc = dalloc(hp, &d.item_ctr, 2))) {
         bsgdtv_destroy(h.release());
         return rc;
     }
-    cudaError_t e = cudaStreamSynchronize(h->stream);
+    cudaError_t e = cudaMemsetAsync(d.item_ctr, 0, 2 * sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         bsgdtv_destroy(h.release());
         return fail(BSGDTV_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));

@@ -34,13 +34,17 @@ void add_launches(int64_t n);
 // column-block band J_j) and the rows into groups (sub-ranges of the row blocks
 // I_i).  A work item is one (group, tile) pair.  Inside a work item every row
 // that touches the tile contributes one segment (its nonzeros in that tile).
-// Segments are packed 32 to a slab; a slab is stored column by column (element
-// k of every segment longer than k, in lane order), so that a warp reads it
-// with coalesced loads, one lane per segment.
+// Segments are packed 32 to a slab; a slab is stored in column groups of
+// kGroup elements (elements [4kk, 4kk+4) of every segment longer than 4kk, in
+// lane order, tails padded with zero weights), so that a warp reads it with
+// coalesced 16-byte loads, one lane per segment.
 constexpr int kTileH = 64;
 constexpr int kTileW = 64;
 constexpr int kTileStride = kTileW + 1;   // padded shared-memory row stride (floats)
 constexpr int kSlab = 32;
+constexpr int kGroup = 4;                            // elements per lane per vector load
+constexpr int kPadBase = kTileH * kTileStride;        // per-lane dummy words for padding
+constexpr int kTileWords = kPadBase + kSlab;          // shared-memory words per tile array
 
 struct Tile {
     int32_t r0, c0, h, w;   // image rows [r0, r0+h), cols [c0, c0+w)
@@ -57,7 +61,7 @@ struct WorkItem {
 
 struct HostLayout {
     int img_h = 0, img_w = 0;
-    int64_t rows = 0, cols = 0, nnz = 0;
+    int64_t rows = 0, cols = 0, nnz = 0, stored = 0;   // stored: nnz + padding
     int M = 0, N = 0;
     std::vector<int64_t> row_bounds, col_bounds;   // I_i, J_j
     std::vector<Tile> tiles;
@@ -103,6 +107,8 @@ struct DevLayout {
     const int32_t *ray_seg_pos = nullptr;
     const int32_t *slab_item = nullptr;
     const int32_t *group_block = nullptr;
+    int *item_ctr = nullptr;   // [2] work-item / exit counters of the product kernel (device)
+    int n_sms = 1;
     int n_items = 0;
     int n_groups = 0;
     int n_tiles = 0;

@@ -156,20 +156,25 @@ int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w
     };
 
     // ---------------------------------------------- pass 1: counts per pair
-    std::vector<int64_t> pair_nnz(n_pairs, 0), pair_seg(n_pairs, 0);
+    // pair_nnz: stored elements (each segment padded to a multiple of kGroup)
+    std::vector<int64_t> pair_nnz(n_pairs, 0), pair_seg(n_pairs, 0), pair_real(n_pairs, 0);
     parallel_for(n_groups, [&](int64_t g) {
-        std::vector<int64_t> last(n_tiles, -1);
-        int64_t *pn = &pair_nnz[g * n_tiles], *ps = &pair_seg[g * n_tiles];
+        std::vector<int32_t> cnt(n_tiles, 0);
+        std::vector<int32_t> touched;
+        int64_t *pn = &pair_nnz[g * n_tiles], *ps = &pair_seg[g * n_tiles], *pr = &pair_real[g * n_tiles];
         for (int64_t r = L.group_bounds[g]; r < L.group_bounds[g + 1]; ++r) {
             for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
                 int32_t loc;
                 int32_t t = tile_of(col_idx[e], loc);
-                pn[t]++;
-                if (last[t] != r) {
-                    last[t] = r;
-                    ps[t]++;
-                }
+                if (cnt[t]++ == 0) touched.push_back(t);
             }
+            for (int32_t t : touched) {
+                ps[t]++;
+                pr[t] += cnt[t];
+                pn[t] += (int64_t)kGroup * ((cnt[t] + kGroup - 1) / kGroup);
+                cnt[t] = 0;
+            }
+            touched.clear();
         }
     });
 
@@ -186,24 +191,28 @@ int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w
     L.slab_item.assign(n_slabs, 0);
     L.seg_ray.assign(n_slabs * kSlab, 0);
     L.seg_len.assign(n_slabs * kSlab, 0);
-    L.vals.assign(nnz, 0.0f);
-    L.idx.assign(nnz, 0);
+    const int64_t stored = pair_nnz0[n_pairs];
+    L.stored = stored;
+    L.vals.assign(stored, 0.0f);
+    L.idx.assign(stored, 0);
 
     // ------------------------------------- pass 2: segments, slab packing
     parallel_for(n_groups, [&](int64_t g) {
         // per pair of this group: segment starts (in a row-ordered scratch copy)
         std::vector<int64_t> cursor_nnz(n_tiles, 0);
-        const int64_t nnz0 = pair_nnz0[g * n_tiles];
-        const int64_t nnz1 = pair_nnz0[(g + 1) * n_tiles];
-        std::vector<float> tv(nnz1 - nnz0);
-        std::vector<int32_t> ti(nnz1 - nnz0);
+        int64_t real_total = 0;
+        std::vector<int64_t> real0(n_tiles + 1, 0);
+        for (int t = 0; t < n_tiles; ++t) real0[t + 1] = real0[t] + pair_real[g * n_tiles + t];
+        real_total = real0[n_tiles];
+        std::vector<float> tv(real_total);
+        std::vector<int32_t> ti(real_total);
         // segments of pair (g,t): row, start (in tv/ti), length
         std::vector<std::vector<int64_t>> srow(n_tiles), sstart(n_tiles), slen(n_tiles);
         for (int t = 0; t < n_tiles; ++t) {
             srow[t].reserve(pair_seg[g * n_tiles + t]);
             sstart[t].reserve(pair_seg[g * n_tiles + t]);
             slen[t].reserve(pair_seg[g * n_tiles + t]);
-            cursor_nnz[t] = pair_nnz0[g * n_tiles + t] - nnz0;
+            cursor_nnz[t] = real0[t];
         }
         std::vector<int64_t> last(n_tiles, -1);
         for (int64_t r = L.group_bounds[g]; r < L.group_bounds[g + 1]; ++r) {
@@ -239,20 +248,34 @@ int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w
                     L.seg_len[sl * kSlab + l] = (int32_t)slen[t][s0 + l];
                     maxlen = std::max<int>(maxlen, (int)slen[t][s0 + l]);
                 }
-                for (int k = 0; k < maxlen; ++k)
-                    for (int l = 0; l < lanes; ++l)
-                        if (slen[t][s0 + l] > k) {
-                            int64_t src = sstart[t][s0 + l] + k;
-                            L.vals[out] = tv[src];
-                            L.idx[out] = ti[src];
+                // column groups of kGroup elements: group kk holds elements
+                // [kGroup*kk, kGroup*kk + kGroup) of every lane whose segment is
+                // longer than kGroup*kk, in lane order; short tails are padded
+                // with zero weights aimed at the lane's private dummy word
+                const int maxg = (maxlen + kGroup - 1) / kGroup;
+                for (int kk = 0; kk < maxg; ++kk)
+                    for (int l = 0; l < lanes; ++l) {
+                        const int64_t len = slen[t][s0 + l];
+                        if (len <= (int64_t)kGroup * kk) continue;
+                        for (int j = 0; j < kGroup; ++j) {
+                            const int64_t k = (int64_t)kGroup * kk + j;
+                            if (k < len) {
+                                const int64_t src = sstart[t][s0 + l] + k;
+                                L.vals[out] = tv[src];
+                                L.idx[out] = ti[src];
+                            } else {
+                                L.vals[out] = 0.0f;
+                                L.idx[out] = kPadBase + l;
+                            }
                             ++out;
                         }
+                    }
             }
             for (int64_t sl = pair_slab0[pair]; sl < pair_slab0[pair + 1]; ++sl)
                 L.slab_item[sl] = (int32_t)pair;
         }
     });
-    L.slab_off[n_slabs] = nnz;
+    L.slab_off[n_slabs] = stored;
 
     // --------------------------------------- per-ray segment slots (z reduce)
     L.ray_seg_ptr.assign(rows + 1, 0);
@@ -313,16 +336,25 @@ int verify_layout(const HostLayout &L, const int64_t *row_ptr, const int32_t *co
             maxlen = std::max(maxlen, len);
         }
         int64_t pos = L.slab_off[sl];
-        for (int k = 0; k < maxlen; ++k)
-            for (int l = 0; l < kSlab; ++l)
-                if (L.seg_len[sl * kSlab + l] > k) {
+        const int maxg = (maxlen + kGroup - 1) / kGroup;
+        for (int kk = 0; kk < maxg; ++kk)
+            for (int l = 0; l < kSlab; ++l) {
+                const int len = L.seg_len[sl * kSlab + l];
+                if (len <= kGroup * kk) continue;
+                for (int j = 0; j < kGroup; ++j, ++pos) {
                     const int32_t loc = L.idx[pos];
+                    if (kGroup * kk + j >= len) {
+                        if (loc != kPadBase + l || L.vals[pos] != 0.0f)
+                            return fail(BSGDTV_ERR_STATE, "bad padding entry");
+                        continue;
+                    }
                     const int lr = loc / kTileStride, lc = loc % kTileStride;
-                    if (lr >= T.h || lc >= T.w) return fail(BSGDTV_ERR_STATE, "local index outside tile");
+                    if (loc < 0 || lr >= T.h || lc >= T.w) return fail(BSGDTV_ERR_STATE, "local index outside tile");
                     const int32_t col = (T.r0 + lr) * L.img_w + T.c0 + lc;
                     per_row[L.seg_ray[sl * kSlab + l]].push_back({col, L.vals[pos]});
-                    ++pos;
                 }
+            }
+        if (pos % kGroup) return fail(BSGDTV_ERR_STATE, "slab not aligned");
         if (pos != L.slab_off[sl + 1]) return fail(BSGDTV_ERR_STATE, "slab size mismatch");
     }
     for (int64_t r = 0; r < L.rows; ++r) {
