@@ -58,6 +58,7 @@ struct bsgdtv_ctx {
     float *mom = nullptr;
     int mom_len = 0;
     int *flag = nullptr;
+    float *rmax = nullptr;   // [3] max |r| of r[0], r[1] and of a test-hook r
     int cur = 0;   // r[cur] holds r^{k-1}
     bool has_data = false;
     double lambda = 0.0, mu = 0.0, u_max = 0.0;
@@ -152,11 +153,13 @@ int enqueue_epoch(bsgdtv_ctx *h, int par, int fgp_iters, cudaStream_t s,
                   cudaEvent_t *marks = nullptr) {
     const bool prox = h->lambda > 0.0 && fgp_iters > 0;
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[0], s, cudaEventRecordExternal));
-    BSG_CUDA(launch_products<float>(h->dl, h->x, h->r[par], h->z_part, h->g_part, s));
+    BSG_CUDA(launch_products32(h->dl, h->x, h->r[par], h->rmax + par, h->rmax + (1 - par),
+                               h->z_part, reinterpret_cast<int32_t *>(h->g_part), s));
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[1], s, cudaEventRecordExternal));
     float *xdst = prox ? h->xhat : h->x;
-    BSG_CUDA(launch_reduce_update<float>(h->dl, h->z_part, h->g_part, h->y, h->r[1 - par], h->x,
-                                         xdst, (float)h->mu, s));
+    BSG_CUDA(launch_reduce_update32(h->dl, h->z_part, reinterpret_cast<const int32_t *>(h->g_part),
+                                    h->rmax + par, h->y, h->r[1 - par], h->rmax + (1 - par), h->x,
+                                    xdst, (float)h->mu, s));
     if (prox) {
         FgpScratch sc{h->fp, h->fq, h->fpp, h->fqp};
         BSG_CUDA(launch_fgp(h->xhat, h->x, h->dl.img_h, h->dl.img_w, (float)(h->mu * h->lambda),
@@ -371,6 +374,8 @@ int bsgdtv_create_csr(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, int 
         d.group_block = gb;
     }
     d.n_sms = sms;
+    d.colsum_max = (float)L.colsum_max;
+    if ((double)d.colsum_max < L.colsum_max) d.colsum_max = std::nextafter(d.colsum_max, 3.0e38f);
     d.n_items = (int)L.items.size();
     d.n_groups = (int)L.n_groups();
     d.n_tiles = (int)L.tiles.size();
@@ -389,7 +394,7 @@ int bsgdtv_create_csr(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, int 
         (rc = dalloc(hp, &h->g_part, (size_t)d.n_groups * cols)) || (rc = dalloc(hp, &h->fp, cols)) ||
         (rc = dalloc(hp, &h->fq, cols)) || (rc = dalloc(hp, &h->fpp, cols)) ||
         (rc = dalloc(hp, &h->fqp, cols)) || (rc = dalloc(hp, &h->flag, 1)) ||
-        (rc = dalloc(hp, &d.item_ctr, 2))) {
+        (rc = dalloc(hp, &d.item_ctr, 2)) || (rc = dalloc(hp, &h->rmax, 3))) {
         bsgdtv_destroy(h.release());
         return rc;
     }
@@ -453,13 +458,13 @@ int bsgdtv_estimate_umax(bsgdtv_t h, int max_iters, double rel_tol, double *u_ma
     int it = 0;
     for (it = 1; it <= max_iters; ++it) {
         // w = A v
-        BSG_CUDA(launch_products<double>(h->dl, h->v64, h->w64, h->z64, h->gp64, s));
-        BSG_CUDA(launch_reduce_update<double>(h->dl, h->z64, h->gp64, nullptr, h->w64, nullptr,
-                                              h->g64, 0.0, s));
+        BSG_CUDA(launch_products64(h->dl, h->v64, h->w64, h->z64, h->gp64, s));
+        BSG_CUDA(launch_reduce_update64(h->dl, h->z64, h->gp64, nullptr, h->w64, nullptr, h->g64,
+                                        0.0, s));
         // g = 2 A^T w  (the product kernel carries line 3's factor 2)
-        BSG_CUDA(launch_products<double>(h->dl, h->v64, h->w64, h->z64, h->gp64, s));
-        BSG_CUDA(launch_reduce_update<double>(h->dl, h->z64, h->gp64, nullptr, h->w64, nullptr,
-                                              h->g64, 0.0, s));
+        BSG_CUDA(launch_products64(h->dl, h->v64, h->w64, h->z64, h->gp64, s));
+        BSG_CUDA(launch_reduce_update64(h->dl, h->z64, h->gp64, nullptr, h->w64, nullptr, h->g64,
+                                        0.0, s));
         BSG_CUDA(launch_dot(h->v64, h->g64, c, h->partials, h->scal + 0, s));
         BSG_CUDA(launch_dot(h->g64, nullptr, c, h->partials, h->scal + 1, s));
         double sc[2];
@@ -509,6 +514,8 @@ int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, 
     BSG_CUDA(cudaMemsetAsync(h->x, 0, c * sizeof(float), s));
     h->cur = 0;
     BSG_CUDA(cudaMemcpyAsync(h->r[0], h->y, R * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    BSG_CUDA(cudaMemsetAsync(h->rmax, 0, sizeof(float), s));
+    BSG_CUDA(launch_absmax(h->r[0], R, h->rmax, s));
     if (mu <= 0.0) {
         if (h->u_max <= 0.0) {
             double u;
@@ -621,6 +628,8 @@ int bsgdtv_set_state(bsgdtv_t h, const float *x, const float *r, int64_t epoch, 
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     BSG_CUDA(cudaMemcpyAsync(h->x, x, h->dl.cols * sizeof(float), k, h->stream));
     BSG_CUDA(cudaMemcpyAsync(h->r[h->cur], r, h->dl.rows * sizeof(float), k, h->stream));
+    BSG_CUDA(cudaMemsetAsync(h->rmax + h->cur, 0, sizeof(float), h->stream));
+    BSG_CUDA(launch_absmax(h->r[h->cur], h->dl.rows, h->rmax + h->cur, h->stream));
     if (!on_device) BSG_CUDA(cudaStreamSynchronize(h->stream));
     h->epoch = epoch;
     return BSGDTV_OK;
@@ -636,10 +645,9 @@ int bsgdtv_objective(bsgdtv_t h, double *data_term, double *tv) {
     BSG_CUDA(launch_f32_to_f64(h->x, h->x64, c, s));
     BSG_CUDA(launch_f32_to_f64(h->y, h->y64, R, s));
     BSG_CUDA(launch_fill64(h->w64, 0.0, R, s));
-    BSG_CUDA(launch_products<double>(h->dl, h->x64, h->w64, h->z64, h->gp64, s));
+    BSG_CUDA(launch_products64(h->dl, h->x64, h->w64, h->z64, h->gp64, s));
     // w = y - A x (FP64)
-    BSG_CUDA(launch_reduce_update<double>(h->dl, h->z64, h->gp64, h->y64, h->w64, nullptr, h->g64,
-                                          0.0, s));
+    BSG_CUDA(launch_reduce_update64(h->dl, h->z64, h->gp64, h->y64, h->w64, nullptr, h->g64, 0.0, s));
     BSG_CUDA(launch_dot(h->w64, nullptr, R, h->partials, h->scal + 2, s));
     BSG_CUDA(launch_tv64(h->x, h->dl.img_h, h->dl.img_w, h->partials, h->scal + 3, s));
     double sc[2];
@@ -656,8 +664,12 @@ int bsgdtv_block_products(bsgdtv_t h, const float *x, const float *r, float *z_b
         return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
     BSG_CHECK(set_device(h));
     cudaStream_t s = h->stream;
-    BSG_CUDA(launch_products<float>(h->dl, x, r, h->z_part, h->g_part, s));
-    BSG_CUDA(launch_block_sums(h->dl, h->z_part, h->g_part, z_blocks, g_blocks, s));
+    BSG_CUDA(cudaMemsetAsync(h->rmax + 2, 0, sizeof(float), s));
+    BSG_CUDA(launch_absmax(r, h->dl.rows, h->rmax + 2, s));
+    BSG_CUDA(launch_products32(h->dl, x, r, h->rmax + 2, nullptr, h->z_part,
+                               reinterpret_cast<int32_t *>(h->g_part), s));
+    BSG_CUDA(launch_block_sums(h->dl, h->z_part, reinterpret_cast<const int32_t *>(h->g_part),
+                               h->rmax + 2, z_blocks, g_blocks, s));
     BSG_CUDA(cudaStreamSynchronize(s));
     return BSGDTV_OK;
 }

@@ -62,6 +62,7 @@ struct WorkItem {
 struct HostLayout {
     int img_h = 0, img_w = 0;
     int64_t rows = 0, cols = 0, nnz = 0, stored = 0;   // stored: nnz + padding
+    double colsum_max = 0.0;   // max over row groups and pixels of sum_rows |a| (FP32 weights)
     int M = 0, N = 0;
     std::vector<int64_t> row_bounds, col_bounds;   // I_i, J_j
     std::vector<Tile> tiles;
@@ -108,6 +109,7 @@ struct DevLayout {
     const int32_t *slab_item = nullptr;
     const int32_t *group_block = nullptr;
     int *item_ctr = nullptr;   // [2] work-item / exit counters of the product kernel (device)
+    float colsum_max = 0.f;    // see HostLayout::colsum_max (rounded up)
     int n_sms = 1;
     int n_items = 0;
     int n_groups = 0;
@@ -121,18 +123,46 @@ struct DevLayout {
 // products.cu: one pass over A.  z_part[slot] = sum over the segment of a*x,
 // g_part[group*cols + pixel] = sum over the group's rows of 2*a*r.
 cudaError_t prepare_products_kernels();   // sets shared-memory limits (call before capture)
-template <typename T>
-cudaError_t launch_products(const DevLayout &d, const T *x, const T *r, T *z_part, T *g_part,
-                            cudaStream_t s);
+// FP64 variant (u_max and objective): g tile accumulated with FP64 atomics.
+cudaError_t launch_products64(const DevLayout &d, const double *x, const double *r, double *z_part,
+                              double *g_part, cudaStream_t s);
+// FP32 hot path: the A^T r tile is accumulated in int32 fixed point with the
+// power-of-two scale fixed_scale(*rmax_in, d.colsum_max); g_part holds int32.
+// rmax_clear (may be null) is set to 0 for the next reduction to fill.
+cudaError_t launch_products32(const DevLayout &d, const float *x, const float *r,
+                              const float *rmax_in, float *rmax_clear, float *z_part,
+                              int32_t *g_part, cudaStream_t s);
+
+// Scale 2^e such that 2 * rmax * colsum_max * 2^e < 2^30: every partial sum of
+// the fixed-point A^T r tile stays below 2^31 in magnitude.
+__host__ __device__ inline float fixed_scale(float rmax, float colsum_max) {
+    const float bound = 2.0f * rmax * colsum_max;
+    if (!(bound > 0.0f) || !(bound < 3.0e38f)) return 1.0f;
+    int ex = 0;
+    frexpf(bound, &ex);   // bound < 2^ex
+    int e = 30 - ex;
+    if (e > 120) e = 120;
+    if (e < -120) e = -120;
+    return ldexpf(1.0f, e);
+}
 
 // reduce.cu
 // r_out = y - sum of each row's segment partials; x_out = x + mu * sum_g g_part
 // (x_out may equal x).  y may be null (then r_out = +sum, used for A v).
-template <typename T>
-cudaError_t launch_reduce_update(const DevLayout &d, const T *z_part, const T *g_part, const T *y,
-                                 T *r_out, const T *x, T *x_out, T mu, cudaStream_t s);
-cudaError_t launch_block_sums(const DevLayout &d, const float *z_part, const float *g_part,
-                              float *z_blocks, float *g_blocks, cudaStream_t s);
+cudaError_t launch_reduce_update64(const DevLayout &d, const double *z_part, const double *g_part,
+                                   const double *y, double *r_out, const double *x, double *x_out,
+                                   double mu, cudaStream_t s);
+// FP32 hot path: g_part is the fixed-point tile of launch_products32 (scale from
+// rmax_in); the new residual's max |r| is folded into rmax_out (pre-zeroed).
+cudaError_t launch_reduce_update32(const DevLayout &d, const float *z_part, const int32_t *g_part,
+                                   const float *rmax_in, const float *y, float *r_out,
+                                   float *rmax_out, const float *x, float *x_out, float mu,
+                                   cudaStream_t s);
+cudaError_t launch_block_sums(const DevLayout &d, const float *z_part, const int32_t *g_part,
+                              const float *rmax_in, float *z_blocks, float *g_blocks,
+                              cudaStream_t s);
+// out[0] = max |v| over n (out must be zeroed first; result via integer max on float bits).
+cudaError_t launch_absmax(const float *v, int64_t n, float *out, cudaStream_t s);
 // Deterministic FP64 reductions: out[0] = sum a*b (b null: sum a*a) over n.
 cudaError_t launch_dot(const double *a, const double *b, int64_t n, double *partials,
                        double *out, cudaStream_t s);

@@ -158,9 +158,19 @@ int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w
     // ---------------------------------------------- pass 1: counts per pair
     // pair_nnz: stored elements (each segment padded to a multiple of kGroup)
     std::vector<int64_t> pair_nnz(n_pairs, 0), pair_seg(n_pairs, 0), pair_real(n_pairs, 0);
+    // largest column sum of |a| (FP32 weights) within one row group: bounds the
+    // fixed-point accumulation of the A^T r tile
+    std::vector<double> group_colmax(n_groups, 0.0);
     parallel_for(n_groups, [&](int64_t g) {
         std::vector<int32_t> cnt(n_tiles, 0);
         std::vector<int32_t> touched;
+        std::vector<double> colsum(cols, 0.0);
+        for (int64_t r = L.group_bounds[g]; r < L.group_bounds[g + 1]; ++r)
+            for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e)
+                colsum[col_idx[e]] += std::fabs((double)(float)vals[e]);
+        double cm = 0.0;
+        for (double v : colsum) cm = std::max(cm, v);
+        group_colmax[g] = cm;
         int64_t *pn = &pair_nnz[g * n_tiles], *ps = &pair_seg[g * n_tiles], *pr = &pair_real[g * n_tiles];
         for (int64_t r = L.group_bounds[g]; r < L.group_bounds[g + 1]; ++r) {
             for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
@@ -177,6 +187,9 @@ int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w
             touched.clear();
         }
     });
+
+    L.colsum_max = 0.0;
+    for (double v : group_colmax) L.colsum_max = std::max(L.colsum_max, v);
 
     // storage order of pairs: group-major, tile ascending
     std::vector<int64_t> pair_slab0(n_pairs + 1, 0), pair_nnz0(n_pairs + 1, 0);

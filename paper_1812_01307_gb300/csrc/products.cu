@@ -29,32 +29,53 @@ constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kCtasPerSm = 2;
 
-template <typename T>
-__device__ __forceinline__ void use_group(const float4 v, const int4 i, const T r2, const T *xs,
-                                          T *gs, T &acc) {
-    acc += (T)v.x * xs[i.x];
-    atomicAdd(gs + i.x, (T)v.x * r2);
-    acc += (T)v.y * xs[i.y];
-    atomicAdd(gs + i.y, (T)v.y * r2);
-    acc += (T)v.z * xs[i.z];
-    atomicAdd(gs + i.z, (T)v.z * r2);
-    acc += (T)v.w * xs[i.w];
-    atomicAdd(gs + i.w, (T)v.w * r2);
+// Accumulation of one column group (four nonzeros of this lane's segment):
+// z partial in a register, the A^T r contribution into the shared g tile.
+// FP32 path: the tile is int32 fixed point (r2 already carries the scale), so
+// the shared-memory updates are native integer atomics and the tile's sums
+// are exact and independent of their order.  FP64 path: FP64 atomics.
+__device__ __forceinline__ void use_group(const float4 v, const int4 i, const float r2s,
+                                          const float *xs, int *gs, float &acc) {
+    acc = fmaf(v.x, xs[i.x], acc);
+    atomicAdd(gs + i.x, __float2int_rn(v.x * r2s));
+    acc = fmaf(v.y, xs[i.y], acc);
+    atomicAdd(gs + i.y, __float2int_rn(v.y * r2s));
+    acc = fmaf(v.z, xs[i.z], acc);
+    atomicAdd(gs + i.z, __float2int_rn(v.z * r2s));
+    acc = fmaf(v.w, xs[i.w], acc);
+    atomicAdd(gs + i.w, __float2int_rn(v.w * r2s));
 }
 
-template <typename T>
+__device__ __forceinline__ void use_group(const float4 v, const int4 i, const double r2,
+                                          const double *xs, double *gs, double &acc) {
+    acc += (double)v.x * xs[i.x];
+    atomicAdd(gs + i.x, (double)v.x * r2);
+    acc += (double)v.y * xs[i.y];
+    atomicAdd(gs + i.y, (double)v.y * r2);
+    acc += (double)v.z * xs[i.z];
+    atomicAdd(gs + i.z, (double)v.z * r2);
+    acc += (double)v.w * xs[i.w];
+    atomicAdd(gs + i.w, (double)v.w * r2);
+}
+
+// T: type of x, r, z (float or double); G: shared g tile (int fixed point or double).
+template <typename T, typename G>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     products_kernel(const DevLayout d, const T *__restrict__ x, const T *__restrict__ r,
-                    T *__restrict__ z_part, T *__restrict__ g_part, int *__restrict__ item_ctr) {
+                    const float *__restrict__ rmax_in, float *__restrict__ rmax_clear,
+                    T *__restrict__ z_part, G *__restrict__ g_part, int *__restrict__ item_ctr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xs = reinterpret_cast<T *>(smem_raw);
-    T *gs = xs + kTileWords;
+    G *gs = reinterpret_cast<G *>(xs + kTileWords);
     __shared__ int s_item, s_next;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const float4 *__restrict__ V4 = reinterpret_cast<const float4 *>(d.vals);
     const int4 *__restrict__ I4 = reinterpret_cast<const int4 *>(d.idx);
+    // 2 r scaled to fixed point (FP32 path) or plain 2 r (FP64 path)
+    const T scale = rmax_in ? (T)fixed_scale(*rmax_in, d.colsum_max) : T(1);
+    if (rmax_clear && blockIdx.x == 0 && threadIdx.x == 0) *rmax_clear = 0.f;
 
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(item_ctr, 1);
@@ -70,7 +91,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             if (e < kPadBase && lr < tl.h && lc < tl.w)
                 v = x[(int64_t)(tl.r0 + lr) * d.img_w + tl.c0 + lc];
             xs[e] = v;
-            gs[e] = T(0);
+            gs[e] = G(0);
         }
         if (threadIdx.x == 0) s_next = it.slab_begin + kWarps;
         __syncthreads();
@@ -81,7 +102,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             const int len = d.seg_len[seg];
             const int ray = d.seg_ray[seg];
             const int ng = (len + kGroup - 1) / kGroup;
-            const T r2 = (len > 0) ? T(2) * r[ray] : T(0);
+            const T r2 = (len > 0) ? T(2) * r[ray] * scale : T(0);
             const int64_t base = d.slab_off[sl] / kGroup;
             const float4 *V = V4 + base;
             const int4 *I = I4 + base;
@@ -109,7 +130,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                 const int p = off + __popc(a & lt);
                 off += __popc(a);
                 if (ng > kk + 2) { vc = __ldcs(V + p); ic = __ldcs(I + p); }
-                if (ng > kk) use_group<T>(va, ia, r2, xs, gs, acc);
+                if (ng > kk) use_group(va, ia, r2, xs, gs, acc);
                 va = vb;
                 ia = ib;
                 vb = vc;
@@ -122,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         }
         __syncthreads();
 
-        T *gp = g_part + (int64_t)it.group * d.cols;
+        G *gp = g_part + (int64_t)it.group * d.cols;
         const int npx = tl.h * tl.w;
         for (int e = threadIdx.x; e < npx; e += kThreads) {
             const int lr = e / tl.w, lc = e - lr * tl.w;
@@ -144,29 +165,37 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 
 }  // namespace
 
-template <typename T>
-cudaError_t launch_products(const DevLayout &d, const T *x, const T *r, T *z_part, T *g_part,
-                            cudaStream_t s) {
+cudaError_t launch_products32(const DevLayout &d, const float *x, const float *r,
+                              const float *rmax_in, float *rmax_clear, float *z_part,
+                              int32_t *g_part, cudaStream_t s) {
     if (d.n_items == 0) return cudaSuccess;
-    const size_t smem = 2u * kTileWords * sizeof(T);
+    const size_t smem = kTileWords * (sizeof(float) + sizeof(int));
     const int grid = std::min(d.n_items, kCtasPerSm * std::max(d.n_sms, 1));
-    products_kernel<T><<<grid, kThreads, smem, s>>>(d, x, r, z_part, g_part, d.item_ctr);
+    products_kernel<float, int><<<grid, kThreads, smem, s>>>(d, x, r, rmax_in, rmax_clear, z_part,
+                                                             g_part, d.item_ctr);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_products64(const DevLayout &d, const double *x, const double *r, double *z_part,
+                              double *g_part, cudaStream_t s) {
+    if (d.n_items == 0) return cudaSuccess;
+    const size_t smem = 2u * kTileWords * sizeof(double);
+    const int grid = std::min(d.n_items, kCtasPerSm * std::max(d.n_sms, 1));
+    products_kernel<double, double><<<grid, kThreads, smem, s>>>(d, x, r, nullptr, nullptr, z_part,
+                                                                 g_part, d.item_ctr);
     add_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t prepare_products_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(products_kernel<float>,
+    cudaError_t e = cudaFuncSetAttribute(products_kernel<float, int>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(2u * kTileWords * sizeof(float)));
+                                         (int)(kTileWords * (sizeof(float) + sizeof(int))));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(products_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(products_kernel<double, double>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(2u * kTileWords * sizeof(double)));
 }
-
-template cudaError_t launch_products<float>(const DevLayout &, const float *, const float *,
-                                            float *, float *, cudaStream_t);
-template cudaError_t launch_products<double>(const DevLayout &, const double *, const double *,
-                                             double *, double *, cudaStream_t);
 
 }  // namespace bsgdtv

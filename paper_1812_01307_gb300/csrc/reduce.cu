@@ -14,32 +14,71 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// FP64 form (u_max, objective).
 // blocks [0, nb_rows): one thread per row,  r = y - sum_j z   (line 6)
 // blocks [nb_rows, ..): one thread per pixel, x' = x + mu sum_i g (lines 7-8)
-template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    reduce_update_kernel(const DevLayout d, const T *__restrict__ z_part,
-                         const T *__restrict__ g_part, const T *__restrict__ y, T *r_out,
-                         const T *x, T *x_out, T mu, int nb_rows) {
+    reduce_update64_kernel(const DevLayout d, const double *__restrict__ z_part,
+                           const double *__restrict__ g_part, const double *__restrict__ y,
+                           double *r_out, const double *x, double *x_out, double mu, int nb_rows) {
     if ((int)blockIdx.x < nb_rows) {
         const int64_t ray = (int64_t)blockIdx.x * kThreads + threadIdx.x;
         if (ray >= d.rows) return;
         const int e0 = d.ray_seg_ptr[ray], e1 = d.ray_seg_ptr[ray + 1];
-        T acc = T(0);
+        double acc = 0.0;
         for (int e = e0; e < e1; ++e) acc += z_part[d.ray_seg_pos[e]];
         r_out[ray] = y ? (y[ray] - acc) : acc;
     } else {
         const int64_t p = (int64_t)(blockIdx.x - nb_rows) * kThreads + threadIdx.x;
         if (p >= d.cols) return;
-        T acc = T(0);
+        double acc = 0.0;
         for (int g = 0; g < d.n_groups; ++g) acc += g_part[(int64_t)g * d.cols + p];
         x_out[p] = x ? (x[p] + mu * acc) : acc;
     }
 }
 
+__device__ __forceinline__ void atomic_max_nonneg(float *dst, float v) {
+    // non-negative floats order like their bit patterns
+    atomicMax(reinterpret_cast<int *>(dst), __float_as_int(v));
+}
+
+// FP32 hot path.  Rows: r = y - sum_j z (line 6) and max |r| for the next
+// product pass.  Pixels: g = exact int64 sum of the groups' fixed-point tiles,
+// one rounding to FP32, x' = x + mu g (lines 7-8).
+__global__ void __launch_bounds__(kThreads)
+    reduce_update32_kernel(const DevLayout d, const float *__restrict__ z_part,
+                           const int32_t *__restrict__ g_part, const float *__restrict__ rmax_in,
+                           const float *__restrict__ y, float *r_out, float *rmax_out,
+                           const float *x, float *x_out, float mu, int nb_rows) {
+    if ((int)blockIdx.x < nb_rows) {
+        const int64_t ray = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+        float rv = 0.f;
+        if (ray < d.rows) {
+            const int e0 = d.ray_seg_ptr[ray], e1 = d.ray_seg_ptr[ray + 1];
+            float acc = 0.f;
+            for (int e = e0; e < e1; ++e) acc += z_part[d.ray_seg_pos[e]];
+            rv = y[ray] - acc;
+            r_out[ray] = rv;
+        }
+        if (rmax_out) {
+            float m = fabsf(rv);
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if ((threadIdx.x & 31) == 0) atomic_max_nonneg(rmax_out, m);
+        }
+    } else {
+        const int64_t p = (int64_t)(blockIdx.x - nb_rows) * kThreads + threadIdx.x;
+        if (p >= d.cols) return;
+        long long acc = 0;
+        for (int g = 0; g < d.n_groups; ++g) acc += g_part[(int64_t)g * d.cols + p];
+        const double inv = 1.0 / (double)fixed_scale(*rmax_in, d.colsum_max);
+        x_out[p] = x[p] + mu * (float)((double)acc * inv);
+    }
+}
+
 // Per-block sums of lines 3-4 for the test hook.
 __global__ void block_sums_kernel(const DevLayout d, const float *__restrict__ z_part,
-                                  const float *__restrict__ g_part, float *z_blocks,
+                                  const int32_t *__restrict__ g_part,
+                                  const float *__restrict__ rmax_in, float *z_blocks,
                                   float *g_blocks, int N, int M, int nb_rows) {
     if ((int)blockIdx.x < nb_rows) {
         const int64_t ray = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -63,20 +102,30 @@ __global__ void block_sums_kernel(const DevLayout d, const float *__restrict__ z
     } else {
         const int64_t p = (int64_t)(blockIdx.x - nb_rows) * kThreads + threadIdx.x;
         if (p >= d.cols) return;
+        const double inv = 1.0 / (double)fixed_scale(*rmax_in, d.colsum_max);
         for (int i = 0; i < M; ++i) g_blocks[(int64_t)i * d.cols + p] = 0.f;
         int blk = -1;
-        float acc = 0.f;
+        long long acc = 0;
         for (int g = 0; g < d.n_groups; ++g) {
             const int b = d.group_block[g];
             if (b != blk) {
-                if (blk >= 0) g_blocks[(int64_t)blk * d.cols + p] = acc;
+                if (blk >= 0) g_blocks[(int64_t)blk * d.cols + p] = (float)((double)acc * inv);
                 blk = b;
-                acc = 0.f;
+                acc = 0;
             }
             acc += g_part[(int64_t)g * d.cols + p];
         }
-        if (blk >= 0) g_blocks[(int64_t)blk * d.cols + p] = acc;
+        if (blk >= 0) g_blocks[(int64_t)blk * d.cols + p] = (float)((double)acc * inv);
     }
+}
+
+__global__ void absmax_kernel(const float *__restrict__ v, int64_t n, float *out) {
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(v[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
 }
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
@@ -165,29 +214,42 @@ int grid_for(int64_t n) {
 
 }  // namespace
 
-template <typename T>
-cudaError_t launch_reduce_update(const DevLayout &d, const T *z_part, const T *g_part, const T *y,
-                                 T *r_out, const T *x, T *x_out, T mu, cudaStream_t s) {
+cudaError_t launch_reduce_update64(const DevLayout &d, const double *z_part, const double *g_part,
+                                   const double *y, double *r_out, const double *x, double *x_out,
+                                   double mu, cudaStream_t s) {
     const int nb_rows = (int)((d.rows + kThreads - 1) / kThreads);
     const int nb_cols = (int)((d.cols + kThreads - 1) / kThreads);
-    reduce_update_kernel<T><<<nb_rows + nb_cols, kThreads, 0, s>>>(d, z_part, g_part, y, r_out, x,
-                                                                   x_out, mu, nb_rows);
+    reduce_update64_kernel<<<nb_rows + nb_cols, kThreads, 0, s>>>(d, z_part, g_part, y, r_out, x,
+                                                                  x_out, mu, nb_rows);
     add_launches(1);
     return cudaGetLastError();
 }
-template cudaError_t launch_reduce_update<float>(const DevLayout &, const float *, const float *,
-                                                 const float *, float *, const float *, float *,
-                                                 float, cudaStream_t);
-template cudaError_t launch_reduce_update<double>(const DevLayout &, const double *,
-                                                  const double *, const double *, double *,
-                                                  const double *, double *, double, cudaStream_t);
 
-cudaError_t launch_block_sums(const DevLayout &d, const float *z_part, const float *g_part,
-                              float *z_blocks, float *g_blocks, cudaStream_t s) {
+cudaError_t launch_reduce_update32(const DevLayout &d, const float *z_part, const int32_t *g_part,
+                                   const float *rmax_in, const float *y, float *r_out,
+                                   float *rmax_out, const float *x, float *x_out, float mu,
+                                   cudaStream_t s) {
     const int nb_rows = (int)((d.rows + kThreads - 1) / kThreads);
     const int nb_cols = (int)((d.cols + kThreads - 1) / kThreads);
-    block_sums_kernel<<<nb_rows + nb_cols, kThreads, 0, s>>>(d, z_part, g_part, z_blocks, g_blocks,
-                                                             d.N, d.M, nb_rows);
+    reduce_update32_kernel<<<nb_rows + nb_cols, kThreads, 0, s>>>(
+        d, z_part, g_part, rmax_in, y, r_out, rmax_out, x, x_out, mu, nb_rows);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_sums(const DevLayout &d, const float *z_part, const int32_t *g_part,
+                              const float *rmax_in, float *z_blocks, float *g_blocks,
+                              cudaStream_t s) {
+    const int nb_rows = (int)((d.rows + kThreads - 1) / kThreads);
+    const int nb_cols = (int)((d.cols + kThreads - 1) / kThreads);
+    block_sums_kernel<<<nb_rows + nb_cols, kThreads, 0, s>>>(d, z_part, g_part, rmax_in, z_blocks,
+                                                             g_blocks, d.N, d.M, nb_rows);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absmax(const float *v, int64_t n, float *out, cudaStream_t s) {
+    absmax_kernel<<<grid_for(n), kThreads, 0, s>>>(v, n, out);
     add_launches(1);
     return cudaGetLastError();
 }

@@ -300,3 +300,16 @@ def test_run_timed_matches_run(B):
         x_timed = rec.x().copy()
     assert 0 < pk < ep
     assert rel(x_timed, x_plain) <= 1e-6
+
+
+def test_epochs_are_deterministic(B):
+    """The A^T r tiles are exact integer sums, so repeated runs agree bit for bit."""
+    A, _, y, n, na, nb, M, N = _problem("wide130")
+    y32 = y.astype(np.float32)
+    outs = []
+    for _ in range(2):
+        with B.Reconstructor(A, (n, n), M, N, row_unit=nb, col_unit=n) as rec:
+            rec.set_data(y32, 0.05)
+            rec.run(9, 13)
+            outs.append(rec.x().copy())
+    assert np.array_equal(outs[0], outs[1])
