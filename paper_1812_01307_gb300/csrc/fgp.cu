@@ -37,6 +37,50 @@ constexpr int V = 8;        // pixels per thread (vertical strip)
 constexpr int RH = TY * V;  // region height
 constexpr int kMaxChunk = 8;  // iterations per launch when tiled (halo = chunk + 1)
 
+// One FGP iteration for this thread's strip.  (p, q) hold the current dual
+// iterate and (pp, qp) the previous one; the new iterate is written over
+// (pp, qp), so the caller swaps the roles of the two register sets.
+__device__ __forceinline__ void fgp_step(float (&p)[V], float (&pp)[V], float (&q)[V],
+                                         float (&qp)[V], const float (&bb)[V], unsigned pmask,
+                                         unsigned qmask, float beta, float tau, float c8,
+                                         float (*s_buf)[RW + 1], float (*u_buf)[RW + 1],
+                                         float (*r_edge)[RW], int tx, int ty) {
+    float rr[V], ss[V], uu[V];
+    // momentum point (r, s) from the last two iterates
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        rr[v] = fmaf(beta, p[v] - pp[v], p[v]);
+        ss[v] = fmaf(beta, q[v] - qp[v], q[v]);
+        s_buf[ty * V + v][tx] = ss[v];
+    }
+    r_edge[ty][tx] = rr[V - 1];
+    __syncthreads();
+    // u = b - tau L(r, s)
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const float r_up = (v > 0) ? rr[v - 1] : (ty > 0 ? r_edge[ty - 1][tx] : 0.f);
+        const float s_left = (tx > 0) ? s_buf[ty * V + v][tx - 1] : 0.f;
+        uu[v] = fmaf(-tau, (rr[v] - r_up) + (ss[v] - s_left), bb[v]);
+        u_buf[ty * V + v][tx] = uu[v];
+    }
+    __syncthreads();
+    // (P, Q) = L^T u, gradient step on the dual, projection onto the unit ball
+    // (p_{i,w-1} and q_{h-1,j} alone: clipping to [-1, 1] is exactly t/max(1,|t|))
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const float u_down =
+            (v < V - 1) ? uu[v + 1] : (ty < TY - 1 ? u_buf[ty * V + v + 1][tx] : 0.f);
+        const float u_right = (tx < RW - 1) ? u_buf[ty * V + v][tx + 1] : 0.f;
+        const float pt = fmaf(uu[v] - u_down, c8, rr[v]);
+        const float qt = fmaf(uu[v] - u_right, c8, ss[v]);
+        const bool pm = (pmask >> v) & 1u, qm = (qmask >> v) & 1u;
+        const float n2 = fmaf(pt, pt, qt * qt);
+        const float inv = n2 > 1.f ? rsqrtf(n2) : 1.f;
+        pp[v] = pm ? (qm ? pt * inv : fminf(fmaxf(pt, -1.f), 1.f)) : 0.f;
+        qp[v] = qm ? (pm ? qt * inv : fminf(fmaxf(qt, -1.f), 1.f)) : 0.f;
+    }
+}
+
 __global__ void __launch_bounds__(RW *TY)
     fgp_kernel(const float *__restrict__ b, float *__restrict__ x_out, int H, int W, float tau,
                float c8, const float *__restrict__ mom, int k0, int iters, int HL, int IH, int IW,
@@ -51,78 +95,51 @@ __global__ void __launch_bounds__(RW *TY)
     const int j = C0 + tx;
     const bool col_in = (j >= 0 && j < W);
 
-    float bb[V], p[V], q[V], pp[V], qp[V], rr[V], ss[V], uu[V];
+    float bb[V], pa[V], pb[V], qa[V], qb[V];
+    unsigned pmask = 0u, qmask = 0u;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         const int i = R0 + ty * V + v;
         const bool in = col_in && i >= 0 && i < H;
+        if (in && i < H - 1) pmask |= 1u << v;
+        if (in && j < W - 1) qmask |= 1u << v;
         const int64_t o = (int64_t)i * W + j;
         bb[v] = in ? b[o] : 0.f;
         if (first || !in) {
-            p[v] = q[v] = pp[v] = qp[v] = 0.f;
+            pa[v] = qa[v] = pb[v] = qb[v] = 0.f;
         } else {
-            p[v] = p_g[o];
-            q[v] = q_g[o];
-            pp[v] = pp_g[o];
-            qp[v] = qp_g[o];
+            pa[v] = p_g[o];
+            qa[v] = q_g[o];
+            pb[v] = pp_g[o];
+            qb[v] = qp_g[o];
         }
     }
 
-    for (int it = 0; it < iters; ++it) {
-        const float beta = mom[k0 + it];
-        // momentum point (r, s) from the last two iterates
+    int it = 0;
+    for (; it + 2 <= iters; it += 2) {
+        fgp_step(pa, pb, qa, qb, bb, pmask, qmask, mom[k0 + it], tau, c8, s_buf, u_buf, r_edge, tx, ty);
+        fgp_step(pb, pa, qb, qa, bb, pmask, qmask, mom[k0 + it + 1], tau, c8, s_buf, u_buf, r_edge,
+                 tx, ty);
+    }
+    if (it < iters) {
+        fgp_step(pa, pb, qa, qb, bb, pmask, qmask, mom[k0 + it], tau, c8, s_buf, u_buf, r_edge, tx, ty);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            rr[v] = p[v] + beta * (p[v] - pp[v]);
-            ss[v] = q[v] + beta * (q[v] - qp[v]);
-            s_buf[ty * V + v][tx] = ss[v];
-        }
-        r_edge[ty][tx] = rr[V - 1];
-        __syncthreads();
-        // u = b - tau L(r, s)
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const float r_up = (v > 0) ? rr[v - 1] : (ty > 0 ? r_edge[ty - 1][tx] : 0.f);
-            const float s_left = (tx > 0) ? s_buf[ty * V + v][tx - 1] : 0.f;
-            uu[v] = bb[v] - tau * (rr[v] + ss[v] - r_up - s_left);
-            u_buf[ty * V + v][tx] = uu[v];
-        }
-        __syncthreads();
-        // gradient step on the dual and projection
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const int i = R0 + ty * V + v;
-            const bool in = col_in && i >= 0 && i < H;
-            const float u_down =
-                (v < V - 1) ? uu[v + 1] : (ty < TY - 1 ? u_buf[ty * V + v + 1][tx] : 0.f);
-            const float u_right = (tx < RW - 1) ? u_buf[ty * V + v][tx + 1] : 0.f;
-            const float pt = rr[v] + (uu[v] - u_down) * c8;
-            const float qt = ss[v] + (uu[v] - u_right) * c8;
-            const bool pm = in && (i < H - 1);
-            const bool qm = in && (j < W - 1);
-            float pn = 0.f, qn = 0.f;
-            if (pm && qm) {
-                const float den = fmaxf(1.f, sqrtf(pt * pt + qt * qt));
-                pn = pt / den;
-                qn = qt / den;
-            } else if (pm) {
-                pn = pt / fmaxf(1.f, fabsf(pt));
-            } else if (qm) {
-                qn = qt / fmaxf(1.f, fabsf(qt));
-            }
-            pp[v] = p[v];
-            qp[v] = q[v];
-            p[v] = pn;
-            q[v] = qn;
+            const float t0 = pa[v], t1 = qa[v];
+            pa[v] = pb[v];
+            qa[v] = qb[v];
+            pb[v] = t0;
+            qb[v] = t1;
         }
     }
+    // (pa, qa): current iterate, (pb, qb): previous one
 
     if (last) {
         // x = b - tau L(p, q) with the final iterate
         __syncthreads();
 #pragma unroll
-        for (int v = 0; v < V; ++v) s_buf[ty * V + v][tx] = q[v];
-        r_edge[ty][tx] = p[V - 1];
+        for (int v = 0; v < V; ++v) s_buf[ty * V + v][tx] = qa[v];
+        r_edge[ty][tx] = pa[V - 1];
         __syncthreads();
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -130,9 +147,9 @@ __global__ void __launch_bounds__(RW *TY)
             const int i = R0 + rr_;
             const bool interior = rr_ >= HL && rr_ < HL + IH && tx >= HL && tx < HL + IW;
             if (!(interior && col_in && i >= 0 && i < H)) continue;
-            const float p_up = (v > 0) ? p[v - 1] : (ty > 0 ? r_edge[ty - 1][tx] : 0.f);
+            const float p_up = (v > 0) ? pa[v - 1] : (ty > 0 ? r_edge[ty - 1][tx] : 0.f);
             const float q_left = (tx > 0) ? s_buf[rr_][tx - 1] : 0.f;
-            x_out[(int64_t)i * W + j] = bb[v] - tau * (p[v] + q[v] - p_up - q_left);
+            x_out[(int64_t)i * W + j] = bb[v] - tau * (pa[v] + qa[v] - p_up - q_left);
         }
     } else {
 #pragma unroll
@@ -142,10 +159,10 @@ __global__ void __launch_bounds__(RW *TY)
             const bool interior = rr_ >= HL && rr_ < HL + IH && tx >= HL && tx < HL + IW;
             if (!(interior && col_in && i >= 0 && i < H)) continue;
             const int64_t o = (int64_t)i * W + j;
-            p_g[o] = p[v];
-            q_g[o] = q[v];
-            pp_g[o] = pp[v];
-            qp_g[o] = qp[v];
+            p_g[o] = pa[v];
+            q_g[o] = qa[v];
+            pp_g[o] = pb[v];
+            qp_g[o] = qb[v];
         }
     }
 }
