@@ -148,22 +148,23 @@ int ensure_mom(bsgdtv_ctx *h, int iters) {
 
 // Enqueues one epoch (lines 2-9) reading r[par] and writing r[1-par].  With
 // `marks`, records marks[0] / marks[1] around the product kernel and marks[2]
-// at the end of the epoch.
+// at the end of the epoch.  Kernels that follow a kernel are launched with
+// programmatic dependent launch (not across the timing marks).
 int enqueue_epoch(bsgdtv_ctx *h, int par, int fgp_iters, cudaStream_t s,
                   cudaEvent_t *marks = nullptr) {
     const bool prox = h->lambda > 0.0 && fgp_iters > 0;
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[0], s, cudaEventRecordExternal));
     BSG_CUDA(launch_products32(h->dl, h->x, h->r[par], h->rmax + par, h->rmax + (1 - par),
-                               h->z_part, reinterpret_cast<int32_t *>(h->g_part), s));
+                               h->z_part, reinterpret_cast<int32_t *>(h->g_part), s, !marks));
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[1], s, cudaEventRecordExternal));
     float *xdst = prox ? h->xhat : h->x;
     BSG_CUDA(launch_reduce_update32(h->dl, h->z_part, reinterpret_cast<const int32_t *>(h->g_part),
                                     h->rmax + par, h->y, h->r[1 - par], h->rmax + (1 - par), h->x,
-                                    xdst, (float)h->mu, s));
+                                    xdst, (float)h->mu, s, !marks));
     if (prox) {
         FgpScratch sc{h->fp, h->fq, h->fpp, h->fqp};
         BSG_CUDA(launch_fgp(h->xhat, h->x, h->dl.img_h, h->dl.img_w, (float)(h->mu * h->lambda),
-                            fgp_iters, h->mom, sc, s));
+                            fgp_iters, h->mom, sc, s, true));
     }
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[2], s, cudaEventRecordExternal));
     return BSGDTV_OK;

@@ -29,6 +29,34 @@ int fail(int code, const std::string &msg);
 
 void add_launches(int64_t n);
 
+// Kernel launch with optional programmatic dependent launch (PDL): the grid
+// may be scheduled while its predecessor in the stream drains; the kernel
+// must execute pdl_wait() before touching memory its predecessor writes.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                          cudaStream_t s, bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+#ifdef __CUDACC__
+// Wait for the predecessor grid (no-op without PDL), then let the successor
+// grid be scheduled.
+__device__ __forceinline__ void pdl_wait_and_release() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+#endif
+
 // ------------------------------------------------------- tiled operator layout
 // The image is cut into pixel tiles (at most kTileH x kTileW, never crossing a
 // column-block band J_j) and the rows into groups (sub-ranges of the row blocks
@@ -131,7 +159,7 @@ cudaError_t launch_products64(const DevLayout &d, const double *x, const double 
 // rmax_clear (may be null) is set to 0 for the next reduction to fill.
 cudaError_t launch_products32(const DevLayout &d, const float *x, const float *r,
                               const float *rmax_in, float *rmax_clear, float *z_part,
-                              int32_t *g_part, cudaStream_t s);
+                              int32_t *g_part, cudaStream_t s, bool pdl = false);
 
 // Scale 2^e such that 2 * rmax * colsum_max * 2^e < 2^30: every partial sum of
 // the fixed-point A^T r tile stays below 2^31 in magnitude.
@@ -157,7 +185,7 @@ cudaError_t launch_reduce_update64(const DevLayout &d, const double *z_part, con
 cudaError_t launch_reduce_update32(const DevLayout &d, const float *z_part, const int32_t *g_part,
                                    const float *rmax_in, const float *y, float *r_out,
                                    float *rmax_out, const float *x, float *x_out, float mu,
-                                   cudaStream_t s);
+                                   cudaStream_t s, bool pdl = false);
 cudaError_t launch_block_sums(const DevLayout &d, const float *z_part, const int32_t *g_part,
                               const float *rmax_in, float *z_blocks, float *g_blocks,
                               cudaStream_t s);
@@ -182,7 +210,7 @@ struct FgpScratch {
 };
 int fgp_plan_launches(int h, int w, int iters);
 cudaError_t launch_fgp(const float *b, float *x, int h, int w, float tau, int iters,
-                       const float *mom, FgpScratch sc, cudaStream_t s);
+                       const float *mom, FgpScratch sc, cudaStream_t s, bool pdl = false);
 void fgp_momentum_host(int iters, std::vector<float> &mom);
 
 }  // namespace bsgdtv

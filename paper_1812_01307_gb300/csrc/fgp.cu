@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(RW *TY)
     const int R0 = blockIdx.y * IH - HL, C0 = blockIdx.x * IW - HL;
     const int j = C0 + tx;
     const bool col_in = (j >= 0 && j < W);
+    pdl_wait_and_release();
 
     float bb[V], pa[V], pb[V], qa[V], qb[V];
     unsigned pmask = 0u, qmask = 0u;
@@ -190,14 +191,14 @@ int fgp_plan_launches(int h, int w, int iters) {
 }
 
 cudaError_t launch_fgp(const float *b, float *x, int h, int w, float tau, int iters,
-                       const float *mom, FgpScratch sc, cudaStream_t s) {
+                       const float *mom, FgpScratch sc, cudaStream_t s, bool pdl) {
     const dim3 block(RW, TY);
     const float c8 = 1.0f / (8.0f * tau);
     if (fits_one_region(h, w)) {
-        fgp_kernel<<<dim3(1, 1), block, 0, s>>>(b, x, h, w, tau, c8, mom, 0, iters, 0, RH, RW, 1, 1,
-                                                sc.p, sc.q, sc.pp, sc.qp);
+        cudaError_t e = launch_kernel(fgp_kernel, dim3(1, 1), block, 0, s, pdl, b, x, h, w, tau, c8,
+                                      mom, 0, iters, 0, RH, RW, 1, 1, sc.p, sc.q, sc.pp, sc.qp);
         add_launches(1);
-        return cudaGetLastError();
+        return e != cudaSuccess ? e : cudaGetLastError();
     }
     int done = 0;
     while (done < iters) {
@@ -206,10 +207,11 @@ cudaError_t launch_fgp(const float *b, float *x, int h, int w, float tau, int it
         const int IH = RH - 2 * HL, IW = RW - 2 * HL;
         const dim3 grid((w + IW - 1) / IW, (h + IH - 1) / IH);
         const int first = (done == 0), last = (done + chunk == iters);
-        fgp_kernel<<<grid, block, 0, s>>>(b, x, h, w, tau, c8, mom, done, chunk, HL, IH, IW, first,
-                                          last, sc.p, sc.q, sc.pp, sc.qp);
+        cudaError_t e = launch_kernel(fgp_kernel, grid, block, 0, s, pdl || done > 0, b, x, h, w, tau,
+                                      c8, mom, done, chunk, HL, IH, IW, first, last, sc.p, sc.q,
+                                      sc.pp, sc.qp);
         add_launches(1);
-        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         done += chunk;
     }

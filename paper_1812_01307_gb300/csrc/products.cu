@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     const unsigned lt = (1u << lane) - 1u;
     const float4 *__restrict__ V4 = reinterpret_cast<const float4 *>(d.vals);
     const int4 *__restrict__ I4 = reinterpret_cast<const int4 *>(d.idx);
+    pdl_wait_and_release();
     // 2 r scaled to fixed point (FP32 path) or plain 2 r (FP64 path)
     const T scale = rmax_in ? (T)fixed_scale(*rmax_in, d.colsum_max) : T(1);
     if (rmax_clear && blockIdx.x == 0 && threadIdx.x == 0) *rmax_clear = 0.f;
@@ -167,14 +168,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 
 cudaError_t launch_products32(const DevLayout &d, const float *x, const float *r,
                               const float *rmax_in, float *rmax_clear, float *z_part,
-                              int32_t *g_part, cudaStream_t s) {
+                              int32_t *g_part, cudaStream_t s, bool pdl) {
     if (d.n_items == 0) return cudaSuccess;
     const size_t smem = kTileWords * (sizeof(float) + sizeof(int));
     const int grid = std::min(d.n_items, kCtasPerSm * std::max(d.n_sms, 1));
-    products_kernel<float, int><<<grid, kThreads, smem, s>>>(d, x, r, rmax_in, rmax_clear, z_part,
-                                                             g_part, d.item_ctr);
+    cudaError_t e = launch_kernel(products_kernel<float, int>, dim3(grid), dim3(kThreads), smem, s,
+                                  pdl, d, x, r, rmax_in, rmax_clear, z_part, g_part, d.item_ctr);
     add_launches(1);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_products64(const DevLayout &d, const double *x, const double *r, double *z_part,

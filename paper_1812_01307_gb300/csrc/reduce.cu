@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(kThreads)
                            const int32_t *__restrict__ g_part, const float *__restrict__ rmax_in,
                            const float *__restrict__ y, float *r_out, float *rmax_out,
                            const float *x, float *x_out, float mu, int nb_rows) {
+    pdl_wait_and_release();
     if ((int)blockIdx.x < nb_rows) {
         const int64_t ray = (int64_t)blockIdx.x * kThreads + threadIdx.x;
         float rv = 0.f;
@@ -228,13 +229,14 @@ cudaError_t launch_reduce_update64(const DevLayout &d, const double *z_part, con
 cudaError_t launch_reduce_update32(const DevLayout &d, const float *z_part, const int32_t *g_part,
                                    const float *rmax_in, const float *y, float *r_out,
                                    float *rmax_out, const float *x, float *x_out, float mu,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, bool pdl) {
     const int nb_rows = (int)((d.rows + kThreads - 1) / kThreads);
     const int nb_cols = (int)((d.cols + kThreads - 1) / kThreads);
-    reduce_update32_kernel<<<nb_rows + nb_cols, kThreads, 0, s>>>(
-        d, z_part, g_part, rmax_in, y, r_out, rmax_out, x, x_out, mu, nb_rows);
+    cudaError_t e = launch_kernel(reduce_update32_kernel, dim3(nb_rows + nb_cols), dim3(kThreads), 0, s,
+                                  pdl, d, z_part, g_part, rmax_in, y, r_out, rmax_out, x, x_out, mu,
+                                  nb_rows);
     add_launches(1);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_block_sums(const DevLayout &d, const float *z_part, const int32_t *g_part,
