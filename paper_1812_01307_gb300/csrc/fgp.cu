@@ -13,8 +13,8 @@
 // vertical strip of 8 pixels' fields (b, p, q, p_prev, q_prev, r, s, u) in
 // registers for all the iterations of one launch.  Only the values a
 // neighbour needs (s to the right neighbour, r across strip boundaries, u to
-// the left / upper neighbour) pass through shared memory, two barriers per
-// iteration.  When the image fits one region the whole FGP is one launch;
+// the left / upper neighbour) pass through zero-padded shared buffers, two
+// barriers per iteration, with no bounds tests in the iteration.  When the image fits one region the whole FGP is one launch;
 // otherwise regions overlap by a halo of (iterations per launch + 1) pixels
 // (temporal blocking), so each launch runs several iterations with no global
 // synchronisation, and the dual fields persist in global memory (L2) between
@@ -37,47 +37,57 @@ constexpr int V = 8;        // pixels per thread (vertical strip)
 constexpr int RH = TY * V;  // region height
 constexpr int kMaxChunk = 8;  // iterations per launch when tiled (halo = chunk + 1)
 
+// Shared buffers are padded with a zero border so that neighbour reads need
+// no bounds tests: column c of the region is stored at c + 1, row -1 of the
+// strip-edge buffer and row RH of u are zero.
+struct FgpShared {
+    float s[RH][RW + 2];        // s of the momentum point, read by the right neighbour
+    float u[RH + 1][RW + 2];    // u, read by the left and upper neighbours
+    float r_edge[TY + 1][RW];   // r of each strip's last pixel, read by the strip below
+};
+
 // One FGP iteration for this thread's strip.  (p, q) hold the current dual
 // iterate and (pp, qp) the previous one; the new iterate is written over
 // (pp, qp), so the caller swaps the roles of the two register sets.
+//
+// The projection is applied jointly everywhere: where only p (last column) or
+// only q (last row) is defined, the other component is zeroed first, which
+// makes the joint projection exactly the single-component clip t/max(1,|t|);
+// outside the image both are zeroed.  rsqrtf(max(n2, 1)) is the scale
+// 1/max(1, sqrt(n2)).
 __device__ __forceinline__ void fgp_step(float (&p)[V], float (&pp)[V], float (&q)[V],
                                          float (&qp)[V], const float (&bb)[V], unsigned pmask,
                                          unsigned qmask, float beta, float tau, float c8,
-                                         float (*s_buf)[RW + 1], float (*u_buf)[RW + 1],
-                                         float (*r_edge)[RW], int tx, int ty) {
+                                         FgpShared &sh, int tx, int ty) {
     float rr[V], ss[V], uu[V];
     // momentum point (r, s) from the last two iterates
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         rr[v] = fmaf(beta, p[v] - pp[v], p[v]);
         ss[v] = fmaf(beta, q[v] - qp[v], q[v]);
-        s_buf[ty * V + v][tx] = ss[v];
+        sh.s[ty * V + v][tx + 1] = ss[v];
     }
-    r_edge[ty][tx] = rr[V - 1];
+    sh.r_edge[ty + 1][tx] = rr[V - 1];
     __syncthreads();
     // u = b - tau L(r, s)
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        const float r_up = (v > 0) ? rr[v - 1] : (ty > 0 ? r_edge[ty - 1][tx] : 0.f);
-        const float s_left = (tx > 0) ? s_buf[ty * V + v][tx - 1] : 0.f;
+        const float r_up = (v > 0) ? rr[v - 1] : sh.r_edge[ty][tx];
+        const float s_left = sh.s[ty * V + v][tx];
         uu[v] = fmaf(-tau, (rr[v] - r_up) + (ss[v] - s_left), bb[v]);
-        u_buf[ty * V + v][tx] = uu[v];
+        sh.u[ty * V + v][tx + 1] = uu[v];
     }
     __syncthreads();
     // (P, Q) = L^T u, gradient step on the dual, projection onto the unit ball
-    // (p_{i,w-1} and q_{h-1,j} alone: clipping to [-1, 1] is exactly t/max(1,|t|))
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        const float u_down =
-            (v < V - 1) ? uu[v + 1] : (ty < TY - 1 ? u_buf[ty * V + v + 1][tx] : 0.f);
-        const float u_right = (tx < RW - 1) ? u_buf[ty * V + v][tx + 1] : 0.f;
-        const float pt = fmaf(uu[v] - u_down, c8, rr[v]);
-        const float qt = fmaf(uu[v] - u_right, c8, ss[v]);
-        const bool pm = (pmask >> v) & 1u, qm = (qmask >> v) & 1u;
-        const float n2 = fmaf(pt, pt, qt * qt);
-        const float inv = n2 > 1.f ? rsqrtf(n2) : 1.f;
-        pp[v] = pm ? (qm ? pt * inv : fminf(fmaxf(pt, -1.f), 1.f)) : 0.f;
-        qp[v] = qm ? (pm ? qt * inv : fminf(fmaxf(qt, -1.f), 1.f)) : 0.f;
+        const float u_down = (v < V - 1) ? uu[v + 1] : sh.u[ty * V + V][tx + 1];
+        const float u_right = sh.u[ty * V + v][tx + 2];
+        const float pt = (pmask & (1u << v)) ? fmaf(uu[v] - u_down, c8, rr[v]) : 0.f;
+        const float qt = (qmask & (1u << v)) ? fmaf(uu[v] - u_right, c8, ss[v]) : 0.f;
+        const float inv = rsqrtf(fmaxf(fmaf(pt, pt, qt * qt), 1.f));
+        pp[v] = pt * inv;
+        qp[v] = qt * inv;
     }
 }
 
@@ -86,18 +96,32 @@ __global__ void __launch_bounds__(RW *TY)
                float c8, const float *__restrict__ mom, int k0, int iters, int HL, int IH, int IW,
                int first, int last, float *__restrict__ p_g, float *__restrict__ q_g,
                float *__restrict__ pp_g, float *__restrict__ qp_g) {
-    __shared__ float s_buf[RH][RW + 1];
-    __shared__ float u_buf[RH][RW + 1];
-    __shared__ float r_edge[TY][RW];
+    __shared__ FgpShared sh;
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int R0 = blockIdx.y * IH - HL, C0 = blockIdx.x * IW - HL;
     const int j = C0 + tx;
     const bool col_in = (j >= 0 && j < W);
+
+    // zero borders (never written afterwards) and the masks
+    if (ty == 0) {
+        sh.r_edge[0][tx] = 0.f;
+        sh.u[RH][tx + 1] = 0.f;
+        if (tx == 0) sh.u[RH][0] = sh.u[RH][RW + 1] = 0.f;
+    }
+    if (tx == 0) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            sh.s[ty * V + v][0] = 0.f;
+            sh.u[ty * V + v][RW + 1] = 0.f;
+            sh.s[ty * V + v][RW + 1] = 0.f;
+            sh.u[ty * V + v][0] = 0.f;
+        }
+    }
     pdl_wait_and_release();
 
     float bb[V], pa[V], pb[V], qa[V], qb[V];
-    unsigned pmask = 0u, qmask = 0u;
+    unsigned pmask = 0u, qmask = 0u;   // bit v: p / q defined at this strip's pixel v
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         const int i = R0 + ty * V + v;
@@ -118,12 +142,11 @@ __global__ void __launch_bounds__(RW *TY)
 
     int it = 0;
     for (; it + 2 <= iters; it += 2) {
-        fgp_step(pa, pb, qa, qb, bb, pmask, qmask, mom[k0 + it], tau, c8, s_buf, u_buf, r_edge, tx, ty);
-        fgp_step(pb, pa, qb, qa, bb, pmask, qmask, mom[k0 + it + 1], tau, c8, s_buf, u_buf, r_edge,
-                 tx, ty);
+        fgp_step(pa, pb, qa, qb, bb, pmask, qmask, mom[k0 + it], tau, c8, sh, tx, ty);
+        fgp_step(pb, pa, qb, qa, bb, pmask, qmask, mom[k0 + it + 1], tau, c8, sh, tx, ty);
     }
     if (it < iters) {
-        fgp_step(pa, pb, qa, qb, bb, pmask, qmask, mom[k0 + it], tau, c8, s_buf, u_buf, r_edge, tx, ty);
+        fgp_step(pa, pb, qa, qb, bb, pmask, qmask, mom[k0 + it], tau, c8, sh, tx, ty);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const float t0 = pa[v], t1 = qa[v];
@@ -139,8 +162,8 @@ __global__ void __launch_bounds__(RW *TY)
         // x = b - tau L(p, q) with the final iterate
         __syncthreads();
 #pragma unroll
-        for (int v = 0; v < V; ++v) s_buf[ty * V + v][tx] = qa[v];
-        r_edge[ty][tx] = pa[V - 1];
+        for (int v = 0; v < V; ++v) sh.s[ty * V + v][tx + 1] = qa[v];
+        sh.r_edge[ty + 1][tx] = pa[V - 1];
         __syncthreads();
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -148,8 +171,8 @@ __global__ void __launch_bounds__(RW *TY)
             const int i = R0 + rr_;
             const bool interior = rr_ >= HL && rr_ < HL + IH && tx >= HL && tx < HL + IW;
             if (!(interior && col_in && i >= 0 && i < H)) continue;
-            const float p_up = (v > 0) ? pa[v - 1] : (ty > 0 ? r_edge[ty - 1][tx] : 0.f);
-            const float q_left = (tx > 0) ? s_buf[rr_][tx - 1] : 0.f;
+            const float p_up = (v > 0) ? pa[v - 1] : sh.r_edge[ty][tx];
+            const float q_left = sh.s[rr_][tx];
             x_out[(int64_t)i * W + j] = bb[v] - tau * (pa[v] + qa[v] - p_up - q_left);
         }
     } else {
