@@ -62,9 +62,17 @@ __global__ void __launch_bounds__(kThreads)
             r_out[ray] = rv;
         }
         if (rmax_out) {
+            // one atomic per block: warp maxima through shared memory
+            __shared__ float wmax[kThreads / 32];
             float m = fabsf(rv);
             for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if ((threadIdx.x & 31) == 0) atomic_max_nonneg(rmax_out, m);
+            if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                m = (threadIdx.x < kThreads / 32) ? wmax[threadIdx.x] : 0.f;
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (threadIdx.x == 0) atomic_max_nonneg(rmax_out, m);
+            }
         }
     } else {
         const int64_t p = (int64_t)(blockIdx.x - nb_rows) * kThreads + threadIdx.x;
@@ -126,7 +134,14 @@ __global__ void absmax_kernel(const float *__restrict__ v, int64_t n, float *out
          i += (int64_t)gridDim.x * blockDim.x)
         m = fmaxf(m, fabsf(v[i]));
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
+    __shared__ float wmax[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = (threadIdx.x < (int)(blockDim.x >> 5)) ? wmax[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) atomic_max_nonneg(out, m);
+    }
 }
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
