@@ -29,7 +29,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "BSGD-TV epochs/s + HBM GB/s (fused Ax,Aᵀr,TV-prox); served p50/p99 latency"
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "products_ellipse512.json")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "products_ellipse512.md")
 TRAFFIC_SOURCES = ["paper_1812_01307_gb300/csrc/products.cu", "paper_1812_01307_gb300/csrc/layout.cpp",
                    "paper_1812_01307_gb300/csrc/bsgdtv_internal.h"]
 
@@ -116,18 +116,32 @@ def hbm_peak():
 def profiled_traffic():
     """DRAM bytes per launch of the product kernel from the committed ncu
     summary, if it was taken on the current kernel source; else None."""
+    prof = {}
     try:
         with open(PROFILE_TRAFFIC) as f:
-            prof = json.load(f)
-    except (OSError, ValueError):
+            for line in f:
+                if ":" in line and not line.startswith(("#", "|", " ")):
+                    k, v = line.split(":", 1)
+                    prof[k.strip()] = v.strip()
+    except OSError:
         return None
+    if prof.get("source_sha256") != kernel_source_hash() or "dram_bytes_per_launch" not in prof:
+        return None
+    return int(prof["dram_bytes_per_launch"])
+
+
+def kernel_source_hash():
+    """sha256 of the product kernel's sources with comments and blank space
+    removed (a comment-only edit does not change the kernel)."""
+    import re
     h = hashlib.sha256()
     for p in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
-    if prof.get("source_sha256") != h.hexdigest():
-        return None
-    return prof.get("dram_bytes_per_launch")
+        with open(os.path.join(ROOT, p)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("".join(src.split()).encode())
+    return h.hexdigest()
 
 
 # ------------------------------------------------------------- CPU oracle

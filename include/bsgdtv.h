@@ -3,13 +3,13 @@
  *
  * BSGD-TV (Gao & Blumensath, arXiv 1812.01307) reconstructs an image x from
  * projections y ~ A x by repeating one epoch of Algorithm 1:
- *   lines 2-5  block products  z^j_{I_i} = A_{I_i}^{J_j} x_{J_j}  and
- *              g^i_{J_j} = 2 (A_{I_i}^{J_j})^T r_{I_i}   (r from the previous epoch)
- *   line 6     r = y - sum_j z^j
- *   line 7     g = sum_i g^i
- *   line 8     x = x + mu g
- *   line 9     x = argmin_t ||t - x||^2 + 2 mu lambda TV(t), solved by Beck &
- *              Teboulle's fast gradient projection (FGP) with tau = mu*lambda.
+ *   block products  z^j_{I_i} = A_{I_i}^{J_j} x_{J_j}  and
+ *                   g^i_{J_j} = 2 (A_{I_i}^{J_j})^T r_{I_i}   (r from the previous epoch)
+ *   residual        r = y - sum_j z^j
+ *   gradient        g = sum_i g^i
+ *   step            x = x + mu g
+ *   TV prox         x = argmin_t ||t - x||^2 + 2 mu lambda TV(t), solved by Beck &
+ *                   Teboulle's fast gradient projection (FGP) with tau = mu*lambda.
  * A is divided into M row blocks I_i and N column blocks J_j (Sec. 2.1).
  *
  * Conventions shared by every entry point
@@ -95,13 +95,13 @@ int bsgdtv_estimate_umax(bsgdtv_t h, int max_iters, double rel_tol, double *u_ma
 int bsgdtv_get_params(bsgdtv_t h, double *mu, double *lambda, double *u_max);
 
 /* Runs `epochs` epochs of Algorithm 1 with `fgp_iters` FGP iterations for
- * line 9 (lambda = 0 or fgp_iters = 0 makes line 9 the identity).  Asynchronous
+ * the TV prox (lambda = 0 or fgp_iters = 0 makes the prox the identity).  Asynchronous
  * on the handle's stream; resumes from the current state. */
 int bsgdtv_run(bsgdtv_t h, int epochs, int fgp_iters);
 
 /* bsgdtv_run that also times, with CUDA events recorded on the handle's
  * stream inside the epoch graphs, every launch of the fused product kernel
- * (lines 2-5) and every whole epoch.  Synchronises.  products_ms / epoch_ms
+ * (the block products) and every whole epoch.  Synchronises.  products_ms / epoch_ms
  * (may be NULL) receive the sums over the `epochs` epochs. */
 int bsgdtv_run_timed(bsgdtv_t h, int epochs, int fgp_iters, double *products_ms,
                      double *epoch_ms);
@@ -115,11 +115,12 @@ int bsgdtv_get_state(bsgdtv_t h, float *x, float *r, int64_t *epoch, int on_devi
 int bsgdtv_set_state(bsgdtv_t h, const float *x, const float *r, int64_t epoch, int on_device);
 
 /* FP64 monitoring of the current x: data term ||y - A x||^2 and TV(x)
- * (Eq. 1; the function line 9 as printed minimises is data + lambda*TV).
+ * (Eq. 1; the function Algorithm 1 with its TV prox as printed minimises is
+ * data + lambda*TV).
  * Synchronises. */
 int bsgdtv_objective(bsgdtv_t h, double *data_term, double *tv);
 
-/* Test hook: the block products of lines 3-4 for given x [cols] and r [rows]
+/* Test hook: the block products of Algorithm 1 for given x [cols] and r [rows]
  * (device pointers), computed by the same fused kernel the epoch uses.
  *   z_blocks [N*rows]:  z_blocks[j*rows + k] = (A_{I_i}^{J_j} x_{J_j})_k for row
  *                       k of block I_i (i.e. z^j stacked over i).
@@ -135,7 +136,7 @@ int bsgdtv_block_products(bsgdtv_t h, const float *x, const float *r, float *z_b
 int bsgdtv_get_info(bsgdtv_t h, int64_t *nnz, int64_t *segments, int64_t *work_items,
                     int64_t *min_bytes_per_pass);
 
-/* Line 9 alone: x = FGP(b, tau, iters) for one img_h x img_w image (device
+/* The TV prox alone: x = FGP(b, tau, iters) for one img_h x img_w image (device
  * pointers b, x; may not alias).  Beck-Teboulle FGP, cold start, isotropic TV,
  * P_C = identity; tau <= 0 or iters <= 0 copies b.  Allocates its scratch (the
  * dual fields) from the device heap for the duration of the call and

@@ -4,21 +4,22 @@ Paper: Y. Gao, T. Blumensath, "BSGD-TV: A parallel algorithm solving total
 variation constrained image reconstruction problems", arXiv 1812.01307.
 TV prox solver: A. Beck, M. Teboulle, "Fast gradient-based algorithms for
 constrained total variation image denoising and deblurring problems",
-IEEE TIP 18(11), 2009 (the method the paper adopts for line 9 of Algorithm 1).
+IEEE TIP 18(11), 2009 (the method the paper adopts for the TV proximal step of
+Algorithm 1).
 
 Readings where the paper is silent or ambiguous (each one is also recorded in
 the design notes):
-  R1  line 9 is taken literally: prox weight 2*mu*lambda, so FGP runs with
+  R1  the TV proximal step is taken as printed: prox weight 2*mu*lambda, so FGP runs with
       tau = mu*lambda, and the algorithm's fixed point minimises
       ||y-Ax||^2 + lambda*TV(x)  (Eq. 1 writes 2*lambda*TV; see F_alg below).
   R2  TV is Beck-Teboulle's isotropic TV_I: forward differences with Neumann
       (zero-difference) border, the discretisation FGP is defined on.
   R3  initialisation: x^0 = 0 and r before the first epoch is y - A x^0 = y,
       so the first epoch's gradient uses r = y.
-  R4  the random pair order of line 2 is drawn, but the sums of lines 6-7
+  R4  the random order of the block pairs is drawn, but the residual and gradient sums
       run in ascending j / i, so the result does not depend on the draw.
   R5  FGP: cold start every epoch, exactly K iterations, P_C = identity.
-  R6  lambda = 0 (or K = 0) makes line 9 the identity.
+  R6  lambda = 0 (or K = 0) makes the TV proximal step the identity.
   R7  uneven blocks follow numpy.array_split: the first (L mod M) blocks get
       one extra unit.
   R8  u_max by power iteration on A^T A from the all-ones vector.
@@ -83,11 +84,11 @@ def split_blocks(A, rb, cb):
 
 
 def block_products(blocks, rb, cb, x, r, order=None):
-    """Lines 2-5 of Algorithm 1 for every pair (i, j).
+    """The block products of Algorithm 1 for every pair (i, j).
 
-    Returns (z, gh) with z[i][j] = A_{I_i}^{J_j} x_{J_j}  (line 4, z^j_{I_i}) and
-    gh[i][j] = 2 (A_{I_i}^{J_j})^T r_{I_i}  (line 3, g-hat^i_{J_j}); `r` is the
-    residual from the previous epoch.  `order` is the sequence of pairs (line 2);
+    Returns (z, gh) with z[i][j] = A_{I_i}^{J_j} x_{J_j}  (z^j_{I_i}) and
+    gh[i][j] = 2 (A_{I_i}^{J_j})^T r_{I_i}  (g-hat^i_{J_j}); `r` is the
+    residual from the previous epoch.  `order` is the sequence of pairs drawn;
     every pair reads the same x and r, so the order does not change the values.
     """
     M, N = len(rb) - 1, len(cb) - 1
@@ -105,7 +106,7 @@ def block_products(blocks, rb, cb, x, r, order=None):
 
 
 def reduce_residual(y, z, rb):
-    """Line 6: r = y - sum_j z^j (ascending j, R4)."""
+    """Residual update of Algorithm 1: r = y - sum_j z^j (ascending j, R4)."""
     r = np.array(y, dtype=np.float64, copy=True)
     for i in range(len(rb) - 1):
         acc = np.zeros(rb[i + 1] - rb[i])
@@ -116,7 +117,7 @@ def reduce_residual(y, z, rb):
 
 
 def reduce_gradient(gh, cb, c):
-    """Line 7: g = sum_i g-hat^i (ascending i, R4)."""
+    """Gradient sum of Algorithm 1: g = sum_i g-hat^i (ascending i, R4)."""
     g = np.zeros(c)
     M, N = len(gh), len(cb) - 1
     for j in range(N):
@@ -178,7 +179,7 @@ def fgp_momentum(K: int):
 
 def fgp(b, tau: float, K: int, return_dual: bool = False):
     """FGP(b, tau, K) of Beck-Teboulle 2009 for argmin_x ||x-b||^2 + 2 tau TV_I(x),
-    unconstrained (P_C = identity, R5).  Line 9 of Algorithm 1 calls it with
+    unconstrained (P_C = identity, R5).  The TV proximal step of Algorithm 1 calls it with
     tau = mu*lambda (R1)."""
     b = np.asarray(b, dtype=np.float64)
     m, n = b.shape
@@ -214,20 +215,20 @@ def tv_iso(x) -> float:
 
 # --------------------------------------------------------------- Algorithm 1
 def epoch(blocks, rb, cb, y, x, r_prev, mu, lam, fgp_iters, img_shape, rng=None):
-    """One epoch of Algorithm 1 (lines 2-9).  Returns (x_new, r_new, x_hat).
+    """One epoch of Algorithm 1.  Returns (x_new, r_new, x_hat).
 
     x: current iterate x^k (flat); r_prev: residual r^{k-1} from the previous
-    epoch (line 6 of the previous epoch, or y before the first one, R3).
+    epoch (its residual update, or y before the first one, R3).
     """
     M, N = len(rb) - 1, len(cb) - 1
     pairs = [(i, j) for i in range(M) for j in range(N)]
     if rng is not None:
         pairs = [pairs[k] for k in rng.permutation(len(pairs))]
-    z, gh = block_products(blocks, rb, cb, x, r_prev, pairs)        # lines 2-5
-    r_new = reduce_residual(y, z, rb)                                 # line 6
-    g = reduce_gradient(gh, cb, x.shape[0])                           # line 7
-    x_hat = x + mu * g                                                # line 8
-    if lam > 0.0 and fgp_iters > 0:                                   # line 9 (R1, R6)
+    z, gh = block_products(blocks, rb, cb, x, r_prev, pairs)        # block products
+    r_new = reduce_residual(y, z, rb)                                 # r = y - sum_j z^j
+    g = reduce_gradient(gh, cb, x.shape[0])                           # g = sum_i g-hat^i
+    x_hat = x + mu * g                                                # gradient step
+    if lam > 0.0 and fgp_iters > 0:                                   # TV prox (R1, R6)
         x_new = fgp(x_hat.reshape(img_shape), mu * lam, fgp_iters).ravel()
     else:
         x_new = x_hat.copy()
@@ -283,7 +284,7 @@ def power_iteration(A, max_iters: int = 5000, rel_tol: float = 1e-12, v0=None):
 # --------------------------------------------------------- monitoring, Eq. 1
 def objective(A, y, x, lam, img_shape):
     """F_alg(x) = ||y - A x||^2 + lambda TV_I(x): the function Algorithm 1 with
-    line 9 as printed minimises (R1).  Returns (F, ||y-Ax||^2, TV_I(x))."""
+    TV proximal step as printed minimises (R1).  Returns (F, ||y-Ax||^2, TV_I(x))."""
     A = to_scipy(A)
     res = np.asarray(y, dtype=np.float64) - A @ np.asarray(x, dtype=np.float64)
     f = float(res @ res)

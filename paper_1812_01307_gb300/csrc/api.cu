@@ -146,7 +146,7 @@ int ensure_mom(bsgdtv_ctx *h, int iters) {
     return BSGDTV_OK;
 }
 
-// Enqueues one epoch (lines 2-9) reading r[par] and writing r[1-par].  With
+// Enqueues one epoch of Algorithm 1 reading r[par] and writing r[1-par].  With
 // `marks`, records marks[0] / marks[1] around the product kernel and marks[2]
 // at the end of the epoch.  Kernels that follow a kernel are launched with
 // programmatic dependent launch (not across the timing marks).
@@ -462,7 +462,7 @@ int bsgdtv_estimate_umax(bsgdtv_t h, int max_iters, double rel_tol, double *u_ma
         BSG_CUDA(launch_products64(h->dl, h->v64, h->w64, h->z64, h->gp64, s));
         BSG_CUDA(launch_reduce_update64(h->dl, h->z64, h->gp64, nullptr, h->w64, nullptr, h->g64,
                                         0.0, s));
-        // g = 2 A^T w  (the product kernel carries line 3's factor 2)
+        // g = 2 A^T w  (the product kernel carries the block gradient's factor 2)
         BSG_CUDA(launch_products64(h->dl, h->v64, h->w64, h->z64, h->gp64, s));
         BSG_CUDA(launch_reduce_update64(h->dl, h->z64, h->gp64, nullptr, h->w64, nullptr, h->g64,
                                         0.0, s));

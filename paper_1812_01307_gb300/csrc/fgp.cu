@@ -1,4 +1,4 @@
-// Line 9 of Algorithm 1: x = argmin_t ||t - b||^2 + 2 tau TV(t), tau = mu*lambda,
+// TV proximal step of Algorithm 1: x = argmin_t ||t - b||^2 + 2 tau TV(t), tau = mu*lambda,
 // by Beck & Teboulle's fast gradient projection (FGP, IEEE TIP 18(11), 2009).
 //
 // One FGP iteration on the dual pair (p, q) (p: (h-1) x w, q: h x (w-1)):

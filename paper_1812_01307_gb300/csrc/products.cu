@@ -1,10 +1,10 @@
-// Fused block products of Algorithm 1, lines 2-5 (one pass over A).
+// Fused block products of Algorithm 1 (one pass over A).
 //
 // For every work item (row group G inside a row block I_i, pixel tile T inside
 // a column band J_j) a CTA computes, from a single read of the item's
 // nonzeros,
-//   z partial:  sum over the row's nonzeros in T of a * x        (line 4)
-//   g partial:  sum over G's rows of 2 a r_row, for each pixel of T (line 3)
+//   z partial:  sum over the row's nonzeros in T of a * x          (z^j_{I_i})
+//   g partial:  sum over G's rows of 2 a r_row, for each pixel of T (g-hat^i_{J_j})
 // where r is the residual of the previous epoch (the paper's stale gradient,
 // Eq. 3).  x_T is staged in shared memory and the g tile accumulates there.
 //

@@ -1,4 +1,4 @@
-// Reductions and the gradient step of Algorithm 1 (lines 6-8), plus the
+// Residual update, gradient sum and gradient step of Algorithm 1, plus the
 // deterministic FP64 reductions used for u_max (Theorem 1) and the objective
 // (Eq. 1).  Every sum runs in a fixed order, so results do not depend on
 // scheduling.
@@ -15,8 +15,8 @@ namespace {
 constexpr int kThreads = 256;
 
 // FP64 form (u_max, objective).
-// blocks [0, nb_rows): one thread per row,  r = y - sum_j z   (line 6)
-// blocks [nb_rows, ..): one thread per pixel, x' = x + mu sum_i g (lines 7-8)
+// blocks [0, nb_rows): one thread per row,  r = y - sum_j z
+// blocks [nb_rows, ..): one thread per pixel, x' = x + mu sum_i g
 __global__ void __launch_bounds__(kThreads)
     reduce_update64_kernel(const DevLayout d, const double *__restrict__ z_part,
                            const double *__restrict__ g_part, const double *__restrict__ y,
@@ -42,9 +42,9 @@ __device__ __forceinline__ void atomic_max_nonneg(float *dst, float v) {
     atomicMax(reinterpret_cast<int *>(dst), __float_as_int(v));
 }
 
-// FP32 hot path.  Rows: r = y - sum_j z (line 6) and max |r| for the next
+// FP32 hot path.  Rows: r = y - sum_j z and max |r| for the next
 // product pass.  Pixels: g = exact int64 sum of the groups' fixed-point tiles,
-// one rounding to FP32, x' = x + mu g (lines 7-8).
+// one rounding to FP32, x' = x + mu g.
 __global__ void __launch_bounds__(kThreads)
     reduce_update32_kernel(const DevLayout d, const float *__restrict__ z_part,
                            const int32_t *__restrict__ g_part, const float *__restrict__ rmax_in,
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// Per-block sums of lines 3-4 for the test hook.
+// Per-block sums of the block products for the test hook.
 __global__ void block_sums_kernel(const DevLayout d, const float *__restrict__ z_part,
                                   const int32_t *__restrict__ g_part,
                                   const float *__restrict__ rmax_in, float *z_blocks,

@@ -1,4 +1,4 @@
-// bsgdtv_tv_prox_static: the line-9 TV prox (FGP) without any allocation.
+// bsgdtv_tv_prox_static: the TV prox of Algorithm 1 (FGP) without any allocation.
 //
 // Some callers cannot allocate device memory at call time: a process whose
 // whole device budget is already claimed by its own pool allocator (a raw

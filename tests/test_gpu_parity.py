@@ -2,7 +2,7 @@
 on the same seeded inputs.
 
 Tolerances: partition bounds bit-exact; relative l2 error <= 1e-5 per block
-product (lines 3-4); <= 1e-4 on x after a full FP32 reconstruction; the prox
+block product; <= 1e-4 on x after a full FP32 reconstruction; the prox
 alone <= 1e-5; u_max and the FP64 objective <= 1e-9."""
 import numpy as np
 import pytest

@@ -138,7 +138,7 @@ def test_theorem2_descent_condition_implies_decrease():
 
 
 def test_fixed_point_solves_tv_problem_independently():
-    """lambda > 0: the limit of Algorithm 1 (line 9 weight 2 mu lambda) minimises
+    """lambda > 0: the limit of Algorithm 1 (prox weight 2 mu lambda) minimises
     ||y-Ax||^2 + lambda TV(x); checked against Chambolle-Pock."""
     A, D, y = _problem()
     lam = 0.6

@@ -1,4 +1,4 @@
-"""Pins for the oracle's TV prox (line 9 of Algorithm 1, solved by
+"""Pins for the oracle's TV prox (the proximal step of Algorithm 1, solved by
 Beck-Teboulle FGP): operator identities, the duality gap, closed forms,
 invariances and an independent convex solver."""
 import numpy as np

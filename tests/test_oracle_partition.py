@@ -1,5 +1,5 @@
 """Pins for the oracle's block bookkeeping and block products (Sec. 2.1,
-Algorithm 1 lines 3-7): against numpy.array_split, exact reassembly and
+the block products and sums of Algorithm 1): against numpy.array_split, exact reassembly and
 dense FP64 products."""
 import numpy as np
 import pytest
