@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the stored-format variants (FP32/16-bit index, FP16, BF16 weights)")
     return ap.parse_args()
 
 
@@ -269,8 +271,33 @@ def run_ours(args):
            "d2h_bytes_per_step": 4 * P.A.cols_n, "steps": E,
            "note": "per step: bsgdtv_set_data(host y) + bsgdtv_run(1 epoch) + bsgdtv_get_x(host x)"}
     rec.close()
-
     peak, peak_kind = hbm_peak()
+
+    # the same workload with the other stored formats of A (one timed run each)
+    variants = {}
+    if not args.no_variants:
+        Kv = max(1, min(K, 1000))
+        for name in ("f32_i16", "f16_i16", "bf16_i16"):
+            fmt = B.FORMATS[name]
+            rv = B.Reconstructor(P.A, (wl.n, wl.n), wl.M, wl.N, row_unit=wl.n_bins, col_unit=wl.n, fmt=fmt)
+            rv.set_data(y_dev, wl.lam, mu)
+            rv.run(W, wl.fgp_iters)
+            torch.cuda.synchronize()
+            D.barrier()
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            v0.record()
+            pk, ep = B.bsgdtv_run_timed(rv.h, Kv, wl.fgp_iters)
+            v1.record()
+            torch.cuda.synchronize()
+            dt = D.max_over_ranks(v0.elapsed_time(v1) / 1e3, dev)
+            vinfo = rv.info()
+            rv.close()
+            ach = vinfo["min_bytes_per_pass"] / (pk / 1e3 / Kv) / 1e9
+            variants[name] = {"value": world * Kv / dt, "unit": "epochs/s", "steps": Kv,
+                              "products_ms": pk / Kv, "bytes_per_launch": vinfo["min_bytes_per_pass"],
+                              "achieved_gbs": ach, "frac": ach / peak}
+
     prod_avg_s = prod_ms / 1e3 / K
     per_launch = info["min_bytes_per_pass"]
     achieved = per_launch / prod_avg_s / 1e9
@@ -290,7 +317,8 @@ def run_ours(args):
                          "traffic": profiled_traffic(), "bytes_per_launch": per_launch,
                          "avg_launch_ms": prod_avg_s * 1e3,
                          "share_of_epoch": prod_ms / epoch_ms if epoch_ms > 0 else None},
-            "gpu_launches": launches, "clocks": clocks, "e2e": e2e}
+            "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
+            "variants": variants or None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, done, dt = oracle_epochs_per_s(P, mu, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "epochs/s", "cores": 1, "kind": "oracle",

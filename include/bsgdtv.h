@@ -51,6 +51,18 @@ enum {
     BSGDTV_ERR_UNSUPPORTED = -7  /* valid request this build does not handle */
 };
 
+/* How the device stores A's weights and tile-local column indices.  F32_I32
+ * keeps FP32 weights and 32-bit indices (8 bytes per nonzero); F32_I16 is the
+ * same operator with 16-bit indices (6 bytes, exact); F16_I16 and BF16_I16
+ * round the weights to IEEE binary16 / bfloat16 (round to nearest even, 4
+ * bytes per nonzero) and compute in FP32 from the rounded values. */
+enum {
+    BSGDTV_FMT_F32_I32 = 0,
+    BSGDTV_FMT_F32_I16 = 1,
+    BSGDTV_FMT_F16_I16 = 2,
+    BSGDTV_FMT_BF16_I16 = 3
+};
+
 /* Creates a handle from a host CSR matrix A (rows = rays, cols = pixels).
  *   rows, cols          size of A; cols must equal img_h*img_w.
  *   row_ptr [rows+1]    int64 offsets, row_ptr[0] = 0, non-decreasing.
@@ -71,6 +83,15 @@ int bsgdtv_create_csr(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, int 
                       const int64_t *row_ptr, const int32_t *col_idx, const double *vals,
                       int M, int N, int64_t row_unit, int64_t col_unit,
                       const int64_t *row_bounds, const int64_t *col_bounds, void *stream);
+
+/* bsgdtv_create_csr with a stored format (BSGDTV_FMT_*); create_csr uses
+ * BSGDTV_FMT_F32_I32.  u_max, the objective and every product of the handle
+ * use the stored (rounded) weights. */
+int bsgdtv_create_csr_ex(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, int img_w,
+                         const int64_t *row_ptr, const int32_t *col_idx, const double *vals,
+                         int M, int N, int64_t row_unit, int64_t col_unit,
+                         const int64_t *row_bounds, const int64_t *col_bounds, int format,
+                         void *stream);
 
 /* Releases every resource of the handle.  NULL is ignored. */
 void bsgdtv_destroy(bsgdtv_t h);
@@ -132,7 +153,7 @@ int bsgdtv_block_products(bsgdtv_t h, const float *x, const float *r, float *z_b
 
 /* Sizes of the stored operator: nnz of A, number of row segments in the tiled
  * layout, work items per product pass, and the bytes one product pass must
- * move at minimum (8 B per nonzero + x, r, z, g once). */
+ * move at minimum (the format's bytes per nonzero + x, r, z, g once). */
 int bsgdtv_get_info(bsgdtv_t h, int64_t *nnz, int64_t *segments, int64_t *work_items,
                     int64_t *min_bytes_per_pass);
 
@@ -174,11 +195,17 @@ int bsgdtv_partition_bounds(int64_t rows, int64_t cols, int M, int N, int64_t ro
  * it gives back A (columns exact, values equal to the FP32-rounded input).
  * stats [6] (may be NULL) receives {nnz, segments, slabs, work items, row
  * groups, pixel tiles}.  Returns BSGDTV_ERR_INVALID_ARG / _NONFINITE for a bad
- * CSR and BSGDTV_ERR_STATE if the layout does not reproduce A. */
+ * CSR and BSGDTV_ERR_STATE if the layout does not reproduce A (with the
+ * weights rounded to `format`). */
 int bsgdtv_layout_check(int64_t rows, int64_t cols, int img_h, int img_w, const int64_t *row_ptr,
                         const int32_t *col_idx, const double *vals, int M, int N,
                         int64_t row_unit, int64_t col_unit, const int64_t *row_bounds,
-                        const int64_t *col_bounds, int target_items, int64_t *stats);
+                        const int64_t *col_bounds, int format, int target_items,
+                        int64_t *stats);
+
+/* Host only: the weight as a handle of the given format stores it, widened to
+ * FP32 (round to nearest even for the 16-bit formats). */
+float bsgdtv_stored_weight(double v, int format);
 
 /* Number of kernels this library has launched in the calling process
  * (graph replays count every kernel node). */

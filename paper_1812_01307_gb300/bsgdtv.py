@@ -37,6 +37,8 @@ def load(path: str | None = None):
     P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
     sig = {
         "bsgdtv_create_csr": (I32, [ctypes.POINTER(P), I64, I64, I32, I32, P, P, P, I32, I32, I64, I64, P, P, P]),
+        "bsgdtv_create_csr_ex": (I32, [ctypes.POINTER(P), I64, I64, I32, I32, P, P, P, I32, I32, I64, I64, P, P, I32, P]),
+        "bsgdtv_stored_weight": (ctypes.c_float, [D, I32]),
         "bsgdtv_destroy": (None, [P]),
         "bsgdtv_get_partition": (I32, [P, P, P]),
         "bsgdtv_set_data": (I32, [P, P, I32, D, D]),
@@ -53,7 +55,7 @@ def load(path: str | None = None):
         "bsgdtv_tv_prox": (I32, [P, P, I32, I32, D, I32, P]),
         "bsgdtv_tv_prox_static": (I32, [P, P, I32, I32, D, I32, P]),
         "bsgdtv_partition_bounds": (I32, [I64, I64, I32, I32, I64, I64, P, P]),
-        "bsgdtv_layout_check": (I32, [I64, I64, I32, I32, P, P, P, I32, I32, I64, I64, P, P, I32, P]),
+        "bsgdtv_layout_check": (I32, [I64, I64, I32, I32, P, P, P, I32, I32, I64, I64, P, P, I32, I32, P]),
         "bsgdtv_launch_count": (I64, []),
         "bsgdtv_last_error": (ctypes.c_char_p, []),
         "bsgdtv_strerror": (ctypes.c_char_p, [I32]),
@@ -68,7 +70,7 @@ def load(path: str | None = None):
 
 def exported_symbols():
     """Names the binding expects the library to export."""
-    return ["bsgdtv_create_csr", "bsgdtv_destroy", "bsgdtv_get_partition", "bsgdtv_set_data",
+    return ["bsgdtv_create_csr", "bsgdtv_create_csr_ex", "bsgdtv_stored_weight", "bsgdtv_destroy", "bsgdtv_get_partition", "bsgdtv_set_data",
             "bsgdtv_estimate_umax", "bsgdtv_get_params", "bsgdtv_run", "bsgdtv_run_timed", "bsgdtv_get_x",
             "bsgdtv_get_state", "bsgdtv_set_state", "bsgdtv_objective", "bsgdtv_block_products",
             "bsgdtv_get_info", "bsgdtv_tv_prox", "bsgdtv_tv_prox_static", "bsgdtv_partition_bounds",
@@ -124,9 +126,14 @@ def current_stream():
     return None
 
 
+FMT_F32_I32, FMT_F32_I16, FMT_F16_I16, FMT_BF16_I16 = 0, 1, 2, 3
+FORMATS = {"f32_i32": FMT_F32_I32, "f32_i16": FMT_F32_I16, "f16_i16": FMT_F16_I16,
+           "bf16_i16": FMT_BF16_I16}
+
+
 # ------------------------------------------------------------------ C names
 def bsgdtv_create_csr(rows, cols, img_h, img_w, row_ptr, col_idx, vals, M, N, row_unit=1,
-                      col_unit=1, row_bounds=None, col_bounds=None, stream=None):
+                      col_unit=1, row_bounds=None, col_bounds=None, stream=None, fmt=FMT_F32_I32):
     lib = load()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
     col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
@@ -136,14 +143,19 @@ def bsgdtv_create_csr(rows, cols, img_h, img_w, row_ptr, col_idx, vals, M, N, ro
     rb = None if row_bounds is None else np.ascontiguousarray(row_bounds, dtype=np.int64)
     cb = None if col_bounds is None else np.ascontiguousarray(col_bounds, dtype=np.int64)
     h = ctypes.c_void_p()
-    rc = lib.bsgdtv_create_csr(ctypes.byref(h), int(rows), int(cols), int(img_h), int(img_w),
-                               _host_ptr(row_ptr, np.int64), _host_ptr(col_idx, np.int32),
-                               _host_ptr(vals, np.float64), int(M), int(N), int(row_unit),
-                               int(col_unit), None if rb is None else _host_ptr(rb, np.int64),
-                               None if cb is None else _host_ptr(cb, np.int64),
-                               stream if stream is not None else current_stream())
-    _check(rc, "bsgdtv_create_csr")
+    rc = lib.bsgdtv_create_csr_ex(ctypes.byref(h), int(rows), int(cols), int(img_h), int(img_w),
+                                  _host_ptr(row_ptr, np.int64), _host_ptr(col_idx, np.int32),
+                                  _host_ptr(vals, np.float64), int(M), int(N), int(row_unit),
+                                  int(col_unit), None if rb is None else _host_ptr(rb, np.int64),
+                                  None if cb is None else _host_ptr(cb, np.int64), int(fmt),
+                                  stream if stream is not None else current_stream())
+    _check(rc, "bsgdtv_create_csr_ex")
     return h
+
+
+def bsgdtv_stored_weight(v, fmt):
+    """Host only: the weight as a handle of format `fmt` stores it (as FP32)."""
+    return float(load().bsgdtv_stored_weight(float(v), int(fmt)))
 
 
 def bsgdtv_destroy(h):
@@ -291,7 +303,8 @@ def bsgdtv_partition_bounds(rows, cols, M, N, row_unit=1, col_unit=1):
 
 
 def bsgdtv_layout_check(rows, cols, img_h, img_w, row_ptr, col_idx, vals, M, N, row_unit=1,
-                        col_unit=1, row_bounds=None, col_bounds=None, target_items=608):
+                        col_unit=1, row_bounds=None, col_bounds=None, target_items=608,
+                        fmt=FMT_F32_I32):
     """Host only: builds the device layout in host memory and checks it decodes
     back to A.  Returns the layout statistics (raises on failure)."""
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
@@ -304,7 +317,7 @@ def bsgdtv_layout_check(rows, cols, img_h, img_w, row_ptr, col_idx, vals, M, N, 
                                     _host_ptr(row_ptr, np.int64), _host_ptr(col_idx, np.int32),
                                     _host_ptr(vals, np.float64), int(M), int(N), int(row_unit),
                                     int(col_unit), None if rb is None else _host_ptr(rb, np.int64),
-                                    None if cb is None else _host_ptr(cb, np.int64),
+                                    None if cb is None else _host_ptr(cb, np.int64), int(fmt),
                                     int(target_items), _host_ptr(stats, np.int64))
     _check(rc, "bsgdtv_layout_check")
     keys = ["nnz", "segments", "slabs", "work_items", "groups", "tiles"]
@@ -326,13 +339,13 @@ class Reconstructor:
     vals, rows and cols_n attributes."""
 
     def __init__(self, A, img_shape, M, N, row_unit=1, col_unit=1, row_bounds=None,
-                 col_bounds=None, stream=None):
+                 col_bounds=None, stream=None, fmt=FMT_F32_I32):
         self.img_shape = tuple(img_shape)
         self.rows, self.cols = int(A.rows), int(A.cols_n)
         self.M, self.N = int(M), int(N)
         self.h = bsgdtv_create_csr(self.rows, self.cols, img_shape[0], img_shape[1], A.row_ptr,
                                    A.cols, A.vals, M, N, row_unit, col_unit, row_bounds,
-                                   col_bounds, stream)
+                                   col_bounds, stream, fmt)
 
     def close(self):
         if getattr(self, "h", None) is not None:

@@ -293,16 +293,19 @@ int bsgdtv_partition_bounds(int64_t rows, int64_t cols, int M, int N, int64_t ro
     return BSGDTV_OK;
 }
 
+float bsgdtv_stored_weight(double v, int format) { return stored_weight(v, format); }
+
 int bsgdtv_layout_check(int64_t rows, int64_t cols, int img_h, int img_w, const int64_t *row_ptr,
                         const int32_t *col_idx, const double *vals, int M, int N,
                         int64_t row_unit, int64_t col_unit, const int64_t *row_bounds,
-                        const int64_t *col_bounds, int target_items, int64_t *stats) {
+                        const int64_t *col_bounds, int format, int target_items,
+                        int64_t *stats) {
     std::vector<int64_t> rb, cb;
     BSG_CHECK(resolve_bounds(rows, cols, M, N, row_unit, col_unit, row_bounds, col_bounds, rb, cb));
     try {
         HostLayout L;
         BSG_CHECK(build_layout(L, rows, cols, img_h, img_w, row_ptr, col_idx, vals, M, N,
-                               rb.data(), cb.data(), target_items));
+                               rb.data(), cb.data(), target_items, format));
         BSG_CHECK(verify_layout(L, row_ptr, col_idx, vals));
         if (stats) {
             stats[0] = L.nnz;
@@ -322,6 +325,15 @@ int bsgdtv_create_csr(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, int 
                       const int64_t *row_ptr, const int32_t *col_idx, const double *vals, int M,
                       int N, int64_t row_unit, int64_t col_unit, const int64_t *row_bounds,
                       const int64_t *col_bounds, void *stream) {
+    return bsgdtv_create_csr_ex(out, rows, cols, img_h, img_w, row_ptr, col_idx, vals, M, N,
+                                row_unit, col_unit, row_bounds, col_bounds, BSGDTV_FMT_F32_I32,
+                                stream);
+}
+
+int bsgdtv_create_csr_ex(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, int img_w,
+                         const int64_t *row_ptr, const int32_t *col_idx, const double *vals, int M,
+                         int N, int64_t row_unit, int64_t col_unit, const int64_t *row_bounds,
+                         const int64_t *col_bounds, int format, void *stream) {
     if (!out) return fail(BSGDTV_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     std::vector<int64_t> rb, cb;
@@ -335,7 +347,7 @@ int bsgdtv_create_csr(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, int 
     cudaGetLastError();
     try {
         BSG_CHECK(build_layout(h->host, rows, cols, img_h, img_w, row_ptr, col_idx, vals, M, N,
-                               rb.data(), cb.data(), 4 * sms));
+                               rb.data(), cb.data(), 4 * sms, format));
     } catch (const std::bad_alloc &) {
         return fail(BSGDTV_ERR_OOM, "host allocation while building the layout");
     }
@@ -346,15 +358,33 @@ int bsgdtv_create_csr(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, int 
     bsgdtv_ctx *hp = h.get();
     DevLayout &d = h->dl;
     {
-        float *v = nullptr;
-        int32_t *ix = nullptr, *sr = nullptr, *sln = nullptr, *rsp = nullptr, *rsq = nullptr,
-                *si = nullptr, *gb = nullptr;
+        void *v = nullptr, *ix = nullptr;
+        int32_t *sr = nullptr, *sln = nullptr, *rsp = nullptr, *rsq = nullptr, *si = nullptr,
+                *gb = nullptr;
         int64_t *so = nullptr;
         WorkItem *it = nullptr;
         Tile *tl = nullptr;
+        float *v32 = nullptr;
+        int32_t *i32 = nullptr;
+        uint16_t *v16 = nullptr, *i16 = nullptr;
         int rc = BSGDTV_OK;
-        if ((rc = upload(hp, &v, L.vals)) || (rc = upload(hp, &ix, L.idx)) ||
-            (rc = upload(hp, &so, L.slab_off)) || (rc = upload(hp, &sr, L.seg_ray)) ||
+        if (format == BSGDTV_FMT_F16_I16 || format == BSGDTV_FMT_BF16_I16) {
+            rc = upload(hp, &v16, L.vals16);
+            v = v16;
+        } else {
+            rc = upload(hp, &v32, L.vals);
+            v = v32;
+        }
+        if (!rc) {
+            if (format == BSGDTV_FMT_F32_I32) {
+                rc = upload(hp, &i32, L.idx);
+                ix = i32;
+            } else {
+                rc = upload(hp, &i16, L.idx16);
+                ix = i16;
+            }
+        }
+        if (rc || (rc = upload(hp, &so, L.slab_off)) || (rc = upload(hp, &sr, L.seg_ray)) ||
             (rc = upload(hp, &sln, L.seg_len)) || (rc = upload(hp, &it, L.items)) ||
             (rc = upload(hp, &tl, L.tiles)) || (rc = upload(hp, &rsp, L.ray_seg_ptr)) ||
             (rc = upload(hp, &rsq, L.ray_seg_pos)) || (rc = upload(hp, &si, L.slab_item)) ||
@@ -364,6 +394,7 @@ int bsgdtv_create_csr(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, int 
         }
         d.vals = v;
         d.idx = ix;
+        d.fmt = format;
         d.slab_off = so;
         d.seg_ray = sr;
         d.seg_len = sln;
@@ -408,6 +439,8 @@ int bsgdtv_create_csr(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, int 
     // bulk host arrays are no longer needed
     std::vector<float>().swap(L.vals);
     std::vector<int32_t>().swap(L.idx);
+    std::vector<uint16_t>().swap(L.vals16);
+    std::vector<uint16_t>().swap(L.idx16);
     std::vector<int32_t>().swap(L.seg_ray);
     std::vector<int32_t>().swap(L.ray_seg_pos);
     *out = h.release();
@@ -441,7 +474,8 @@ int bsgdtv_get_info(bsgdtv_t h, int64_t *nnz, int64_t *segments, int64_t *work_i
     if (segments) *segments = h->seg_count;
     if (work_items) *work_items = h->dl.n_items;
     if (min_bytes_per_pass)
-        *min_bytes_per_pass = 8 * h->host.nnz + 4 * (2 * h->dl.rows + 2 * h->dl.cols);
+        *min_bytes_per_pass = (int64_t)bytes_per_entry(h->host.fmt) * h->host.nnz +
+                              4 * (2 * h->dl.rows + 2 * h->dl.cols);
     return BSGDTV_OK;
 }
 

@@ -101,8 +101,11 @@ struct HostLayout {
     std::vector<int64_t> slab_off;                  // [n_slabs+1]
     std::vector<int32_t> slab_item;                 // [n_slabs] item index (storage order)
     std::vector<int32_t> seg_ray, seg_len;          // [n_slabs*32]
-    std::vector<float> vals;                        // [nnz] slab-ordered
-    std::vector<int32_t> idx;                       // [nnz] tile-local shared-memory word
+    int fmt = 0;                                    // BSGDTV_FMT_*
+    std::vector<float> vals;                        // [stored] slab-ordered (as stored, in FP32)
+    std::vector<int32_t> idx;                       // [stored] tile-local shared-memory word
+    std::vector<uint16_t> vals16;                   // binary16 / bfloat16 bits (16-bit formats)
+    std::vector<uint16_t> idx16;                    // 16-bit indices (all but FMT_F32_I32)
     std::vector<int32_t> ray_seg_ptr;               // [rows+1]
     std::vector<int32_t> ray_seg_pos;               // [n_segments] segment slots, ascending tile
     int64_t n_groups() const { return (int64_t)group_block.size(); }
@@ -113,7 +116,12 @@ struct HostLayout {
 // BSGDTV_* code; on failure set_error has the reason.
 int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w,
                  const int64_t *row_ptr, const int32_t *col_idx, const double *vals, int M, int N,
-                 const int64_t *row_bounds, const int64_t *col_bounds, int target_items);
+                 const int64_t *row_bounds, const int64_t *col_bounds, int target_items, int fmt);
+// Stored-weight conversions (round to nearest even) and sizes.
+uint16_t double_to_half_bits(double v);
+uint16_t double_to_bf16_bits(double v);
+float stored_weight(double v, int fmt);
+int bytes_per_entry(int fmt);
 
 // Decodes the layout back into CSR and compares with the input (host check).
 int verify_layout(const HostLayout &L, const int64_t *row_ptr, const int32_t *col_idx,
@@ -125,8 +133,9 @@ int resolve_bounds(int64_t rows, int64_t cols, int M, int N, int64_t row_unit, i
 
 // ------------------------------------------------------------ device views
 struct DevLayout {
-    const float *vals = nullptr;
-    const int32_t *idx = nullptr;
+    const void *vals = nullptr;   // float, or 16-bit weight bits (see fmt)
+    const void *idx = nullptr;    // int32, or uint16 (see fmt)
+    int fmt = 0;
     const int64_t *slab_off = nullptr;
     const int32_t *seg_ray = nullptr;
     const int32_t *seg_len = nullptr;

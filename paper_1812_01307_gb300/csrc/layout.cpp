@@ -8,6 +8,7 @@
 // 3-4 of Algorithm 1 is a sum of work-item partials.
 #include <algorithm>
 #include <atomic>
+#include <cstring>
 #include <cmath>
 #include <numeric>
 #include <thread>
@@ -49,10 +50,113 @@ static void parallel_for(int64_t n, F &&f) {
     for (auto &t : th) t.join();
 }
 
+// ------------------------------------------------ stored weight formats
+// Round-to-nearest-even conversion of a double to IEEE binary16 / bfloat16
+// bits, written from the formats' definitions (sign, biased exponent,
+// truncated significand; ties to the even significand).
+static uint16_t round_bits(uint64_t mant53, int shift, uint16_t base) {
+    // base + (mant53 >> shift), rounded to nearest even on the dropped bits
+    if (shift >= 64) return base;
+    const uint64_t kept = mant53 >> shift;
+    const uint64_t rem = mant53 & ((shift ? (1ull << shift) : 1ull) - 1ull);
+    const uint64_t half = shift ? (1ull << (shift - 1)) : 0ull;
+    uint64_t r = kept;
+    if (shift && (rem > half || (rem == half && (kept & 1ull)))) ++r;
+    return (uint16_t)(base + r);
+}
+
+uint16_t double_to_half_bits(double v) {
+    uint64_t x;
+    std::memcpy(&x, &v, 8);
+    const uint16_t sign = (uint16_t)((x >> 48) & 0x8000u);
+    const int ex = (int)((x >> 52) & 0x7FF);
+    const uint64_t m = x & ((1ull << 52) - 1);
+    if (ex == 0x7FF) return (uint16_t)(sign | 0x7C00u | (m ? 0x200u : 0u));
+    if (ex == 0) return sign;   // zero or double subnormal (far below half's range)
+    const int e = ex - 1023;
+    const uint64_t full = m | (1ull << 52);
+    if (e >= -14) {             // normal half: 10 significand bits, carry may bump the exponent
+        if (e > 15) return (uint16_t)(sign | 0x7C00u);
+        const uint16_t h = round_bits(full, 42, 0) ;   // 11 bits incl. the implicit one
+        const uint32_t biased = (uint32_t)(e + 15);
+        uint32_t bits = (biased << 10) + (uint32_t)(h - 0x400u);
+        if (bits >= 0x7C00u) bits = 0x7C00u;
+        return (uint16_t)(sign | bits);
+    }
+    // subnormal half: units of 2^-24
+    return (uint16_t)(sign | round_bits(full, 28 - e, 0));
+}
+
+uint16_t double_to_bf16_bits(double v) {
+    uint64_t x;
+    std::memcpy(&x, &v, 8);
+    const uint16_t sign = (uint16_t)((x >> 48) & 0x8000u);
+    const int ex = (int)((x >> 52) & 0x7FF);
+    const uint64_t m = x & ((1ull << 52) - 1);
+    if (ex == 0x7FF) return (uint16_t)(sign | 0x7F80u | (m ? 0x40u : 0u));
+    if (ex == 0) return sign;
+    const int e = ex - 1023;
+    const uint64_t full = m | (1ull << 52);
+    if (e >= -126) {            // normal bfloat16: 7 significand bits
+        if (e > 127) return (uint16_t)(sign | 0x7F80u);
+        const uint16_t h = round_bits(full, 45, 0);     // 8 bits incl. the implicit one
+        const uint32_t biased = (uint32_t)(e + 127);
+        uint32_t bits = (biased << 7) + (uint32_t)(h - 0x80u);
+        if (bits >= 0x7F80u) bits = 0x7F80u;
+        return (uint16_t)(sign | bits);
+    }
+    return (uint16_t)(sign | round_bits(full, -e - 81, 0));   // units of 2^-133
+}
+
+float half_bits_to_float(uint16_t h) {
+    const uint32_t sign = (uint32_t)(h & 0x8000u) << 16;
+    const int ex = (h >> 10) & 0x1F;
+    const uint32_t m = h & 0x3FFu;
+    float f;
+    if (ex == 0) {
+        f = std::ldexp((float)m, -24);
+    } else if (ex == 31) {
+        f = m ? NAN : INFINITY;
+    } else {
+        f = std::ldexp((float)(m | 0x400u), ex - 25);
+    }
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    b |= sign;
+    std::memcpy(&f, &b, 4);
+    return f;
+}
+
+float bf16_bits_to_float(uint16_t h) {
+    const uint32_t b = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &b, 4);
+    return f;
+}
+
+// The weight as the device stores it, widened back to FP32 (exact).
+float stored_weight(double v, int fmt) {
+    switch (fmt) {
+        case BSGDTV_FMT_F16_I16: return half_bits_to_float(double_to_half_bits(v));
+        case BSGDTV_FMT_BF16_I16: return bf16_bits_to_float(double_to_bf16_bits(v));
+        default: return (float)v;
+    }
+}
+
+int bytes_per_entry(int fmt) {
+    switch (fmt) {
+        case BSGDTV_FMT_F32_I32: return 8;
+        case BSGDTV_FMT_F32_I16: return 6;
+        default: return 4;
+    }
+}
+
 int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w,
                  const int64_t *row_ptr, const int32_t *col_idx, const double *vals, int M, int N,
-                 const int64_t *row_bounds, const int64_t *col_bounds, int target_items) {
+                 const int64_t *row_bounds, const int64_t *col_bounds, int target_items, int fmt) {
     // ---------------------------------------------------------- validation
+    if (fmt < BSGDTV_FMT_F32_I32 || fmt > BSGDTV_FMT_BF16_I16)
+        return fail(BSGDTV_ERR_INVALID_ARG, "unknown weight format");
     if (rows < 1 || cols < 1 || img_h < 1 || img_w < 1 || (int64_t)img_h * img_w != cols)
         return fail(BSGDTV_ERR_INVALID_ARG, "bad sizes: need rows>=1 and cols == img_h*img_w");
     if (rows >= (int64_t)1 << 31 || cols >= (int64_t)1 << 31)
@@ -80,6 +184,7 @@ int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w
             return fail(BSGDTV_ERR_INVALID_ARG, "column index out of range or not ascending in a row");
         if (bad.load() == 2) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in A");
     }
+    L.fmt = fmt;
     L.img_h = img_h;
     L.img_w = img_w;
     L.rows = rows;
@@ -167,7 +272,7 @@ int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w
         std::vector<double> colsum(cols, 0.0);
         for (int64_t r = L.group_bounds[g]; r < L.group_bounds[g + 1]; ++r)
             for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e)
-                colsum[col_idx[e]] += std::fabs((double)(float)vals[e]);
+                colsum[col_idx[e]] += std::fabs((double)stored_weight(vals[e], fmt));
         double cm = 0.0;
         for (double v : colsum) cm = std::max(cm, v);
         group_colmax[g] = cm;
@@ -240,7 +345,7 @@ int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w
                     slen[t].push_back(0);
                 }
                 int64_t pos = cursor_nnz[t]++;
-                tv[pos] = (float)vals[e];
+                tv[pos] = stored_weight(vals[e], fmt);
                 ti[pos] = loc;
                 slen[t].back()++;
             }
@@ -324,6 +429,17 @@ int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w
         L.items[k] = w;
         L.item_nnz[k] = pair_nnz[p];
     }
+    // 16-bit forms: indices fit (kTileWords < 2^16); weights as binary16 / bfloat16 bits
+    if (fmt != BSGDTV_FMT_F32_I32) {
+        L.idx16.resize(L.idx.size());
+        for (size_t k = 0; k < L.idx.size(); ++k) L.idx16[k] = (uint16_t)L.idx[k];
+    }
+    if (fmt == BSGDTV_FMT_F16_I16 || fmt == BSGDTV_FMT_BF16_I16) {
+        L.vals16.resize(L.vals.size());
+        for (size_t k = 0; k < L.vals.size(); ++k)
+            L.vals16[k] = fmt == BSGDTV_FMT_F16_I16 ? double_to_half_bits(L.vals[k])
+                                                     : double_to_bf16_bits(L.vals[k]);
+    }
     return BSGDTV_OK;
 }
 
@@ -376,7 +492,7 @@ int verify_layout(const HostLayout &L, const int64_t *row_ptr, const int32_t *co
         if ((int64_t)v.size() != row_ptr[r + 1] - row_ptr[r]) return fail(BSGDTV_ERR_STATE, "row nnz mismatch");
         for (size_t k = 0; k < v.size(); ++k) {
             const int64_t e = row_ptr[r] + (int64_t)k;
-            if (v[k].first != col_idx[e] || v[k].second != (float)vals[e])
+            if (v[k].first != col_idx[e] || v[k].second != stored_weight(vals[e], L.fmt))
                 return fail(BSGDTV_ERR_STATE, "entry mismatch");
         }
         // the reduction visits exactly this row's segments, tiles ascending

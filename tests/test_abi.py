@@ -12,6 +12,8 @@ import oracle
 from paper_1812_01307_gb300 import build as build_mod
 from paper_1812_01307_gb300 import synth
 
+from _formats import bf16_round
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -121,3 +123,26 @@ def test_rejects_nonfinite_values_and_bad_bounds(B):
         B.bsgdtv_layout_check(rows, 64, 8, 9, rp, ci, v, 2, 2, 13, 8)
     with pytest.raises(B.BsgdtvError):     # more column blocks than image rows
         B.bsgdtv_partition_bounds(rows, 64, 2, 9, 13, 8)
+
+
+def test_stored_weight_rounding_matches_numpy(B):
+    rng = np.random.default_rng(0)
+    vals = np.concatenate([rng.uniform(0, 1.5, 4000), 10.0 ** rng.uniform(-12, 0.2, 4000),
+                           [0.0, 1.0, 1.4142135623730951, 6.1e-5, 5.96e-8, 3e-8, 65504.0, 70000.0,
+                            1 + 2 ** -11, 1 + 3 * 2 ** -11, 1 + 2 ** -8, 1 + 3 * 2 ** -8]])
+    f32 = np.array([B.bsgdtv_stored_weight(v, B.FMT_F32_I32) for v in vals])
+    f16 = np.array([B.bsgdtv_stored_weight(v, B.FMT_F16_I16) for v in vals])
+    b16 = np.array([B.bsgdtv_stored_weight(v, B.FMT_BF16_I16) for v in vals])
+    assert np.array_equal(f32, vals.astype(np.float32).astype(np.float64))
+    with np.errstate(over="ignore"):
+        ref16 = vals.astype(np.float16).astype(np.float64)
+    assert np.array_equal(f16, ref16)
+    assert np.array_equal(b16, bf16_round(vals))
+
+
+@pytest.mark.parametrize("fmt", [1, 2, 3])
+def test_layout_reassembles_in_every_format(B, fmt):
+    A = synth.parallel_beam_csr(37, 11, 55)
+    st = B.bsgdtv_layout_check(A.rows, A.cols_n, 37, 37, A.row_ptr, A.cols, A.vals, 3, 5, 55, 37,
+                               fmt=fmt)
+    assert st["nnz"] == A.nnz

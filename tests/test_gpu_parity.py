@@ -313,3 +313,60 @@ def test_epochs_are_deterministic(B):
             rec.run(9, 13)
             outs.append(rec.x().copy())
     assert np.array_equal(outs[0], outs[1])
+
+
+# ------------------------------------------------------------ stored formats
+from _formats import stored_operator  # noqa: E402
+
+FORMATS = {1: "f32_i16", 2: "f16_i16", 3: "bf16_i16"}
+
+
+@pytest.mark.parametrize("fmt", [1, 2, 3])
+@pytest.mark.parametrize("name", ["ellipse64", "ragged37"])
+def test_block_products_formats(B, fmt, name):
+    """Each stored format computes the block products of its own (rounded)
+    operator to FP32 accuracy."""
+    A, _, _, n, na, nb, M, N = _problem(name)
+    As = stored_operator(A, fmt)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(A.cols_n).astype(np.float32)
+    r = rng.standard_normal(A.rows).astype(np.float32)
+    with B.Reconstructor(A, (n, n), M, N, row_unit=nb, col_unit=n, fmt=fmt) as rec:
+        zb = torch.zeros(N * A.rows, device="cuda")
+        gb = torch.zeros(M * A.cols_n, device="cuda")
+        B.bsgdtv_block_products(rec.h, torch.from_numpy(x).cuda(), torch.from_numpy(r).cuda(), zb, gb)
+        zb = zb.cpu().numpy().reshape(N, A.rows)
+        gb = gb.cpu().numpy().reshape(M, A.cols_n)
+    rb, cb = oracle.partition(A.rows, A.cols_n, M, N, nb, n)
+    z, gh = oracle.block_products(oracle.split_blocks(As, rb, cb), rb, cb, x.astype(np.float64),
+                                  r.astype(np.float64))
+    for i in range(M):
+        for j in range(N):
+            assert rel(zb[j, rb[i]:rb[i + 1]], z[i][j]) <= 1e-5
+            assert rel(gb[i, cb[j]:cb[j + 1]], gh[i][j]) <= 1e-5
+
+
+@pytest.mark.parametrize("fmt,bound", [(1, 1e-4), (2, 2e-3), (3, 2e-2)])
+def test_full_reconstruction_formats(B, fmt, bound):
+    """64x64 workload end to end per format: x matches the oracle run on the
+    rounded operator to 1e-4; its distance to the oracle on the FP64 operator
+    is the quantisation error (FP16 weights: <= 2e-3)."""
+    wl = synth.WORKLOADS["ellipse64"]
+    A, _, y, n, na, nb, M, N = _problem("ellipse64")
+    As = stored_operator(A, fmt)
+    u_ref, _ = oracle.power_iteration(A)
+    mu = 0.9 / (2 * u_ref)
+    y32 = y.astype(np.float32).astype(np.float64)
+    with B.Reconstructor(A, (n, n), M, N, row_unit=nb, col_unit=n, fmt=fmt) as rec:
+        u, _ = rec.estimate_umax(5000, 1e-12)
+        rec.set_data(y32.astype(np.float32), wl.lam, mu)
+        rec.run(wl.epochs, wl.fgp_iters)
+        x_gpu = rec.x().astype(np.float64)
+    u_s, _ = oracle.power_iteration(As, 5000, 1e-12)
+    assert abs(u - u_s) <= 1e-9 * u_s
+    x_s, _ = oracle.run(As, y32, (n, n), M, N, wl.lam, mu, wl.epochs, wl.fgp_iters, row_unit=nb, col_unit=n)
+    x_64, _ = oracle.run(A, y32, (n, n), M, N, wl.lam, mu, wl.epochs, wl.fgp_iters, row_unit=nb, col_unit=n)
+    assert rel(x_gpu, x_s) <= 1e-4
+    err = rel(x_gpu, x_64)
+    print(f"format {FORMATS[fmt]}: x rel err vs FP64 operator {err:.3e}")
+    assert err <= bound
