@@ -160,6 +160,13 @@ struct DevLayout {
 // products.cu: one pass over A.  z_part[slot] = sum over the segment of a*x,
 // g_part[group*cols + pixel] = sum over the group's rows of 2*a*r.
 cudaError_t prepare_products_kernels();   // sets shared-memory limits (call before capture)
+// 16-bit formats (products_fmt.cu), dispatched by launch_products32/64.
+cudaError_t launch_products32_fmt(const DevLayout &d, const float *x, const float *r,
+                                  const float *rmax_in, float *rmax_clear, float *z_part,
+                                  int32_t *g_part, cudaStream_t s, bool pdl);
+cudaError_t launch_products64_fmt(const DevLayout &d, const double *x, const double *r,
+                                  double *z_part, double *g_part, cudaStream_t s);
+cudaError_t prepare_products_fmt_kernels();
 // FP64 variant (u_max and objective): g tile accumulated with FP64 atomics.
 cudaError_t launch_products64(const DevLayout &d, const double *x, const double *r, double *z_part,
                               double *g_part, cudaStream_t s);

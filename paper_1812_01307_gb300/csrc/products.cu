@@ -9,113 +9,35 @@
 // Eq. 3).  x_T is staged in shared memory and the g tile accumulates there.
 //
 // GPU mapping: persistent CTAs (two per SM) take work items from a global
-// counter, largest items first (the counter resets itself at kernel exit).  Inside an item each warp takes slabs of 32
-// row segments from a shared counter, one lane per segment, so a segment's z
+// counter, largest items first (the counter resets itself at kernel exit).
+// Inside an item each warp takes slabs of 32 row segments from a shared
+// counter, one lane per segment, so a segment's z
 // partial stays in a register.  A slab is read in 16-byte column groups (four
 // consecutive nonzeros of each lane's segment per load, coalesced across the
 // warp) with the loads of the next groups in flight while the current one is
 // used (two groups of 32 B per lane for FP32 weights + 32-bit indices, four of
 // 16 B for 16-bit weights and indices), so each warp keeps ~2 KB of A in
 // flight.
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "bsgdtv_internal.h"
+#include "products_common.cuh"
 
 namespace bsgdtv {
 
 namespace {
 
-constexpr int kThreads = 512;
-constexpr int kWarps = kThreads / 32;
-constexpr int kCtasPerSm = 2;
+using namespace prod;
 
-// Stored formats of one column group (four entries of one lane's segment).
-template <int FMT> struct GroupFmt;
-// kDepth: column groups loaded ahead (about 2 KB of A in flight per warp).
-template <> struct GroupFmt<BSGDTV_FMT_F32_I32> {
-    static constexpr int kDepth = 2;
-    using VT = float4;
-    using IT = int4;
-    static __device__ __forceinline__ void decode(const VT &v, const IT &i, float4 &w, int4 &k) {
-        w = v;
-        k = i;
-    }
-};
-template <> struct GroupFmt<BSGDTV_FMT_F32_I16> {
-    static constexpr int kDepth = 3;
-    using VT = float4;
-    using IT = uint2;   // four 16-bit indices
-    static __device__ __forceinline__ void decode(const VT &v, const IT &i, float4 &w, int4 &k) {
-        w = v;
-        k = make_int4((int)(i.x & 0xFFFFu), (int)(i.x >> 16), (int)(i.y & 0xFFFFu), (int)(i.y >> 16));
-    }
-};
-template <> struct GroupFmt<BSGDTV_FMT_F16_I16> {
-    static constexpr int kDepth = 4;
-    using VT = uint2;   // four binary16 weights
-    using IT = uint2;
-    static __device__ __forceinline__ void decode(const VT &v, const IT &i, float4 &w, int4 &k) {
-        w = make_float4(__half2float(__ushort_as_half((unsigned short)(v.x & 0xFFFFu))),
-                        __half2float(__ushort_as_half((unsigned short)(v.x >> 16))),
-                        __half2float(__ushort_as_half((unsigned short)(v.y & 0xFFFFu))),
-                        __half2float(__ushort_as_half((unsigned short)(v.y >> 16))));
-        k = make_int4((int)(i.x & 0xFFFFu), (int)(i.x >> 16), (int)(i.y & 0xFFFFu), (int)(i.y >> 16));
-    }
-};
-template <> struct GroupFmt<BSGDTV_FMT_BF16_I16> {
-    static constexpr int kDepth = 4;
-    using VT = uint2;   // four bfloat16 weights: the upper halves of FP32 values
-    using IT = uint2;
-    static __device__ __forceinline__ void decode(const VT &v, const IT &i, float4 &w, int4 &k) {
-        w = make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xFFFF0000u),
-                        __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xFFFF0000u));
-        k = make_int4((int)(i.x & 0xFFFFu), (int)(i.x >> 16), (int)(i.y & 0xFFFFu), (int)(i.y >> 16));
-    }
-};
-
-template <typename X>
-__device__ __forceinline__ X zero_of();
-template <> __device__ __forceinline__ float4 zero_of<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-template <> __device__ __forceinline__ int4 zero_of<int4>() { return make_int4(0, 0, 0, 0); }
-template <> __device__ __forceinline__ uint2 zero_of<uint2>() { return make_uint2(0u, 0u); }
-
-// Accumulation of one column group (four nonzeros of this lane's segment):
-// z partial in a register, the A^T r contribution into the shared g tile.
-// FP32 path: the tile is int32 fixed point (r2 already carries the scale), so
-// the shared-memory updates are native integer atomics and the tile's sums
-// are exact and independent of their order.  FP64 path: FP64 atomics.
-__device__ __forceinline__ void use_group(const float4 v, const int4 i, const float r2s,
-                                          const float *xs, int *gs, float &acc) {
-    acc = fmaf(v.x, xs[i.x], acc);
-    atomicAdd(gs + i.x, __float2int_rn(v.x * r2s));
-    acc = fmaf(v.y, xs[i.y], acc);
-    atomicAdd(gs + i.y, __float2int_rn(v.y * r2s));
-    acc = fmaf(v.z, xs[i.z], acc);
-    atomicAdd(gs + i.z, __float2int_rn(v.z * r2s));
-    acc = fmaf(v.w, xs[i.w], acc);
-    atomicAdd(gs + i.w, __float2int_rn(v.w * r2s));
-}
-
-__device__ __forceinline__ void use_group(const float4 v, const int4 i, const double r2,
-                                          const double *xs, double *gs, double &acc) {
-    acc += (double)v.x * xs[i.x];
-    atomicAdd(gs + i.x, (double)v.x * r2);
-    acc += (double)v.y * xs[i.y];
-    atomicAdd(gs + i.y, (double)v.y * r2);
-    acc += (double)v.z * xs[i.z];
-    atomicAdd(gs + i.z, (double)v.z * r2);
-    acc += (double)v.w * xs[i.w];
-    atomicAdd(gs + i.w, (double)v.w * r2);
-}
-
-// T: type of x, r, z (float or double); G: shared g tile (int fixed point or
-// double); FMT: stored weight / index format.
-template <typename T, typename G, int FMT>
+// FP32 weights with 32-bit indices.  T: type of x, r, z (float or double); G:
+// shared g tile (int fixed point or double).  The 16-bit formats have their
+// own kernel in products_fmt.cu: sharing this translation unit with it made
+// this kernel about 10 % slower on GB300.
+template <typename T, typename G>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
-    products_kernel(const DevLayout d, const T *__restrict__ x, const T *__restrict__ r,
+    products_f32_kernel(const DevLayout d, const T *__restrict__ x, const T *__restrict__ r,
                     const float *__restrict__ rmax_in, float *__restrict__ rmax_clear,
                     T *__restrict__ z_part, G *__restrict__ g_part, int *__restrict__ item_ctr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -125,10 +47,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    using VT = typename GroupFmt<FMT>::VT;
-    using IT = typename GroupFmt<FMT>::IT;
-    const VT *__restrict__ V4 = reinterpret_cast<const VT *>(d.vals);
-    const IT *__restrict__ I4 = reinterpret_cast<const IT *>(d.idx);
+    const float4 *__restrict__ V4 = reinterpret_cast<const float4 *>(d.vals);
+    const int4 *__restrict__ I4 = reinterpret_cast<const int4 *>(d.idx);
     pdl_wait_and_release();
     // 2 r scaled to fixed point (FP32 path) or plain 2 r (FP64 path)
     const T scale = rmax_in ? (T)fixed_scale(*rmax_in, d.colsum_max) : T(1);
@@ -161,44 +81,37 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             const int ng = (len + kGroup - 1) / kGroup;
             const T r2 = (len > 0) ? T(2) * r[ray] * scale : T(0);
             const int64_t base = d.slab_off[sl] / kGroup;
-            const VT *V = V4 + base;
-            const IT *I = I4 + base;
+            const float4 *V = V4 + base;
+            const int4 *I = I4 + base;
             const int maxg = __reduce_max_sync(0xffffffffu, ng);
-            // kDepth column groups in flight ahead of the one in use
-            constexpr int kDepth = GroupFmt<FMT>::kDepth;
             int off = 0;
-            VT vq[kDepth];
-            IT iq[kDepth];
-#pragma unroll
-            for (int t = 0; t < kDepth; ++t) {
-                vq[t] = zero_of<VT>();
-                iq[t] = zero_of<IT>();
-                const unsigned a = __ballot_sync(0xffffffffu, ng > t);
+            float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
+            int4 ia = make_int4(0, 0, 0, 0), ib = ia;
+            {
+                const unsigned a = __ballot_sync(0xffffffffu, ng > 0);
                 const int p = off + __popc(a & lt);
                 off += __popc(a);
-                if (ng > t) { vq[t] = __ldcs(V + p); iq[t] = __ldcs(I + p); }
+                if (ng > 0) { va = __ldcs(V + p); ia = __ldcs(I + p); }
+            }
+            {
+                const unsigned a = __ballot_sync(0xffffffffu, ng > 1);
+                const int p = off + __popc(a & lt);
+                off += __popc(a);
+                if (ng > 1) { vb = __ldcs(V + p); ib = __ldcs(I + p); }
             }
             T acc = T(0);
             for (int kk = 0; kk < maxg; ++kk) {
-                VT vn = zero_of<VT>();
-                IT in_ = zero_of<IT>();
-                const unsigned a = __ballot_sync(0xffffffffu, ng > kk + kDepth);
+                float4 vc = make_float4(0.f, 0.f, 0.f, 0.f);
+                int4 ic = make_int4(0, 0, 0, 0);
+                const unsigned a = __ballot_sync(0xffffffffu, ng > kk + 2);
                 const int p = off + __popc(a & lt);
                 off += __popc(a);
-                if (ng > kk + kDepth) { vn = __ldcs(V + p); in_ = __ldcs(I + p); }
-                if (ng > kk) {
-                    float4 w;
-                    int4 k4;
-                    GroupFmt<FMT>::decode(vq[0], iq[0], w, k4);
-                    use_group(w, k4, r2, xs, gs, acc);
-                }
-#pragma unroll
-                for (int t = 0; t + 1 < kDepth; ++t) {
-                    vq[t] = vq[t + 1];
-                    iq[t] = iq[t + 1];
-                }
-                vq[kDepth - 1] = vn;
-                iq[kDepth - 1] = in_;
+                if (ng > kk + 2) { vc = __ldcs(V + p); ic = __ldcs(I + p); }
+                if (ng > kk) use_group(va, ia, r2, xs, gs, acc);
+                va = vb;
+                ia = ib;
+                vb = vc;
+                ib = ic;
             }
             z_part[seg] = acc;
             int nx = 0;
@@ -229,22 +142,20 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 
 }  // namespace
 
-template <int FMT>
-static cudaError_t launch_p32(const DevLayout &d, const float *x, const float *r, const float *rmax_in,
-                              float *rmax_clear, float *z_part, int32_t *g_part, cudaStream_t s,
-                              bool pdl) {
+static cudaError_t launch_p32_plain(const DevLayout &d, const float *x, const float *r,
+                                    const float *rmax_in, float *rmax_clear, float *z_part,
+                                    int32_t *g_part, cudaStream_t s, bool pdl) {
     const size_t smem = kTileWords * (sizeof(float) + sizeof(int));
     const int grid = std::min(d.n_items, kCtasPerSm * std::max(d.n_sms, 1));
-    return launch_kernel(products_kernel<float, int, FMT>, dim3(grid), dim3(kThreads), smem, s, pdl,
+    return launch_kernel(products_f32_kernel<float, int>, dim3(grid), dim3(kThreads), smem, s, pdl,
                          d, x, r, rmax_in, rmax_clear, z_part, g_part, d.item_ctr);
 }
 
-template <int FMT>
-static cudaError_t launch_p64(const DevLayout &d, const double *x, const double *r, double *z_part,
-                              double *g_part, cudaStream_t s) {
+static cudaError_t launch_p64_plain(const DevLayout &d, const double *x, const double *r,
+                                    double *z_part, double *g_part, cudaStream_t s) {
     const size_t smem = 2u * kTileWords * sizeof(double);
     const int grid = std::min(d.n_items, kCtasPerSm * std::max(d.n_sms, 1));
-    return launch_kernel(products_kernel<double, double, FMT>, dim3(grid), dim3(kThreads), smem, s,
+    return launch_kernel(products_f32_kernel<double, double>, dim3(grid), dim3(kThreads), smem, s,
                          false, d, x, r, (const float *)nullptr, (float *)nullptr, z_part, g_part,
                          d.item_ctr);
 }
@@ -253,13 +164,10 @@ cudaError_t launch_products32(const DevLayout &d, const float *x, const float *r
                               const float *rmax_in, float *rmax_clear, float *z_part,
                               int32_t *g_part, cudaStream_t s, bool pdl) {
     if (d.n_items == 0) return cudaSuccess;
-    cudaError_t e;
-    switch (d.fmt) {
-        case BSGDTV_FMT_F32_I16: e = launch_p32<BSGDTV_FMT_F32_I16>(d, x, r, rmax_in, rmax_clear, z_part, g_part, s, pdl); break;
-        case BSGDTV_FMT_F16_I16: e = launch_p32<BSGDTV_FMT_F16_I16>(d, x, r, rmax_in, rmax_clear, z_part, g_part, s, pdl); break;
-        case BSGDTV_FMT_BF16_I16: e = launch_p32<BSGDTV_FMT_BF16_I16>(d, x, r, rmax_in, rmax_clear, z_part, g_part, s, pdl); break;
-        default: e = launch_p32<BSGDTV_FMT_F32_I32>(d, x, r, rmax_in, rmax_clear, z_part, g_part, s, pdl); break;
-    }
+    const cudaError_t e =
+        d.fmt == BSGDTV_FMT_F32_I32
+            ? launch_p32_plain(d, x, r, rmax_in, rmax_clear, z_part, g_part, s, pdl)
+            : launch_products32_fmt(d, x, r, rmax_in, rmax_clear, z_part, g_part, s, pdl);
     add_launches(1);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -267,33 +175,22 @@ cudaError_t launch_products32(const DevLayout &d, const float *x, const float *r
 cudaError_t launch_products64(const DevLayout &d, const double *x, const double *r, double *z_part,
                               double *g_part, cudaStream_t s) {
     if (d.n_items == 0) return cudaSuccess;
-    cudaError_t e;
-    switch (d.fmt) {
-        case BSGDTV_FMT_F32_I16: e = launch_p64<BSGDTV_FMT_F32_I16>(d, x, r, z_part, g_part, s); break;
-        case BSGDTV_FMT_F16_I16: e = launch_p64<BSGDTV_FMT_F16_I16>(d, x, r, z_part, g_part, s); break;
-        case BSGDTV_FMT_BF16_I16: e = launch_p64<BSGDTV_FMT_BF16_I16>(d, x, r, z_part, g_part, s); break;
-        default: e = launch_p64<BSGDTV_FMT_F32_I32>(d, x, r, z_part, g_part, s); break;
-    }
+    const cudaError_t e = d.fmt == BSGDTV_FMT_F32_I32
+                              ? launch_p64_plain(d, x, r, z_part, g_part, s)
+                              : launch_products64_fmt(d, x, r, z_part, g_part, s);
     add_launches(1);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-template <int FMT>
-static cudaError_t prepare_fmt() {
-    cudaError_t e = cudaFuncSetAttribute(products_kernel<float, int, FMT>,
+cudaError_t prepare_products_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(products_f32_kernel<float, int>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kTileWords * (sizeof(float) + sizeof(int))));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(products_kernel<double, double, FMT>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(2u * kTileWords * sizeof(double)));
-}
-
-cudaError_t prepare_products_kernels() {
-    cudaError_t e = prepare_fmt<BSGDTV_FMT_F32_I32>();
-    if (e == cudaSuccess) e = prepare_fmt<BSGDTV_FMT_F32_I16>();
-    if (e == cudaSuccess) e = prepare_fmt<BSGDTV_FMT_F16_I16>();
-    if (e == cudaSuccess) e = prepare_fmt<BSGDTV_FMT_BF16_I16>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(products_f32_kernel<double, double>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(2u * kTileWords * sizeof(double)));
+    if (e == cudaSuccess) e = prepare_products_fmt_kernels();
     return e;
 }
 

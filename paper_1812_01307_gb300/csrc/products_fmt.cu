@@ -1,0 +1,240 @@
+// Fused block products of Algorithm 1 for A stored with 16-bit tile-local
+// indices and FP32, binary16 or bfloat16 weights (see products.cu for the
+// work decomposition; this kernel differs only in how a column group of four
+// entries is loaded and decoded, and in a deeper prefetch).
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "bsgdtv_internal.h"
+#include "products_common.cuh"
+
+namespace bsgdtv {
+
+namespace {
+
+using namespace prod;
+
+// Stored formats of one column group (four entries of one lane's segment).
+template <int FMT> struct GroupFmt;
+// kDepth: column groups loaded ahead (about 2 KB of A in flight per warp).
+template <> struct GroupFmt<BSGDTV_FMT_F32_I16> {
+    static constexpr int kDepth = 3;
+    using VT = float4;
+    using IT = uint2;   // four 16-bit indices
+    static __device__ __forceinline__ void decode(const VT &v, const IT &i, float4 &w, int4 &k) {
+        w = v;
+        k = make_int4((int)(i.x & 0xFFFFu), (int)(i.x >> 16), (int)(i.y & 0xFFFFu), (int)(i.y >> 16));
+    }
+};
+template <> struct GroupFmt<BSGDTV_FMT_F16_I16> {
+    static constexpr int kDepth = 4;
+    using VT = uint2;   // four binary16 weights
+    using IT = uint2;
+    static __device__ __forceinline__ void decode(const VT &v, const IT &i, float4 &w, int4 &k) {
+        w = make_float4(__half2float(__ushort_as_half((unsigned short)(v.x & 0xFFFFu))),
+                        __half2float(__ushort_as_half((unsigned short)(v.x >> 16))),
+                        __half2float(__ushort_as_half((unsigned short)(v.y & 0xFFFFu))),
+                        __half2float(__ushort_as_half((unsigned short)(v.y >> 16))));
+        k = make_int4((int)(i.x & 0xFFFFu), (int)(i.x >> 16), (int)(i.y & 0xFFFFu), (int)(i.y >> 16));
+    }
+};
+template <> struct GroupFmt<BSGDTV_FMT_BF16_I16> {
+    static constexpr int kDepth = 4;
+    using VT = uint2;   // four bfloat16 weights: the upper halves of FP32 values
+    using IT = uint2;
+    static __device__ __forceinline__ void decode(const VT &v, const IT &i, float4 &w, int4 &k) {
+        w = make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xFFFF0000u),
+                        __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xFFFF0000u));
+        k = make_int4((int)(i.x & 0xFFFFu), (int)(i.x >> 16), (int)(i.y & 0xFFFFu), (int)(i.y >> 16));
+    }
+};
+
+template <typename X>
+__device__ __forceinline__ X zero_of();
+template <> __device__ __forceinline__ float4 zero_of<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ uint2 zero_of<uint2>() { return make_uint2(0u, 0u); }
+
+// T: type of x, r, z (float or double); G: shared g tile (int fixed point or
+// double); FMT: stored weight / index format.
+template <typename T, typename G, int FMT>
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
+    products_kernel(const DevLayout d, const T *__restrict__ x, const T *__restrict__ r,
+                    const float *__restrict__ rmax_in, float *__restrict__ rmax_clear,
+                    T *__restrict__ z_part, G *__restrict__ g_part, int *__restrict__ item_ctr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    G *gs = reinterpret_cast<G *>(xs + kTileWords);
+    __shared__ int s_item, s_next;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    using VT = typename GroupFmt<FMT>::VT;
+    using IT = typename GroupFmt<FMT>::IT;
+    const VT *__restrict__ V4 = reinterpret_cast<const VT *>(d.vals);
+    const IT *__restrict__ I4 = reinterpret_cast<const IT *>(d.idx);
+    pdl_wait_and_release();
+    // 2 r scaled to fixed point (FP32 path) or plain 2 r (FP64 path)
+    const T scale = rmax_in ? (T)fixed_scale(*rmax_in, d.colsum_max) : T(1);
+    if (rmax_clear && blockIdx.x == 0 && threadIdx.x == 0) *rmax_clear = 0.f;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(item_ctr, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= d.n_items) break;
+        const WorkItem it = d.items[item];
+        const Tile tl = d.tiles[it.tile];
+
+        for (int e = threadIdx.x; e < kTileWords; e += kThreads) {
+            const int lr = e / kTileStride, lc = e - lr * kTileStride;
+            T v = T(0);
+            if (e < kPadBase && lr < tl.h && lc < tl.w)
+                v = x[(int64_t)(tl.r0 + lr) * d.img_w + tl.c0 + lc];
+            xs[e] = v;
+            gs[e] = G(0);
+        }
+        if (threadIdx.x == 0) s_next = it.slab_begin + kWarps;
+        __syncthreads();
+
+        int sl = it.slab_begin + warp;
+        while (sl < it.slab_end) {
+            const int64_t seg = (int64_t)sl * kSlab + lane;
+            const int len = d.seg_len[seg];
+            const int ray = d.seg_ray[seg];
+            const int ng = (len + kGroup - 1) / kGroup;
+            const T r2 = (len > 0) ? T(2) * r[ray] * scale : T(0);
+            const int64_t base = d.slab_off[sl] / kGroup;
+            const VT *V = V4 + base;
+            const IT *I = I4 + base;
+            const int maxg = __reduce_max_sync(0xffffffffu, ng);
+            // kDepth column groups in flight ahead of the one in use
+            constexpr int kDepth = GroupFmt<FMT>::kDepth;
+            int off = 0;
+            T acc = T(0);
+            {
+                VT vq[kDepth];
+                IT iq[kDepth];
+#pragma unroll
+                for (int t = 0; t < kDepth; ++t) {
+                    vq[t] = zero_of<VT>();
+                    iq[t] = zero_of<IT>();
+                    const unsigned a = __ballot_sync(0xffffffffu, ng > t);
+                    const int p = off + __popc(a & lt);
+                    off += __popc(a);
+                    if (ng > t) { vq[t] = __ldcs(V + p); iq[t] = __ldcs(I + p); }
+                }
+                for (int kk = 0; kk < maxg; ++kk) {
+                    VT vn = zero_of<VT>();
+                    IT in_ = zero_of<IT>();
+                    const unsigned a = __ballot_sync(0xffffffffu, ng > kk + kDepth);
+                    const int p = off + __popc(a & lt);
+                    off += __popc(a);
+                    if (ng > kk + kDepth) { vn = __ldcs(V + p); in_ = __ldcs(I + p); }
+                    if (ng > kk) {
+                        float4 w;
+                        int4 k4;
+                        GroupFmt<FMT>::decode(vq[0], iq[0], w, k4);
+                        use_group(w, k4, r2, xs, gs, acc);
+                    }
+#pragma unroll
+                    for (int t = 0; t + 1 < kDepth; ++t) {
+                        vq[t] = vq[t + 1];
+                        iq[t] = iq[t + 1];
+                    }
+                    vq[kDepth - 1] = vn;
+                    iq[kDepth - 1] = in_;
+                }
+            }
+            z_part[seg] = acc;
+            int nx = 0;
+            if (lane == 0) nx = atomicAdd(&s_next, 1);
+            sl = __shfl_sync(0xffffffffu, nx, 0);
+        }
+        __syncthreads();
+
+        G *gp = g_part + (int64_t)it.group * d.cols;
+        const int npx = tl.h * tl.w;
+        for (int e = threadIdx.x; e < npx; e += kThreads) {
+            const int lr = e / tl.w, lc = e - lr * tl.w;
+            gp[(int64_t)(tl.r0 + lr) * d.img_w + tl.c0 + lc] = gs[lr * kTileStride + lc];
+        }
+        __syncthreads();
+    }
+    // The last CTA out resets both counters for the next launch: every CTA
+    // has made its final claim on item_ctr[0] before it counts itself out.
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(item_ctr + 1, 1) == (int)gridDim.x - 1) {
+            item_ctr[0] = 0;
+            item_ctr[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+template <int FMT>
+cudaError_t launch_p32(const DevLayout &d, const float *x, const float *r, const float *rmax_in,
+                       float *rmax_clear, float *z_part, int32_t *g_part, cudaStream_t s, bool pdl) {
+    const size_t smem = kTileWords * (sizeof(float) + sizeof(int));
+    const int grid = std::min(d.n_items, kCtasPerSm * std::max(d.n_sms, 1));
+    return launch_kernel(products_kernel<float, int, FMT>, dim3(grid), dim3(kThreads), smem, s, pdl,
+                         d, x, r, rmax_in, rmax_clear, z_part, g_part, d.item_ctr);
+}
+
+template <int FMT>
+cudaError_t launch_p64(const DevLayout &d, const double *x, const double *r, double *z_part,
+                       double *g_part, cudaStream_t s) {
+    const size_t smem = 2u * kTileWords * sizeof(double);
+    const int grid = std::min(d.n_items, kCtasPerSm * std::max(d.n_sms, 1));
+    return launch_kernel(products_kernel<double, double, FMT>, dim3(grid), dim3(kThreads), smem, s,
+                         false, d, x, r, (const float *)nullptr, (float *)nullptr, z_part, g_part,
+                         d.item_ctr);
+}
+
+template <int FMT>
+cudaError_t prepare_fmt() {
+    cudaError_t e = cudaFuncSetAttribute(products_kernel<float, int, FMT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kTileWords * (sizeof(float) + sizeof(int))));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(products_kernel<double, double, FMT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2u * kTileWords * sizeof(double)));
+}
+
+}  // namespace
+
+cudaError_t launch_products32_fmt(const DevLayout &d, const float *x, const float *r,
+                                  const float *rmax_in, float *rmax_clear, float *z_part,
+                                  int32_t *g_part, cudaStream_t s, bool pdl) {
+    switch (d.fmt) {
+        case BSGDTV_FMT_F32_I16:
+            return launch_p32<BSGDTV_FMT_F32_I16>(d, x, r, rmax_in, rmax_clear, z_part, g_part, s, pdl);
+        case BSGDTV_FMT_F16_I16:
+            return launch_p32<BSGDTV_FMT_F16_I16>(d, x, r, rmax_in, rmax_clear, z_part, g_part, s, pdl);
+        case BSGDTV_FMT_BF16_I16:
+            return launch_p32<BSGDTV_FMT_BF16_I16>(d, x, r, rmax_in, rmax_clear, z_part, g_part, s, pdl);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_products64_fmt(const DevLayout &d, const double *x, const double *r,
+                                  double *z_part, double *g_part, cudaStream_t s) {
+    switch (d.fmt) {
+        case BSGDTV_FMT_F32_I16: return launch_p64<BSGDTV_FMT_F32_I16>(d, x, r, z_part, g_part, s);
+        case BSGDTV_FMT_F16_I16: return launch_p64<BSGDTV_FMT_F16_I16>(d, x, r, z_part, g_part, s);
+        case BSGDTV_FMT_BF16_I16: return launch_p64<BSGDTV_FMT_BF16_I16>(d, x, r, z_part, g_part, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t prepare_products_fmt_kernels() {
+    cudaError_t e = prepare_fmt<BSGDTV_FMT_F32_I16>();
+    if (e == cudaSuccess) e = prepare_fmt<BSGDTV_FMT_F16_I16>();
+    if (e == cudaSuccess) e = prepare_fmt<BSGDTV_FMT_BF16_I16>();
+    return e;
+}
+
+}  // namespace bsgdtv
