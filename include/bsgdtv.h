@@ -217,6 +217,58 @@ const char *bsgdtv_last_error(void);
 /* Static description of an error code. */
 const char *bsgdtv_strerror(int code);
 
+/* ------------------------------------------------------------ batched slices
+ * B independent reconstructions (e.g. the slices of a parallel-beam volume)
+ * that share one matrix A: slice b has projections y_b, TV weight lambda_b,
+ * iterate x_b and residual r_b, and every slice uses the same step mu.  Each
+ * slice follows Algorithm 1 exactly as a single-slice handle does (x^0 = 0,
+ * r^{-1} = y_b, stale residual in the gradient, FGP prox with
+ * tau_b = mu*lambda_b); the block partition of Sec. 2.1 changes only how the
+ * work is divided, not the iterates, so a batch has no M, N.  Both products of
+ * an epoch come from one pass over A each (in CSR for A x, in CSC for A^T r)
+ * that applies every nonzero to all B slices, with FP32 accumulation in a
+ * fixed order (deterministic).  Device memory: A twice (12 bytes per nonzero
+ * each) plus about 4 (rows + cols) Bp + 7 cols B floats, Bp = B rounded up to
+ * 32, 64 or a multiple of 128. */
+typedef struct bsgdtv_batch_ctx *bsgdtv_batch_t;
+
+/* Creates a batch of `slices` (1 .. 4096) slices from a host CSR matrix A; the
+ * arguments rows .. vals and `stream` mean what they mean for
+ * bsgdtv_create_csr (A stored as FP32 weights, 32-bit indices).  Fails with
+ * BSGDTV_ERR_INVALID_ARG / BSGDTV_ERR_NONFINITE on a malformed CSR. */
+int bsgdtv_batch_create_csr(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int img_h, int img_w,
+                            const int64_t *row_ptr, const int32_t *col_idx, const double *vals,
+                            int slices, void *stream);
+
+/* Releases every resource of the batch.  NULL is ignored. */
+void bsgdtv_batch_destroy(bsgdtv_batch_t h);
+
+/* Sets every slice's projections y [slices][rows] (slice-major FP32), the
+ * weights lambdas [slices] (host, each finite and >= 0) and the step mu > 0
+ * (finite; Theorem 1 asks mu < 1/(2 u_max), with u_max from
+ * bsgdtv_estimate_umax of a single-slice handle on the same A).  Resets every
+ * slice: x^0 = 0, r^{-1} = y_b.  Rejects NaN/Inf in y (BSGDTV_ERR_NONFINITE).
+ * Synchronises the stream. */
+int bsgdtv_batch_set_data(bsgdtv_batch_t h, const float *y, int y_on_device,
+                          const double *lambdas, double mu);
+
+/* Runs `epochs` epochs of Algorithm 1 on every slice, with `fgp_iters` FGP
+ * iterations for each prox (a slice with lambda_b = 0, or fgp_iters = 0, has
+ * the identity prox).  Asynchronous on the batch's stream; resumes from the
+ * current state.  BSGDTV_ERR_STATE before set_data. */
+int bsgdtv_batch_run(bsgdtv_batch_t h, int epochs, int fgp_iters);
+
+/* bsgdtv_batch_run that also times, with CUDA events recorded on the stream
+ * inside the epoch graphs, the two product passes of every epoch and every
+ * whole epoch.  Synchronises.  products_ms / epoch_ms (may be NULL) receive
+ * the sums over the `epochs` epochs. */
+int bsgdtv_batch_run_timed(bsgdtv_batch_t h, int epochs, int fgp_iters, double *products_ms,
+                           double *epoch_ms);
+
+/* Copies every slice's x into x [slices][cols] (slice-major FP32).  To the
+ * host: synchronises the stream. */
+int bsgdtv_batch_get_x(bsgdtv_batch_t h, float *x, int out_on_device);
+
 #ifdef __cplusplus
 }
 #endif

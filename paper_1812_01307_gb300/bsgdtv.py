@@ -56,6 +56,12 @@ def load(path: str | None = None):
         "bsgdtv_tv_prox_static": (I32, [P, P, I32, I32, D, I32, P]),
         "bsgdtv_partition_bounds": (I32, [I64, I64, I32, I32, I64, I64, P, P]),
         "bsgdtv_layout_check": (I32, [I64, I64, I32, I32, P, P, P, I32, I32, I64, I64, P, P, I32, I32, P]),
+        "bsgdtv_batch_create_csr": (I32, [ctypes.POINTER(P), I64, I64, I32, I32, P, P, P, I32, P]),
+        "bsgdtv_batch_destroy": (None, [P]),
+        "bsgdtv_batch_set_data": (I32, [P, P, I32, P, D]),
+        "bsgdtv_batch_run": (I32, [P, I32, I32]),
+        "bsgdtv_batch_run_timed": (I32, [P, I32, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "bsgdtv_batch_get_x": (I32, [P, P, I32]),
         "bsgdtv_launch_count": (I64, []),
         "bsgdtv_last_error": (ctypes.c_char_p, []),
         "bsgdtv_strerror": (ctypes.c_char_p, [I32]),
@@ -74,7 +80,9 @@ def exported_symbols():
             "bsgdtv_estimate_umax", "bsgdtv_get_params", "bsgdtv_run", "bsgdtv_run_timed", "bsgdtv_get_x",
             "bsgdtv_get_state", "bsgdtv_set_state", "bsgdtv_objective", "bsgdtv_block_products",
             "bsgdtv_get_info", "bsgdtv_tv_prox", "bsgdtv_tv_prox_static", "bsgdtv_partition_bounds",
-            "bsgdtv_layout_check",
+            "bsgdtv_layout_check", "bsgdtv_batch_create_csr", "bsgdtv_batch_destroy",
+            "bsgdtv_batch_set_data", "bsgdtv_batch_run", "bsgdtv_batch_run_timed",
+            "bsgdtv_batch_get_x",
             "bsgdtv_launch_count", "bsgdtv_last_error", "bsgdtv_strerror"]
 
 
@@ -324,6 +332,66 @@ def bsgdtv_layout_check(rows, cols, img_h, img_w, row_ptr, col_idx, vals, M, N, 
     return dict(zip(keys, (int(v) for v in stats)))
 
 
+def bsgdtv_batch_create_csr(rows, cols, img_h, img_w, row_ptr, col_idx, vals, slices,
+                            stream=None):
+    lib = load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    vals = np.ascontiguousarray(vals, dtype=np.float64)
+    if row_ptr.size != rows + 1:
+        raise ValueError("row_ptr must have rows+1 entries")
+    h = ctypes.c_void_p()
+    rc = lib.bsgdtv_batch_create_csr(ctypes.byref(h), int(rows), int(cols), int(img_h), int(img_w),
+                                     _host_ptr(row_ptr, np.int64), _host_ptr(col_idx, np.int32),
+                                     _host_ptr(vals, np.float64), int(slices),
+                                     stream if stream is not None else current_stream())
+    _check(rc, "bsgdtv_batch_create_csr")
+    return h
+
+
+def bsgdtv_batch_destroy(h):
+    load().bsgdtv_batch_destroy(h)
+
+
+def bsgdtv_batch_set_data(h, y, lambdas, mu):
+    """y: [slices, rows] float32 (CUDA tensor or numpy); lambdas: [slices]."""
+    lib = load()
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    if _is_tensor(y):
+        import torch
+        rc = lib.bsgdtv_batch_set_data(h, _dev_ptr(y, torch.float32), 1,
+                                       _host_ptr(lam, np.float64), float(mu))
+    else:
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        rc = lib.bsgdtv_batch_set_data(h, _host_ptr(y, np.float32), 0, _host_ptr(lam, np.float64),
+                                       float(mu))
+    _check(rc, "bsgdtv_batch_set_data")
+
+
+def bsgdtv_batch_run(h, epochs, fgp_iters):
+    _check(load().bsgdtv_batch_run(h, int(epochs), int(fgp_iters)), "bsgdtv_batch_run")
+
+
+def bsgdtv_batch_run_timed(h, epochs, fgp_iters):
+    """Runs epochs and returns (sum of product-pass ms, sum of epoch ms)."""
+    pk, ep = ctypes.c_double(), ctypes.c_double()
+    _check(load().bsgdtv_batch_run_timed(h, int(epochs), int(fgp_iters), ctypes.byref(pk),
+                                         ctypes.byref(ep)), "bsgdtv_batch_run_timed")
+    return pk.value, ep.value
+
+
+def bsgdtv_batch_get_x(h, out):
+    """Copies every slice's x into `out` ([slices, cols] float32, CUDA tensor or numpy)."""
+    lib = load()
+    if _is_tensor(out):
+        import torch
+        rc = lib.bsgdtv_batch_get_x(h, _dev_ptr(out, torch.float32), 1)
+    else:
+        rc = lib.bsgdtv_batch_get_x(h, _host_ptr(out, np.float32), 0)
+    _check(rc, "bsgdtv_batch_get_x")
+    return out
+
+
 def bsgdtv_launch_count() -> int:
     return int(load().bsgdtv_launch_count())
 
@@ -389,3 +457,46 @@ class Reconstructor:
 
     def objective(self):
         return bsgdtv_objective(self.h)
+
+
+class BatchReconstructor:
+    """Owns one batch handle: B slices sharing the matrix A, each with its own
+    y_b and lambda_b; ``set_data(Y, lambdas, mu)`` / ``run`` / ``x()``."""
+
+    def __init__(self, A, img_shape, slices, stream=None):
+        self.img_shape = tuple(img_shape)
+        self.rows, self.cols = int(A.rows), int(A.cols_n)
+        self.slices = int(slices)
+        self.h = bsgdtv_batch_create_csr(self.rows, self.cols, img_shape[0], img_shape[1],
+                                         A.row_ptr, A.cols, A.vals, slices, stream)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            bsgdtv_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_data(self, Y, lambdas, mu):
+        bsgdtv_batch_set_data(self.h, Y, lambdas, mu)
+
+    def run(self, epochs, fgp_iters):
+        bsgdtv_batch_run(self.h, epochs, fgp_iters)
+
+    def run_timed(self, epochs, fgp_iters):
+        return bsgdtv_batch_run_timed(self.h, epochs, fgp_iters)
+
+    def x(self, out=None):
+        if out is None:
+            out = np.empty((self.slices, self.cols), dtype=np.float32)
+        return bsgdtv_batch_get_x(self.h, out)

@@ -1,0 +1,611 @@
+// Batched BSGD-TV: B slices (independent images, e.g. the slices of a
+// parallel-beam volume) that share one projection matrix A, each with its own
+// projections y_b, TV weight lambda_b, iterate x_b and residual r_b, and one
+// step mu (u_max belongs to A, so one step bound serves every slice).
+//
+// Every slice runs Algorithm 1 exactly as the single-slice path does.  The
+// block partition of Sec. 2.1 only distributes work: summed over the blocks,
+// the products of one epoch are r = y - A x and g = 2 A^T r_prev, so the
+// batch computes them with two passes over A for all slices at once:
+//   row pass     (A in CSR)  r_b  = y_b - A x_b                  (residual)
+//   column pass  (A in CSC)  x^_b = x_b + mu * 2 A^T r_b^{prev}  (gradient sum and step)
+// One warp handles one row (or one pixel) and its lanes the slices, so each
+// nonzero of A is read from HBM once per pass and applied to every slice.  x
+// and r are stored interleaved ([element][slice], slice stride Bp, B padded)
+// so that gathering element k for all slices is one contiguous 128-512 B
+// read, mostly served from L2.  There are no atomics and every sum runs in a
+// fixed order: results are deterministic.  The TV prox runs on planar images
+// (transposed out and back) with one FGP launch per chunk of iterations
+// covering every slice, tau_b = mu * lambda_b.
+//
+// Why not the single-slice fused kernel: its shared-memory x and g tiles
+// (64 x 64 pixels) hold only a handful of slices, and smaller tiles multiply
+// the per-segment z partials by the number of slices until they outweigh A.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <memory>
+#include <new>
+
+#include "bsgdtv_internal.h"
+#include "fgp_common.cuh"
+
+namespace bsgdtv {
+namespace {
+
+constexpr int kPassWarps = 8;   // warps (rows or pixels) per CTA
+
+template <int VEC>
+struct VecOf;
+template <>
+struct VecOf<1> {
+    using T = float;
+};
+template <>
+struct VecOf<2> {
+    using T = float2;
+};
+template <>
+struct VecOf<4> {
+    using T = float4;
+};
+
+template <int VEC>
+__device__ __forceinline__ void load_vec(const float *p, float (&v)[VEC]) {
+    using T = typename VecOf<VEC>::T;
+    const T t = __ldg(reinterpret_cast<const T *>(p));
+    const float *f = reinterpret_cast<const float *>(&t);
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) v[u] = f[u];
+}
+
+template <int VEC>
+__device__ __forceinline__ void store_vec(float *p, const float (&v)[VEC]) {
+    using T = typename VecOf<VEC>::T;
+    T t;
+    float *f = reinterpret_cast<float *>(&t);
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) f[u] = v[u];
+    *reinterpret_cast<T *>(p) = t;
+}
+
+// One warp per output element k (a row of A in the row pass, a column in the
+// column pass); lane l owns slices c0 + l*VEC .. c0 + l*VEC + VEC - 1 of each
+// chunk of 32*VEC slices.  acc = sum_e a_e v[idx_e][slice] in the order of
+// the stored nonzeros; then
+//   row pass:    out[k] = base[k] - acc       (base = y, v = x)
+//   column pass: out[k] = base[k] + mu*2*acc  (base = x, v = r_prev)
+// The 32 nonzeros of each round are staged in shared memory once and read
+// back as broadcasts.  A is streamed (evict-first) to keep v resident in L2.
+template <int VEC, bool kRowPass>
+__global__ void __launch_bounds__(kPassWarps * 32)
+    pass_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                const float *__restrict__ vals, const float *__restrict__ v,
+                const float *__restrict__ base, float *__restrict__ out, int64_t n_out, int Bp,
+                float mu) {
+    __shared__ int2 stage[kPassWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t k = (int64_t)blockIdx.x * kPassWarps + w;
+    if (k >= n_out) return;   // warp-uniform
+    const int64_t e0 = ptr[k], e1 = ptr[k + 1];
+    for (int c0 = 0; c0 < Bp; c0 += 32 * VEC) {
+        const float *vl = v + c0 + lane * VEC;
+        float acc[VEC];
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) acc[u] = 0.f;
+        for (int64_t r0 = e0; r0 < e1; r0 += 32) {
+            const int64_t e = r0 + lane;
+            int2 t = make_int2(0, 0);
+            if (e < e1) t = make_int2(__float_as_int(__ldcs(vals + e)), __ldcs(idx + e));
+            stage[w][lane] = t;
+            __syncwarp();
+            const int n = (e1 - r0 < 32) ? (int)(e1 - r0) : 32;
+            int j = 0;
+            for (; j + 4 <= n; j += 4) {
+                int2 s[4];
+                float x[4][VEC];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s[q] = stage[w][j + q];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) load_vec<VEC>(vl + (int64_t)s[q].y * Bp, x[q]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int u = 0; u < VEC; ++u)
+                        acc[u] = fmaf(__int_as_float(s[q].x), x[q][u], acc[u]);
+            }
+            for (; j < n; ++j) {
+                const int2 s = stage[w][j];
+                float x[VEC];
+                load_vec<VEC>(vl + (int64_t)s.y * Bp, x);
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) acc[u] = fmaf(__int_as_float(s.x), x[u], acc[u]);
+            }
+            __syncwarp();
+        }
+        const int64_t o = k * Bp + c0 + lane * VEC;
+        float b[VEC], res[VEC];
+        load_vec<VEC>(base + o, b);
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) res[u] = kRowPass ? b[u] - acc[u] : b[u] + mu * (2.f * acc[u]);
+        store_vec<VEC>(out + o, res);
+    }
+}
+
+template <bool kRowPass>
+cudaError_t launch_pass(int vec, const int64_t *ptr, const int32_t *idx, const float *vals,
+                        const float *v, const float *base, float *out, int64_t n_out, int Bp,
+                        float mu, cudaStream_t s) {
+    const dim3 grid((unsigned)((n_out + kPassWarps - 1) / kPassWarps));
+    const dim3 block(kPassWarps * 32);
+    if (vec == 1)
+        pass_kernel<1, kRowPass><<<grid, block, 0, s>>>(ptr, idx, vals, v, base, out, n_out, Bp, mu);
+    else if (vec == 2)
+        pass_kernel<2, kRowPass><<<grid, block, 0, s>>>(ptr, idx, vals, v, base, out, n_out, Bp, mu);
+    else
+        pass_kernel<4, kRowPass><<<grid, block, 0, s>>>(ptr, idx, vals, v, base, out, n_out, Bp, mu);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+// Planar [B][n] <-> interleaved [n][Bp] (only slices b < B are touched).
+__global__ void transpose_kernel(const float *__restrict__ in, float *__restrict__ out, int64_t n,
+                                 int B, int Bp, int to_planar) {
+    __shared__ float t[32][33];
+    const int64_t k0 = (int64_t)blockIdx.x * 32;
+    const int b0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8 threads
+    for (int yy = ty; yy < 32; yy += 8) {
+        if (to_planar) {   // interleaved rows k, slices along x
+            const int64_t k = k0 + yy;
+            const int b = b0 + tx;
+            if (k < n && b < B) t[yy][tx] = in[k * Bp + b];
+        } else {           // planar rows b, elements along x
+            const int b = b0 + yy;
+            const int64_t k = k0 + tx;
+            if (k < n && b < B) t[tx][yy] = in[(int64_t)b * n + k];
+        }
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        if (to_planar) {
+            const int b = b0 + yy;
+            const int64_t k = k0 + tx;
+            if (k < n && b < B) out[(int64_t)b * n + k] = t[tx][yy];
+        } else {
+            const int64_t k = k0 + yy;
+            const int b = b0 + tx;
+            if (k < n && b < B) out[k * Bp + b] = t[yy][tx];
+        }
+    }
+}
+
+cudaError_t launch_transpose(const float *in, float *out, int64_t n, int B, int Bp, bool to_planar,
+                             cudaStream_t s) {
+    const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((B + 31) / 32));
+    transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(in, out, n, B, Bp, to_planar ? 1 : 0);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+// Slice stride and vector width: a warp-wide load covers 32 slices as float,
+// 64 as float2, 128 as float4.
+void slice_stride(int B, int &Bp, int &vec) {
+    if (B <= 32) {
+        Bp = 32;
+        vec = 1;
+    } else if (B <= 64) {
+        Bp = 64;
+        vec = 2;
+    } else {
+        Bp = (B + 127) / 128 * 128;
+        vec = 4;
+    }
+}
+
+}  // namespace
+}  // namespace bsgdtv
+
+using namespace bsgdtv;
+
+struct bsgdtv_batch_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int64_t rows = 0, cols = 0, nnz = 0;
+    int img_h = 0, img_w = 0, B = 0, Bp = 0, vec = 1;
+    std::vector<void *> allocs;
+    int64_t *row_ptr = nullptr, *col_ptr = nullptr;
+    int32_t *cols_idx = nullptr, *rows_idx = nullptr;
+    float *vals_r = nullptr, *vals_c = nullptr;
+    float *X = nullptr, *Xhat = nullptr, *Y = nullptr, *R[2] = {nullptr, nullptr};   // interleaved
+    float *Xp = nullptr, *Xhp = nullptr;                                           // planar [B][cols]
+    float *fp = nullptr, *fq = nullptr, *fpp = nullptr, *fqp = nullptr;            // planar FGP duals
+    float *tau = nullptr;                                                          // [B]
+    int *flag = nullptr;
+    float *mom = nullptr;
+    int mom_len = 0;
+    int cur = 0;
+    bool has_data = false;
+    double mu = 0.0;
+    std::vector<double> lambdas;
+    int64_t epoch = 0;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraph_t tgraph[2] = {nullptr, nullptr};
+    cudaGraphExec_t texec[2] = {nullptr, nullptr};
+    cudaGraphNode_t tnode[2][3] = {};
+    cudaEvent_t tmark[3] = {nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> tevents;
+    int graph_fgp_iters = -1;
+    int64_t graph_kernels = 0;
+};
+
+namespace {
+
+template <typename T>
+int balloc(bsgdtv_batch_ctx *h, T **out, size_t count) {
+    void *p = nullptr;
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BSGDTV_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) +
+                                        "): " + cudaGetErrorString(e));
+    }
+    h->allocs.push_back(p);
+    *out = static_cast<T *>(p);
+    return BSGDTV_OK;
+}
+
+template <typename T>
+int bupload(bsgdtv_batch_ctx *h, T **out, const T *src, size_t count) {
+    BSG_CHECK(balloc(h, out, count));
+    if (count)
+        BSG_CUDA(cudaMemcpyAsync(*out, src, count * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+    return BSGDTV_OK;
+}
+
+void bdrop_graphs(bsgdtv_batch_ctx *h) {
+    for (auto &g : h->gexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    for (auto &g : h->texec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    for (auto &g : h->tgraph)
+        if (g) {
+            cudaGraphDestroy(g);
+            g = nullptr;
+        }
+    for (auto &row : h->tnode)
+        for (auto &nd : row) nd = nullptr;
+    h->graph_fgp_iters = -1;
+}
+
+bool any_prox(const bsgdtv_batch_ctx *h, int fgp_iters) {
+    if (fgp_iters <= 0) return false;
+    for (double l : h->lambdas)
+        if (l > 0.0) return true;
+    return false;
+}
+
+// One epoch of every slice: reads R[par], writes R[1 - par].
+int benqueue_epoch(bsgdtv_batch_ctx *h, int par, int fgp_iters, cudaStream_t s,
+                   cudaEvent_t *marks) {
+    const bool prox = any_prox(h, fgp_iters);
+    if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[0], s, cudaEventRecordExternal));
+    // r^k = y - A x^k (reads x before the column pass updates it)
+    BSG_CUDA(launch_pass<true>(h->vec, h->row_ptr, h->cols_idx, h->vals_r, h->X, h->Y,
+                               h->R[1 - par], h->rows, h->Bp, 0.f, s));
+    // x^ = x^k + mu * 2 A^T r^{k-1}
+    BSG_CUDA(launch_pass<false>(h->vec, h->col_ptr, h->rows_idx, h->vals_c, h->R[par], h->X,
+                                prox ? h->Xhat : h->X, h->cols, h->Bp, (float)h->mu, s));
+    if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[1], s, cudaEventRecordExternal));
+    if (prox) {
+        const int64_t c = h->cols;
+        BSG_CUDA(launch_transpose(h->Xhat, h->Xhp, c, h->B, h->Bp, true, s));
+        FgpScratch sc{h->fp, h->fq, h->fpp, h->fqp};
+        BSG_CUDA(fgpk::launch_fgp_regions<true>(h->Xhp, h->Xp, h->img_h, h->img_w, 1.f, h->tau,
+                                                h->B, c, fgp_iters, h->mom, sc, s, false));
+        BSG_CUDA(launch_transpose(h->Xp, h->X, c, h->B, h->Bp, false, s));
+    }
+    if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[2], s, cudaEventRecordExternal));
+    return BSGDTV_OK;
+}
+
+int bensure_mom(bsgdtv_batch_ctx *h, int iters) {
+    if (iters <= h->mom_len) return BSGDTV_OK;
+    std::vector<float> m;
+    fgp_momentum_host(iters, m);
+    float *d = nullptr;
+    BSG_CHECK(balloc(h, &d, m.size()));
+    BSG_CUDA(cudaMemcpy(d, m.data(), m.size() * sizeof(float), cudaMemcpyHostToDevice));
+    h->mom = d;
+    h->mom_len = iters;
+    return BSGDTV_OK;
+}
+
+int bbuild_graphs(bsgdtv_batch_ctx *h, int fgp_iters) {
+    bdrop_graphs(h);
+    BSG_CHECK(bensure_mom(h, std::max(fgp_iters, 1)));
+    for (int k = 0; k < 3; ++k)
+        if (!h->tmark[k]) BSG_CUDA(cudaEventCreate(&h->tmark[k]));
+    const int64_t before = bsgdtv_launch_count();
+    for (int timed = 0; timed < 2; ++timed) {
+        for (int par = 0; par < 2; ++par) {
+            cudaGraph_t g = nullptr;
+            BSG_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+            int rc = benqueue_epoch(h, par, fgp_iters, h->cap_stream, timed ? h->tmark : nullptr);
+            cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+            if (rc != BSGDTV_OK) {
+                if (g) cudaGraphDestroy(g);
+                add_launches(before - bsgdtv_launch_count());
+                return rc;
+            }
+            if (e != cudaSuccess)
+                return fail(BSGDTV_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            if (!timed) {
+                e = cudaGraphInstantiate(&h->gexec[par], g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess)
+                    return fail(BSGDTV_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+                continue;
+            }
+            h->tgraph[par] = g;
+            size_t n = 0;
+            BSG_CUDA(cudaGraphGetNodes(g, nullptr, &n));
+            std::vector<cudaGraphNode_t> nodes(n);
+            BSG_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
+            for (cudaGraphNode_t nd : nodes) {
+                cudaGraphNodeType t;
+                BSG_CUDA(cudaGraphNodeGetType(nd, &t));
+                if (t != cudaGraphNodeTypeEventRecord) continue;
+                cudaEvent_t ev;
+                BSG_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+                for (int k = 0; k < 3; ++k)
+                    if (ev == h->tmark[k]) h->tnode[par][k] = nd;
+            }
+            for (int k = 0; k < 3; ++k)
+                if (!h->tnode[par][k]) return fail(BSGDTV_ERR_CUDA, "timed graph: event node not found");
+            BSG_CUDA(cudaGraphInstantiate(&h->texec[par], g, 0));
+        }
+    }
+    // capture counted each epoch's kernels four times; replays are counted in run
+    const int64_t captured = bsgdtv_launch_count() - before;
+    add_launches(-captured);
+    h->graph_kernels = captured / 4;
+    h->graph_fgp_iters = fgp_iters;
+    return BSGDTV_OK;
+}
+
+// CSR -> CSC on the host (rows ascending inside each column); FP32 weights.
+void to_csc(int64_t rows, int64_t cols, const int64_t *row_ptr, const int32_t *col_idx,
+            const double *vals, std::vector<int64_t> &col_ptr, std::vector<int32_t> &row_idx,
+            std::vector<float> &cvals) {
+    const int64_t nnz = row_ptr[rows];
+    col_ptr.assign(cols + 1, 0);
+    for (int64_t e = 0; e < nnz; ++e) col_ptr[col_idx[e] + 1]++;
+    for (int64_t c = 0; c < cols; ++c) col_ptr[c + 1] += col_ptr[c];
+    row_idx.resize(nnz);
+    cvals.resize(nnz);
+    std::vector<int64_t> cur(col_ptr.begin(), col_ptr.end() - 1);
+    for (int64_t r = 0; r < rows; ++r)
+        for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+            const int64_t k = cur[col_idx[e]]++;
+            row_idx[k] = (int32_t)r;
+            cvals[k] = (float)vals[e];
+        }
+}
+
+int validate_csr(int64_t rows, int64_t cols, int img_h, int img_w, const int64_t *row_ptr,
+                 const int32_t *col_idx, const double *vals) {
+    if (!row_ptr || !col_idx || !vals) return fail(BSGDTV_ERR_INVALID_ARG, "null CSR array");
+    if (rows < 1 || cols < 1 || img_h < 1 || img_w < 1 || (int64_t)img_h * img_w != cols)
+        return fail(BSGDTV_ERR_INVALID_ARG, "bad sizes: need rows >= 1 and cols == img_h*img_w");
+    if (rows > INT32_MAX || cols > INT32_MAX)
+        return fail(BSGDTV_ERR_INVALID_ARG, "rows and cols must fit int32");
+    if (row_ptr[0] != 0) return fail(BSGDTV_ERR_INVALID_ARG, "row_ptr[0] must be 0");
+    for (int64_t r = 0; r < rows; ++r) {
+        if (row_ptr[r + 1] < row_ptr[r]) return fail(BSGDTV_ERR_INVALID_ARG, "row_ptr decreases");
+        for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+            if (col_idx[e] < 0 || col_idx[e] >= cols)
+                return fail(BSGDTV_ERR_INVALID_ARG, "column index out of range");
+            if (e > row_ptr[r] && col_idx[e] <= col_idx[e - 1])
+                return fail(BSGDTV_ERR_INVALID_ARG, "column indices must ascend within a row");
+            if (!std::isfinite(vals[e])) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in A");
+        }
+    }
+    return BSGDTV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bsgdtv_batch_create_csr(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int img_h, int img_w,
+                            const int64_t *row_ptr, const int32_t *col_idx, const double *vals,
+                            int slices, void *stream) {
+    if (!out) return fail(BSGDTV_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (slices < 1 || slices > 4096) return fail(BSGDTV_ERR_INVALID_ARG, "slices must be in [1, 4096]");
+    BSG_CHECK(validate_csr(rows, cols, img_h, img_w, row_ptr, col_idx, vals));
+    std::unique_ptr<bsgdtv_batch_ctx> h(new (std::nothrow) bsgdtv_batch_ctx());
+    if (!h) return fail(BSGDTV_ERR_OOM, "host allocation");
+    BSG_CUDA(cudaGetDevice(&h->device));
+    h->stream = (cudaStream_t)stream;
+    h->rows = rows;
+    h->cols = cols;
+    h->nnz = row_ptr[rows];
+    h->img_h = img_h;
+    h->img_w = img_w;
+    h->B = slices;
+    slice_stride(slices, h->Bp, h->vec);
+    bsgdtv_batch_ctx *hp = h.get();
+    int rc = BSGDTV_OK;
+    try {
+        std::vector<float> rvals(h->nnz);
+        for (int64_t e = 0; e < h->nnz; ++e) rvals[e] = (float)vals[e];
+        std::vector<int64_t> cptr;
+        std::vector<int32_t> ridx;
+        std::vector<float> cvals;
+        to_csc(rows, cols, row_ptr, col_idx, vals, cptr, ridx, cvals);
+        const size_t Ri = (size_t)rows * h->Bp, Ci = (size_t)cols * h->Bp;
+        const size_t Cp = (size_t)cols * slices;
+        rc = [&]() -> int {
+            BSG_CUDA(cudaStreamCreateWithFlags(&hp->cap_stream, cudaStreamNonBlocking));
+            BSG_CHECK(bupload(hp, &hp->row_ptr, row_ptr, rows + 1));
+            BSG_CHECK(bupload(hp, &hp->cols_idx, col_idx, hp->nnz));
+            BSG_CHECK(bupload(hp, &hp->vals_r, rvals.data(), hp->nnz));
+            BSG_CHECK(bupload(hp, &hp->col_ptr, cptr.data(), cols + 1));
+            BSG_CHECK(bupload(hp, &hp->rows_idx, ridx.data(), hp->nnz));
+            BSG_CHECK(bupload(hp, &hp->vals_c, cvals.data(), hp->nnz));
+            for (float **p : {&hp->X, &hp->Xhat}) BSG_CHECK(balloc(hp, p, Ci));
+            for (float **p : {&hp->Y, &hp->R[0], &hp->R[1]}) BSG_CHECK(balloc(hp, p, Ri));
+            for (float **p : {&hp->Xp, &hp->Xhp, &hp->fp, &hp->fq, &hp->fpp, &hp->fqp})
+                BSG_CHECK(balloc(hp, p, Cp));
+            BSG_CHECK(balloc(hp, &hp->tau, (size_t)slices));
+            BSG_CHECK(balloc(hp, &hp->flag, 1));
+            // padded slices (b >= B) stay zero for good: y = x = r = 0 there
+            for (float *p : {hp->X, hp->Xhat})
+                BSG_CUDA(cudaMemsetAsync(p, 0, Ci * sizeof(float), hp->stream));
+            for (float *p : {hp->Y, hp->R[0], hp->R[1]})
+                BSG_CUDA(cudaMemsetAsync(p, 0, Ri * sizeof(float), hp->stream));
+            BSG_CUDA(cudaStreamSynchronize(hp->stream));   // the host vectors die here
+            return BSGDTV_OK;
+        }();
+    } catch (const std::bad_alloc &) {
+        rc = fail(BSGDTV_ERR_OOM, "host allocation");
+    }
+    if (rc != BSGDTV_OK) {
+        bsgdtv_batch_destroy(h.release());
+        return rc;
+    }
+    *out = h.release();
+    return BSGDTV_OK;
+}
+
+void bsgdtv_batch_destroy(bsgdtv_batch_t h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    bdrop_graphs(h);
+    for (cudaEvent_t ev : h->tevents) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : h->tmark)
+        if (ev) cudaEventDestroy(ev);
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+}
+
+int bsgdtv_batch_set_data(bsgdtv_batch_t h, const float *y, int y_on_device,
+                          const double *lambdas, double mu) {
+    if (!h || !y || !lambdas) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    if (!(mu > 0.0) || !std::isfinite(mu)) return fail(BSGDTV_ERR_INVALID_ARG, "mu must be finite and > 0");
+    for (int b = 0; b < h->B; ++b)
+        if (!(lambdas[b] >= 0.0) || !std::isfinite(lambdas[b]))
+            return fail(BSGDTV_ERR_INVALID_ARG, "every lambda must be finite and >= 0");
+    BSG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    const int64_t rows = h->rows, n_in = rows * h->B;
+    if (!y_on_device)
+        for (int64_t i = 0; i < n_in; ++i)
+            if (!std::isfinite(y[i])) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+    // y arrives slice-major [B][rows]; it is staged in R[1] (rows * Bp >= rows * B
+    // floats) and interleaved into Y; the first epoch rewrites R[1] in full
+    BSG_CUDA(cudaMemcpyAsync(h->R[1], y, (size_t)n_in * sizeof(float),
+                             y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (y_on_device) {
+        int hflag = 0;
+        BSG_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+        BSG_CUDA(launch_check_finite(h->R[1], n_in, h->flag, s));
+        BSG_CUDA(cudaMemcpyAsync(&hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BSG_CUDA(cudaStreamSynchronize(s));
+        if (hflag) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+    }
+    BSG_CUDA(launch_transpose(h->R[1], h->Y, rows, h->B, h->Bp, false, s));
+    // x^0 = 0 and r^{-1} = y - A x^0 = y for every slice
+    BSG_CUDA(cudaMemsetAsync(h->X, 0, (size_t)h->cols * h->Bp * sizeof(float), s));
+    BSG_CUDA(cudaMemcpyAsync(h->R[0], h->Y, (size_t)rows * h->Bp * sizeof(float),
+                             cudaMemcpyDeviceToDevice, s));
+    std::vector<float> tau(h->B);
+    for (int b = 0; b < h->B; ++b) tau[b] = (float)(mu * lambdas[b]);
+    BSG_CUDA(cudaMemcpyAsync(h->tau, tau.data(), h->B * sizeof(float), cudaMemcpyHostToDevice, s));
+    // mu is a kernel argument of the captured epochs and the weights decide
+    // whether the epoch has a prox at all: the graphs are rebuilt on next run
+    bdrop_graphs(h);
+    h->mu = mu;
+    h->lambdas.assign(lambdas, lambdas + h->B);
+    h->cur = 0;
+    h->epoch = 0;
+    h->has_data = true;
+    BSG_CUDA(cudaStreamSynchronize(s));
+    return BSGDTV_OK;
+}
+
+int bsgdtv_batch_run_timed(bsgdtv_batch_t h, int epochs, int fgp_iters, double *products_ms,
+                           double *epoch_ms) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (!h->has_data) return fail(BSGDTV_ERR_STATE, "run before set_data");
+    if (epochs < 0 || fgp_iters < 0) return fail(BSGDTV_ERR_INVALID_ARG, "negative epochs / fgp_iters");
+    if (epochs == 0) return BSGDTV_OK;
+    BSG_CUDA(cudaSetDevice(h->device));
+    if (!h->gexec[0] || h->graph_fgp_iters != fgp_iters) BSG_CHECK(bbuild_graphs(h, fgp_iters));
+    const bool timed = products_ms || epoch_ms;
+    if (timed)
+        while (h->tevents.size() < (size_t)3 * epochs) {
+            cudaEvent_t ev;
+            BSG_CUDA(cudaEventCreate(&ev));
+            h->tevents.push_back(ev);
+        }
+    for (int e = 0; e < epochs; ++e) {
+        if (timed) {
+            cudaGraphExec_t ex = h->texec[h->cur];
+            for (int k = 0; k < 3; ++k)
+                BSG_CUDA(cudaGraphExecEventRecordNodeSetEvent(ex, h->tnode[h->cur][k],
+                                                              h->tevents[3 * e + k]));
+            BSG_CUDA(cudaGraphLaunch(ex, h->stream));
+        } else {
+            BSG_CUDA(cudaGraphLaunch(h->gexec[h->cur], h->stream));
+        }
+        add_launches(h->graph_kernels);
+        h->cur ^= 1;
+        h->epoch++;
+    }
+    if (timed) {
+        BSG_CUDA(cudaStreamSynchronize(h->stream));
+        double pk = 0.0, ep = 0.0;
+        for (int e = 0; e < epochs; ++e) {
+            float a = 0.f, b = 0.f;
+            BSG_CUDA(cudaEventElapsedTime(&a, h->tevents[3 * e], h->tevents[3 * e + 1]));
+            BSG_CUDA(cudaEventElapsedTime(&b, h->tevents[3 * e], h->tevents[3 * e + 2]));
+            pk += a;
+            ep += b;
+        }
+        if (products_ms) *products_ms = pk;
+        if (epoch_ms) *epoch_ms = ep;
+    }
+    return BSGDTV_OK;
+}
+
+int bsgdtv_batch_run(bsgdtv_batch_t h, int epochs, int fgp_iters) {
+    return bsgdtv_batch_run_timed(h, epochs, fgp_iters, nullptr, nullptr);
+}
+
+int bsgdtv_batch_get_x(bsgdtv_batch_t h, float *x, int out_on_device) {
+    if (!h || !x) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    BSG_CUDA(cudaSetDevice(h->device));
+    const int64_t c = h->cols;
+    BSG_CUDA(launch_transpose(h->X, h->Xp, c, h->B, h->Bp, true, h->stream));
+    BSG_CUDA(cudaMemcpyAsync(x, h->Xp, (size_t)c * h->B * sizeof(float),
+                             out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             h->stream));
+    if (!out_on_device) BSG_CUDA(cudaStreamSynchronize(h->stream));
+    return BSGDTV_OK;
+}
+
+}  // extern "C"

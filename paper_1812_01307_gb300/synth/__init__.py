@@ -159,6 +159,21 @@ def noisy_projections(A: CSR, x_true: np.ndarray, seed: int, frac: float = 0.01)
     return y_clean + sigma * rng.standard_normal(y_clean.shape[0])
 
 
+def slice_stack(A: CSR, n: int, n_ellipses: int, slices: int, seed: int = 0,
+                frac: float = 0.01):
+    """A stack of independent slices through one geometry A (as the slices of
+    a parallel-beam volume): slice b is the phantom of seed `seed + b` and its
+    projections with 1% Gaussian noise of seed `seed + b`.  Returns
+    (X_true [slices, n*n], Y [slices, rows]), float64."""
+    X = np.stack([phantom(n, n_ellipses, seed + b).ravel() for b in range(slices)])
+    Yc = np.ascontiguousarray(np.asarray(A.to_scipy() @ X.T).T)   # clean projections, [slices, rows]
+    Y = np.empty(Yc.shape)
+    for b in range(slices):
+        sigma = frac * float(np.mean(np.abs(Yc[b])))
+        Y[b] = Yc[b] + sigma * np.random.default_rng(seed + b + 1).standard_normal(Yc.shape[1])
+    return X, Y
+
+
 @dataclasses.dataclass(frozen=True)
 class Workload:
     """One reconstruction problem: geometry, phantom recipe and solver settings."""

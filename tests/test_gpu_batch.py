@@ -1,0 +1,202 @@
+"""GPU parity of the batched path (B slices sharing one matrix A, each with its
+own y_b and lambda_b) against the FP64 oracle run slice by slice with the
+block partition of the single-slice workload.
+
+Tolerance: relative l2 error <= 1e-4 per slice after a full FP32
+reconstruction (the single-slice bar); <= 1e-5 after the 3 epochs of the
+full-size check."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_01307_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_01307_gb300 import build
+    build.build_library()
+    from paper_1812_01307_gb300 import bsgdtv
+    bsgdtv.load()
+    torch.cuda.set_device(0)
+    return bsgdtv
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+GEOM = {
+    # name: (n, n_angles, n_bins, n_ellipses, M, N)
+    "ellipse64": (64, 60, 91, 10, 4, 4),
+    "ragged37": (37, 11, 55, 4, 3, 5),    # rays that miss the image: empty rows of A
+}
+
+_cache = {}
+
+
+def _setup(name, slices):
+    key = (name, slices)
+    if key not in _cache:
+        n, na, nb, ne, M, N = GEOM[name]
+        A = synth.parallel_beam_csr(n, na, nb)
+        _, Y = synth.slice_stack(A, n, ne, slices, seed=7)
+        u, _ = oracle.power_iteration(A)
+        _cache[key] = (A, Y.astype(np.float32), 0.9 / (2 * u))
+    return _cache[key]
+
+
+def _lambdas(slices):
+    # a spread of weights, with lambda = 0 (identity prox) on every 4th slice
+    lam = 0.02 * (1 + np.arange(slices) % 3)
+    lam[1::4] = 0.0
+    return lam
+
+
+def _oracle_slice(name, A, y, lam, mu, epochs, K):
+    n, na, nb, ne, M, N = GEOM[name]
+    x, _ = oracle.run(A, y.astype(np.float64), (n, n), M, N, lam, mu, epochs, K, row_unit=nb,
+                      col_unit=n)
+    return x
+
+
+@pytest.mark.parametrize("name,slices,epochs,K,check", [
+    ("ellipse64", 1, 30, 20, None),
+    ("ellipse64", 5, 30, 20, None),
+    ("ellipse64", 33, 12, 20, [0, 1, 2, 31, 32]),        # float2 lanes, padded to 64
+    ("ellipse64", 70, 8, 20, [0, 5, 63, 64, 69]),        # float4 lanes, padded to 128
+    ("ragged37", 130, 6, 9, [0, 1, 127, 128, 129]),      # two chunks of 128 slices
+])
+def test_batch_matches_oracle_per_slice(B, name, slices, epochs, K, check):
+    n = GEOM[name][0]
+    A, Y, mu = _setup(name, slices)
+    lam = _lambdas(slices)
+    with B.BatchReconstructor(A, (n, n), slices) as bt:
+        bt.set_data(Y, lam, mu)
+        bt.run(epochs, K)
+        X = bt.x()
+    for b in (range(slices) if check is None else check):
+        x_ref = _oracle_slice(name, A, Y[b], lam[b], mu, epochs, K)
+        assert rel(X[b], x_ref) <= 1e-4, (b, rel(X[b], x_ref))
+
+
+def test_batch_without_prox_and_device_inputs(B):
+    """lambda = 0 everywhere (no prox in the epoch), y and x passed as device tensors."""
+    name, slices = "ellipse64", 3
+    n = GEOM[name][0]
+    A, Y, mu = _setup(name, slices)
+    lam = np.zeros(slices)
+    out = torch.zeros((slices, n * n), device="cuda")
+    with B.BatchReconstructor(A, (n, n), slices) as bt:
+        bt.set_data(torch.from_numpy(Y).cuda(), lam, mu)
+        bt.run(10, 20)
+        bt.x(out)
+    X = out.cpu().numpy()
+    for b in range(slices):
+        assert rel(X[b], _oracle_slice(name, A, Y[b], 0.0, mu, 10, 20)) <= 1e-4
+
+
+def test_batch_slice_equals_single_handle(B):
+    """A slice of a batch and a single-slice handle on the same y reach the same x."""
+    name, slices = "ellipse64", 4
+    n, na, nb, ne, M, N = GEOM[name]
+    A, Y, mu = _setup(name, slices)
+    lam = np.full(slices, 0.05)
+    with B.BatchReconstructor(A, (n, n), slices) as bt:
+        bt.set_data(Y, lam, mu)
+        bt.run(20, 20)
+        X = bt.x()
+    with B.Reconstructor(A, (n, n), M, N, row_unit=nb, col_unit=n) as rec:
+        rec.set_data(Y[2], 0.05, mu)
+        rec.run(20, 20)
+        x1 = rec.x()
+    assert rel(X[2], x1) <= 1e-5
+
+
+def test_batch_deterministic_and_timed(B):
+    name, slices = "ellipse64", 33
+    n = GEOM[name][0]
+    A, Y, mu = _setup(name, slices)
+    lam = _lambdas(slices)
+    with B.BatchReconstructor(A, (n, n), slices) as bt:
+        bt.set_data(Y, lam, mu)
+        bt.run(5, 12)
+        X1 = bt.x().copy()
+        bt.set_data(Y, lam, mu)
+        bt.run(5, 12)
+        X2 = bt.x().copy()
+        bt.set_data(Y, lam, mu)
+        before = B.bsgdtv_launch_count()
+        pk, ep = bt.run_timed(5, 12)
+        launched = B.bsgdtv_launch_count() - before
+        X3 = bt.x().copy()
+    assert np.array_equal(X1, X2) and np.array_equal(X1, X3)
+    assert 0 < pk < ep
+    # per epoch: row pass, column pass, two transposes, one FGP launch (64x64
+    # fits one region); plus the transpose of get_x after the loop
+    assert launched == 5 * 5
+
+
+def test_batch_errors(B):
+    n = 37
+    A, Y, mu = _setup("ragged37", 130)
+    with pytest.raises(B.BsgdtvError) as e:
+        B.bsgdtv_batch_create_csr(A.rows, A.cols_n, n, n, A.row_ptr, A.cols, A.vals, 0)
+    assert e.value.code == -1
+    bad = A.vals.copy()
+    bad[3] = np.inf
+    with pytest.raises(B.BsgdtvError) as e:
+        B.bsgdtv_batch_create_csr(A.rows, A.cols_n, n, n, A.row_ptr, A.cols, bad, 2)
+    assert e.value.code == -6
+    with B.BatchReconstructor(A, (n, n), 2) as bt:
+        with pytest.raises(B.BsgdtvError) as e:
+            bt.run(1, 5)
+        assert e.value.code == -4
+        with pytest.raises(B.BsgdtvError) as e:
+            bt.set_data(Y[:2], [0.1, -0.1], mu)
+        assert e.value.code == -1
+        with pytest.raises(B.BsgdtvError) as e:
+            bt.set_data(Y[:2], [0.1, 0.1], 0.0)
+        assert e.value.code == -1
+        y = Y[:2].copy()
+        y[1, 17] = np.nan
+        with pytest.raises(B.BsgdtvError) as e:
+            bt.set_data(y, [0.1, 0.1], mu)
+        assert e.value.code == -6
+        with pytest.raises(B.BsgdtvError) as e:
+            bt.set_data(torch.from_numpy(y).cuda(), [0.1, 0.1], mu)
+        assert e.value.code == -6
+        bt.set_data(Y[:2], [0.1, 0.1], mu)      # still usable after the rejections
+        bt.run(2, 5)
+        assert np.all(np.isfinite(bt.x()))
+
+
+def test_batch_ellipse512_full_size(B):
+    """64 slices of the 512x512 geometry (360 angles x 727 bins, lambda 0.02,
+    50 FGP iterations) in the configuration bench.py times: 3 epochs, sampled
+    slices against the oracle."""
+    wl = synth.WORKLOADS["ellipse512"]
+    A = synth.make_problem(wl).A
+    slices = 64
+    _, Y = synth.slice_stack(A, wl.n, wl.n_ellipses, slices, seed=wl.seed)
+    Y = Y.astype(np.float32)
+    u, _ = oracle.power_iteration(A, 200, 1e-10)
+    mu = 0.9 / (2 * u)
+    lam = np.full(slices, wl.lam)
+    with B.BatchReconstructor(A, (wl.n, wl.n), slices) as bt:
+        bt.set_data(torch.from_numpy(Y).cuda(), lam, mu)
+        bt.run(3, wl.fgp_iters)
+        X = bt.x()
+    for b in (0, 63):
+        x_ref, _ = oracle.run(A, Y[b].astype(np.float64), (wl.n, wl.n), wl.M, wl.N, wl.lam, mu, 3,
+                              wl.fgp_iters, row_unit=wl.n_bins, col_unit=wl.n)
+        assert rel(X[b], x_ref) <= 1e-5, (b, rel(X[b], x_ref))
