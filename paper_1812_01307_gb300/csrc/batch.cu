@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <memory>
 #include <new>
 
@@ -34,117 +35,124 @@
 namespace bsgdtv {
 namespace {
 
-constexpr int kPassWarps = 8;   // warps (rows or pixels) per CTA
+constexpr int kPassWarps = 8;       // warps (rows or pixels) per CTA
+constexpr int kPassMinBlocks = 6;   // 48 resident warps per SM (<= 40 registers): the
+                                    // gathers are latency-bound, occupancy beats depth
 
-template <int VEC>
-struct VecOf;
-template <>
-struct VecOf<1> {
-    using T = float;
-};
-template <>
-struct VecOf<2> {
-    using T = float2;
-};
-template <>
-struct VecOf<4> {
-    using T = float4;
-};
-
-template <int VEC>
-__device__ __forceinline__ void load_vec(const float *p, float (&v)[VEC]) {
-    using T = typename VecOf<VEC>::T;
-    const T t = __ldg(reinterpret_cast<const T *>(p));
-    const float *f = reinterpret_cast<const float *>(&t);
-#pragma unroll
-    for (int u = 0; u < VEC; ++u) v[u] = f[u];
+// Packed nonzero of A for the passes: the weight's FP32 bits and the offset
+// (in floats) of the gathered element's slice vector, idx * Bp.
+// Gathered slice vectors are loaded with an L2 evict-last policy so that they
+// stay resident while A streams past them (evict-first).
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 
-template <int VEC>
-__device__ __forceinline__ void store_vec(float *p, const float (&v)[VEC]) {
-    using T = typename VecOf<VEC>::T;
-    T t;
-    float *f = reinterpret_cast<float *>(&t);
-#pragma unroll
-    for (int u = 0; u < VEC; ++u) f[u] = v[u];
-    *reinterpret_cast<T *>(p) = t;
+__device__ __forceinline__ float4 ld_keep(const float *ptr, uint64_t pol) {
+    float4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(ptr), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ void fma4(float a, const float4 &x, float4 &acc) {
+    acc.x = fmaf(a, x.x, acc.x);
+    acc.y = fmaf(a, x.y, acc.y);
+    acc.z = fmaf(a, x.z, acc.z);
+    acc.w = fmaf(a, x.w, acc.w);
 }
 
 // One warp per output element k (a row of A in the row pass, a column in the
-// column pass); lane l owns slices c0 + l*VEC .. c0 + l*VEC + VEC - 1 of each
-// chunk of 32*VEC slices.  acc = sum_e a_e v[idx_e][slice] in the order of
-// the stored nonzeros; then
+// column pass).  Each lane owns 4 consecutive slices; LPN lanes cover the 4*LPN
+// slices of one chunk, so the warp applies G = 32/LPN nonzeros at a time
+// (group g takes the nonzeros j = g, g + G, ...).  acc = sum_e a_e v[idx_e][slices]
+// in that fixed order, the G group sums are added by a fixed butterfly, then
 //   row pass:    out[k] = base[k] - acc       (base = y, v = x)
 //   column pass: out[k] = base[k] + mu*2*acc  (base = x, v = r_prev)
-// The 32 nonzeros of each round are staged in shared memory once and read
-// back as broadcasts.  A is streamed (evict-first) to keep v resident in L2.
-template <int VEC, bool kRowPass>
-__global__ void __launch_bounds__(kPassWarps * 32)
-    pass_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                const float *__restrict__ vals, const float *__restrict__ v,
-                const float *__restrict__ base, float *__restrict__ out, int64_t n_out, int Bp,
-                float mu) {
+// The 32 nonzeros of a round are staged in shared memory once; a partial last
+// round is padded with zero weights aimed at element 0.
+template <int LPN, bool kRowPass>
+__global__ void __launch_bounds__(kPassWarps * 32, kPassMinBlocks)
+    pass_kernel(const int64_t *__restrict__ ptr, const int2 *__restrict__ ent,
+                const float *__restrict__ v, const float *__restrict__ base,
+                float *__restrict__ out, int64_t n_out, int Bp, float mu) {
+    constexpr int G = 32 / LPN;
+    constexpr int NB = (32 / G < 4) ? 32 / G : 4;
     __shared__ int2 stage[kPassWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int g = lane / LPN, sl = lane % LPN;
     const int64_t k = (int64_t)blockIdx.x * kPassWarps + w;
     if (k >= n_out) return;   // warp-uniform
+    const uint64_t pol = l2_evict_last_policy();
     const int64_t e0 = ptr[k], e1 = ptr[k + 1];
-    for (int c0 = 0; c0 < Bp; c0 += 32 * VEC) {
-        const float *vl = v + c0 + lane * VEC;
-        float acc[VEC];
-#pragma unroll
-        for (int u = 0; u < VEC; ++u) acc[u] = 0.f;
+    for (int c0 = 0; c0 < Bp; c0 += 4 * LPN) {
+        const float *vl = v + c0 + sl * 4;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int64_t r0 = e0; r0 < e1; r0 += 32) {
             const int64_t e = r0 + lane;
             int2 t = make_int2(0, 0);
-            if (e < e1) t = make_int2(__float_as_int(__ldcs(vals + e)), __ldcs(idx + e));
+            if (e < e1) t = __ldcs(ent + e);
             stage[w][lane] = t;
             __syncwarp();
-            const int n = (e1 - r0 < 32) ? (int)(e1 - r0) : 32;
-            int j = 0;
-            for (; j + 4 <= n; j += 4) {
-                int2 s[4];
-                float x[4][VEC];
+            // NB gathers issued per lane before their FMAs
 #pragma unroll
-                for (int q = 0; q < 4; ++q) s[q] = stage[w][j + q];
+            for (int q0 = 0; q0 < 32 / G; q0 += NB) {
+                int2 st[NB];
+                float4 xv[NB];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) load_vec<VEC>(vl + (int64_t)s[q].y * Bp, x[q]);
+                for (int q = 0; q < NB; ++q) st[q] = stage[w][(q0 + q) * G + g];
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
+                for (int q = 0; q < NB; ++q) xv[q] = ld_keep(vl + st[q].y, pol);
 #pragma unroll
-                    for (int u = 0; u < VEC; ++u)
-                        acc[u] = fmaf(__int_as_float(s[q].x), x[q][u], acc[u]);
-            }
-            for (; j < n; ++j) {
-                const int2 s = stage[w][j];
-                float x[VEC];
-                load_vec<VEC>(vl + (int64_t)s.y * Bp, x);
-#pragma unroll
-                for (int u = 0; u < VEC; ++u) acc[u] = fmaf(__int_as_float(s.x), x[u], acc[u]);
+                for (int q = 0; q < NB; ++q) fma4(__int_as_float(st[q].x), xv[q], acc);
             }
             __syncwarp();
         }
-        const int64_t o = k * Bp + c0 + lane * VEC;
-        float b[VEC], res[VEC];
-        load_vec<VEC>(base + o, b);
 #pragma unroll
-        for (int u = 0; u < VEC; ++u) res[u] = kRowPass ? b[u] - acc[u] : b[u] + mu * (2.f * acc[u]);
-        store_vec<VEC>(out + o, res);
+        for (int off = LPN; off < 32; off *= 2) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off);
+            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off);
+        }
+        if (g == 0) {
+            const int64_t o = k * Bp + c0 + sl * 4;
+            const float4 b = __ldcs(reinterpret_cast<const float4 *>(base + o));
+            float4 res;
+            if (kRowPass) {
+                res = make_float4(b.x - acc.x, b.y - acc.y, b.z - acc.z, b.w - acc.w);
+            } else {
+                res = make_float4(b.x + mu * (2.f * acc.x), b.y + mu * (2.f * acc.y),
+                                  b.z + mu * (2.f * acc.z), b.w + mu * (2.f * acc.w));
+            }
+            *reinterpret_cast<float4 *>(out + o) = res;
+        }
     }
 }
 
 template <bool kRowPass>
-cudaError_t launch_pass(int vec, const int64_t *ptr, const int32_t *idx, const float *vals,
-                        const float *v, const float *base, float *out, int64_t n_out, int Bp,
-                        float mu, cudaStream_t s) {
+cudaError_t launch_pass(int lpn, const int64_t *ptr, const int2 *ent, const float *v,
+                        const float *base, float *out, int64_t n_out, int Bp, float mu,
+                        cudaStream_t s) {
     const dim3 grid((unsigned)((n_out + kPassWarps - 1) / kPassWarps));
     const dim3 block(kPassWarps * 32);
-    if (vec == 1)
-        pass_kernel<1, kRowPass><<<grid, block, 0, s>>>(ptr, idx, vals, v, base, out, n_out, Bp, mu);
-    else if (vec == 2)
-        pass_kernel<2, kRowPass><<<grid, block, 0, s>>>(ptr, idx, vals, v, base, out, n_out, Bp, mu);
-    else
-        pass_kernel<4, kRowPass><<<grid, block, 0, s>>>(ptr, idx, vals, v, base, out, n_out, Bp, mu);
+#define BSG_PASS(L)                                                                              \
+    case L:                                                                                      \
+        pass_kernel<L, kRowPass><<<grid, block, 0, s>>>(ptr, ent, v, base, out, n_out, Bp, mu); \
+        break;
+    switch (lpn) {
+        BSG_PASS(1)
+        BSG_PASS(2)
+        BSG_PASS(4)
+        BSG_PASS(8)
+        BSG_PASS(16)
+        BSG_PASS(32)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef BSG_PASS
     add_launches(1);
     return cudaGetLastError();
 }
@@ -189,19 +197,13 @@ cudaError_t launch_transpose(const float *in, float *out, int64_t n, int B, int 
     return cudaGetLastError();
 }
 
-// Slice stride and vector width: a warp-wide load covers 32 slices as float,
-// 64 as float2, 128 as float4.
-void slice_stride(int B, int &Bp, int &vec) {
-    if (B <= 32) {
-        Bp = 32;
-        vec = 1;
-    } else if (B <= 64) {
-        Bp = 64;
-        vec = 2;
-    } else {
-        Bp = (B + 127) / 128 * 128;
-        vec = 4;
-    }
+// Slice stride Bp (B padded) and lanes per nonzero: a lane holds 4 slices,
+// so Bp = 4 * LPN for B <= 128 (LPN = 1 .. 32), else a multiple of 128 taken
+// in chunks of 128 by the full warp.
+void slice_stride(int B, int &Bp, int &lpn) {
+    lpn = 1;
+    while (lpn < 32 && 4 * lpn < B) lpn *= 2;
+    Bp = (lpn < 32) ? 4 * lpn : (B + 127) / 128 * 128;
 }
 
 }  // namespace
@@ -214,11 +216,10 @@ struct bsgdtv_batch_ctx {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     int64_t rows = 0, cols = 0, nnz = 0;
-    int img_h = 0, img_w = 0, B = 0, Bp = 0, vec = 1;
+    int img_h = 0, img_w = 0, B = 0, Bp = 0, lpn = 1;
     std::vector<void *> allocs;
     int64_t *row_ptr = nullptr, *col_ptr = nullptr;
-    int32_t *cols_idx = nullptr, *rows_idx = nullptr;
-    float *vals_r = nullptr, *vals_c = nullptr;
+    int2 *ent_r = nullptr, *ent_c = nullptr;   // A in CSR / CSC as packed (weight, idx * Bp)
     float *X = nullptr, *Xhat = nullptr, *Y = nullptr, *R[2] = {nullptr, nullptr};   // interleaved
     float *Xp = nullptr, *Xhp = nullptr;                                           // planar [B][cols]
     float *fp = nullptr, *fq = nullptr, *fpp = nullptr, *fqp = nullptr;            // planar FGP duals
@@ -300,10 +301,10 @@ int benqueue_epoch(bsgdtv_batch_ctx *h, int par, int fgp_iters, cudaStream_t s,
     const bool prox = any_prox(h, fgp_iters);
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[0], s, cudaEventRecordExternal));
     // r^k = y - A x^k (reads x before the column pass updates it)
-    BSG_CUDA(launch_pass<true>(h->vec, h->row_ptr, h->cols_idx, h->vals_r, h->X, h->Y,
-                               h->R[1 - par], h->rows, h->Bp, 0.f, s));
+    BSG_CUDA(launch_pass<true>(h->lpn, h->row_ptr, h->ent_r, h->X, h->Y, h->R[1 - par], h->rows,
+                               h->Bp, 0.f, s));
     // x^ = x^k + mu * 2 A^T r^{k-1}
-    BSG_CUDA(launch_pass<false>(h->vec, h->col_ptr, h->rows_idx, h->vals_c, h->R[par], h->X,
+    BSG_CUDA(launch_pass<false>(h->lpn, h->col_ptr, h->ent_c, h->R[par], h->X,
                                 prox ? h->Xhat : h->X, h->cols, h->Bp, (float)h->mu, s));
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[1], s, cudaEventRecordExternal));
     if (prox) {
@@ -383,23 +384,29 @@ int bbuild_graphs(bsgdtv_batch_ctx *h, int fgp_iters) {
     return BSGDTV_OK;
 }
 
-// CSR -> CSC on the host (rows ascending inside each column); FP32 weights.
-void to_csc(int64_t rows, int64_t cols, const int64_t *row_ptr, const int32_t *col_idx,
-            const double *vals, std::vector<int64_t> &col_ptr, std::vector<int32_t> &row_idx,
-            std::vector<float> &cvals) {
+int2 pack_entry(double a, int64_t idx, int Bp) {
+    const float f = (float)a;
+    int bits;
+    std::memcpy(&bits, &f, sizeof(bits));
+    return make_int2(bits, (int)(idx * Bp));
+}
+
+// Packed CSR of A and its CSC (rows ascending inside each column), weights
+// rounded to FP32, element offsets idx * Bp.
+void pack_operator(int64_t rows, int64_t cols, const int64_t *row_ptr, const int32_t *col_idx,
+                   const double *vals, int Bp, std::vector<int2> &ent_r,
+                   std::vector<int64_t> &col_ptr, std::vector<int2> &ent_c) {
     const int64_t nnz = row_ptr[rows];
+    ent_r.resize(nnz);
+    for (int64_t e = 0; e < nnz; ++e) ent_r[e] = pack_entry(vals[e], col_idx[e], Bp);
     col_ptr.assign(cols + 1, 0);
     for (int64_t e = 0; e < nnz; ++e) col_ptr[col_idx[e] + 1]++;
     for (int64_t c = 0; c < cols; ++c) col_ptr[c + 1] += col_ptr[c];
-    row_idx.resize(nnz);
-    cvals.resize(nnz);
+    ent_c.resize(nnz);
     std::vector<int64_t> cur(col_ptr.begin(), col_ptr.end() - 1);
     for (int64_t r = 0; r < rows; ++r)
-        for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
-            const int64_t k = cur[col_idx[e]]++;
-            row_idx[k] = (int32_t)r;
-            cvals[k] = (float)vals[e];
-        }
+        for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e)
+            ent_c[cur[col_idx[e]]++] = pack_entry(vals[e], r, Bp);
 }
 
 int validate_csr(int64_t rows, int64_t cols, int img_h, int img_w, const int64_t *row_ptr,
@@ -444,26 +451,23 @@ int bsgdtv_batch_create_csr(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int
     h->img_h = img_h;
     h->img_w = img_w;
     h->B = slices;
-    slice_stride(slices, h->Bp, h->vec);
+    slice_stride(slices, h->Bp, h->lpn);
+    if (std::max(rows, cols) * h->Bp > INT32_MAX)
+        return fail(BSGDTV_ERR_UNSUPPORTED, "max(rows, cols) * padded slices must fit int32");
     bsgdtv_batch_ctx *hp = h.get();
     int rc = BSGDTV_OK;
     try {
-        std::vector<float> rvals(h->nnz);
-        for (int64_t e = 0; e < h->nnz; ++e) rvals[e] = (float)vals[e];
+        std::vector<int2> ent_r, ent_c;
         std::vector<int64_t> cptr;
-        std::vector<int32_t> ridx;
-        std::vector<float> cvals;
-        to_csc(rows, cols, row_ptr, col_idx, vals, cptr, ridx, cvals);
+        pack_operator(rows, cols, row_ptr, col_idx, vals, h->Bp, ent_r, cptr, ent_c);
         const size_t Ri = (size_t)rows * h->Bp, Ci = (size_t)cols * h->Bp;
         const size_t Cp = (size_t)cols * slices;
         rc = [&]() -> int {
             BSG_CUDA(cudaStreamCreateWithFlags(&hp->cap_stream, cudaStreamNonBlocking));
             BSG_CHECK(bupload(hp, &hp->row_ptr, row_ptr, rows + 1));
-            BSG_CHECK(bupload(hp, &hp->cols_idx, col_idx, hp->nnz));
-            BSG_CHECK(bupload(hp, &hp->vals_r, rvals.data(), hp->nnz));
+            BSG_CHECK(bupload(hp, &hp->ent_r, ent_r.data(), hp->nnz));
             BSG_CHECK(bupload(hp, &hp->col_ptr, cptr.data(), cols + 1));
-            BSG_CHECK(bupload(hp, &hp->rows_idx, ridx.data(), hp->nnz));
-            BSG_CHECK(bupload(hp, &hp->vals_c, cvals.data(), hp->nnz));
+            BSG_CHECK(bupload(hp, &hp->ent_c, ent_c.data(), hp->nnz));
             for (float **p : {&hp->X, &hp->Xhat}) BSG_CHECK(balloc(hp, p, Ci));
             for (float **p : {&hp->Y, &hp->R[0], &hp->R[1]}) BSG_CHECK(balloc(hp, p, Ri));
             for (float **p : {&hp->Xp, &hp->Xhp, &hp->fp, &hp->fq, &hp->fpp, &hp->fqp})
