@@ -240,6 +240,21 @@ int bsgdtv_batch_create_csr(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int
                             const int64_t *row_ptr, const int32_t *col_idx, const double *vals,
                             int slices, void *stream);
 
+/* bsgdtv_batch_create_csr with a weight format: BSGDTV_FMT_F32_I32 (FP32
+ * weights, 8 bytes per nonzero and pass), BSGDTV_FMT_F16_I16 or
+ * BSGDTV_FMT_BF16_I16 (weights rounded to nearest even binary16 / bfloat16,
+ * 6 bytes per nonzero and pass, FP32 arithmetic).  A batch always keeps
+ * 32-bit element offsets, so the index width in the format's name does not
+ * apply; BSGDTV_FMT_F32_I16 is BSGDTV_ERR_UNSUPPORTED here. */
+int bsgdtv_batch_create_csr_ex(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int img_h,
+                               int img_w, const int64_t *row_ptr, const int32_t *col_idx,
+                               const double *vals, int slices, int format, void *stream);
+
+/* Host only: the device bytes a batch of these sizes allocates (A twice,
+ * the interleaved and planar vectors, FGP fields), within a few KiB; -1 on
+ * bad sizes.  Used for admission by free memory. */
+int64_t bsgdtv_batch_device_bytes(int64_t rows, int64_t cols, int64_t nnz, int slices, int format);
+
 /* Releases every resource of the batch.  NULL is ignored. */
 void bsgdtv_batch_destroy(bsgdtv_batch_t h);
 
@@ -268,6 +283,75 @@ int bsgdtv_batch_run_timed(bsgdtv_batch_t h, int epochs, int fgp_iters, double *
 /* Copies every slice's x into x [slices][cols] (slice-major FP32).  To the
  * host: synchronises the stream. */
 int bsgdtv_batch_get_x(bsgdtv_batch_t h, float *x, int out_on_device);
+
+/* Restarts slice b alone (a slot of a continuously batched server): y_b
+ * [rows] (FP32, host or device) and lambda >= 0 replace the slice's data and
+ * the slice resets to x^0 = 0, r^{-1} = y_b; the step mu stays the one of
+ * set_data.  y = NULL empties the slot (y = x = r = 0, lambda = 0).  The other
+ * slices are untouched, and since every slice's arithmetic is independent of
+ * the others, a slice's iterates do not depend on what the other slots hold.
+ * Stream-ordered with run; BSGDTV_ERR_STATE before set_data. */
+int bsgdtv_batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_device, double lambda);
+
+/* Copies slice b's x [cols] (FP32).  To the host: synchronises the stream. */
+int bsgdtv_batch_get_slice_x(bsgdtv_batch_t h, int b, float *x, int out_on_device);
+
+/* ------------------------------------------------------ continuous batching
+ * A reconstruction server: requests (projections of a registered geometry,
+ * a TV weight and an epoch budget) are submitted at any time from any host
+ * thread and run as slots of batch groups (bsgdtv_batch_*), one group per
+ * geometry and more while the HBM budget allows.  A request is admitted into
+ * a free slot as soon as one exists (between the group's ticks), keeps its x,
+ * r and FGP state on the device, and leaves when its budget of epochs is
+ * done; its x is then copied to host memory.  One worker thread inside the
+ * server drives the device; groups of different geometries run on their own
+ * streams and overlap.  A group's device bytes are those of
+ * bsgdtv_batch_device_bytes; admission keeps their sum within the budget,
+ * releasing idle groups of other geometries first.  Every request runs
+ * Algorithm 1 exactly as a batch slice does, so its result does not depend
+ * on the other requests it shares a group with. */
+typedef struct bsgdtv_server_ctx *bsgdtv_server_t;
+
+/* Starts a server on the current device.  hbm_budget_bytes bounds the device
+ * bytes of all groups; fgp_iters is the FGP iteration count of every prox;
+ * max_tick_epochs caps the epochs a group runs between admissions. */
+int bsgdtv_server_create(bsgdtv_server_t *out, int64_t hbm_budget_bytes, int fgp_iters,
+                         int max_tick_epochs);
+
+/* Stops the worker (requests still queued or running are abandoned), waits
+ * for the device and frees everything.  NULL is ignored. */
+void bsgdtv_server_destroy(bsgdtv_server_t s);
+
+/* Registers a geometry: host CSR A as for bsgdtv_create_csr (validated and
+ * copied), the batch weight format (bsgdtv_batch_create_csr_ex), the slots
+ * per group, the step mu > 0 for this A (Theorem 1: mu < 1/(2 u_max), e.g.
+ * from bsgdtv_estimate_umax) and how many groups to create now (prewarm, as
+ * far as the budget allows; the rest are made on demand).  Writes the
+ * geometry id.  Fails with BSGDTV_ERR_OOM if one group exceeds the budget. */
+int bsgdtv_server_add_geometry(bsgdtv_server_t s, int64_t rows, int64_t cols, int img_h, int img_w,
+                               const int64_t *row_ptr, const int32_t *col_idx, const double *vals,
+                               int format, int slots, double mu, int prewarm, int *geom_id);
+
+/* Queues a request: y [rows of the geometry] (host FP32, copied), lambda >= 0,
+ * epochs >= 1.  Writes its id.  Never blocks on the device. */
+int bsgdtv_server_submit(bsgdtv_server_t s, int geom_id, const float *y, double lambda, int epochs,
+                         int64_t *request_id);
+
+/* Request state: 0 queued, 1 running, 2 done, 3 failed. */
+int bsgdtv_server_poll(bsgdtv_server_t s, int64_t request_id, int *state);
+
+/* Waits up to timeout_s seconds (< 0: no limit) for the request; on success
+ * copies its x [cols] to host memory x (may be NULL) and forgets the request.
+ * times (may be NULL) receives [0] the latency from submit to x in host
+ * memory and [1] the time spent queued, in seconds.  A failed request returns
+ * its error code (and is forgotten); BSGDTV_ERR_TIMEOUT leaves it pending. */
+int bsgdtv_server_wait(bsgdtv_server_t s, int64_t request_id, double timeout_s, float *x,
+                       double *times);
+
+/* stats [12]: submitted, completed, failed, queued, running, groups, device
+ * bytes of the groups, most requests running at once, ticks, epochs run by
+ * groups, slice-epochs of requests, groups created. */
+int bsgdtv_server_stats(bsgdtv_server_t s, int64_t *stats);
 
 #ifdef __cplusplus
 }

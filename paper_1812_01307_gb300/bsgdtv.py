@@ -57,11 +57,22 @@ def load(path: str | None = None):
         "bsgdtv_partition_bounds": (I32, [I64, I64, I32, I32, I64, I64, P, P]),
         "bsgdtv_layout_check": (I32, [I64, I64, I32, I32, P, P, P, I32, I32, I64, I64, P, P, I32, I32, P]),
         "bsgdtv_batch_create_csr": (I32, [ctypes.POINTER(P), I64, I64, I32, I32, P, P, P, I32, P]),
+        "bsgdtv_batch_create_csr_ex": (I32, [ctypes.POINTER(P), I64, I64, I32, I32, P, P, P, I32, I32, P]),
+        "bsgdtv_batch_set_slice": (I32, [P, I32, P, I32, D]),
+        "bsgdtv_batch_get_slice_x": (I32, [P, I32, P, I32]),
         "bsgdtv_batch_destroy": (None, [P]),
         "bsgdtv_batch_set_data": (I32, [P, P, I32, P, D]),
         "bsgdtv_batch_run": (I32, [P, I32, I32]),
         "bsgdtv_batch_run_timed": (I32, [P, I32, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "bsgdtv_batch_get_x": (I32, [P, P, I32]),
+        "bsgdtv_batch_device_bytes": (I64, [I64, I64, I64, I32, I32]),
+        "bsgdtv_server_create": (I32, [ctypes.POINTER(P), I64, I32, I32]),
+        "bsgdtv_server_destroy": (None, [P]),
+        "bsgdtv_server_add_geometry": (I32, [P, I64, I64, I32, I32, P, P, P, I32, I32, D, I32, ctypes.POINTER(I32)]),
+        "bsgdtv_server_submit": (I32, [P, I32, P, D, I32, ctypes.POINTER(I64)]),
+        "bsgdtv_server_poll": (I32, [P, I64, ctypes.POINTER(I32)]),
+        "bsgdtv_server_wait": (I32, [P, I64, D, P, P]),
+        "bsgdtv_server_stats": (I32, [P, P]),
         "bsgdtv_launch_count": (I64, []),
         "bsgdtv_last_error": (ctypes.c_char_p, []),
         "bsgdtv_strerror": (ctypes.c_char_p, [I32]),
@@ -82,7 +93,10 @@ def exported_symbols():
             "bsgdtv_get_info", "bsgdtv_tv_prox", "bsgdtv_tv_prox_static", "bsgdtv_partition_bounds",
             "bsgdtv_layout_check", "bsgdtv_batch_create_csr", "bsgdtv_batch_destroy",
             "bsgdtv_batch_set_data", "bsgdtv_batch_run", "bsgdtv_batch_run_timed",
-            "bsgdtv_batch_get_x",
+            "bsgdtv_batch_get_x", "bsgdtv_batch_create_csr_ex", "bsgdtv_batch_set_slice",
+            "bsgdtv_batch_get_slice_x", "bsgdtv_batch_device_bytes", "bsgdtv_server_create",
+            "bsgdtv_server_destroy", "bsgdtv_server_add_geometry", "bsgdtv_server_submit",
+            "bsgdtv_server_poll", "bsgdtv_server_wait", "bsgdtv_server_stats",
             "bsgdtv_launch_count", "bsgdtv_last_error", "bsgdtv_strerror"]
 
 
@@ -333,7 +347,7 @@ def bsgdtv_layout_check(rows, cols, img_h, img_w, row_ptr, col_idx, vals, M, N, 
 
 
 def bsgdtv_batch_create_csr(rows, cols, img_h, img_w, row_ptr, col_idx, vals, slices,
-                            stream=None):
+                            stream=None, fmt=FMT_F32_I32):
     lib = load()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
     col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
@@ -341,11 +355,12 @@ def bsgdtv_batch_create_csr(rows, cols, img_h, img_w, row_ptr, col_idx, vals, sl
     if row_ptr.size != rows + 1:
         raise ValueError("row_ptr must have rows+1 entries")
     h = ctypes.c_void_p()
-    rc = lib.bsgdtv_batch_create_csr(ctypes.byref(h), int(rows), int(cols), int(img_h), int(img_w),
-                                     _host_ptr(row_ptr, np.int64), _host_ptr(col_idx, np.int32),
-                                     _host_ptr(vals, np.float64), int(slices),
-                                     stream if stream is not None else current_stream())
-    _check(rc, "bsgdtv_batch_create_csr")
+    rc = lib.bsgdtv_batch_create_csr_ex(ctypes.byref(h), int(rows), int(cols), int(img_h),
+                                        int(img_w), _host_ptr(row_ptr, np.int64),
+                                        _host_ptr(col_idx, np.int32), _host_ptr(vals, np.float64),
+                                        int(slices), int(fmt),
+                                        stream if stream is not None else current_stream())
+    _check(rc, "bsgdtv_batch_create_csr_ex")
     return h
 
 
@@ -390,6 +405,95 @@ def bsgdtv_batch_get_x(h, out):
         rc = lib.bsgdtv_batch_get_x(h, _host_ptr(out, np.float32), 0)
     _check(rc, "bsgdtv_batch_get_x")
     return out
+
+
+def bsgdtv_batch_set_slice(h, b, y, lam):
+    """Restarts slice b with projections y (None empties the slot)."""
+    lib = load()
+    if y is None:
+        rc = lib.bsgdtv_batch_set_slice(h, int(b), None, 0, 0.0)
+    elif _is_tensor(y):
+        import torch
+        rc = lib.bsgdtv_batch_set_slice(h, int(b), _dev_ptr(y, torch.float32), 1, float(lam))
+    else:
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        rc = lib.bsgdtv_batch_set_slice(h, int(b), _host_ptr(y, np.float32), 0, float(lam))
+    _check(rc, "bsgdtv_batch_set_slice")
+
+
+def bsgdtv_batch_get_slice_x(h, b, out):
+    lib = load()
+    if _is_tensor(out):
+        import torch
+        rc = lib.bsgdtv_batch_get_slice_x(h, int(b), _dev_ptr(out, torch.float32), 1)
+    else:
+        rc = lib.bsgdtv_batch_get_slice_x(h, int(b), _host_ptr(out, np.float32), 0)
+    _check(rc, "bsgdtv_batch_get_slice_x")
+    return out
+
+
+def bsgdtv_batch_device_bytes(rows, cols, nnz, slices, fmt=FMT_F32_I32) -> int:
+    """Host only: device bytes of a batch of these sizes (-1 on bad sizes)."""
+    return int(load().bsgdtv_batch_device_bytes(int(rows), int(cols), int(nnz), int(slices), int(fmt)))
+
+
+def bsgdtv_server_create(hbm_budget_bytes, fgp_iters, max_tick_epochs=8):
+    h = ctypes.c_void_p()
+    _check(load().bsgdtv_server_create(ctypes.byref(h), int(hbm_budget_bytes), int(fgp_iters),
+                                       int(max_tick_epochs)), "bsgdtv_server_create")
+    return h
+
+
+def bsgdtv_server_destroy(h):
+    load().bsgdtv_server_destroy(h)
+
+
+def bsgdtv_server_add_geometry(h, rows, cols, img_h, img_w, row_ptr, col_idx, vals, fmt, slots, mu,
+                               prewarm=1):
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    vals = np.ascontiguousarray(vals, dtype=np.float64)
+    gid = ctypes.c_int()
+    _check(load().bsgdtv_server_add_geometry(h, int(rows), int(cols), int(img_h), int(img_w),
+                                             _host_ptr(row_ptr, np.int64), _host_ptr(col_idx, np.int32),
+                                             _host_ptr(vals, np.float64), int(fmt), int(slots),
+                                             float(mu), int(prewarm), ctypes.byref(gid)),
+           "bsgdtv_server_add_geometry")
+    return gid.value
+
+
+def bsgdtv_server_submit(h, geom_id, y, lam, epochs):
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    rid = ctypes.c_int64()
+    _check(load().bsgdtv_server_submit(h, int(geom_id), _host_ptr(y, np.float32), float(lam),
+                                       int(epochs), ctypes.byref(rid)), "bsgdtv_server_submit")
+    return rid.value
+
+
+def bsgdtv_server_poll(h, request_id):
+    st = ctypes.c_int()
+    _check(load().bsgdtv_server_poll(h, int(request_id), ctypes.byref(st)), "bsgdtv_server_poll")
+    return st.value
+
+
+def bsgdtv_server_wait(h, request_id, out=None, timeout_s=-1.0):
+    """Waits for a request; fills `out` (float32 numpy, or None) and returns
+    (latency_s, queued_s)."""
+    times = np.zeros(2, dtype=np.float64)
+    _check(load().bsgdtv_server_wait(h, int(request_id), float(timeout_s),
+                                     None if out is None else _host_ptr(out, np.float32),
+                                     _host_ptr(times, np.float64)), "bsgdtv_server_wait")
+    return float(times[0]), float(times[1])
+
+
+SERVER_STATS = ["submitted", "completed", "failed", "queued", "running", "groups", "device_bytes",
+                "max_running", "ticks", "epochs_run", "slice_epochs", "groups_made"]
+
+
+def bsgdtv_server_stats(h):
+    v = np.zeros(12, dtype=np.int64)
+    _check(load().bsgdtv_server_stats(h, _host_ptr(v, np.int64)), "bsgdtv_server_stats")
+    return dict(zip(SERVER_STATS, (int(a) for a in v)))
 
 
 def bsgdtv_launch_count() -> int:
@@ -463,12 +567,12 @@ class BatchReconstructor:
     """Owns one batch handle: B slices sharing the matrix A, each with its own
     y_b and lambda_b; ``set_data(Y, lambdas, mu)`` / ``run`` / ``x()``."""
 
-    def __init__(self, A, img_shape, slices, stream=None):
+    def __init__(self, A, img_shape, slices, stream=None, fmt=FMT_F32_I32):
         self.img_shape = tuple(img_shape)
         self.rows, self.cols = int(A.rows), int(A.cols_n)
         self.slices = int(slices)
         self.h = bsgdtv_batch_create_csr(self.rows, self.cols, img_shape[0], img_shape[1],
-                                         A.row_ptr, A.cols, A.vals, slices, stream)
+                                         A.row_ptr, A.cols, A.vals, slices, stream, fmt)
 
     def close(self):
         if getattr(self, "h", None) is not None:
@@ -500,3 +604,58 @@ class BatchReconstructor:
         if out is None:
             out = np.empty((self.slices, self.cols), dtype=np.float32)
         return bsgdtv_batch_get_x(self.h, out)
+
+    def set_slice(self, b, y, lam):
+        bsgdtv_batch_set_slice(self.h, b, y, lam)
+
+    def slice_x(self, b, out=None):
+        if out is None:
+            out = np.empty(self.cols, dtype=np.float32)
+        return bsgdtv_batch_get_slice_x(self.h, b, out)
+
+
+class Server:
+    """Continuous-batching server: ``add_geometry(A, img_shape, mu, ...)`` then
+    ``submit(geom, y, lam, epochs)`` from any thread and ``wait(request)``."""
+
+    def __init__(self, hbm_budget_bytes, fgp_iters, max_tick_epochs=8):
+        self.h = bsgdtv_server_create(hbm_budget_bytes, fgp_iters, max_tick_epochs)
+        self.cols = {}
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            bsgdtv_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def add_geometry(self, A, img_shape, mu, slots=32, fmt=FMT_F32_I32, prewarm=1):
+        gid = bsgdtv_server_add_geometry(self.h, A.rows, A.cols_n, img_shape[0], img_shape[1],
+                                         A.row_ptr, A.cols, A.vals, fmt, slots, mu, prewarm)
+        self.cols[gid] = int(A.cols_n)
+        return gid
+
+    def submit(self, geom_id, y, lam, epochs):
+        return bsgdtv_server_submit(self.h, geom_id, y, lam, epochs)
+
+    def poll(self, request_id):
+        return bsgdtv_server_poll(self.h, request_id)
+
+    def wait(self, request_id, geom_id, timeout_s=-1.0):
+        """Returns (x, latency_s, queued_s)."""
+        x = np.empty(self.cols[geom_id], dtype=np.float32)
+        lat, q = bsgdtv_server_wait(self.h, request_id, x, timeout_s)
+        return x, lat, q
+
+    def stats(self):
+        return bsgdtv_server_stats(self.h)

@@ -21,6 +21,8 @@
 // Why not the single-slice fused kernel: its shared-memory x and g tiles
 // (64 x 64 pixels) hold only a handful of slices, and smaller tiles multiply
 // the per-segment z partials by the number of slices until they outweigh A.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -73,10 +75,35 @@ __device__ __forceinline__ void fma4(float a, const float4 &x, float4 &acc) {
 //   column pass: out[k] = base[k] + mu*2*acc  (base = x, v = r_prev)
 // The 32 nonzeros of a round are staged in shared memory once; a partial last
 // round is padded with zero weights aimed at element 0.
-template <int LPN, bool kRowPass>
+// The nonzeros of A as the passes read them.  kW = 0: packed 8-byte entries
+// (FP32 weight bits, offset); kW = BSGDTV_FMT_F16_I16 / BSGDTV_FMT_BF16_I16:
+// 16-bit weights and 32-bit offsets in two arrays (6 bytes per nonzero).
+struct PassOperand {
+    const int64_t *ptr;
+    const int2 *ent;
+    const uint16_t *w16;
+    const int32_t *off;
+};
+
+template <int kW>
+__device__ __forceinline__ int2 load_entry(const PassOperand &A, int64_t e) {
+    if constexpr (kW == 0) {
+        return __ldcs(A.ent + e);
+    } else {
+        const unsigned short wb = __ldcs(reinterpret_cast<const unsigned short *>(A.w16) + e);
+        const int off = __ldcs(A.off + e);
+        float a;
+        if constexpr (kW == BSGDTV_FMT_F16_I16)
+            a = __half2float(__ushort_as_half(wb));
+        else
+            a = __uint_as_float((unsigned)wb << 16);   // bfloat16 = high half of an FP32
+        return make_int2(__float_as_int(a), off);
+    }
+}
+
+template <int LPN, bool kRowPass, int kW>
 __global__ void __launch_bounds__(kPassWarps * 32, kPassMinBlocks)
-    pass_kernel(const int64_t *__restrict__ ptr, const int2 *__restrict__ ent,
-                const float *__restrict__ v, const float *__restrict__ base,
+    pass_kernel(const PassOperand A, const float *__restrict__ v, const float *__restrict__ base,
                 float *__restrict__ out, int64_t n_out, int Bp, float mu) {
     constexpr int G = 32 / LPN;
     constexpr int NB = (32 / G < 4) ? 32 / G : 4;
@@ -86,14 +113,14 @@ __global__ void __launch_bounds__(kPassWarps * 32, kPassMinBlocks)
     const int64_t k = (int64_t)blockIdx.x * kPassWarps + w;
     if (k >= n_out) return;   // warp-uniform
     const uint64_t pol = l2_evict_last_policy();
-    const int64_t e0 = ptr[k], e1 = ptr[k + 1];
+    const int64_t e0 = A.ptr[k], e1 = A.ptr[k + 1];
     for (int c0 = 0; c0 < Bp; c0 += 4 * LPN) {
         const float *vl = v + c0 + sl * 4;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int64_t r0 = e0; r0 < e1; r0 += 32) {
             const int64_t e = r0 + lane;
             int2 t = make_int2(0, 0);
-            if (e < e1) t = __ldcs(ent + e);
+            if (e < e1) t = load_entry<kW>(A, e);
             stage[w][lane] = t;
             __syncwarp();
             // NB gathers issued per lane before their FMAs
@@ -132,15 +159,14 @@ __global__ void __launch_bounds__(kPassWarps * 32, kPassMinBlocks)
     }
 }
 
-template <bool kRowPass>
-cudaError_t launch_pass(int lpn, const int64_t *ptr, const int2 *ent, const float *v,
-                        const float *base, float *out, int64_t n_out, int Bp, float mu,
-                        cudaStream_t s) {
+template <bool kRowPass, int kW>
+cudaError_t launch_pass_w(int lpn, const PassOperand &A, const float *v, const float *base,
+                          float *out, int64_t n_out, int Bp, float mu, cudaStream_t s) {
     const dim3 grid((unsigned)((n_out + kPassWarps - 1) / kPassWarps));
     const dim3 block(kPassWarps * 32);
-#define BSG_PASS(L)                                                                              \
-    case L:                                                                                      \
-        pass_kernel<L, kRowPass><<<grid, block, 0, s>>>(ptr, ent, v, base, out, n_out, Bp, mu); \
+#define BSG_PASS(L)                                                                          \
+    case L:                                                                                  \
+        pass_kernel<L, kRowPass, kW><<<grid, block, 0, s>>>(A, v, base, out, n_out, Bp, mu); \
         break;
     switch (lpn) {
         BSG_PASS(1)
@@ -155,6 +181,42 @@ cudaError_t launch_pass(int lpn, const int64_t *ptr, const int2 *ent, const floa
 #undef BSG_PASS
     add_launches(1);
     return cudaGetLastError();
+}
+
+template <bool kRowPass>
+cudaError_t launch_pass(int fmt, int lpn, const PassOperand &A, const float *v, const float *base,
+                        float *out, int64_t n_out, int Bp, float mu, cudaStream_t s) {
+    switch (fmt) {
+        case BSGDTV_FMT_F32_I32:
+            return launch_pass_w<kRowPass, 0>(lpn, A, v, base, out, n_out, Bp, mu, s);
+        case BSGDTV_FMT_F16_I16:
+            return launch_pass_w<kRowPass, BSGDTV_FMT_F16_I16>(lpn, A, v, base, out, n_out, Bp, mu, s);
+        case BSGDTV_FMT_BF16_I16:
+            return launch_pass_w<kRowPass, BSGDTV_FMT_BF16_I16>(lpn, A, v, base, out, n_out, Bp, mu, s);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+// Slot reset: slice b of the interleaved Y, X and R becomes (y_b, 0, y_b),
+// with y_b planar [n]; y_b null clears the slice (y = x = r = 0).
+__global__ void slice_reset_kernel(const float *__restrict__ yb, float *__restrict__ Y,
+                                   float *__restrict__ X, float *__restrict__ R, int64_t rows,
+                                   int64_t cols, int Bp, int b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < rows) {
+        const float y = yb ? yb[i] : 0.f;
+        Y[i * Bp + b] = y;
+        R[i * Bp + b] = y;
+    }
+    if (i < cols) X[i * Bp + b] = 0.f;
+}
+
+// Planar copy of slice b of an interleaved [n][Bp] array.
+__global__ void slice_gather_kernel(const float *__restrict__ in, float *__restrict__ out, int64_t n,
+                                    int Bp, int b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i * Bp + b];
 }
 
 // Planar [B][n] <-> interleaved [n][Bp] (only slices b < B are touched).
@@ -218,8 +280,9 @@ struct bsgdtv_batch_ctx {
     int64_t rows = 0, cols = 0, nnz = 0;
     int img_h = 0, img_w = 0, B = 0, Bp = 0, lpn = 1;
     std::vector<void *> allocs;
-    int64_t *row_ptr = nullptr, *col_ptr = nullptr;
-    int2 *ent_r = nullptr, *ent_c = nullptr;   // A in CSR / CSC as packed (weight, idx * Bp)
+    int fmt = BSGDTV_FMT_F32_I32;
+    PassOperand op_r = {}, op_c = {};   // A in CSR / CSC: entries (weight, idx * Bp)
+    float *ystage = nullptr;            // [max(rows, cols)] planar staging for one slice
     float *X = nullptr, *Xhat = nullptr, *Y = nullptr, *R[2] = {nullptr, nullptr};   // interleaved
     float *Xp = nullptr, *Xhp = nullptr;                                           // planar [B][cols]
     float *fp = nullptr, *fq = nullptr, *fpp = nullptr, *fqp = nullptr;            // planar FGP duals
@@ -301,11 +364,11 @@ int benqueue_epoch(bsgdtv_batch_ctx *h, int par, int fgp_iters, cudaStream_t s,
     const bool prox = any_prox(h, fgp_iters);
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[0], s, cudaEventRecordExternal));
     // r^k = y - A x^k (reads x before the column pass updates it)
-    BSG_CUDA(launch_pass<true>(h->lpn, h->row_ptr, h->ent_r, h->X, h->Y, h->R[1 - par], h->rows,
-                               h->Bp, 0.f, s));
+    BSG_CUDA(launch_pass<true>(h->fmt, h->lpn, h->op_r, h->X, h->Y, h->R[1 - par], h->rows, h->Bp,
+                               0.f, s));
     // x^ = x^k + mu * 2 A^T r^{k-1}
-    BSG_CUDA(launch_pass<false>(h->lpn, h->col_ptr, h->ent_c, h->R[par], h->X,
-                                prox ? h->Xhat : h->X, h->cols, h->Bp, (float)h->mu, s));
+    BSG_CUDA(launch_pass<false>(h->fmt, h->lpn, h->op_c, h->R[par], h->X, prox ? h->Xhat : h->X,
+                                h->cols, h->Bp, (float)h->mu, s));
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[1], s, cudaEventRecordExternal));
     if (prox) {
         const int64_t c = h->cols;
@@ -384,33 +447,57 @@ int bbuild_graphs(bsgdtv_batch_ctx *h, int fgp_iters) {
     return BSGDTV_OK;
 }
 
-int2 pack_entry(double a, int64_t idx, int Bp) {
-    const float f = (float)a;
-    int bits;
-    std::memcpy(&bits, &f, sizeof(bits));
-    return make_int2(bits, (int)(idx * Bp));
-}
+// Packed CSR of A and its CSC (rows ascending inside each column): weights
+// as the format stores them, element offsets idx * Bp.
+struct PackedOperator {
+    std::vector<int64_t> col_ptr;
+    std::vector<int2> ent_r, ent_c;                // FP32 weights
+    std::vector<uint16_t> w_r, w_c;                // 16-bit weights
+    std::vector<int32_t> off_r, off_c;
+};
 
-// Packed CSR of A and its CSC (rows ascending inside each column), weights
-// rounded to FP32, element offsets idx * Bp.
 void pack_operator(int64_t rows, int64_t cols, const int64_t *row_ptr, const int32_t *col_idx,
-                   const double *vals, int Bp, std::vector<int2> &ent_r,
-                   std::vector<int64_t> &col_ptr, std::vector<int2> &ent_c) {
+                   const double *vals, int Bp, int fmt, PackedOperator &P) {
     const int64_t nnz = row_ptr[rows];
-    ent_r.resize(nnz);
-    for (int64_t e = 0; e < nnz; ++e) ent_r[e] = pack_entry(vals[e], col_idx[e], Bp);
-    col_ptr.assign(cols + 1, 0);
-    for (int64_t e = 0; e < nnz; ++e) col_ptr[col_idx[e] + 1]++;
-    for (int64_t c = 0; c < cols; ++c) col_ptr[c + 1] += col_ptr[c];
-    ent_c.resize(nnz);
-    std::vector<int64_t> cur(col_ptr.begin(), col_ptr.end() - 1);
+    const bool f32 = (fmt == BSGDTV_FMT_F32_I32);
+    auto put = [&](std::vector<int2> &ent, std::vector<uint16_t> &w, std::vector<int32_t> &off,
+                   int64_t k, double a, int64_t idx) {
+        const int32_t o = (int32_t)(idx * Bp);
+        if (f32) {
+            const float f = (float)a;
+            int bits;
+            std::memcpy(&bits, &f, sizeof(bits));
+            ent[k] = make_int2(bits, o);
+        } else {
+            w[k] = (fmt == BSGDTV_FMT_F16_I16) ? double_to_half_bits(a) : double_to_bf16_bits(a);
+            off[k] = o;
+        }
+    };
+    if (f32) {
+        P.ent_r.resize(nnz);
+        P.ent_c.resize(nnz);
+    } else {
+        P.w_r.resize(nnz);
+        P.w_c.resize(nnz);
+        P.off_r.resize(nnz);
+        P.off_c.resize(nnz);
+    }
+    for (int64_t e = 0; e < nnz; ++e) put(P.ent_r, P.w_r, P.off_r, e, vals[e], col_idx[e]);
+    P.col_ptr.assign(cols + 1, 0);
+    for (int64_t e = 0; e < nnz; ++e) P.col_ptr[col_idx[e] + 1]++;
+    for (int64_t c = 0; c < cols; ++c) P.col_ptr[c + 1] += P.col_ptr[c];
+    std::vector<int64_t> cur(P.col_ptr.begin(), P.col_ptr.end() - 1);
     for (int64_t r = 0; r < rows; ++r)
         for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e)
-            ent_c[cur[col_idx[e]]++] = pack_entry(vals[e], r, Bp);
+            put(P.ent_c, P.w_c, P.off_c, cur[col_idx[e]]++, vals[e], r);
 }
 
-int validate_csr(int64_t rows, int64_t cols, int img_h, int img_w, const int64_t *row_ptr,
-                 const int32_t *col_idx, const double *vals) {
+}  // namespace
+
+namespace bsgdtv {
+
+int validate_image_csr(int64_t rows, int64_t cols, int img_h, int img_w, const int64_t *row_ptr,
+                       const int32_t *col_idx, const double *vals) {
     if (!row_ptr || !col_idx || !vals) return fail(BSGDTV_ERR_INVALID_ARG, "null CSR array");
     if (rows < 1 || cols < 1 || img_h < 1 || img_w < 1 || (int64_t)img_h * img_w != cols)
         return fail(BSGDTV_ERR_INVALID_ARG, "bad sizes: need rows >= 1 and cols == img_h*img_w");
@@ -430,17 +517,20 @@ int validate_csr(int64_t rows, int64_t cols, int img_h, int img_w, const int64_t
     return BSGDTV_OK;
 }
 
-}  // namespace
+}  // namespace bsgdtv
 
 extern "C" {
 
-int bsgdtv_batch_create_csr(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int img_h, int img_w,
-                            const int64_t *row_ptr, const int32_t *col_idx, const double *vals,
-                            int slices, void *stream) {
+int bsgdtv_batch_create_csr_ex(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int img_h,
+                               int img_w, const int64_t *row_ptr, const int32_t *col_idx,
+                               const double *vals, int slices, int format, void *stream) {
     if (!out) return fail(BSGDTV_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     if (slices < 1 || slices > 4096) return fail(BSGDTV_ERR_INVALID_ARG, "slices must be in [1, 4096]");
-    BSG_CHECK(validate_csr(rows, cols, img_h, img_w, row_ptr, col_idx, vals));
+    if (format != BSGDTV_FMT_F32_I32 && format != BSGDTV_FMT_F16_I16 && format != BSGDTV_FMT_BF16_I16)
+        return fail(format == BSGDTV_FMT_F32_I16 ? BSGDTV_ERR_UNSUPPORTED : BSGDTV_ERR_INVALID_ARG,
+                    "batch formats: BSGDTV_FMT_F32_I32, BSGDTV_FMT_F16_I16, BSGDTV_FMT_BF16_I16");
+    BSG_CHECK(validate_image_csr(rows, cols, img_h, img_w, row_ptr, col_idx, vals));
     std::unique_ptr<bsgdtv_batch_ctx> h(new (std::nothrow) bsgdtv_batch_ctx());
     if (!h) return fail(BSGDTV_ERR_OOM, "host allocation");
     BSG_CUDA(cudaGetDevice(&h->device));
@@ -451,23 +541,43 @@ int bsgdtv_batch_create_csr(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int
     h->img_h = img_h;
     h->img_w = img_w;
     h->B = slices;
+    h->fmt = format;
     slice_stride(slices, h->Bp, h->lpn);
     if (std::max(rows, cols) * h->Bp > INT32_MAX)
         return fail(BSGDTV_ERR_UNSUPPORTED, "max(rows, cols) * padded slices must fit int32");
     bsgdtv_batch_ctx *hp = h.get();
     int rc = BSGDTV_OK;
     try {
-        std::vector<int2> ent_r, ent_c;
-        std::vector<int64_t> cptr;
-        pack_operator(rows, cols, row_ptr, col_idx, vals, h->Bp, ent_r, cptr, ent_c);
+        PackedOperator P;
+        pack_operator(rows, cols, row_ptr, col_idx, vals, h->Bp, format, P);
         const size_t Ri = (size_t)rows * h->Bp, Ci = (size_t)cols * h->Bp;
         const size_t Cp = (size_t)cols * slices;
         rc = [&]() -> int {
             BSG_CUDA(cudaStreamCreateWithFlags(&hp->cap_stream, cudaStreamNonBlocking));
-            BSG_CHECK(bupload(hp, &hp->row_ptr, row_ptr, rows + 1));
-            BSG_CHECK(bupload(hp, &hp->ent_r, ent_r.data(), hp->nnz));
-            BSG_CHECK(bupload(hp, &hp->col_ptr, cptr.data(), cols + 1));
-            BSG_CHECK(bupload(hp, &hp->ent_c, ent_c.data(), hp->nnz));
+            int64_t *rp = nullptr, *cp = nullptr;
+            BSG_CHECK(bupload(hp, &rp, row_ptr, rows + 1));
+            BSG_CHECK(bupload(hp, &cp, P.col_ptr.data(), cols + 1));
+            hp->op_r.ptr = rp;
+            hp->op_c.ptr = cp;
+            if (format == BSGDTV_FMT_F32_I32) {
+                int2 *er = nullptr, *ec = nullptr;
+                BSG_CHECK(bupload(hp, &er, P.ent_r.data(), hp->nnz));
+                BSG_CHECK(bupload(hp, &ec, P.ent_c.data(), hp->nnz));
+                hp->op_r.ent = er;
+                hp->op_c.ent = ec;
+            } else {
+                uint16_t *wr = nullptr, *wc = nullptr;
+                int32_t *orr = nullptr, *oc = nullptr;
+                BSG_CHECK(bupload(hp, &wr, P.w_r.data(), hp->nnz));
+                BSG_CHECK(bupload(hp, &orr, P.off_r.data(), hp->nnz));
+                BSG_CHECK(bupload(hp, &wc, P.w_c.data(), hp->nnz));
+                BSG_CHECK(bupload(hp, &oc, P.off_c.data(), hp->nnz));
+                hp->op_r.w16 = wr;
+                hp->op_r.off = orr;
+                hp->op_c.w16 = wc;
+                hp->op_c.off = oc;
+            }
+            BSG_CHECK(balloc(hp, &hp->ystage, (size_t)std::max(rows, cols)));
             for (float **p : {&hp->X, &hp->Xhat}) BSG_CHECK(balloc(hp, p, Ci));
             for (float **p : {&hp->Y, &hp->R[0], &hp->R[1]}) BSG_CHECK(balloc(hp, p, Ri));
             for (float **p : {&hp->Xp, &hp->Xhp, &hp->fp, &hp->fq, &hp->fpp, &hp->fqp})
@@ -491,6 +601,24 @@ int bsgdtv_batch_create_csr(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int
     }
     *out = h.release();
     return BSGDTV_OK;
+}
+
+int64_t bsgdtv_batch_device_bytes(int64_t rows, int64_t cols, int64_t nnz, int slices, int format) {
+    if (rows < 1 || cols < 1 || nnz < 0 || slices < 1) return -1;
+    int Bp = 0, lpn = 0;
+    slice_stride(slices, Bp, lpn);
+    const int64_t per_nz = (format == BSGDTV_FMT_F32_I32) ? 8 : 6;
+    const int64_t a = 2 * (nnz * per_nz + 8 * (rows + cols + 2));
+    const int64_t inter = 4 * (int64_t)Bp * (2 * cols + 3 * rows);
+    const int64_t planar = 4 * (int64_t)slices * 6 * cols;
+    return a + inter + planar + 4 * (std::max(rows, cols) + slices + 64) + 4 * 4096;
+}
+
+int bsgdtv_batch_create_csr(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int img_h, int img_w,
+                            const int64_t *row_ptr, const int32_t *col_idx, const double *vals,
+                            int slices, void *stream) {
+    return bsgdtv_batch_create_csr_ex(out, rows, cols, img_h, img_w, row_ptr, col_idx, vals, slices,
+                                      BSGDTV_FMT_F32_I32, stream);
 }
 
 void bsgdtv_batch_destroy(bsgdtv_batch_t h) {
@@ -606,6 +734,59 @@ int bsgdtv_batch_get_x(bsgdtv_batch_t h, float *x, int out_on_device) {
     const int64_t c = h->cols;
     BSG_CUDA(launch_transpose(h->X, h->Xp, c, h->B, h->Bp, true, h->stream));
     BSG_CUDA(cudaMemcpyAsync(x, h->Xp, (size_t)c * h->B * sizeof(float),
+                             out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             h->stream));
+    if (!out_on_device) BSG_CUDA(cudaStreamSynchronize(h->stream));
+    return BSGDTV_OK;
+}
+
+int bsgdtv_batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_device, double lambda) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (!h->has_data) return fail(BSGDTV_ERR_STATE, "set_slice before set_data");
+    if (b < 0 || b >= h->B) return fail(BSGDTV_ERR_INVALID_ARG, "slice index out of range");
+    if (!(lambda >= 0.0) || !std::isfinite(lambda))
+        return fail(BSGDTV_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+    BSG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    const int64_t rows = h->rows;
+    if (y && !y_on_device)
+        for (int64_t i = 0; i < rows; ++i)
+            if (!std::isfinite(y[i])) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+    if (y) {
+        BSG_CUDA(cudaMemcpyAsync(h->ystage, y, (size_t)rows * sizeof(float),
+                                 y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        if (y_on_device) {
+            int hflag = 0;
+            BSG_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+            BSG_CUDA(launch_check_finite(h->ystage, rows, h->flag, s));
+            BSG_CUDA(cudaMemcpyAsync(&hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+            BSG_CUDA(cudaStreamSynchronize(s));
+            if (hflag) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+        }
+    }
+    const double lam = y ? lambda : 0.0;
+    const int64_t n = std::max(rows, h->cols);
+    slice_reset_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y ? h->ystage : nullptr, h->Y, h->X,
+                                                                   h->R[h->cur], rows, h->cols, h->Bp, b);
+    add_launches(1);
+    BSG_CUDA(cudaGetLastError());
+    const float tau = (float)(h->mu * lam);
+    BSG_CUDA(cudaMemcpyAsync(h->tau + b, &tau, sizeof(float), cudaMemcpyHostToDevice, s));
+    const bool prox_before = any_prox(h, 1);
+    h->lambdas[b] = lam;
+    if (any_prox(h, 1) != prox_before) bdrop_graphs(h);   // the epoch gains or loses its prox
+    return BSGDTV_OK;
+}
+
+int bsgdtv_batch_get_slice_x(bsgdtv_batch_t h, int b, float *x, int out_on_device) {
+    if (!h || !x) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    if (b < 0 || b >= h->B) return fail(BSGDTV_ERR_INVALID_ARG, "slice index out of range");
+    BSG_CUDA(cudaSetDevice(h->device));
+    const int64_t c = h->cols;
+    slice_gather_kernel<<<(unsigned)((c + 255) / 256), 256, 0, h->stream>>>(h->X, h->ystage, c, h->Bp, b);
+    add_launches(1);
+    BSG_CUDA(cudaGetLastError());
+    BSG_CUDA(cudaMemcpyAsync(x, h->ystage, (size_t)c * sizeof(float),
                              out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              h->stream));
     if (!out_on_device) BSG_CUDA(cudaStreamSynchronize(h->stream));

@@ -229,4 +229,9 @@ cudaError_t launch_fgp(const float *b, float *x, int h, int w, float tau, int it
                        const float *mom, FgpScratch sc, cudaStream_t s, bool pdl = false);
 void fgp_momentum_host(int iters, std::vector<float> &mom);
 
+// batch.cu: host check of a CSR image operator (sizes, sorted in-range
+// columns, finite weights); BSGDTV_* code.
+int validate_image_csr(int64_t rows, int64_t cols, int img_h, int img_w, const int64_t *row_ptr,
+                       const int32_t *col_idx, const double *vals);
+
 }  // namespace bsgdtv

@@ -146,3 +146,16 @@ def test_layout_reassembles_in_every_format(B, fmt):
     st = B.bsgdtv_layout_check(A.rows, A.cols_n, 37, 37, A.row_ptr, A.cols, A.vals, 3, 5, 55, 37,
                                fmt=fmt)
     assert st["nnz"] == A.nnz
+
+
+def test_batch_device_bytes(B):
+    """Host-only size of a batch: grows with slices and with the weight width,
+    rejects bad sizes."""
+    A = synth.parallel_beam_csr(64, 60, 91)
+    f32 = [B.bsgdtv_batch_device_bytes(A.rows, A.cols_n, A.nnz, s) for s in (1, 4, 32, 33, 64, 129)]
+    assert all(a <= b for a, b in zip(f32, f32[1:]))
+    assert f32[0] > 2 * 8 * A.nnz                       # A twice, 8 bytes per nonzero
+    f16 = B.bsgdtv_batch_device_bytes(A.rows, A.cols_n, A.nnz, 4, B.FMT_F16_I16)
+    assert f32[1] - f16 == 2 * 2 * A.nnz                # 6 instead of 8 bytes, twice
+    assert B.bsgdtv_batch_device_bytes(0, 10, 5, 1) == -1
+    assert B.bsgdtv_batch_device_bytes(10, 10, 5, 0) == -1

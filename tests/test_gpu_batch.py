@@ -200,3 +200,56 @@ def test_batch_ellipse512_full_size(B):
         x_ref, _ = oracle.run(A, Y[b].astype(np.float64), (wl.n, wl.n), wl.M, wl.N, wl.lam, mu, 3,
                               wl.fgp_iters, row_unit=wl.n_bins, col_unit=wl.n)
         assert rel(X[b], x_ref) <= 1e-5, (b, rel(X[b], x_ref))
+
+
+@pytest.mark.parametrize("fmt,bound", [(2, 2e-3), (3, 2e-2)])
+def test_batch_16bit_weights(B, fmt, bound):
+    """FP16 / BF16 weights: each slice matches the oracle on the rounded
+    operator to 1e-4; the distance to the oracle on the FP64 operator is the
+    quantisation error (FP16 <= 2e-3)."""
+    from _formats import stored_operator
+    name, slices, epochs, K = "ellipse64", 5, 30, 20
+    n, na, nb, ne, M, N = GEOM[name]
+    A, Y, mu = _setup(name, slices)
+    As = stored_operator(A, fmt)
+    lam = _lambdas(slices)
+    with B.BatchReconstructor(A, (n, n), slices, fmt=fmt) as bt:
+        bt.set_data(Y, lam, mu)
+        bt.run(epochs, K)
+        X = bt.x()
+    for b in range(slices):
+        x_s = _oracle_slice(name, As, Y[b], lam[b], mu, epochs, K)
+        assert rel(X[b], x_s) <= 1e-4, (b, rel(X[b], x_s))
+        x_64 = _oracle_slice(name, A, Y[b], lam[b], mu, epochs, K)
+        assert rel(X[b], x_64) <= bound
+
+
+def test_batch_set_slice_restarts_one_slot(B):
+    """A slot restarted mid-run follows Algorithm 1 from its own x^0 = 0 while
+    the other slots carry on; the restarted slot's iterates are bit-identical
+    to the same request run with every other slot empty."""
+    name, slices = "ellipse64", 6
+    n = GEOM[name][0]
+    A, Y, mu = _setup(name, slices)
+    lam = np.full(slices, 0.04)
+    A2, Ynew, _ = _setup(name, slices + 1)
+    y_new = Ynew[slices]                     # a seventh, different slice
+    with B.BatchReconstructor(A, (n, n), slices) as bt:
+        bt.set_data(Y, lam, mu)
+        bt.run(5, 20)
+        bt.set_slice(3, y_new, 0.08)
+        bt.run(10, 20)
+        X = bt.x()
+        x3 = bt.slice_x(3)
+        bt.set_slice(1, None, 0.0)          # emptied slot stays zero
+        bt.run(2, 20)
+        assert not np.any(bt.slice_x(1))
+    assert np.array_equal(x3, X[3])
+    assert rel(X[3], _oracle_slice(name, A, y_new, 0.08, mu, 10, 20)) <= 1e-4
+    for b in (0, 5):
+        assert rel(X[b], _oracle_slice(name, A, Y[b], 0.04, mu, 15, 20)) <= 1e-4
+    with B.BatchReconstructor(A, (n, n), slices) as alone:
+        alone.set_data(np.zeros_like(Y), np.zeros(slices), mu)
+        alone.set_slice(3, y_new, 0.08)
+        alone.run(10, 20)
+        assert np.array_equal(alone.slice_x(3), x3)

@@ -1,0 +1,144 @@
+"""GPU tests of the continuous-batching server: every request's result is
+bit-identical alone and in a mix of geometries, weights, budgets and arrival
+times, and matches the FP64 oracle (relative l2 <= 1e-4); admission keeps the
+groups' device bytes within the HBM budget."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_01307_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_01307_gb300 import build
+    build.build_library()
+    from paper_1812_01307_gb300 import bsgdtv
+    bsgdtv.load()
+    torch.cuda.set_device(0)
+    return bsgdtv
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+GEOMS = {"g64": (64, 60, 91, 10), "g37": (37, 11, 55, 4)}
+K = 12
+_geo = {}
+
+
+def geometry(name):
+    if name not in _geo:
+        n, na, nb, ne = GEOMS[name]
+        A = synth.parallel_beam_csr(n, na, nb)
+        u, _ = oracle.power_iteration(A)
+        _geo[name] = (A, n, ne, 0.9 / (2 * u))
+    return _geo[name]
+
+
+def request(name, seed):
+    A, n, ne, _ = geometry(name)
+    x = synth.phantom(n, ne, seed)
+    return synth.noisy_projections(A, x, seed).astype(np.float32)
+
+
+# (geometry, seed, lambda, epochs)
+MIX = [("g64", 1, 0.05, 14), ("g37", 2, 0.02, 9), ("g64", 3, 0.1, 23), ("g64", 4, 0.03, 5),
+       ("g37", 5, 0.08, 17), ("g64", 6, 0.05, 11), ("g37", 7, 0.04, 3), ("g64", 8, 0.07, 19),
+       ("g64", 9, 0.02, 8), ("g37", 10, 0.06, 12)]
+
+
+def _serve(B, reqs, slots=3, max_tick=4, budget=1 << 34, stagger=0):
+    """Runs the requests through one server; submits `stagger` at a time from
+    a second thread while the first ones run.  Returns {index: x}."""
+    with B.Server(budget, K, max_tick) as srv:
+        gid = {}
+        for name in sorted({r[0] for r in reqs}):
+            A, n, _, mu = geometry(name)
+            gid[name] = srv.add_geometry(A, (n, n), mu, slots=slots)
+        ids = {}
+
+        def submit(lo, hi):
+            for i in range(lo, hi):
+                name, seed, lam, ep = reqs[i]
+                ids[i] = srv.submit(gid[name], request(name, seed), lam, ep)
+
+        if stagger:
+            submit(0, stagger)
+            t = threading.Thread(target=lambda: (time.sleep(0.01), submit(stagger, len(reqs))))
+            t.start()
+            t.join()
+        else:
+            submit(0, len(reqs))
+        out = {}
+        for i, rid in ids.items():
+            x, lat, q = srv.wait(rid, gid[reqs[i][0]], timeout_s=120)
+            assert lat >= q >= 0
+            out[i] = x
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    return out, st
+
+
+def test_server_alone_equals_mixed_and_oracle(B):
+    mixed, st = _serve(B, MIX, stagger=4)
+    assert st["max_running"] >= 2                  # requests did share the device
+    for i in (0, 2, 4, 9):
+        alone, _ = _serve(B, [MIX[i]])
+        assert np.array_equal(alone[0], mixed[i]), i
+    for i in (1, 2, 6):
+        name, seed, lam, ep = MIX[i]
+        A, n, _, mu = geometry(name)
+        x_ref, _ = oracle.run(A, request(name, seed).astype(np.float64), (n, n), 1, 1, lam, mu, ep, K)
+        assert rel(mixed[i], x_ref) <= 1e-4, i
+
+
+def test_server_admission_by_hbm_budget(B):
+    """A budget that holds one group at a time: the two geometries take turns
+    (idle groups are released), every request completes."""
+    A, n, _, _ = geometry("g64")
+    one = B.bsgdtv_batch_device_bytes(A.rows, A.cols_n, A.nnz, 3)
+    reqs = MIX[:6]
+    out, st = _serve(B, reqs, budget=one + 4096)
+    assert st["groups_made"] >= 3 and st["device_bytes"] <= one + 4096
+    ref, _ = _serve(B, reqs)
+    for i in out:
+        assert np.array_equal(out[i], ref[i])
+
+
+def test_server_errors(B):
+    A, n, _, mu = geometry("g64")
+    with pytest.raises(B.BsgdtvError) as e:       # one group exceeds the budget
+        with B.Server(1 << 20, K) as srv:
+            srv.add_geometry(A, (n, n), mu, slots=3)
+    assert e.value.code == -2
+    with B.Server(1 << 34, K) as srv:
+        gid = srv.add_geometry(A, (n, n), mu, slots=2, prewarm=0)
+        y = request("g64", 1)
+        with pytest.raises(B.BsgdtvError):
+            srv.submit(gid + 5, y, 0.05, 3)
+        with pytest.raises(B.BsgdtvError):
+            srv.submit(gid, y, 0.05, 0)
+        bad = y.copy()
+        bad[7] = np.nan
+        with pytest.raises(B.BsgdtvError) as e:
+            srv.submit(gid, bad, 0.05, 3)
+        assert e.value.code == -6
+        rid = srv.submit(gid, y, 0.05, 400)
+        with pytest.raises(B.BsgdtvError) as e:
+            srv.wait(rid, gid, timeout_s=0.0)     # still running: timeout, request kept
+        assert e.value.code == -5
+        x, lat, _ = srv.wait(rid, gid, timeout_s=120)
+        assert np.all(np.isfinite(x)) and lat > 0
