@@ -46,8 +46,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-slices", type=int, default=64,
                     help="slices of the batched variant (many slices sharing one A); 0 skips it")
+    ap.add_argument("--served-requests", type=int, default=200,
+                    help="requests of the served stream (0 skips it)")
+    ap.add_argument("--served-full", action="store_true",
+                    help="include 1024x1024 requests (p = 0.1) in the served stream")
+    ap.add_argument("--served-budget-gb", type=float, default=64.0)
+    ap.add_argument("--served-tick", type=int, default=10, help="max epochs between admissions")
     ap.add_argument("--no-variants", action="store_true",
-                    help="skip the stored-format variants (FP32/16-bit index, FP16, BF16 weights)")
+                    help="skip every variant (stored formats and the batch)")
+    ap.add_argument("--variants", default="f32_i16,f16_i16,bf16_i16,batch",
+                    help="comma-separated variants to run: f32_i16, f16_i16, bf16_i16, batch")
     return ap.parse_args()
 
 
@@ -146,6 +154,93 @@ def kernel_source_hash():
         src = re.sub(r"//[^\n]*", "", src)
         h.update("".join(src.split()).encode())
     return h.hexdigest()
+
+
+# ------------------------------------------------------------- served stream
+def served_stream(args, B, synth):
+    """Continuous batching under a Poisson stream of reconstruction requests:
+    image n in {128, 256, 512} (p = .4, .3, .2, renormalised; 1024 with p = .1
+    under --served-full), angles = round(0.7 n), bins = ceil(sqrt(2) n) + 1,
+    lambda ~ U(0.01, 0.1), epochs ~ U{100..300}, 30 FGP iterations, FP16
+    weights, A cached per geometry.  Phase 1 submits every request at once
+    (saturated throughput); phase 2 replays them with Poisson arrivals at 0.7x
+    that rate.  Latency = submit -> x in host memory."""
+    import math
+    import threading
+
+    import numpy as np
+    sizes = [128, 256, 512] + ([1024] if args.served_full else [])
+    probs = np.array([0.4, 0.3, 0.2] + ([0.1] if args.served_full else []))
+    probs = probs / probs.sum()
+    ellipses = {128: 10, 256: 20, 512: 30, 1024: 40}
+    K, N, pool = 30, args.served_requests, 8
+    rng = np.random.default_rng(2024)
+    budget = int(args.served_budget_gb * 2 ** 30)
+    t_setup = time.perf_counter()
+    geoms = {}
+    srv = B.Server(budget, K, args.served_tick)
+    for n in sizes:
+        na, nb = int(round(0.7 * n)), int(math.ceil(math.sqrt(2) * n)) + 1
+        A = synth.parallel_beam_csr(n, na, nb)
+        with B.Reconstructor(A, (n, n), 1, 1) as rec:
+            u, _ = rec.estimate_umax(300, 1e-9)
+        gid = srv.add_geometry(A, (n, n), 0.9 / (2 * u), slots=32, fmt=B.FMT_F16_I16, prewarm=1)
+        ys = [synth.noisy_projections(A, synth.phantom(n, ellipses[n], s), s).astype(np.float32)
+              for s in range(pool)]
+        geoms[n] = (gid, ys, A.nnz)
+    reqs = []
+    for i in range(N):
+        n = int(rng.choice(sizes, p=probs))
+        reqs.append((n, int(rng.integers(pool)), float(rng.uniform(0.01, 0.1)), int(rng.integers(100, 301))))
+    t_setup = time.perf_counter() - t_setup
+
+    def run(arrivals):
+        ids = [None] * N
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i, (n, k, lam, ep) in enumerate(reqs):
+                wait = arrivals[i] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+                ids[i] = srv.submit(geoms[n][0], geoms[n][1][k], lam, ep)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, done_at = [], []
+        for i in range(N):
+            while ids[i] is None:
+                time.sleep(0.0005)
+            x, l, _ = srv.wait(ids[i], geoms[reqs[i][0]][0], timeout_s=600)
+            lat.append(l)
+        th.join()
+        return np.array(lat), time.perf_counter() - t0
+
+    st0 = srv.stats()
+    lat_sat, span_sat = run(np.zeros(N))
+    sat_rps = N / span_sat
+    rate = 0.7 * sat_rps
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, N))
+    st1 = srv.stats()
+    lat, span = run(arrivals)
+    st2 = srv.stats()
+    srv.close()
+    slice_epochs = sum(r[3] for r in reqs)
+    mix = {str(n): int(sum(1 for r in reqs if r[0] == n)) for n in sizes}
+    return {"requests": N, "mix": mix, "fgp_iters": K, "epochs": "U{100..300}", "lambda": "U(0.01,0.1)",
+            "weights": "f16", "slots_per_group": 32, "hbm_budget_gb": args.served_budget_gb,
+            "max_tick_epochs": args.served_tick,
+            "saturated": {"requests_per_s": sat_rps, "slice_epochs_per_s": slice_epochs / span_sat,
+                          "p50_ms": 1e3 * float(np.percentile(lat_sat, 50)),
+                          "p99_ms": 1e3 * float(np.percentile(lat_sat, 99))},
+            "poisson_rate_per_s": rate,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "mean_ms": 1e3 * float(lat.mean()), "throughput_requests_per_s": N / span,
+            "slice_epochs_per_s": slice_epochs / span,
+            "max_running": st2["max_running"], "groups_made": st2["groups_made"],
+            "ticks": st2["ticks"] - st1["ticks"], "setup_s": t_setup,
+            "note": "latency = submit to x in host memory; inputs drawn from a pool of %d seeded "
+                    "phantoms per size; phase 1 all at once, phase 2 Poisson at 0.7x phase 1" % pool}
 
 
 # ------------------------------------------------------------- CPU oracle
@@ -279,7 +374,7 @@ def run_ours(args):
     variants = {}
     if not args.no_variants:
         Kv = max(1, min(K, 1000))
-        for name in ("f32_i16", "f16_i16", "bf16_i16"):
+        for name in [v for v in ("f32_i16", "f16_i16", "bf16_i16") if v in args.variants.split(",")]:
             fmt = B.FORMATS[name]
             rv = B.Reconstructor(P.A, (wl.n, wl.n), wl.M, wl.N, row_unit=wl.n_bins, col_unit=wl.n, fmt=fmt)
             rv.set_data(y_dev, wl.lam, mu)
@@ -301,7 +396,7 @@ def run_ours(args):
                               "achieved_gbs": ach, "frac": ach / peak}
 
     # many slices sharing one A: B slices of the same geometry, one batch handle
-    if not args.no_variants and args.batch_slices > 0:
+    if not args.no_variants and args.batch_slices > 0 and "batch" in args.variants.split(","):
         Bs = args.batch_slices
         _, Ys = synth.slice_stack(P.A, wl.n, wl.n_ellipses, Bs, seed=wl.seed)
         Ys_dev = torch.tensor(Ys, dtype=torch.float32, device=dev)
@@ -331,6 +426,10 @@ def run_ours(args):
                              "note": "two passes over A (CSR then CSC) per epoch, lanes = slices; "
                                      "x and r gathered from L2"}
 
+    served = None
+    if rank == 0 and world == 1 and args.served_requests > 0:
+        served = served_stream(args, B, synth)
+
     prod_avg_s = prod_ms / 1e3 / K
     per_launch = info["min_bytes_per_pass"]
     achieved = per_launch / prod_avg_s / 1e9
@@ -351,7 +450,7 @@ def run_ours(args):
                          "avg_launch_ms": prod_avg_s * 1e3,
                          "share_of_epoch": prod_ms / epoch_ms if epoch_ms > 0 else None},
             "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
-            "variants": variants or None}
+            "served": served, "variants": variants or None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, done, dt = oracle_epochs_per_s(P, mu, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "epochs/s", "cores": 1, "kind": "oracle",

@@ -72,8 +72,8 @@ def _oracle_slice(name, A, y, lam, mu, epochs, K):
 @pytest.mark.parametrize("name,slices,epochs,K,check", [
     ("ellipse64", 1, 30, 20, None),
     ("ellipse64", 5, 30, 20, None),
-    ("ellipse64", 33, 12, 20, [0, 1, 2, 31, 32]),        # float2 lanes, padded to 64
-    ("ellipse64", 70, 8, 20, [0, 5, 63, 64, 69]),        # float4 lanes, padded to 128
+    ("ellipse64", 33, 12, 20, [0, 1, 2, 31, 32]),        # 16 lanes per nonzero, padded to 64
+    ("ellipse64", 70, 8, 20, [0, 5, 63, 64, 69]),        # 32 lanes per nonzero, padded to 128
     ("ragged37", 130, 6, 9, [0, 1, 127, 128, 129]),      # two chunks of 128 slices
 ])
 def test_batch_matches_oracle_per_slice(B, name, slices, epochs, K, check):
