@@ -252,8 +252,36 @@ int bsgdtv_batch_create_csr_ex(bsgdtv_batch_t *out, int64_t rows, int64_t cols, 
 
 /* Host only: the device bytes a batch of these sizes allocates (A twice,
  * the interleaved and planar vectors, FGP fields), within a few KiB; -1 on
- * bad sizes.  Used for admission by free memory. */
+ * bad sizes; nnz = 0 for a matrix-free batch.  Used for admission by free
+ * memory. */
 int64_t bsgdtv_batch_device_bytes(int64_t rows, int64_t cols, int64_t nnz, int slices, int format);
+
+/* A matrix-free batch for the 2-D parallel-beam geometry of an n x n image
+ * (pixel size 1, centred), n_angles angles k*pi/n_angles and n_bins unit
+ * detector bins centred on the origin: the weights of A (exact intersection
+ * lengths of ray and pixel, the convention of the stored-matrix generator:
+ * half-open pixels, |sin|, |cos| < 1e-15 taken as 0) are computed on the fly
+ * in both passes, so A takes no device memory.  Rows are k*n_bins + d,
+ * columns s*n + t.  Each weight is formed in compensated FP32 and agrees with
+ * the FP64 intersection length to about 1e-7; the row and column passes use
+ * bit-identical weights.  Everything else is as for bsgdtv_batch_create_csr. */
+int bsgdtv_batch_create_parallel_beam(bsgdtv_batch_t *out, int n, int n_angles, int n_bins,
+                                      int slices, void *stream);
+
+/* Test hook: the weights the matrix-free row pass uses for the listed rays
+ * (host rays [n_rays], row indices), written per ray i to cols / vals
+ * [i*capacity ...] (host, n_rays*capacity entries) in the pass's order, with
+ * counts[i] entries (at most capacity kept).  Synchronous. */
+int bsgdtv_mf_ray_weights(int n, int n_angles, int n_bins, const int64_t *rays, int n_rays,
+                          int capacity, int32_t *cols, float *vals, int *counts);
+
+/* Largest eigenvalue u_max of A^T A for a batch's A (stored or matrix free)
+ * by power iteration from the all-ones vector on the batch's own passes (FP32
+ * products, FP64 norms and Rayleigh quotients), stopping at relative change
+ * <= rel_tol or max_iters.  Uses the batch's vectors as scratch: every slice
+ * must be set again (bsgdtv_batch_set_data) afterwards. */
+int bsgdtv_batch_estimate_umax(bsgdtv_batch_t h, int max_iters, double rel_tol, double *u_max,
+                               int *iters);
 
 /* Releases every resource of the batch.  NULL is ignored. */
 void bsgdtv_batch_destroy(bsgdtv_batch_t h);

@@ -66,6 +66,9 @@ def load(path: str | None = None):
         "bsgdtv_batch_run_timed": (I32, [P, I32, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "bsgdtv_batch_get_x": (I32, [P, P, I32]),
         "bsgdtv_batch_device_bytes": (I64, [I64, I64, I64, I32, I32]),
+        "bsgdtv_batch_create_parallel_beam": (I32, [ctypes.POINTER(P), I32, I32, I32, I32, P]),
+        "bsgdtv_mf_ray_weights": (I32, [I32, I32, I32, P, I32, I32, P, P, P]),
+        "bsgdtv_batch_estimate_umax": (I32, [P, I32, D, ctypes.POINTER(D), ctypes.POINTER(I32)]),
         "bsgdtv_server_create": (I32, [ctypes.POINTER(P), I64, I32, I32]),
         "bsgdtv_server_destroy": (None, [P]),
         "bsgdtv_server_add_geometry": (I32, [P, I64, I64, I32, I32, P, P, P, I32, I32, D, I32, ctypes.POINTER(I32)]),
@@ -97,6 +100,7 @@ def exported_symbols():
             "bsgdtv_batch_get_slice_x", "bsgdtv_batch_device_bytes", "bsgdtv_server_create",
             "bsgdtv_server_destroy", "bsgdtv_server_add_geometry", "bsgdtv_server_submit",
             "bsgdtv_server_poll", "bsgdtv_server_wait", "bsgdtv_server_stats",
+            "bsgdtv_batch_create_parallel_beam", "bsgdtv_mf_ray_weights", "bsgdtv_batch_estimate_umax",
             "bsgdtv_launch_count", "bsgdtv_last_error", "bsgdtv_strerror"]
 
 
@@ -432,6 +436,38 @@ def bsgdtv_batch_get_slice_x(h, b, out):
     return out
 
 
+def bsgdtv_batch_create_parallel_beam(n, n_angles, n_bins, slices, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().bsgdtv_batch_create_parallel_beam(ctypes.byref(h), int(n), int(n_angles),
+                                                    int(n_bins), int(slices),
+                                                    stream if stream is not None else current_stream()),
+           "bsgdtv_batch_create_parallel_beam")
+    return h
+
+
+def bsgdtv_mf_ray_weights(n, n_angles, n_bins, rays, capacity=None):
+    """Weights of the matrix-free row pass for the given rays: list of
+    (cols int32, vals float32) per ray."""
+    rays = np.ascontiguousarray(rays, dtype=np.int64)
+    cap = int(capacity or 3 * n + 3)
+    cols = np.zeros(rays.size * cap, dtype=np.int32)
+    vals = np.zeros(rays.size * cap, dtype=np.float32)
+    cnt = np.zeros(rays.size, dtype=np.int32)
+    _check(load().bsgdtv_mf_ray_weights(int(n), int(n_angles), int(n_bins), _host_ptr(rays, np.int64),
+                                        int(rays.size), cap, _host_ptr(cols, np.int32),
+                                        _host_ptr(vals, np.float32), _host_ptr(cnt, np.int32)),
+           "bsgdtv_mf_ray_weights")
+    return [(cols[i * cap:i * cap + cnt[i]].copy(), vals[i * cap:i * cap + cnt[i]].copy())
+            for i in range(rays.size)]
+
+
+def bsgdtv_batch_estimate_umax(h, max_iters=1000, rel_tol=1e-9):
+    u, it = ctypes.c_double(), ctypes.c_int()
+    _check(load().bsgdtv_batch_estimate_umax(h, int(max_iters), float(rel_tol), ctypes.byref(u),
+                                             ctypes.byref(it)), "bsgdtv_batch_estimate_umax")
+    return u.value, it.value
+
+
 def bsgdtv_batch_device_bytes(rows, cols, nnz, slices, fmt=FMT_F32_I32) -> int:
     """Host only: device bytes of a batch of these sizes (-1 on bad sizes)."""
     return int(load().bsgdtv_batch_device_bytes(int(rows), int(cols), int(nnz), int(slices), int(fmt)))
@@ -567,12 +603,20 @@ class BatchReconstructor:
     """Owns one batch handle: B slices sharing the matrix A, each with its own
     y_b and lambda_b; ``set_data(Y, lambdas, mu)`` / ``run`` / ``x()``."""
 
-    def __init__(self, A, img_shape, slices, stream=None, fmt=FMT_F32_I32):
+    def __init__(self, A, img_shape, slices, stream=None, fmt=FMT_F32_I32, parallel_beam=None):
+        """`A`: host CSR, or None with parallel_beam = (n_angles, n_bins) for
+        the matrix-free projector of an img_shape = (n, n) image."""
         self.img_shape = tuple(img_shape)
-        self.rows, self.cols = int(A.rows), int(A.cols_n)
         self.slices = int(slices)
-        self.h = bsgdtv_batch_create_csr(self.rows, self.cols, img_shape[0], img_shape[1],
-                                         A.row_ptr, A.cols, A.vals, slices, stream, fmt)
+        if A is None:
+            n = int(img_shape[0])
+            na, nb = parallel_beam
+            self.rows, self.cols = int(na) * int(nb), n * n
+            self.h = bsgdtv_batch_create_parallel_beam(n, na, nb, slices, stream)
+        else:
+            self.rows, self.cols = int(A.rows), int(A.cols_n)
+            self.h = bsgdtv_batch_create_csr(self.rows, self.cols, img_shape[0], img_shape[1],
+                                             A.row_ptr, A.cols, A.vals, slices, stream, fmt)
 
     def close(self):
         if getattr(self, "h", None) is not None:
@@ -607,6 +651,9 @@ class BatchReconstructor:
 
     def set_slice(self, b, y, lam):
         bsgdtv_batch_set_slice(self.h, b, y, lam)
+
+    def estimate_umax(self, max_iters=1000, rel_tol=1e-9):
+        return bsgdtv_batch_estimate_umax(self.h, max_iters, rel_tol)
 
     def slice_x(self, b, out=None):
         if out is None:

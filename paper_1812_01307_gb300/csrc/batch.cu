@@ -33,6 +33,7 @@
 
 #include "bsgdtv_internal.h"
 #include "fgp_common.cuh"
+#include "matrix_free.h"
 
 namespace bsgdtv {
 namespace {
@@ -259,6 +260,33 @@ cudaError_t launch_transpose(const float *in, float *out, int64_t n, int B, int 
     return cudaGetLastError();
 }
 
+// Power iteration helpers on slice 0 of interleaved [n][Bp] vectors:
+// per-block FP64 partial sums of a*b (fixed grid, summed on the host in block
+// order), and v = s * w written to slice 0 (the other slices stay zero).
+constexpr int kDotBlocks = 512;
+
+__global__ void slice_dot_kernel(const float *__restrict__ a, const float *__restrict__ b,
+                                 int64_t n, int Bp, double *__restrict__ partials) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)a[i * Bp] * (double)b[i * Bp];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__global__ void slice_scale_kernel(const float *__restrict__ w, float *__restrict__ v, int64_t n,
+                                   int Bp, float scale) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i * Bp] = w ? scale * w[i * Bp] : scale;
+}
+
 // Slice stride Bp (B padded) and lanes per nonzero: a lane holds 4 slices,
 // so Bp = 4 * LPN for B <= 128 (LPN = 1 .. 32), else a multiple of 128 taken
 // in chunks of 128 by the full warp.
@@ -282,6 +310,8 @@ struct bsgdtv_batch_ctx {
     std::vector<void *> allocs;
     int fmt = BSGDTV_FMT_F32_I32;
     PassOperand op_r = {}, op_c = {};   // A in CSR / CSC: entries (weight, idx * Bp)
+    bool matrix_free = false;           // weights computed on the fly (parallel beam)
+    MfGeometry mfg;
     float *ystage = nullptr;            // [max(rows, cols)] planar staging for one slice
     float *X = nullptr, *Xhat = nullptr, *Y = nullptr, *R[2] = {nullptr, nullptr};   // interleaved
     float *Xp = nullptr, *Xhp = nullptr;                                           // planar [B][cols]
@@ -363,12 +393,18 @@ int benqueue_epoch(bsgdtv_batch_ctx *h, int par, int fgp_iters, cudaStream_t s,
                    cudaEvent_t *marks) {
     const bool prox = any_prox(h, fgp_iters);
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[0], s, cudaEventRecordExternal));
-    // r^k = y - A x^k (reads x before the column pass updates it)
-    BSG_CUDA(launch_pass<true>(h->fmt, h->lpn, h->op_r, h->X, h->Y, h->R[1 - par], h->rows, h->Bp,
-                               0.f, s));
-    // x^ = x^k + mu * 2 A^T r^{k-1}
-    BSG_CUDA(launch_pass<false>(h->fmt, h->lpn, h->op_c, h->R[par], h->X, prox ? h->Xhat : h->X,
-                                h->cols, h->Bp, (float)h->mu, s));
+    if (h->matrix_free) {
+        BSG_CUDA(launch_mf_pass(true, h->lpn, h->mfg, h->X, h->Y, h->R[1 - par], h->Bp, 0.f, s));
+        BSG_CUDA(launch_mf_pass(false, h->lpn, h->mfg, h->R[par], h->X, prox ? h->Xhat : h->X, h->Bp,
+                                (float)h->mu, s));
+    } else {
+        // r^k = y - A x^k (reads x before the column pass updates it)
+        BSG_CUDA(launch_pass<true>(h->fmt, h->lpn, h->op_r, h->X, h->Y, h->R[1 - par], h->rows,
+                                   h->Bp, 0.f, s));
+        // x^ = x^k + mu * 2 A^T r^{k-1}
+        BSG_CUDA(launch_pass<false>(h->fmt, h->lpn, h->op_c, h->R[par], h->X, prox ? h->Xhat : h->X,
+                                    h->cols, h->Bp, (float)h->mu, s));
+    }
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[1], s, cudaEventRecordExternal));
     if (prox) {
         const int64_t c = h->cols;
@@ -519,6 +555,28 @@ int validate_image_csr(int64_t rows, int64_t cols, int img_h, int img_w, const i
 
 }  // namespace bsgdtv
 
+namespace {
+
+// Vectors of a batch (interleaved, planar, FGP fields, staging), zeroed.
+int alloc_vectors(bsgdtv_batch_ctx *hp) {
+    const size_t Ri = (size_t)hp->rows * hp->Bp, Ci = (size_t)hp->cols * hp->Bp;
+    const size_t Cp = (size_t)hp->cols * hp->B;
+    BSG_CHECK(balloc(hp, &hp->ystage, (size_t)std::max(hp->rows, hp->cols)));
+    for (float **p : {&hp->X, &hp->Xhat}) BSG_CHECK(balloc(hp, p, Ci));
+    for (float **p : {&hp->Y, &hp->R[0], &hp->R[1]}) BSG_CHECK(balloc(hp, p, Ri));
+    for (float **p : {&hp->Xp, &hp->Xhp, &hp->fp, &hp->fq, &hp->fpp, &hp->fqp})
+        BSG_CHECK(balloc(hp, p, Cp));
+    BSG_CHECK(balloc(hp, &hp->tau, (size_t)hp->B));
+    BSG_CHECK(balloc(hp, &hp->flag, 1));
+    // padded slices (b >= B) stay zero for good: y = x = r = 0 there
+    for (float *p : {hp->X, hp->Xhat}) BSG_CUDA(cudaMemsetAsync(p, 0, Ci * sizeof(float), hp->stream));
+    for (float *p : {hp->Y, hp->R[0], hp->R[1]})
+        BSG_CUDA(cudaMemsetAsync(p, 0, Ri * sizeof(float), hp->stream));
+    return BSGDTV_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int bsgdtv_batch_create_csr_ex(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int img_h,
@@ -550,8 +608,6 @@ int bsgdtv_batch_create_csr_ex(bsgdtv_batch_t *out, int64_t rows, int64_t cols, 
     try {
         PackedOperator P;
         pack_operator(rows, cols, row_ptr, col_idx, vals, h->Bp, format, P);
-        const size_t Ri = (size_t)rows * h->Bp, Ci = (size_t)cols * h->Bp;
-        const size_t Cp = (size_t)cols * slices;
         rc = [&]() -> int {
             BSG_CUDA(cudaStreamCreateWithFlags(&hp->cap_stream, cudaStreamNonBlocking));
             int64_t *rp = nullptr, *cp = nullptr;
@@ -577,18 +633,7 @@ int bsgdtv_batch_create_csr_ex(bsgdtv_batch_t *out, int64_t rows, int64_t cols, 
                 hp->op_c.w16 = wc;
                 hp->op_c.off = oc;
             }
-            BSG_CHECK(balloc(hp, &hp->ystage, (size_t)std::max(rows, cols)));
-            for (float **p : {&hp->X, &hp->Xhat}) BSG_CHECK(balloc(hp, p, Ci));
-            for (float **p : {&hp->Y, &hp->R[0], &hp->R[1]}) BSG_CHECK(balloc(hp, p, Ri));
-            for (float **p : {&hp->Xp, &hp->Xhp, &hp->fp, &hp->fq, &hp->fpp, &hp->fqp})
-                BSG_CHECK(balloc(hp, p, Cp));
-            BSG_CHECK(balloc(hp, &hp->tau, (size_t)slices));
-            BSG_CHECK(balloc(hp, &hp->flag, 1));
-            // padded slices (b >= B) stay zero for good: y = x = r = 0 there
-            for (float *p : {hp->X, hp->Xhat})
-                BSG_CUDA(cudaMemsetAsync(p, 0, Ci * sizeof(float), hp->stream));
-            for (float *p : {hp->Y, hp->R[0], hp->R[1]})
-                BSG_CUDA(cudaMemsetAsync(p, 0, Ri * sizeof(float), hp->stream));
+            BSG_CHECK(alloc_vectors(hp));
             BSG_CUDA(cudaStreamSynchronize(hp->stream));   // the host vectors die here
             return BSGDTV_OK;
         }();
@@ -612,6 +657,93 @@ int64_t bsgdtv_batch_device_bytes(int64_t rows, int64_t cols, int64_t nnz, int s
     const int64_t inter = 4 * (int64_t)Bp * (2 * cols + 3 * rows);
     const int64_t planar = 4 * (int64_t)slices * 6 * cols;
     return a + inter + planar + 4 * (std::max(rows, cols) + slices + 64) + 4 * 4096;
+}
+
+int bsgdtv_batch_create_parallel_beam(bsgdtv_batch_t *out, int n, int n_angles, int n_bins,
+                                      int slices, void *stream) {
+    if (!out) return fail(BSGDTV_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (slices < 1 || slices > 4096) return fail(BSGDTV_ERR_INVALID_ARG, "slices must be in [1, 4096]");
+    if (n < 1 || n > 16384 || n_angles < 1 || n_bins < 1 || (int64_t)n_angles * n_bins > INT32_MAX)
+        return fail(BSGDTV_ERR_INVALID_ARG, "need 1 <= n <= 16384, n_angles, n_bins >= 1");
+    std::unique_ptr<bsgdtv_batch_ctx> h(new (std::nothrow) bsgdtv_batch_ctx());
+    if (!h) return fail(BSGDTV_ERR_OOM, "host allocation");
+    BSG_CUDA(cudaGetDevice(&h->device));
+    h->stream = (cudaStream_t)stream;
+    h->rows = (int64_t)n_angles * n_bins;
+    h->cols = (int64_t)n * n;
+    h->img_h = h->img_w = n;
+    h->B = slices;
+    h->matrix_free = true;
+    slice_stride(slices, h->Bp, h->lpn);
+    if (std::max(h->rows, h->cols) * h->Bp > INT32_MAX)
+        return fail(BSGDTV_ERR_UNSUPPORTED, "max(rows, cols) * padded slices must fit int32");
+    bsgdtv_batch_ctx *hp = h.get();
+    int rc = [&]() -> int {
+        std::vector<AngleGeo> table;
+        mf_angle_table(n_angles, table);
+        AngleGeo *geo = nullptr;
+        BSG_CUDA(cudaStreamCreateWithFlags(&hp->cap_stream, cudaStreamNonBlocking));
+        BSG_CHECK(bupload(hp, &geo, table.data(), table.size()));
+        hp->mfg.geo = geo;
+        hp->mfg.n = n;
+        hp->mfg.n_angles = n_angles;
+        hp->mfg.n_bins = n_bins;
+        BSG_CHECK(alloc_vectors(hp));
+        BSG_CUDA(cudaStreamSynchronize(hp->stream));   // the host table dies here
+        return BSGDTV_OK;
+    }();
+    if (rc != BSGDTV_OK) {
+        bsgdtv_batch_destroy(h.release());
+        return rc;
+    }
+    *out = h.release();
+    return BSGDTV_OK;
+}
+
+int bsgdtv_mf_ray_weights(int n, int n_angles, int n_bins, const int64_t *rays, int n_rays,
+                          int capacity, int32_t *cols, float *vals, int *counts) {
+    if (!rays || !cols || !vals || !counts || n < 1 || n_angles < 1 || n_bins < 1 || n_rays < 0 ||
+        capacity < 1)
+        return fail(BSGDTV_ERR_INVALID_ARG, "bad argument");
+    const int64_t total_rays = (int64_t)n_angles * n_bins;
+    for (int i = 0; i < n_rays; ++i)
+        if (rays[i] < 0 || rays[i] >= total_rays) return fail(BSGDTV_ERR_INVALID_ARG, "ray out of range");
+    if (n_rays == 0) return BSGDTV_OK;
+    std::vector<AngleGeo> table;
+    mf_angle_table(n_angles, table);
+    const size_t cap = (size_t)n_rays * capacity;
+    void *buf = nullptr;
+    const size_t bytes = table.size() * sizeof(AngleGeo) + n_rays * sizeof(int64_t) +
+                         cap * (sizeof(int32_t) + sizeof(float)) + n_rays * sizeof(int) + 1024;
+    BSG_CUDA(cudaMalloc(&buf, bytes));
+    char *p = static_cast<char *>(buf);
+    auto take = [&](size_t b) {
+        char *q = p;
+        p += (b + 255) / 256 * 256;
+        return q;
+    };
+    AngleGeo *geo = reinterpret_cast<AngleGeo *>(take(table.size() * sizeof(AngleGeo)));
+    int64_t *d_rays = reinterpret_cast<int64_t *>(take(n_rays * sizeof(int64_t)));
+    int32_t *d_cols = reinterpret_cast<int32_t *>(take(cap * sizeof(int32_t)));
+    float *d_vals = reinterpret_cast<float *>(take(cap * sizeof(float)));
+    int *d_cnt = reinterpret_cast<int *>(take(n_rays * sizeof(int)));
+    int rc = [&]() -> int {
+        BSG_CUDA(cudaMemcpy(geo, table.data(), table.size() * sizeof(AngleGeo), cudaMemcpyHostToDevice));
+        BSG_CUDA(cudaMemcpy(d_rays, rays, n_rays * sizeof(int64_t), cudaMemcpyHostToDevice));
+        MfGeometry G;
+        G.geo = geo;
+        G.n = n;
+        G.n_angles = n_angles;
+        G.n_bins = n_bins;
+        BSG_CUDA(launch_mf_weights(G, d_rays, n_rays, capacity, d_cols, d_vals, d_cnt, 0));
+        BSG_CUDA(cudaMemcpy(cols, d_cols, cap * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        BSG_CUDA(cudaMemcpy(vals, d_vals, cap * sizeof(float), cudaMemcpyDeviceToHost));
+        BSG_CUDA(cudaMemcpy(counts, d_cnt, n_rays * sizeof(int), cudaMemcpyDeviceToHost));
+        return BSGDTV_OK;
+    }();
+    cudaFree(buf);
+    return rc;
 }
 
 int bsgdtv_batch_create_csr(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int img_h, int img_w,
@@ -775,6 +907,73 @@ int bsgdtv_batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_dev
     const bool prox_before = any_prox(h, 1);
     h->lambdas[b] = lam;
     if (any_prox(h, 1) != prox_before) bdrop_graphs(h);   // the epoch gains or loses its prox
+    return BSGDTV_OK;
+}
+
+int bsgdtv_batch_estimate_umax(bsgdtv_batch_t h, int max_iters, double rel_tol, double *u_max,
+                               int *iters) {
+    if (!h || max_iters < 1 || !(rel_tol >= 0.0)) return fail(BSGDTV_ERR_INVALID_ARG, "bad argument");
+    BSG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    const int64_t c = h->cols, R = h->rows;
+    std::vector<double> part(kDotBlocks);
+    double *d_part = nullptr;
+    BSG_CHECK(balloc(h, &d_part, kDotBlocks));   // kept with the batch's memory
+    auto dot = [&](const float *a, const float *b, double *out) -> int {
+        slice_dot_kernel<<<kDotBlocks, 256, 0, s>>>(a, b, c, h->Bp, d_part);
+        add_launches(1);
+        BSG_CUDA(cudaGetLastError());
+        BSG_CUDA(cudaMemcpyAsync(part.data(), d_part, kDotBlocks * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s));
+        BSG_CUDA(cudaStreamSynchronize(s));
+        double acc = 0.0;
+        for (double v : part) acc += v;
+        *out = acc;
+        return BSGDTV_OK;
+    };
+    const unsigned grid = (unsigned)((c + 255) / 256);
+    // all slices zero; v = ones / sqrt(c) in slice 0 of X; R[0] = 0 stands for y = 0
+    BSG_CUDA(cudaMemsetAsync(h->X, 0, (size_t)c * h->Bp * sizeof(float), s));
+    BSG_CUDA(cudaMemsetAsync(h->R[0], 0, (size_t)R * h->Bp * sizeof(float), s));
+    slice_scale_kernel<<<grid, 256, 0, s>>>(nullptr, h->X, c, h->Bp, (float)(1.0 / std::sqrt((double)c)));
+    add_launches(1);
+    BSG_CUDA(cudaGetLastError());
+    double u = 0.0;
+    int it = 0;
+    for (it = 1; it <= max_iters; ++it) {
+        BSG_CUDA(cudaMemsetAsync(h->Xhat, 0, (size_t)c * h->Bp * sizeof(float), s));
+        // R1 = 0 - A v; Xhat = 0 + 2 * 0.5 * A^T R1 = -A^T A v
+        if (h->matrix_free) {
+            BSG_CUDA(launch_mf_pass(true, h->lpn, h->mfg, h->X, h->R[0], h->R[1], h->Bp, 0.f, s));
+            BSG_CUDA(launch_mf_pass(false, h->lpn, h->mfg, h->R[1], h->Xhat, h->Xhat, h->Bp, 0.5f, s));
+        } else {
+            BSG_CUDA(launch_pass<true>(h->fmt, h->lpn, h->op_r, h->X, h->R[0], h->R[1], R, h->Bp, 0.f, s));
+            BSG_CUDA(launch_pass<false>(h->fmt, h->lpn, h->op_c, h->R[1], h->Xhat, h->Xhat, c, h->Bp,
+                                        0.5f, s));
+        }
+        double vw = 0.0, ww = 0.0;
+        BSG_CHECK(dot(h->X, h->Xhat, &vw));
+        BSG_CHECK(dot(h->Xhat, h->Xhat, &ww));
+        const double u_new = -vw;   // Rayleigh quotient, |v| = 1
+        if (!(ww > 0.0)) {
+            u = 0.0;
+            break;
+        }
+        slice_scale_kernel<<<grid, 256, 0, s>>>(h->Xhat, h->X, c, h->Bp, (float)(-1.0 / std::sqrt(ww)));
+        add_launches(1);
+        BSG_CUDA(cudaGetLastError());
+        const bool done = it > 1 && std::fabs(u_new - u) <= rel_tol * std::fabs(u_new);
+        u = u_new;
+        if (done) break;
+    }
+    // the iteration used the batch's vectors: its state must be set again
+    BSG_CUDA(cudaMemsetAsync(h->X, 0, (size_t)c * h->Bp * sizeof(float), s));
+    BSG_CUDA(cudaMemsetAsync(h->Xhat, 0, (size_t)c * h->Bp * sizeof(float), s));
+    for (float *p : {h->R[0], h->R[1]}) BSG_CUDA(cudaMemsetAsync(p, 0, (size_t)R * h->Bp * sizeof(float), s));
+    BSG_CUDA(cudaStreamSynchronize(s));
+    h->has_data = false;
+    if (u_max) *u_max = u;
+    if (iters) *iters = std::min(it, max_iters);
     return BSGDTV_OK;
 }
 
