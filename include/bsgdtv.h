@@ -321,6 +321,12 @@ int bsgdtv_batch_get_x(bsgdtv_batch_t h, float *x, int out_on_device);
  * Stream-ordered with run; BSGDTV_ERR_STATE before set_data. */
 int bsgdtv_batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_device, double lambda);
 
+/* Forward projection y_b = A x_b of every slice with the batch's A (stored
+ * or matrix free): x [slices][cols] and y [slices][rows], both device FP32,
+ * slice-major.  Uses the batch's vectors as scratch: every slice must be set
+ * again (bsgdtv_batch_set_data) afterwards.  Synchronises. */
+int bsgdtv_batch_project(bsgdtv_batch_t h, const float *x, float *y);
+
 /* Copies slice b's x [cols] (FP32).  To the host: synchronises the stream. */
 int bsgdtv_batch_get_slice_x(bsgdtv_batch_t h, int b, float *x, int out_on_device);
 

@@ -69,6 +69,7 @@ def load(path: str | None = None):
         "bsgdtv_batch_create_parallel_beam": (I32, [ctypes.POINTER(P), I32, I32, I32, I32, P]),
         "bsgdtv_mf_ray_weights": (I32, [I32, I32, I32, P, I32, I32, P, P, P]),
         "bsgdtv_batch_estimate_umax": (I32, [P, I32, D, ctypes.POINTER(D), ctypes.POINTER(I32)]),
+        "bsgdtv_batch_project": (I32, [P, P, P]),
         "bsgdtv_server_create": (I32, [ctypes.POINTER(P), I64, I32, I32]),
         "bsgdtv_server_destroy": (None, [P]),
         "bsgdtv_server_add_geometry": (I32, [P, I64, I64, I32, I32, P, P, P, I32, I32, D, I32, ctypes.POINTER(I32)]),
@@ -101,6 +102,7 @@ def exported_symbols():
             "bsgdtv_server_destroy", "bsgdtv_server_add_geometry", "bsgdtv_server_submit",
             "bsgdtv_server_poll", "bsgdtv_server_wait", "bsgdtv_server_stats",
             "bsgdtv_batch_create_parallel_beam", "bsgdtv_mf_ray_weights", "bsgdtv_batch_estimate_umax",
+            "bsgdtv_batch_project",
             "bsgdtv_launch_count", "bsgdtv_last_error", "bsgdtv_strerror"]
 
 
@@ -468,6 +470,14 @@ def bsgdtv_batch_estimate_umax(h, max_iters=1000, rel_tol=1e-9):
     return u.value, it.value
 
 
+def bsgdtv_batch_project(h, x, y):
+    """y = A x for every slice: CUDA float32 tensors x [slices, cols], y [slices, rows]."""
+    import torch
+    _check(load().bsgdtv_batch_project(h, _dev_ptr(x, torch.float32), _dev_ptr(y, torch.float32)),
+           "bsgdtv_batch_project")
+    return y
+
+
 def bsgdtv_batch_device_bytes(rows, cols, nnz, slices, fmt=FMT_F32_I32) -> int:
     """Host only: device bytes of a batch of these sizes (-1 on bad sizes)."""
     return int(load().bsgdtv_batch_device_bytes(int(rows), int(cols), int(nnz), int(slices), int(fmt)))
@@ -654,6 +664,13 @@ class BatchReconstructor:
 
     def estimate_umax(self, max_iters=1000, rel_tol=1e-9):
         return bsgdtv_batch_estimate_umax(self.h, max_iters, rel_tol)
+
+    def project(self, x, y=None):
+        """y = A x per slice (CUDA tensors); resets the batch's state."""
+        import torch
+        if y is None:
+            y = torch.empty((self.slices, self.rows), dtype=torch.float32, device=x.device)
+        return bsgdtv_batch_project(self.h, x, y)
 
     def slice_x(self, b, out=None):
         if out is None:

@@ -287,6 +287,11 @@ __global__ void slice_scale_kernel(const float *__restrict__ w, float *__restric
     if (i < n) v[i * Bp] = w ? scale * w[i * Bp] : scale;
 }
 
+__global__ void negate_kernel(float *__restrict__ v, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = -v[i];
+}
+
 // Slice stride Bp (B padded) and lanes per nonzero: a lane holds 4 slices,
 // so Bp = 4 * LPN for B <= 128 (LPN = 1 .. 32), else a multiple of 128 taken
 // in chunks of 128 by the full warp.
@@ -974,6 +979,32 @@ int bsgdtv_batch_estimate_umax(bsgdtv_batch_t h, int max_iters, double rel_tol, 
     h->has_data = false;
     if (u_max) *u_max = u;
     if (iters) *iters = std::min(it, max_iters);
+    return BSGDTV_OK;
+}
+
+int bsgdtv_batch_project(bsgdtv_batch_t h, const float *x, float *y) {
+    if (!h || !x || !y) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    BSG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    const int64_t c = h->cols, R = h->rows;
+    // x (planar) -> X (interleaved); R[0] = 0 stands for y; R[1] = 0 - A x
+    BSG_CUDA(cudaMemcpyAsync(h->Xp, x, (size_t)c * h->B * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    BSG_CUDA(launch_transpose(h->Xp, h->X, c, h->B, h->Bp, false, s));
+    BSG_CUDA(cudaMemsetAsync(h->R[0], 0, (size_t)R * h->Bp * sizeof(float), s));
+    if (h->matrix_free)
+        BSG_CUDA(launch_mf_pass(true, h->lpn, h->mfg, h->X, h->R[0], h->R[1], h->Bp, 0.f, s));
+    else
+        BSG_CUDA(launch_pass<true>(h->fmt, h->lpn, h->op_r, h->X, h->R[0], h->R[1], R, h->Bp, 0.f, s));
+    BSG_CUDA(launch_transpose(h->R[1], y, R, h->B, h->Bp, true, s));
+    const int64_t n = R * h->B;
+    negate_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, n);
+    add_launches(1);
+    BSG_CUDA(cudaGetLastError());
+    // the projection used the batch's vectors: its state must be set again
+    BSG_CUDA(cudaMemsetAsync(h->X, 0, (size_t)c * h->Bp * sizeof(float), s));
+    for (float *p : {h->R[0], h->R[1]}) BSG_CUDA(cudaMemsetAsync(p, 0, (size_t)R * h->Bp * sizeof(float), s));
+    BSG_CUDA(cudaStreamSynchronize(s));
+    h->has_data = false;
     return BSGDTV_OK;
 }
 

@@ -112,3 +112,20 @@ def test_noise_level_and_determinism():
     assert abs(np.std(e) / sigma - 1.0) < 0.05
     P2 = synth.make_problem("ellipse64", cache=False)
     assert np.array_equal(P.y, P2.y) and np.array_equal(P.A.vals, P2.A.vals)
+
+
+def test_phantom_bounding_box_equals_whole_grid():
+    """The phantom evaluates each ellipse only inside a widened bounding box;
+    evaluating every pixel of the grid gives the same image bit for bit."""
+    for n, ne, seed in [(64, 10, 0), (37, 4, 1), (128, 10, 2), (9, 3, 3), (200, 25, 4)]:
+        params = synth.ellipse_params(ne, seed, n / 64.0)
+        t = np.arange(n, dtype=np.float64) - 0.5 * (n - 1)
+        X = t[None, :].repeat(n, axis=0)
+        Y = (-t)[:, None].repeat(n, axis=1)
+        ref = np.zeros((n, n))
+        for cx, cy, a, b, phi, inten in params:
+            dx, dy = X - cx, Y - cy
+            xr = dx * np.cos(phi) + dy * np.sin(phi)
+            yr = -dx * np.sin(phi) + dy * np.cos(phi)
+            ref[(xr / a) ** 2 + (yr / b) ** 2 <= 1.0] += inten
+        assert np.array_equal(synth.phantom(n, ne, seed), ref)
