@@ -72,7 +72,8 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
             if err:
                 print(err)
     tmp = LIB + ".tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lpthread"]
+    cmd = ([nvcc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] +
+           ["-lpthread", "-Xlinker", "--no-undefined"])
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stderr}")

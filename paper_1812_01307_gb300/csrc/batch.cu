@@ -399,8 +399,8 @@ int benqueue_epoch(bsgdtv_batch_ctx *h, int par, int fgp_iters, cudaStream_t s,
     const bool prox = any_prox(h, fgp_iters);
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[0], s, cudaEventRecordExternal));
     if (h->matrix_free) {
-        BSG_CUDA(launch_mf_pass(true, h->lpn, h->mfg, h->X, h->Y, h->R[1 - par], h->Bp, 0.f, s));
-        BSG_CUDA(launch_mf_pass(false, h->lpn, h->mfg, h->R[par], h->X, prox ? h->Xhat : h->X, h->Bp,
+        BSG_CUDA(launch_mf_pass(true, h->Bp, h->mfg, h->X, h->Y, h->R[1 - par], 0.f, s));
+        BSG_CUDA(launch_mf_pass(false, h->Bp, h->mfg, h->R[par], h->X, prox ? h->Xhat : h->X,
                                 (float)h->mu, s));
     } else {
         // r^k = y - A x^k (reads x before the column pass updates it)
@@ -949,8 +949,8 @@ int bsgdtv_batch_estimate_umax(bsgdtv_batch_t h, int max_iters, double rel_tol, 
         BSG_CUDA(cudaMemsetAsync(h->Xhat, 0, (size_t)c * h->Bp * sizeof(float), s));
         // R1 = 0 - A v; Xhat = 0 + 2 * 0.5 * A^T R1 = -A^T A v
         if (h->matrix_free) {
-            BSG_CUDA(launch_mf_pass(true, h->lpn, h->mfg, h->X, h->R[0], h->R[1], h->Bp, 0.f, s));
-            BSG_CUDA(launch_mf_pass(false, h->lpn, h->mfg, h->R[1], h->Xhat, h->Xhat, h->Bp, 0.5f, s));
+            BSG_CUDA(launch_mf_pass(true, h->Bp, h->mfg, h->X, h->R[0], h->R[1], 0.f, s));
+            BSG_CUDA(launch_mf_pass(false, h->Bp, h->mfg, h->R[1], h->Xhat, h->Xhat, 0.5f, s));
         } else {
             BSG_CUDA(launch_pass<true>(h->fmt, h->lpn, h->op_r, h->X, h->R[0], h->R[1], R, h->Bp, 0.f, s));
             BSG_CUDA(launch_pass<false>(h->fmt, h->lpn, h->op_c, h->R[1], h->Xhat, h->Xhat, c, h->Bp,
@@ -992,7 +992,7 @@ int bsgdtv_batch_project(bsgdtv_batch_t h, const float *x, float *y) {
     BSG_CUDA(launch_transpose(h->Xp, h->X, c, h->B, h->Bp, false, s));
     BSG_CUDA(cudaMemsetAsync(h->R[0], 0, (size_t)R * h->Bp * sizeof(float), s));
     if (h->matrix_free)
-        BSG_CUDA(launch_mf_pass(true, h->lpn, h->mfg, h->X, h->R[0], h->R[1], h->Bp, 0.f, s));
+        BSG_CUDA(launch_mf_pass(true, h->Bp, h->mfg, h->X, h->R[0], h->R[1], 0.f, s));
     else
         BSG_CUDA(launch_pass<true>(h->fmt, h->lpn, h->op_r, h->X, h->R[0], h->R[1], R, h->Bp, 0.f, s));
     BSG_CUDA(launch_transpose(h->R[1], y, R, h->B, h->Bp, true, s));

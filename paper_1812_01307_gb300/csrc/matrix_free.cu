@@ -26,6 +26,7 @@
 // row pass is exactly the transpose of the A of the column pass.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -68,17 +69,19 @@ __device__ __forceinline__ float chord(const AngleGeo &g, float x0, float y0, fl
 }
 
 // Up to 3 (element, weight) candidates of one band of ray (k, d): the image
-// row srow (|c| > |s|) or column t (|s| >= |c|) with index m.  Returns the
-// count; weights may be 0 (pixels the line only grazes).
+// row srow (|c| > |s|) or column t (|s| >= |c|) with index m, restricted to
+// the image rows [s_lo, s_hi) (all rows by default).  Returns the count;
+// weights may be 0 (pixels the line only grazes).
 __device__ __forceinline__ int ray_band(const AngleGeo &g, int n, float h, float u, int m,
-                                        int (&col)[3], float (&w)[3]) {
+                                        int (&col)[3], float (&w)[3], int s_lo = 0, int s_hi = -1) {
+    if (s_hi < 0) s_hi = n;
     int cnt = 0;
     const float eps = 1e-3f;
     if (!g.xmajor) {
         // row band: fy = n - 1 - srow, y in [fy - h, fy - h + 1)
         const int fy = n - 1 - m;
         const float ya = (float)fy - h, yb = ya + 1.f;
-        const float xa = (u - ya * g.s[0]) / g.c[0], xb = (u - yb * g.s[0]) / g.c[0];
+        const float xa = (u - ya * g.s[0]) * g.inv_c, xb = (u - yb * g.s[0]) * g.inv_c;
         int t0 = (int)floorf(fminf(xa, xb) + h - eps), t1 = (int)floorf(fmaxf(xa, xb) + h + eps);
         t0 = max(t0, 0);
         t1 = min(t1, n - 1);
@@ -90,10 +93,10 @@ __device__ __forceinline__ int ray_band(const AngleGeo &g, int n, float h, float
     } else {
         // column band: x in [m - h, m - h + 1)
         const float xa = (float)m - h, xb = xa + 1.f;
-        const float ya = (u - xa * g.c[0]) / g.s[0], yb = (u - xb * g.c[0]) / g.s[0];
+        const float ya = (u - xa * g.c[0]) * g.inv_s, yb = (u - xb * g.c[0]) * g.inv_s;
         int f0 = (int)floorf(fminf(ya, yb) + h - eps), f1 = (int)floorf(fmaxf(ya, yb) + h + eps);
-        f0 = max(f0, 0);
-        f1 = min(f1, n - 1);
+        f0 = max(f0, n - s_hi);        // rows of the stripe [s_lo, s_hi) only
+        f1 = min(f1, n - 1 - s_lo);
         for (int fy = f1; fy >= f0 && cnt < 3; --fy) {   // ascending srow = n - 1 - fy
             col[cnt] = (n - 1 - fy) * n + m;
             w[cnt] = chord(g, xa, (float)fy - h, u);
@@ -134,134 +137,157 @@ __device__ __forceinline__ float4 ld_keep(const float *ptr, uint64_t pol) {
     return v;
 }
 
-constexpr int kWarps = 8;
+constexpr int kThreads = 256;
 
-// Compacts each lane's cnt entries (weight > 0) into stage[0 .. total) in lane
-// order and pads to a multiple of G with zero weights aimed at element 0.
-template <int G>
-__device__ __forceinline__ int stage_entries(int2 *stage, int lane, int cnt, const int (&idx)[3],
-                                             const float (&w)[3], int Bp) {
-    int mine = 0;
-    for (int i = 0; i < cnt; ++i) mine += (w[i] > 0.f);
-    int incl = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
+// Bands [m_lo, m_hi] of ray (k, d) that can hold pixels of the image rows
+// [s_lo, s_hi) (y in [h - s_hi, h - s_lo)): the other coordinate along the
+// band must lie within the image, or the stripe, widened by one pixel.
+__device__ __forceinline__ void band_range(const AngleGeo &g, int n, float h, float u, int s_lo,
+                                           int s_hi, int &m_lo, int &m_hi) {
+    const float lim = 2.f * (float)n;   // keeps the float -> int conversions in range
+    const float y_bot = h - (float)s_hi - 1.f, y_top = h - (float)s_lo + 1.f;
+    if (!g.xmajor) {
+        // bands are rows of the stripe; x(y) = (u - y s) / c within [-h - 1, h + 1]
+        m_lo = s_lo;
+        m_hi = s_hi - 1;
+        if (g.s[0] == 0.f) {
+            if (fabsf(u * g.inv_c) > h + 1.f) m_hi = -1;
+            return;
+        }
+        const float ya = (u - (h + 1.f) * g.c[0]) * g.inv_s, yb = (u + (h + 1.f) * g.c[0]) * g.inv_s;
+        const float y0 = fmaxf(fminf(ya, yb) - 1.f, -lim), y1 = fminf(fmaxf(ya, yb) + 1.f, lim);
+        // row srow holds y in [h - srow - 1, h - srow)
+        m_lo = max(m_lo, (int)floorf(h - y1) - 1);
+        m_hi = min(m_hi, (int)ceilf(h - y0) + 1);
+    } else {
+        // bands are columns; y(x) = (u - x c) / s within the stripe
+        m_lo = 0;
+        m_hi = n - 1;
+        if (g.c[0] == 0.f) {
+            const float y = u * g.inv_s;
+            if (y < y_bot || y > y_top) m_hi = -1;
+            return;
+        }
+        const float xa = (u - y_top * g.s[0]) * g.inv_c, xb = (u - y_bot * g.s[0]) * g.inv_c;
+        const float x0 = fmaxf(fminf(xa, xb) - 1.f, -lim), x1 = fminf(fmaxf(xa, xb) + 1.f, lim);
+        m_lo = max(m_lo, (int)floorf(x0 + h) - 1);
+        m_hi = min(m_hi, (int)ceilf(x1 + h) + 1);
     }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    int pos = incl - mine;
-    for (int i = 0; i < cnt; ++i)
-        if (w[i] > 0.f) stage[pos++] = make_int2(__float_as_int(w[i]), idx[i] * Bp);
-    const int padded = (total + G - 1) / G * G;
-    if (lane < padded - total) stage[total + lane] = make_int2(0, 0);
-    __syncwarp();
-    return padded;
+}
+
+__device__ __forceinline__ void fma4(float a, const float4 &x, float4 &acc) {
+    acc.x = fmaf(a, x.x, acc.x);
+    acc.y = fmaf(a, x.y, acc.y);
+    acc.z = fmaf(a, x.z, acc.z);
+    acc.w = fmaf(a, x.w, acc.w);
+}
+
+// Candidates of this lane's band / angle go to its three mailbox slots as
+// (weight bits, element offset), zero where there is no entry; the LPN lanes
+// of an element then read the group's slots in order and each applies every
+// entry to its own 4 slices.
+__device__ __forceinline__ void post(int2 (&slot)[3], const int (&idx)[3], const float (&wt)[3],
+                                     int Bp) {
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+        slot[e] = wt[e] > 0.f ? make_int2(__float_as_int(wt[e]), idx[e] * Bp) : make_int2(0, 0);
 }
 
 template <int LPN>
-__device__ __forceinline__ void apply_stage(const int2 *stage, int n_ent, int g, const float *vl,
+__device__ __forceinline__ void apply_group(const int2 (*box)[3], int grp, const float *vl,
                                             uint64_t pol, float4 &acc) {
-    constexpr int G = 32 / LPN;
-    for (int j = g; j < n_ent; j += G) {
-        const int2 e = stage[j];
-        const float4 x = ld_keep(vl + e.y, pol);
-        const float a = __int_as_float(e.x);
-        acc.x = fmaf(a, x.x, acc.x);
-        acc.y = fmaf(a, x.y, acc.y);
-        acc.z = fmaf(a, x.z, acc.z);
-        acc.w = fmaf(a, x.w, acc.w);
-    }
-}
-
-template <int LPN>
-__device__ __forceinline__ void reduce_groups(float4 &acc) {
 #pragma unroll
-    for (int off = LPN; off < 32; off *= 2) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-        acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off);
-        acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off);
-    }
+    for (int src = 0; src < LPN; ++src)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const int2 t = box[grp * LPN + src][e];
+            if (t.x != 0) fma4(__int_as_float(t.x), ld_keep(vl + t.y, pol), acc);
+        }
 }
 
-// Row pass: one warp per ray; lanes take 32 bands at a time, then apply the
-// staged entries to the slices as the stored-matrix pass does.
-// r[ray] = y[ray] - sum_pixels a x[pixel] (all slices).
+// Row pass over the image rows [s_lo, s_hi): LPN lanes per ray, 32/LPN
+// neighbouring rays (bins) per warp.  The lanes of a ray take its bands in
+// turn (lane j: bands m = j mod LPN of each round), post their entries, and
+// every lane applies all of them to its 4 slices of the chunk:
+// r[ray] = (first ? y[ray] : r[ray]) - sum over bands ascending, then
+// candidates ascending, of a x[pixel] (the same order for every LPN).
 template <int LPN>
-__global__ void __launch_bounds__(kWarps * 32, 4)
+__global__ void __launch_bounds__(kThreads)
     mf_row_kernel(const AngleGeo *__restrict__ geo, int n, int n_angles, int n_bins,
                   const float *__restrict__ X, const float *__restrict__ Y, float *__restrict__ R,
-                  int Bp) {
-    constexpr int G = 32 / LPN;
-    __shared__ int2 stage[kWarps][3 * 32 + 32];
+                  int Bp, int s_lo, int s_hi, int first) {
+    constexpr int EPW = 32 / LPN;
+    __shared__ int2 box[kThreads / 32][32][3];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int g = lane / LPN, sl = lane % LPN;
-    const int64_t ray = (int64_t)blockIdx.x * kWarps + w;
-    if (ray >= (int64_t)n_angles * n_bins) return;
-    const int k = (int)(ray / n_bins), d = (int)(ray % n_bins);
-    const AngleGeo ag = geo[k];
+    const int grp = lane / LPN, j = lane % LPN;
+    const int64_t ray = ((int64_t)blockIdx.x * (kThreads / 32) + w) * EPW + grp;
+    const bool valid = ray < (int64_t)n_angles * n_bins;
+    const int k = valid ? (int)(ray / n_bins) : 0, d = valid ? (int)(ray % n_bins) : 0;
+    const AngleGeo g = geo[k];
     const float h = 0.5f * (float)n, u = (float)d - 0.5f * (float)(n_bins - 1);
     const uint64_t pol = l2_evict_last_policy();
+    int m_lo = 0, m_hi = -1;
+    if (valid) band_range(g, n, h, u, s_lo, s_hi, m_lo, m_hi);
+    const int w_lo = __reduce_min_sync(0xffffffffu, m_hi >= m_lo ? m_lo : n);
+    const int w_hi = __reduce_max_sync(0xffffffffu, m_hi);
     for (int c0 = 0; c0 < Bp; c0 += 4 * LPN) {
-        const float *vl = X + c0 + sl * 4;
+        const float *vl = X + c0 + j * 4;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int m0 = 0; m0 < n; m0 += 32) {
-            int idx[3];
-            float wt[3];
-            const int m = m0 + lane;
-            const int cnt = (m < n) ? ray_band(ag, n, h, u, m, idx, wt) : 0;
-            const int n_ent = stage_entries<G>(stage[w], lane, cnt, idx, wt, Bp);
-            apply_stage<LPN>(stage[w], n_ent, g, vl, pol, acc);
+        for (int mb = w_lo; mb <= w_hi; mb += LPN) {
+            const int m = mb + j;
+            int idx[3] = {0, 0, 0};
+            float wt[3] = {0.f, 0.f, 0.f};
+            if (m >= m_lo && m <= m_hi) ray_band(g, n, h, u, m, idx, wt, s_lo, s_hi);
+            post(box[w][lane], idx, wt, Bp);
+            __syncwarp();
+            apply_group<LPN>(box[w], grp, vl, pol, acc);
             __syncwarp();
         }
-        reduce_groups<LPN>(acc);
-        if (g == 0) {
-            const int64_t o = ray * Bp + c0 + sl * 4;
-            const float4 yv = __ldcs(reinterpret_cast<const float4 *>(Y + o));
+        if (valid) {
+            const int64_t o = ray * Bp + c0 + j * 4;
+            const float4 yv = first ? __ldcs(reinterpret_cast<const float4 *>(Y + o))
+                                    : *reinterpret_cast<const float4 *>(R + o);
             *reinterpret_cast<float4 *>(R + o) =
                 make_float4(yv.x - acc.x, yv.y - acc.y, yv.z - acc.z, yv.w - acc.w);
         }
     }
 }
 
-// Column pass: one warp per pixel; lanes take 32 angles at a time.
-// out[pixel] = base[pixel] + mu * 2 * sum_rays a r[ray] (all slices).
+// Column pass over the angles [k_lo, k_hi): LPN lanes per pixel, 32/LPN
+// neighbouring pixels of an image row per warp; lane j takes the angles
+// k = j mod LPN of each round.  out[pixel] = (first ? base : out)[pixel] +
+// mu * 2 * sum over angles ascending, then bins ascending, of a r[ray].
 template <int LPN>
-__global__ void __launch_bounds__(kWarps * 32, 4)
+__global__ void __launch_bounds__(kThreads)
     mf_col_kernel(const AngleGeo *__restrict__ geo, int n, int n_angles, int n_bins,
-                  const float *__restrict__ Rv, const float *__restrict__ base,
-                  float *__restrict__ out, int Bp, float mu) {
-    constexpr int G = 32 / LPN;
-    __shared__ int2 stage[kWarps][3 * 32 + 32];
+                  const float *__restrict__ Rv, const float *base, float *out, int Bp, float mu,
+                  int k_lo, int k_hi, int first) {
+    constexpr int EPW = 32 / LPN;
+    __shared__ int2 box[kThreads / 32][32][3];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int g = lane / LPN, sl = lane % LPN;
-    const int64_t px = (int64_t)blockIdx.x * kWarps + w;
-    if (px >= (int64_t)n * n) return;
-    const int srow = (int)(px / n), t = (int)(px % n);
+    const int grp = lane / LPN, j = lane % LPN;
+    const int64_t px = ((int64_t)blockIdx.x * (kThreads / 32) + w) * EPW + grp;
+    const bool valid = px < (int64_t)n * n;
+    const int srow = valid ? (int)(px / n) : 0, t = valid ? (int)(px % n) : 0;
     const float h = 0.5f * (float)n, off = 0.5f * (float)(n_bins - 1);
     const float x0 = (float)t - h, y0 = h - (float)srow - 1.f;
     const uint64_t pol = l2_evict_last_policy();
     for (int c0 = 0; c0 < Bp; c0 += 4 * LPN) {
-        const float *vl = Rv + c0 + sl * 4;
+        const float *vl = Rv + c0 + j * 4;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int k0 = 0; k0 < n_angles; k0 += 32) {
-            int idx[3];
-            float wt[3];
-            const int k = k0 + lane;
-            int cnt = 0;
-            if (k < n_angles) {
-                const AngleGeo ag = geo[k];
-                cnt = pixel_angle(ag, k, n_bins, off, x0, y0, idx, wt);
-            }
-            const int n_ent = stage_entries<G>(stage[w], lane, cnt, idx, wt, Bp);
-            apply_stage<LPN>(stage[w], n_ent, g, vl, pol, acc);
+        for (int kb = k_lo; kb < k_hi; kb += LPN) {
+            const int k = kb + j;
+            int idx[3] = {0, 0, 0};
+            float wt[3] = {0.f, 0.f, 0.f};
+            if (valid && k < k_hi) pixel_angle(geo[k], k, n_bins, off, x0, y0, idx, wt);
+            post(box[w][lane], idx, wt, Bp);
+            __syncwarp();
+            apply_group<LPN>(box[w], grp, vl, pol, acc);
             __syncwarp();
         }
-        reduce_groups<LPN>(acc);
-        if (g == 0) {
-            const int64_t o = px * Bp + c0 + sl * 4;
-            const float4 b = __ldcs(reinterpret_cast<const float4 *>(base + o));
+        if (valid) {
+            const int64_t o = px * Bp + c0 + j * 4;
+            const float4 b = *reinterpret_cast<const float4 *>((first ? base : out) + o);
             *reinterpret_cast<float4 *>(out + o) =
                 make_float4(b.x + mu * (2.f * acc.x), b.y + mu * (2.f * acc.y),
                             b.z + mu * (2.f * acc.z), b.w + mu * (2.f * acc.w));
@@ -322,35 +348,53 @@ void mf_angle_table(int n_angles, std::vector<AngleGeo> &out) {
         const double a = std::max(std::fabs(c), std::fabs(s)), b = std::min(std::fabs(c), std::fabs(s));
         g.inv_a = (float)(1.0 / a);
         g.inv_ab = b > 0.0 ? (float)(1.0 / (a * b)) : 0.f;
+        g.inv_c = c != 0.0 ? (float)(1.0 / c) : 0.f;
+        g.inv_s = s != 0.0 ? (float)(1.0 / s) : 0.f;
+        g.pad[0] = g.pad[1] = 0;
         g.axis = (b == 0.0) ? 1 : 0;
         g.xmajor = (std::fabs(s) >= std::fabs(c)) ? 1 : 0;
     }
 }
 
+// Gathered vectors are split so that the slice vectors one launch gathers
+// (rows of x for the row pass, angles of r for the column pass) fit about
+// half of the L2: beyond that every angle streams the whole vector from HBM.
+constexpr int64_t kGatherBudget = 48ll << 20;
+
 template <int LPN>
 static cudaError_t launch_mf_lpn(bool row_pass, const MfGeometry &G, const float *v,
                                  const float *base, float *out, int Bp, float mu, cudaStream_t s) {
     const int64_t n_out = row_pass ? (int64_t)G.n_angles * G.n_bins : (int64_t)G.n * G.n;
-    const dim3 grid((unsigned)((n_out + mf::kWarps - 1) / mf::kWarps)), block(mf::kWarps * 32);
-    if (row_pass)
-        mf::mf_row_kernel<LPN><<<grid, block, 0, s>>>(G.geo, G.n, G.n_angles, G.n_bins, v, base, out, Bp);
-    else
-        mf::mf_col_kernel<LPN><<<grid, block, 0, s>>>(G.geo, G.n, G.n_angles, G.n_bins, v, base, out,
-                                                       Bp, mu);
-    add_launches(1);
-    return cudaGetLastError();
+    const int64_t per_block = (int64_t)(mf::kThreads / 32) * (32 / LPN);
+    const dim3 grid((unsigned)((n_out + per_block - 1) / per_block)), block(mf::kThreads);
+    const int64_t unit = 4ll * Bp * (row_pass ? G.n : G.n_bins);   // bytes of one image row / angle
+    const int total = row_pass ? G.n : G.n_angles;
+    const int step = (int)std::max<int64_t>(1, std::min<int64_t>(total, kGatherBudget / unit));
+    for (int lo = 0; lo < total; lo += step) {
+        const int hi = std::min(total, lo + step), first = (lo == 0);
+        if (row_pass)
+            mf::mf_row_kernel<LPN><<<grid, block, 0, s>>>(G.geo, G.n, G.n_angles, G.n_bins, v, base,
+                                                           out, Bp, lo, hi, first);
+        else
+            mf::mf_col_kernel<LPN><<<grid, block, 0, s>>>(G.geo, G.n, G.n_angles, G.n_bins, v, base,
+                                                           out, Bp, mu, lo, hi, first);
+        add_launches(1);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
-cudaError_t launch_mf_pass(bool row_pass, int lpn, const MfGeometry &G, const float *v,
-                           const float *base, float *out, int Bp, float mu, cudaStream_t s) {
-    switch (lpn) {
-        case 1: return launch_mf_lpn<1>(row_pass, G, v, base, out, Bp, mu, s);
-        case 2: return launch_mf_lpn<2>(row_pass, G, v, base, out, Bp, mu, s);
-        case 4: return launch_mf_lpn<4>(row_pass, G, v, base, out, Bp, mu, s);
-        case 8: return launch_mf_lpn<8>(row_pass, G, v, base, out, Bp, mu, s);
-        case 16: return launch_mf_lpn<16>(row_pass, G, v, base, out, Bp, mu, s);
-        case 32: return launch_mf_lpn<32>(row_pass, G, v, base, out, Bp, mu, s);
-        default: return cudaErrorInvalidValue;
+cudaError_t launch_mf_pass(bool row_pass, int Bp, const MfGeometry &G, const float *v,
+                           const float *base, float *out, float mu, cudaStream_t s) {
+    // LPN lanes of 4 slices each per element; strides above 32 go in chunks of 32
+    switch (Bp) {
+        case 4: return launch_mf_lpn<1>(row_pass, G, v, base, out, Bp, mu, s);
+        case 8: return launch_mf_lpn<2>(row_pass, G, v, base, out, Bp, mu, s);
+        case 16: return launch_mf_lpn<4>(row_pass, G, v, base, out, Bp, mu, s);
+        default:
+            if (Bp % 32 == 0) return launch_mf_lpn<8>(row_pass, G, v, base, out, Bp, mu, s);
+            return cudaErrorInvalidValue;
     }
 }
 
