@@ -327,6 +327,16 @@ int bsgdtv_batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_dev
  * again (bsgdtv_batch_set_data) afterwards.  Synchronises. */
 int bsgdtv_batch_project(bsgdtv_batch_t h, const float *x, float *y);
 
+/* Autotuner: times epochs_per_trial epochs of this batch (on its current
+ * data, state restored after every trial) for each candidate launch shape
+ * and keeps the fastest.  The candidates are the FGP iterations per launch
+ * (3, 4, 5, 6, 8: fewer iterations per launch mean a smaller halo per
+ * 64 x 64 region but more launches and field traffic); every candidate gives
+ * bit-identical iterates, so tuning never changes results.  Writes the choice
+ * and its time per epoch (may be NULL).  Synchronises; needs set_data. */
+int bsgdtv_batch_autotune(bsgdtv_batch_t h, int fgp_iters, int epochs_per_trial, int *fgp_chunk,
+                          double *epoch_ms);
+
 /* Copies slice b's x [cols] (FP32).  To the host: synchronises the stream. */
 int bsgdtv_batch_get_slice_x(bsgdtv_batch_t h, int b, float *x, int out_on_device);
 

@@ -70,6 +70,7 @@ def load(path: str | None = None):
         "bsgdtv_mf_ray_weights": (I32, [I32, I32, I32, P, I32, I32, P, P, P]),
         "bsgdtv_batch_estimate_umax": (I32, [P, I32, D, ctypes.POINTER(D), ctypes.POINTER(I32)]),
         "bsgdtv_batch_project": (I32, [P, P, P]),
+        "bsgdtv_batch_autotune": (I32, [P, I32, I32, ctypes.POINTER(I32), ctypes.POINTER(D)]),
         "bsgdtv_server_create": (I32, [ctypes.POINTER(P), I64, I32, I32]),
         "bsgdtv_server_destroy": (None, [P]),
         "bsgdtv_server_add_geometry": (I32, [P, I64, I64, I32, I32, P, P, P, I32, I32, D, I32, ctypes.POINTER(I32)]),
@@ -102,7 +103,7 @@ def exported_symbols():
             "bsgdtv_server_destroy", "bsgdtv_server_add_geometry", "bsgdtv_server_submit",
             "bsgdtv_server_poll", "bsgdtv_server_wait", "bsgdtv_server_stats",
             "bsgdtv_batch_create_parallel_beam", "bsgdtv_mf_ray_weights", "bsgdtv_batch_estimate_umax",
-            "bsgdtv_batch_project",
+            "bsgdtv_batch_project", "bsgdtv_batch_autotune",
             "bsgdtv_launch_count", "bsgdtv_last_error", "bsgdtv_strerror"]
 
 
@@ -478,6 +479,14 @@ def bsgdtv_batch_project(h, x, y):
     return y
 
 
+def bsgdtv_batch_autotune(h, fgp_iters, epochs_per_trial=3):
+    """Picks the batch's FGP iterations per launch by timing; returns (chunk, epoch ms)."""
+    c, ms = ctypes.c_int(), ctypes.c_double()
+    _check(load().bsgdtv_batch_autotune(h, int(fgp_iters), int(epochs_per_trial), ctypes.byref(c),
+                                        ctypes.byref(ms)), "bsgdtv_batch_autotune")
+    return c.value, ms.value
+
+
 def bsgdtv_batch_device_bytes(rows, cols, nnz, slices, fmt=FMT_F32_I32) -> int:
     """Host only: device bytes of a batch of these sizes (-1 on bad sizes)."""
     return int(load().bsgdtv_batch_device_bytes(int(rows), int(cols), int(nnz), int(slices), int(fmt)))
@@ -664,6 +673,9 @@ class BatchReconstructor:
 
     def estimate_umax(self, max_iters=1000, rel_tol=1e-9):
         return bsgdtv_batch_estimate_umax(self.h, max_iters, rel_tol)
+
+    def autotune(self, fgp_iters, epochs_per_trial=3):
+        return bsgdtv_batch_autotune(self.h, fgp_iters, epochs_per_trial)
 
     def project(self, x, y=None):
         """y = A x per slice (CUDA tensors); resets the batch's state."""

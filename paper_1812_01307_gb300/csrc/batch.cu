@@ -38,6 +38,8 @@
 namespace bsgdtv {
 namespace {
 
+constexpr int kBatchFgpChunk = 5;   // default FGP iterations per launch (halo = chunk + 1)
+constexpr int kFgpChunkChoices[] = {3, 4, 5, 6, 8};   // what the autotuner tries
 constexpr int kPassWarps = 8;       // warps (rows or pixels) per CTA
 constexpr int kPassMinBlocks = 6;   // 48 resident warps per SM (<= 40 registers): the
                                     // gathers are latency-bound, occupancy beats depth
@@ -316,6 +318,7 @@ struct bsgdtv_batch_ctx {
     int fmt = BSGDTV_FMT_F32_I32;
     PassOperand op_r = {}, op_c = {};   // A in CSR / CSC: entries (weight, idx * Bp)
     bool matrix_free = false;           // weights computed on the fly (parallel beam)
+    int fgp_chunk = kBatchFgpChunk;     // FGP iterations per launch (autotuned)
     MfGeometry mfg;
     float *ystage = nullptr;            // [max(rows, cols)] planar staging for one slice
     float *X = nullptr, *Xhat = nullptr, *Y = nullptr, *R[2] = {nullptr, nullptr};   // interleaved
@@ -416,7 +419,8 @@ int benqueue_epoch(bsgdtv_batch_ctx *h, int par, int fgp_iters, cudaStream_t s,
         BSG_CUDA(launch_transpose(h->Xhat, h->Xhp, c, h->B, h->Bp, true, s));
         FgpScratch sc{h->fp, h->fq, h->fpp, h->fqp};
         BSG_CUDA(fgpk::launch_fgp_regions<true>(h->Xhp, h->Xp, h->img_h, h->img_w, 1.f, h->tau,
-                                                h->B, c, fgp_iters, h->mom, sc, s, false));
+                                                h->B, c, fgp_iters, h->mom, sc, s, false,
+                                                h->fgp_chunk));
         BSG_CUDA(launch_transpose(h->Xp, h->X, c, h->B, h->Bp, false, s));
     }
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[2], s, cudaEventRecordExternal));
@@ -1005,6 +1009,54 @@ int bsgdtv_batch_project(bsgdtv_batch_t h, const float *x, float *y) {
     for (float *p : {h->R[0], h->R[1]}) BSG_CUDA(cudaMemsetAsync(p, 0, (size_t)R * h->Bp * sizeof(float), s));
     BSG_CUDA(cudaStreamSynchronize(s));
     h->has_data = false;
+    return BSGDTV_OK;
+}
+
+int bsgdtv_batch_autotune(bsgdtv_batch_t h, int fgp_iters, int epochs_per_trial, int *fgp_chunk,
+                          double *epoch_ms) {
+    if (!h || fgp_iters < 0 || epochs_per_trial < 1)
+        return fail(BSGDTV_ERR_INVALID_ARG, "need fgp_iters >= 0 and epochs_per_trial >= 1");
+    if (!h->has_data) return fail(BSGDTV_ERR_STATE, "autotune before set_data");
+    BSG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    const size_t xb = (size_t)h->cols * h->Bp * sizeof(float), rb = (size_t)h->rows * h->Bp * sizeof(float);
+    // the trials run real epochs: keep x^k, r^{k-1} (and r^k's buffer) to restore after each
+    float *sx = nullptr, *sr0 = nullptr, *sr1 = nullptr;
+    BSG_CHECK(balloc(h, &sx, xb / sizeof(float)));
+    BSG_CHECK(balloc(h, &sr0, rb / sizeof(float)));
+    BSG_CHECK(balloc(h, &sr1, rb / sizeof(float)));
+    BSG_CUDA(cudaMemcpyAsync(sx, h->X, xb, cudaMemcpyDeviceToDevice, s));
+    BSG_CUDA(cudaMemcpyAsync(sr0, h->R[0], rb, cudaMemcpyDeviceToDevice, s));
+    BSG_CUDA(cudaMemcpyAsync(sr1, h->R[1], rb, cudaMemcpyDeviceToDevice, s));
+    const int cur = h->cur;
+    const int64_t epoch = h->epoch;
+    auto restore = [&]() -> int {
+        BSG_CUDA(cudaMemcpyAsync(h->X, sx, xb, cudaMemcpyDeviceToDevice, s));
+        BSG_CUDA(cudaMemcpyAsync(h->R[0], sr0, rb, cudaMemcpyDeviceToDevice, s));
+        BSG_CUDA(cudaMemcpyAsync(h->R[1], sr1, rb, cudaMemcpyDeviceToDevice, s));
+        h->cur = cur;
+        h->epoch = epoch;
+        return BSGDTV_OK;
+    };
+    int best = h->fgp_chunk;
+    double best_ms = 1e300;
+    for (int chunk : kFgpChunkChoices) {
+        h->fgp_chunk = chunk;
+        bdrop_graphs(h);
+        BSG_CHECK(bsgdtv_batch_run(h, 1, fgp_iters));   // builds the graphs, warms up
+        double pk = 0.0, ep = 0.0;
+        BSG_CHECK(bsgdtv_batch_run_timed(h, epochs_per_trial, fgp_iters, &pk, &ep));
+        BSG_CHECK(restore());
+        if (ep < best_ms) {
+            best_ms = ep;
+            best = chunk;
+        }
+    }
+    h->fgp_chunk = best;
+    bdrop_graphs(h);
+    BSG_CUDA(cudaStreamSynchronize(s));
+    if (fgp_chunk) *fgp_chunk = best;
+    if (epoch_ms) *epoch_ms = best_ms / epochs_per_trial;
     return BSGDTV_OK;
 }
 

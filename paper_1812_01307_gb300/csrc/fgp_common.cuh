@@ -210,7 +210,8 @@ inline bool fits_one_region(int h, int w) { return h <= RH && w <= RW; }
 template <bool kBatch>
 cudaError_t launch_fgp_regions(const float *b, float *x, int h, int w, float tau,
                                const float *tau_z, int planes, int64_t plane, int iters,
-                               const float *mom, FgpScratch sc, cudaStream_t s, bool pdl) {
+                               const float *mom, FgpScratch sc, cudaStream_t s, bool pdl,
+                               int max_chunk = kMaxChunk) {
     const dim3 block(RW, TY);
     const float c8 = 1.0f / (8.0f * tau);
     if (fits_one_region(h, w)) {
@@ -222,7 +223,7 @@ cudaError_t launch_fgp_regions(const float *b, float *x, int h, int w, float tau
     }
     int done = 0;
     while (done < iters) {
-        const int chunk = std::min(kMaxChunk, iters - done);
+        const int chunk = std::min(max_chunk, iters - done);
         const int HL = chunk + 1;
         const int IH = RH - 2 * HL, IW = RW - 2 * HL;
         const dim3 grid((w + IW - 1) / IW, (h + IH - 1) / IH, planes);

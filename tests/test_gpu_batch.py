@@ -253,3 +253,26 @@ def test_batch_set_slice_restarts_one_slot(B):
         alone.set_slice(3, y_new, 0.08)
         alone.run(10, 20)
         assert np.array_equal(alone.slice_x(3), x3)
+
+
+def test_batch_autotune_keeps_results(B):
+    """The autotuner times every candidate FGP launch shape on the batch's data,
+    restores the state after each trial and keeps the fastest; the iterates
+    are bit-identical whatever it picks.  130x130 images (several regions)."""
+    n, na, nb = 130, 12, 185
+    A = synth.parallel_beam_csr(n, na, nb)
+    _, Y = synth.slice_stack(A, n, 8, 6, seed=3)
+    Y = Y.astype(np.float32)
+    u, _ = oracle.power_iteration(A)
+    mu, lam = 0.9 / (2 * u), np.full(6, 0.05)
+    with B.BatchReconstructor(A, (n, n), 6) as bt:
+        bt.set_data(Y, lam, mu)
+        bt.run(4, 30)
+        X_plain = bt.x().copy()
+        bt.set_data(Y, lam, mu)
+        bt.run(2, 30)
+        chunk, ms = bt.autotune(30, 2)
+        assert chunk in (3, 4, 5, 6, 8) and ms > 0
+        bt.run(2, 30)
+        X_tuned = bt.x().copy()
+    assert np.array_equal(X_plain, X_tuned)
