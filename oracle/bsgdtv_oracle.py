@@ -23,6 +23,15 @@ the design notes):
   R7  uneven blocks follow numpy.array_split: the first (L mod M) blocks get
       one extra unit.
   R8  u_max by power iteration on A^T A from the all-ones vector.
+  R10 stochastic variant (Sec. 3: only a fraction alpha of the column blocks
+      and gamma of the row blocks take part in an iteration): the drawn
+      subsets S_I, S_J are inputs; only the pairs in S_I x S_J form their
+      block products (from the current x and stored r); r_{I_i}, i in S_I,
+      becomes y_{I_i} - sum_j z^j_{I_i} with z^j of unselected j the value
+      last computed (0 before the first, consistent with x^0 = 0); x_{J_j},
+      j in S_J, gains mu * sum_{i in S_I} g-hat^i_{J_j} (no rescaling); the rest
+      of x and r is unchanged; the TV prox then acts on the whole image.
+      With every block selected this is exactly Algorithm 1's epoch.
 """
 from __future__ import annotations
 
@@ -35,7 +44,7 @@ __all__ = [
     "split_bounds", "partition", "split_blocks", "block_products", "reduce_residual",
     "reduce_gradient", "epoch", "run", "L_op", "Lt_op", "proj_iso", "fgp", "fgp_momentum",
     "tv_iso", "objective", "power_iteration", "descent_condition", "relative_error",
-    "to_scipy",
+    "to_scipy", "run_subsets",
 ]
 
 
@@ -257,6 +266,46 @@ def run(A, y, img_shape, M, N, lam, mu, epochs, fgp_iters, row_unit=1, col_unit=
         if callback is not None:
             callback(k, x, x_new, r)
         x = x_new
+    return x, r
+
+
+def run_subsets(A, y, img_shape, M, N, lam, mu, row_sel, col_sel, fgp_iters, row_unit=1,
+                col_unit=1):
+    """The stochastic variant of Sec. 3 under reading R10, one iteration per
+    row of the boolean masks row_sel [iters, M] and col_sel [iters, N], from
+    x^0 = 0 and r = y.  Returns (x, r)."""
+    A = to_scipy(A)
+    rows, cols = A.shape
+    rb, cb = partition(rows, cols, M, N, row_unit, col_unit)
+    blocks = split_blocks(A, rb, cb)
+    y = np.asarray(y, dtype=np.float64)
+    x = np.zeros(cols)
+    r = y.copy()
+    z = [[np.zeros(rb[i + 1] - rb[i]) for j in range(N)] for i in range(M)]   # last block products
+    for sel_i, sel_j in zip(np.asarray(row_sel, dtype=bool), np.asarray(col_sel, dtype=bool)):
+        S_I = [i for i in range(M) if sel_i[i]]
+        S_J = [j for j in range(N) if sel_j[j]]
+        gh = {}
+        for i in S_I:                                   # block products of the drawn pairs
+            for j in S_J:
+                gh[i, j] = 2.0 * (blocks[i][j].T @ r[rb[i]:rb[i + 1]])
+                z[i][j] = blocks[i][j] @ x[cb[j]:cb[j + 1]]
+        r = r.copy()
+        for i in S_I:                                   # residual of the drawn row blocks
+            acc = np.zeros(rb[i + 1] - rb[i])
+            for j in range(N):
+                acc = acc + z[i][j]
+            r[rb[i]:rb[i + 1]] = y[rb[i]:rb[i + 1]] - acc
+        x_hat = x.copy()
+        for j in S_J:                                   # gradient step on the drawn column blocks
+            acc = np.zeros(cb[j + 1] - cb[j])
+            for i in S_I:
+                acc = acc + gh[i, j]
+            x_hat[cb[j]:cb[j + 1]] = x[cb[j]:cb[j + 1]] + mu * acc
+        if lam > 0.0 and fgp_iters > 0:                 # TV prox on the whole image
+            x = fgp(x_hat.reshape(img_shape), mu * lam, fgp_iters).ravel()
+        else:
+            x = x_hat
     return x, r
 
 

@@ -186,6 +186,23 @@ def slice_stack(A: CSR, n: int, n_ellipses: int, slices: int, seed: int = 0,
     return X, Y
 
 
+def subset_draws(M: int, N: int, alpha: float, gamma: float, iters: int, seed: int = 0):
+    """Random block subsets for the stochastic variant (the draws are inputs of
+    the method, not part of it): per iteration max(1, round(gamma*M)) of the M
+    row blocks and max(1, round(alpha*N)) of the N column blocks, uniformly
+    without replacement, numpy default_rng(seed).  Returns boolean masks
+    (row_sel [iters, M], col_sel [iters, N])."""
+    rng = np.random.default_rng(seed)
+    kM = min(M, max(1, int(round(gamma * M))))
+    kN = min(N, max(1, int(round(alpha * N))))
+    row_sel = np.zeros((iters, M), dtype=bool)
+    col_sel = np.zeros((iters, N), dtype=bool)
+    for k in range(iters):
+        row_sel[k, rng.choice(M, kM, replace=False)] = True
+        col_sel[k, rng.choice(N, kN, replace=False)] = True
+    return row_sel, col_sel
+
+
 @dataclasses.dataclass(frozen=True)
 class Workload:
     """One reconstruction problem: geometry, phantom recipe and solver settings."""

@@ -3,6 +3,7 @@ Eq. 3 (stale-gradient recurrence), the fixed point of Sec. 2.2 (least
 squares), Theorem 1 and the companion-matrix eigenvalues of its proof,
 Theorem 2's descent condition, and an independent solver for lambda > 0."""
 import numpy as np
+import scipy.sparse as sp
 import pytest
 
 import oracle
@@ -150,3 +151,60 @@ def test_fixed_point_solves_tv_problem_independently():
     # the other reading of the weight (Eq. 1, 2 lambda TV) is a different point
     x_cp2 = cp_reconstruct(D, y, 2 * lam, (5, 5)).ravel()
     assert np.linalg.norm(x - x_cp2) / np.linalg.norm(x_cp2) > 10 * np.linalg.norm(x - x_cp) / np.linalg.norm(x_cp)
+
+
+# ------------------------------------------------- stochastic variant (Sec. 3, R10)
+def test_subset_draws_sizes_and_determinism():
+    R, C = synth.subset_draws(8, 6, 0.5, 0.25, 50, seed=4)
+    assert R.shape == (50, 8) and C.shape == (50, 6)
+    assert np.all(R.sum(1) == 2) and np.all(C.sum(1) == 3)
+    R2, C2 = synth.subset_draws(8, 6, 0.5, 0.25, 50, seed=4)
+    assert np.array_equal(R, R2) and np.array_equal(C, C2)
+    R3, C3 = synth.subset_draws(3, 3, 0.01, 0.01, 5)       # at least one block each
+    assert np.all(R3.sum(1) == 1) and np.all(C3.sum(1) == 1)
+
+
+def test_subsets_all_selected_is_algorithm1():
+    """Every block drawn every iteration: exactly the epochs of Algorithm 1."""
+    A = synth.parallel_beam_csr(16, 8, 23)
+    y = synth.noisy_projections(A, synth.phantom(16, 4, 0), 0)
+    u, _ = oracle.power_iteration(A)
+    mu = 0.9 / (2 * u)
+    rs, cs = np.ones((12, 3), bool), np.ones((12, 4), bool)
+    xa, ra = oracle.run_subsets(A, y, (16, 16), 3, 4, 0.05, mu, rs, cs, 10, row_unit=23, col_unit=16)
+    xb, rb_ = oracle.run(A, y, (16, 16), 3, 4, 0.05, mu, 12, 10, row_unit=23, col_unit=16)
+    assert np.array_equal(xa, xb) and np.array_equal(ra, rb_)
+
+
+def test_subsets_touch_only_the_drawn_blocks():
+    """With lambda = 0 one iteration changes x only on the drawn column blocks
+    and r only on the drawn row blocks."""
+    A = synth.parallel_beam_csr(16, 8, 23)
+    y = synth.noisy_projections(A, synth.phantom(16, 4, 1), 1)
+    rb, cb = oracle.partition(A.rows, A.cols_n, 4, 4, 23, 16)
+    u, _ = oracle.power_iteration(A)
+    mu = 0.9 / (2 * u)
+    R = np.array([[True] * 4, [False, True, False, False]])
+    C = np.array([[True] * 4, [False, False, True, False]])
+    x1, r1 = oracle.run_subsets(A, y, (16, 16), 4, 4, 0.0, mu, R[:1], C[:1], 0, 23, 16)
+    x2, r2 = oracle.run_subsets(A, y, (16, 16), 4, 4, 0.0, mu, R, C, 0, 23, 16)
+    outside = np.ones(A.cols_n, bool)
+    outside[cb[2]:cb[3]] = False
+    assert np.array_equal(x1[outside], x2[outside]) and not np.array_equal(x1, x2)
+    rows_out = np.ones(A.rows, bool)
+    rows_out[rb[1]:rb[2]] = False
+    assert np.array_equal(r1[rows_out], r2[rows_out]) and not np.array_equal(r1, r2)
+
+
+def test_subsets_converge_on_a_consistent_system():
+    """lambda = 0 and y = A x_true with A of full column rank: the stochastic
+    iteration (stale block products included) reaches x_true."""
+    rng = np.random.default_rng(1)
+    D = rng.random((48, 16)) * (rng.random((48, 16)) < 0.5)
+    x_true = rng.random(16)
+    y = D @ x_true
+    mu = 0.9 / (2 * np.linalg.eigvalsh(D.T @ D).max())
+    for a, g in [(0.5, 0.5), (0.25, 0.75)]:
+        R, C = synth.subset_draws(4, 4, a, g, 20000, seed=3)
+        x, _ = oracle.run_subsets(sp.csr_matrix(D), y, (4, 4), 4, 4, 0.0, mu, R, C, 0)
+        assert np.linalg.norm(x - x_true) <= 1e-10 * np.linalg.norm(x_true)
