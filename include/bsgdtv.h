@@ -120,6 +120,21 @@ int bsgdtv_get_params(bsgdtv_t h, double *mu, double *lambda, double *u_max);
  * on the handle's stream; resumes from the current state. */
 int bsgdtv_run(bsgdtv_t h, int epochs, int fgp_iters);
 
+/* The stochastic variant of Sec. 3: `iters` iterations in which only the
+ * drawn row blocks (row_sel [iters][M], nonzero = drawn) and column blocks
+ * (col_sel [iters][N]) take part; the draws are the caller's (host arrays).
+ * Iteration k: the pairs (i, j) with both drawn form their block products
+ * from the current x and r; r on the drawn row blocks becomes
+ * y - sum_j z^j with z^j of undrawn j the last one computed (0 after
+ * set_data, consistent with x^0 = 0); x on the drawn column blocks gains
+ * mu * sum over drawn i of g-hat^i; other parts of r and x are unchanged; the
+ * TV prox then acts on the whole image.  With every block drawn it is
+ * bsgdtv_run.  Every iteration must draw at least one row and one column
+ * block (else BSGDTV_ERR_INVALID_ARG).  Counts iterations in the epoch
+ * counter; synchronises before returning (the host arrays may be freed). */
+int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_sel,
+                       const uint8_t *col_sel);
+
 /* bsgdtv_run that also times, with CUDA events recorded on the handle's
  * stream inside the epoch graphs, every launch of the fused product kernel
  * (the block products) and every whole epoch.  Synchronises.  products_ms / epoch_ms

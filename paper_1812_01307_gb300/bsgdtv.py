@@ -46,6 +46,7 @@ def load(path: str | None = None):
         "bsgdtv_get_params": (I32, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
         "bsgdtv_run": (I32, [P, I32, I32]),
         "bsgdtv_run_timed": (I32, [P, I32, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "bsgdtv_run_subsets": (I32, [P, I32, I32, P, P]),
         "bsgdtv_get_x": (I32, [P, P, I32]),
         "bsgdtv_get_state": (I32, [P, P, P, ctypes.POINTER(I64), I32]),
         "bsgdtv_set_state": (I32, [P, P, P, I64, I32]),
@@ -96,7 +97,7 @@ def exported_symbols():
             "bsgdtv_estimate_umax", "bsgdtv_get_params", "bsgdtv_run", "bsgdtv_run_timed", "bsgdtv_get_x",
             "bsgdtv_get_state", "bsgdtv_set_state", "bsgdtv_objective", "bsgdtv_block_products",
             "bsgdtv_get_info", "bsgdtv_tv_prox", "bsgdtv_tv_prox_static", "bsgdtv_partition_bounds",
-            "bsgdtv_layout_check", "bsgdtv_batch_create_csr", "bsgdtv_batch_destroy",
+            "bsgdtv_layout_check", "bsgdtv_run_subsets", "bsgdtv_batch_create_csr", "bsgdtv_batch_destroy",
             "bsgdtv_batch_set_data", "bsgdtv_batch_run", "bsgdtv_batch_run_timed",
             "bsgdtv_batch_get_x", "bsgdtv_batch_create_csr_ex", "bsgdtv_batch_set_slice",
             "bsgdtv_batch_get_slice_x", "bsgdtv_batch_device_bytes", "bsgdtv_server_create",
@@ -235,6 +236,16 @@ def bsgdtv_run_timed(h, epochs, fgp_iters):
     _check(load().bsgdtv_run_timed(h, int(epochs), int(fgp_iters), ctypes.byref(pk),
                                    ctypes.byref(ep)), "bsgdtv_run_timed")
     return pk.value, ep.value
+
+
+def bsgdtv_run_subsets(h, row_sel, col_sel, fgp_iters):
+    """Stochastic iterations: boolean masks row_sel [iters, M], col_sel [iters, N]."""
+    rs = np.ascontiguousarray(row_sel, dtype=np.uint8)
+    cs = np.ascontiguousarray(col_sel, dtype=np.uint8)
+    if rs.ndim != 2 or cs.ndim != 2 or rs.shape[0] != cs.shape[0]:
+        raise ValueError("row_sel [iters, M] and col_sel [iters, N] with the same iters")
+    _check(load().bsgdtv_run_subsets(h, int(rs.shape[0]), int(fgp_iters), _host_ptr(rs, np.uint8),
+                                     _host_ptr(cs, np.uint8)), "bsgdtv_run_subsets")
 
 
 def bsgdtv_get_info(h):
@@ -608,6 +619,9 @@ class Reconstructor:
 
     def run(self, epochs, fgp_iters):
         bsgdtv_run(self.h, epochs, fgp_iters)
+
+    def run_subsets(self, row_sel, col_sel, fgp_iters):
+        bsgdtv_run_subsets(self.h, row_sel, col_sel, fgp_iters)
 
     def x(self, out=None):
         if out is None:

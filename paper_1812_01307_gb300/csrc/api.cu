@@ -69,6 +69,12 @@ struct bsgdtv_ctx {
     double *v64 = nullptr, *w64 = nullptr, *g64 = nullptr, *z64 = nullptr, *gp64 = nullptr,
            *y64 = nullptr, *x64 = nullptr, *partials = nullptr, *scal = nullptr;
 
+    // stochastic variant: block bounds on the device and a scratch buffer for
+    // the per-iteration work-item lists and block masks (grown on demand)
+    int64_t *rb_dev = nullptr, *cb_dev = nullptr;
+    void *sub_buf = nullptr;
+    size_t sub_bytes = 0;
+
     // graphs: one per parity of the r double buffer
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     // timed variant: event-record nodes around the product kernel and at the
@@ -545,8 +551,9 @@ int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, 
         BSG_CUDA(cudaStreamSynchronize(s));
         if (flag) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
     }
-    // x^0 = 0, r^{-1} = y - A x^0 = y
+    // x^0 = 0, r^{-1} = y - A x^0 = y; the last block products are A x^0 = 0
     BSG_CUDA(cudaMemsetAsync(h->x, 0, c * sizeof(float), s));
+    BSG_CUDA(cudaMemsetAsync(h->z_part, 0, (size_t)h->dl.n_slabs * kSlab * sizeof(float), s));
     h->cur = 0;
     BSG_CUDA(cudaMemcpyAsync(h->r[0], h->y, R * sizeof(float), cudaMemcpyDeviceToDevice, s));
     BSG_CUDA(cudaMemsetAsync(h->rmax, 0, sizeof(float), s));
@@ -629,6 +636,79 @@ int bsgdtv_run_timed(bsgdtv_t h, int epochs, int fgp_iters, double *products_ms,
     }
     if (products_ms) *products_ms = pk;
     if (epoch_ms) *epoch_ms = ep;
+    return BSGDTV_OK;
+}
+
+int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_sel,
+                       const uint8_t *col_sel) {
+    if (!h || !row_sel || !col_sel) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    if (!h->has_data) return fail(BSGDTV_ERR_STATE, "bsgdtv_run_subsets before bsgdtv_set_data");
+    if (iters < 0 || fgp_iters < 0) return fail(BSGDTV_ERR_INVALID_ARG, "negative iters / fgp_iters");
+    if (iters == 0) return BSGDTV_OK;
+    const HostLayout &L = h->host;
+    const int M = L.M, N = L.N;
+    for (int k = 0; k < iters; ++k) {
+        int ni = 0, nj = 0;
+        for (int i = 0; i < M; ++i) ni += row_sel[(size_t)k * M + i] != 0;
+        for (int j = 0; j < N; ++j) nj += col_sel[(size_t)k * N + j] != 0;
+        if (ni == 0 || nj == 0)
+            return fail(BSGDTV_ERR_INVALID_ARG, "every iteration must draw at least one row and one column block");
+    }
+    BSG_CHECK(set_device(h));
+    cudaStream_t s = h->stream;
+    if (!h->rb_dev) {
+        BSG_CHECK(upload(h, &h->rb_dev, L.row_bounds));
+        BSG_CHECK(upload(h, &h->cb_dev, L.col_bounds));
+    }
+    // per iteration: the work items of the drawn pairs (launch order kept), then the masks
+    const int n_items = (int)L.items.size();
+    const size_t item_bytes = (size_t)n_items * sizeof(WorkItem);
+    const size_t stride = (item_bytes + (size_t)M + N + 255) / 256 * 256;
+    std::vector<unsigned char> host(stride * iters, 0);
+    std::vector<int> count(iters, 0);
+    for (int k = 0; k < iters; ++k) {
+        unsigned char *base = host.data() + stride * k;
+        WorkItem *list = reinterpret_cast<WorkItem *>(base);
+        const uint8_t *si = row_sel + (size_t)k * M, *sj = col_sel + (size_t)k * N;
+        for (const WorkItem &it : L.items)
+            if (si[L.group_block[it.group]] && sj[L.tiles[it.tile].band]) list[count[k]++] = it;
+        for (int i = 0; i < M; ++i) base[item_bytes + i] = si[i] ? 1 : 0;
+        for (int j = 0; j < N; ++j) base[item_bytes + M + j] = sj[j] ? 1 : 0;
+    }
+    if (host.size() > h->sub_bytes) {
+        BSG_CUDA(cudaStreamSynchronize(s));   // the previous buffer may still be read
+        unsigned char *p = nullptr;
+        BSG_CHECK(dalloc(h, &p, host.size()));
+        h->sub_buf = p;
+        h->sub_bytes = host.size();
+    }
+    unsigned char *dev = static_cast<unsigned char *>(h->sub_buf);
+    BSG_CUDA(cudaMemcpyAsync(dev, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+    BSG_CHECK(ensure_mom(h, std::max(fgp_iters, 1)));
+    const bool prox = h->lambda > 0.0 && fgp_iters > 0;
+    for (int k = 0; k < iters; ++k) {
+        const int par = h->cur;
+        unsigned char *base = dev + stride * k;
+        DevLayout ds = h->dl;
+        ds.items = reinterpret_cast<const WorkItem *>(base);
+        ds.n_items = count[k];
+        BSG_CUDA(launch_products32(ds, h->x, h->r[par], h->rmax + par, h->rmax + (1 - par), h->z_part,
+                                   reinterpret_cast<int32_t *>(h->g_part), s, false));
+        float *xdst = prox ? h->xhat : h->x;
+        BSG_CUDA(launch_reduce_subset32(h->dl, h->z_part, reinterpret_cast<const int32_t *>(h->g_part),
+                                        h->rmax + par, h->y, h->r[par], h->r[1 - par],
+                                        h->rmax + (1 - par), h->x, xdst, (float)h->mu, h->rb_dev,
+                                        h->cb_dev, base + item_bytes, base + item_bytes + M, s));
+        if (prox) {
+            FgpScratch sc{h->fp, h->fq, h->fpp, h->fqp};
+            BSG_CUDA(launch_fgp(h->xhat, h->x, h->dl.img_h, h->dl.img_w, (float)(h->mu * h->lambda),
+                                fgp_iters, h->mom, sc, s, false));
+        }
+        h->cur ^= 1;
+        h->epoch++;
+    }
+    // the host copy of the lists dies here: wait for the upload
+    BSG_CUDA(cudaStreamSynchronize(s));
     return BSGDTV_OK;
 }
 

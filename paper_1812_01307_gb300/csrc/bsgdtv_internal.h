@@ -202,6 +202,14 @@ cudaError_t launch_reduce_update32(const DevLayout &d, const float *z_part, cons
                                    const float *rmax_in, const float *y, float *r_out,
                                    float *rmax_out, const float *x, float *x_out, float mu,
                                    cudaStream_t s, bool pdl = false);
+// Stochastic variant: the reductions restricted to the drawn row blocks
+// (sel_i [M]) and column blocks (sel_j [N]); rb [M+1], cb [N+1] are the block
+// bounds; rows / pixels outside keep r_in / x.
+cudaError_t launch_reduce_subset32(const DevLayout &d, const float *z_part, const int32_t *g_part,
+                                   const float *rmax_in, const float *y, const float *r_in,
+                                   float *r_out, float *rmax_out, const float *x, float *x_out,
+                                   float mu, const int64_t *rb, const int64_t *cb,
+                                   const uint8_t *sel_i, const uint8_t *sel_j, cudaStream_t s);
 cudaError_t launch_block_sums(const DevLayout &d, const float *z_part, const int32_t *g_part,
                               const float *rmax_in, float *z_blocks, float *g_blocks,
                               cudaStream_t s);

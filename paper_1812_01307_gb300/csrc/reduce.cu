@@ -84,6 +84,67 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+__device__ __forceinline__ int block_of(const int64_t *__restrict__ bounds, int nb, int64_t v) {
+    int lo = 0, hi = nb - 1;   // largest b with bounds[b] <= v
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bounds[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Stochastic variant: the same reductions restricted to the drawn blocks.
+// Rows of drawn row blocks: r = y - sum of all segment partials (partials of
+// undrawn pairs are the last ones computed); other rows keep r_in.  Pixels of
+// drawn column blocks: x' = x + mu * (sum over groups of drawn row blocks of
+// the fixed-point tiles); other pixels keep x.
+__global__ void __launch_bounds__(kThreads)
+    reduce_subset32_kernel(const DevLayout d, const float *__restrict__ z_part,
+                           const int32_t *__restrict__ g_part, const float *__restrict__ rmax_in,
+                           const float *__restrict__ y, const float *__restrict__ r_in,
+                           float *__restrict__ r_out, float *rmax_out, const float *x,
+                           float *x_out, float mu, int nb_rows, const int64_t *__restrict__ rb,
+                           const int64_t *__restrict__ cb, const uint8_t *__restrict__ sel_i,
+                           const uint8_t *__restrict__ sel_j) {
+    if ((int)blockIdx.x < nb_rows) {
+        const int64_t ray = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+        float rv = 0.f;
+        if (ray < d.rows) {
+            if (sel_i[block_of(rb, d.M, ray)]) {
+                const int e0 = d.ray_seg_ptr[ray], e1 = d.ray_seg_ptr[ray + 1];
+                float acc = 0.f;
+                for (int e = e0; e < e1; ++e) acc += z_part[d.ray_seg_pos[e]];
+                rv = y[ray] - acc;
+            } else {
+                rv = r_in[ray];
+            }
+            r_out[ray] = rv;
+        }
+        __shared__ float wmax[kThreads / 32];
+        float m = fabsf(rv);
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            m = (threadIdx.x < kThreads / 32) ? wmax[threadIdx.x] : 0.f;
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (threadIdx.x == 0) atomic_max_nonneg(rmax_out, m);
+        }
+    } else {
+        const int64_t p = (int64_t)(blockIdx.x - nb_rows) * kThreads + threadIdx.x;
+        if (p >= d.cols) return;
+        if (!sel_j[block_of(cb, d.N, p)]) {
+            x_out[p] = x[p];
+            return;
+        }
+        long long acc = 0;
+        for (int g = 0; g < d.n_groups; ++g)
+            if (sel_i[d.group_block[g]]) acc += g_part[(int64_t)g * d.cols + p];
+        const double inv = 1.0 / (double)fixed_scale(*rmax_in, d.colsum_max);
+        x_out[p] = x[p] + mu * (float)((double)acc * inv);
+    }
+}
+
 // Per-block sums of the block products for the test hook.
 __global__ void block_sums_kernel(const DevLayout d, const float *__restrict__ z_part,
                                   const int32_t *__restrict__ g_part,
@@ -237,6 +298,20 @@ cudaError_t launch_reduce_update64(const DevLayout &d, const double *z_part, con
     const int nb_cols = (int)((d.cols + kThreads - 1) / kThreads);
     reduce_update64_kernel<<<nb_rows + nb_cols, kThreads, 0, s>>>(d, z_part, g_part, y, r_out, x,
                                                                   x_out, mu, nb_rows);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_subset32(const DevLayout &d, const float *z_part, const int32_t *g_part,
+                                   const float *rmax_in, const float *y, const float *r_in,
+                                   float *r_out, float *rmax_out, const float *x, float *x_out,
+                                   float mu, const int64_t *rb, const int64_t *cb,
+                                   const uint8_t *sel_i, const uint8_t *sel_j, cudaStream_t s) {
+    const int nb_rows = (int)((d.rows + kThreads - 1) / kThreads);
+    const int nb_cols = (int)((d.cols + kThreads - 1) / kThreads);
+    reduce_subset32_kernel<<<nb_rows + nb_cols, kThreads, 0, s>>>(
+        d, z_part, g_part, rmax_in, y, r_in, r_out, rmax_out, x, x_out, mu, nb_rows, rb, cb, sel_i,
+        sel_j);
     add_launches(1);
     return cudaGetLastError();
 }
