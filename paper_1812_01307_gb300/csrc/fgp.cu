@@ -9,9 +9,9 @@
 //   (r, s)   = (p, q) + beta_k (p - p_prev, q - q_prev)
 // and finally x = b - tau L(p, q).
 //
-// GPU mapping: each CTA owns a 64 x 64 pixel region; every thread keeps a
-// vertical strip of 8 pixels' fields (b, p, q, p_prev, q_prev, r, s, u) in
-// registers for all the iterations of one launch.  Only the values a
+// GPU mapping: each CTA owns a 64 x 64 pixel region (64 x 16 threads); every
+// thread keeps a vertical strip of 4 pixels' fields (b, p, q, p_prev, q_prev,
+// r, s, u) in registers for all the iterations of one launch.  Only the values a
 // neighbour needs (s to the right neighbour, r across strip boundaries, u to
 // the left / upper neighbour) pass through zero-padded shared buffers, two
 // barriers per iteration, with no bounds tests in the iteration.  When the image fits one region the whole FGP is one launch;
