@@ -539,8 +539,7 @@ int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, 
     cudaStream_t s = h->stream;
     const int64_t R = h->dl.rows, c = h->dl.cols;
     if (!y_on_device) {
-        for (int64_t i = 0; i < R; ++i)
-            if (!std::isfinite(y[i])) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+        if (!all_finite(y, R)) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
         BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float), cudaMemcpyHostToDevice, s));
     } else {
         BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float), cudaMemcpyDeviceToDevice, s));

@@ -785,9 +785,8 @@ int bsgdtv_batch_set_data(bsgdtv_batch_t h, const float *y, int y_on_device,
     BSG_CUDA(cudaSetDevice(h->device));
     cudaStream_t s = h->stream;
     const int64_t rows = h->rows, n_in = rows * h->B;
-    if (!y_on_device)
-        for (int64_t i = 0; i < n_in; ++i)
-            if (!std::isfinite(y[i])) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+    if (!y_on_device && !all_finite(y, n_in))
+        return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
     // y arrives slice-major [B][rows]; it is staged in R[1] (rows * Bp >= rows * B
     // floats) and interleaved into Y; the first epoch rewrites R[1] in full
     BSG_CUDA(cudaMemcpyAsync(h->R[1], y, (size_t)n_in * sizeof(float),
@@ -890,9 +889,8 @@ int bsgdtv_batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_dev
     BSG_CUDA(cudaSetDevice(h->device));
     cudaStream_t s = h->stream;
     const int64_t rows = h->rows;
-    if (y && !y_on_device)
-        for (int64_t i = 0; i < rows; ++i)
-            if (!std::isfinite(y[i])) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+    if (y && !y_on_device && !all_finite(y, rows))
+        return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
     if (y) {
         BSG_CUDA(cudaMemcpyAsync(h->ystage, y, (size_t)rows * sizeof(float),
                                  y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -28,6 +29,18 @@ int fail(int code, const std::string &msg);
     } while (0)
 
 void add_launches(int64_t n);
+
+// True if no entry of y[0..n) is NaN or +-Inf (exponent bits all ones);
+// branch-free over the whole array so the compiler can vectorise it.
+inline bool all_finite(const float *y, int64_t n) {
+    uint32_t bad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t b;
+        std::memcpy(&b, y + i, sizeof(b));
+        bad |= (uint32_t)((b & 0x7f800000u) == 0x7f800000u);
+    }
+    return bad == 0;
+}
 
 // Kernel launch with optional programmatic dependent launch (PDL): the grid
 // may be scheduled while its predecessor in the stream drains; the kernel

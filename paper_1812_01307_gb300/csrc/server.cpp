@@ -445,8 +445,7 @@ int bsgdtv_server_submit(bsgdtv_server_t s, int geom_id, const float *y, double 
             return fail(BSGDTV_ERR_INVALID_ARG, "unknown geometry");
         if (s->stop) return fail(BSGDTV_ERR_STATE, "server is stopping");
         const int64_t rows = s->geoms[geom_id]->rows;
-        for (int64_t i = 0; i < rows; ++i)
-            if (!std::isfinite(y[i])) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+        if (!bsgdtv::all_finite(y, rows)) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
         try {
             r->y.assign(y, y + rows);
         } catch (const std::bad_alloc &) {
