@@ -170,7 +170,8 @@ int enqueue_epoch(bsgdtv_ctx *h, int par, int fgp_iters, cudaStream_t s,
     if (prox) {
         FgpScratch sc{h->fp, h->fq, h->fpp, h->fqp};
         BSG_CUDA(launch_fgp(h->xhat, h->x, h->dl.img_h, h->dl.img_w, (float)(h->mu * h->lambda),
-                            fgp_iters, h->mom, sc, s, true));
+                            fgp_iters, h->mom, sc, s, true,
+                            fgp_chunk_for(h->dl.img_h, h->dl.img_w, fgp_iters, h->dl.n_sms)));
     }
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[2], s, cudaEventRecordExternal));
     return BSGDTV_OK;
@@ -701,7 +702,8 @@ int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_
         if (prox) {
             FgpScratch sc{h->fp, h->fq, h->fpp, h->fqp};
             BSG_CUDA(launch_fgp(h->xhat, h->x, h->dl.img_h, h->dl.img_w, (float)(h->mu * h->lambda),
-                                fgp_iters, h->mom, sc, s, false));
+                                fgp_iters, h->mom, sc, s, false,
+                                fgp_chunk_for(h->dl.img_h, h->dl.img_w, fgp_iters, h->dl.n_sms)));
         }
         h->cur ^= 1;
         h->epoch++;

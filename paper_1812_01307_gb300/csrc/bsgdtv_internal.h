@@ -245,9 +245,13 @@ constexpr int kDotPartials = 1024;
 struct FgpScratch {
     float *p, *q, *pp, *qp;
 };
-int fgp_plan_launches(int h, int w, int iters);
+// Iterations per launch for an h x w image on n_sms SMs (a cost model of
+// halo recomputation, waves and launches; every choice gives the same iterates).
+int fgp_chunk_for(int h, int w, int iters, int n_sms);
+int fgp_plan_launches(int h, int w, int iters, int max_chunk = 8);
 cudaError_t launch_fgp(const float *b, float *x, int h, int w, float tau, int iters,
-                       const float *mom, FgpScratch sc, cudaStream_t s, bool pdl = false);
+                       const float *mom, FgpScratch sc, cudaStream_t s, bool pdl = false,
+                       int max_chunk = 8);
 void fgp_momentum_host(int iters, std::vector<float> &mom);
 
 // batch.cu: host check of a CSR image operator (sizes, sorted in-range

@@ -43,15 +43,37 @@ void fgp_momentum_host(int iters, std::vector<float> &mom) {
     }
 }
 
-int fgp_plan_launches(int h, int w, int iters) {
+int fgp_chunk_for(int h, int w, int iters, int n_sms) {
+    if (iters <= 0 || fits_one_region(h, w)) return std::max(iters, 1);
+    // cost in iteration-times of one region: per launch, the waves of
+    // 1-CTA-per-SM regions times the iterations, plus about two iterations of
+    // launch ramp; fewer iterations per launch shrink the halo (more useful
+    // pixels per region, fewer regions) but add launches
+    int best = kMaxChunk;
+    long long best_cost = -1;
+    for (int c = 4; c <= 12; ++c) {
+        const int inner = RW - 2 * (c + 1);
+        const long long grid = (long long)((w + inner - 1) / inner) * ((h + inner - 1) / inner);
+        const long long waves = (grid + std::max(n_sms, 1) - 1) / std::max(n_sms, 1);
+        const long long cost = (long long)((iters + c - 1) / c) * (waves * c + 2);
+        if (best_cost < 0 || cost <= best_cost) {
+            best_cost = cost;
+            best = c;
+        }
+    }
+    return best;
+}
+
+int fgp_plan_launches(int h, int w, int iters, int max_chunk) {
     if (iters <= 0) return 0;
     if (fits_one_region(h, w)) return 1;
-    return (iters + kMaxChunk - 1) / kMaxChunk;
+    return (iters + max_chunk - 1) / max_chunk;
 }
 
 cudaError_t launch_fgp(const float *b, float *x, int h, int w, float tau, int iters,
-                       const float *mom, FgpScratch sc, cudaStream_t s, bool pdl) {
-    return launch_fgp_regions<false>(b, x, h, w, tau, nullptr, 1, 0, iters, mom, sc, s, pdl);
+                       const float *mom, FgpScratch sc, cudaStream_t s, bool pdl, int max_chunk) {
+    return launch_fgp_regions<false>(b, x, h, w, tau, nullptr, 1, 0, iters, mom, sc, s, pdl,
+                                     max_chunk);
 }
 
 }  // namespace bsgdtv

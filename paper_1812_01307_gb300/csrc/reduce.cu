@@ -42,6 +42,26 @@ __device__ __forceinline__ void atomic_max_nonneg(float *dst, float v) {
     atomicMax(reinterpret_cast<int *>(dst), __float_as_int(v));
 }
 
+// Sum of a row's segment partials in segment (ascending tile) order, with
+// four loads in flight.
+__device__ __forceinline__ float row_partial_sum(const DevLayout &d, const float *__restrict__ z_part,
+                                                 int64_t ray) {
+    const int e0 = d.ray_seg_ptr[ray], e1 = d.ray_seg_ptr[ray + 1];
+    float acc = 0.f;
+    int e = e0;
+    for (; e + 4 <= e1; e += 4) {
+        const int p0 = d.ray_seg_pos[e], p1 = d.ray_seg_pos[e + 1], p2 = d.ray_seg_pos[e + 2],
+                  p3 = d.ray_seg_pos[e + 3];
+        const float z0 = z_part[p0], z1 = z_part[p1], z2 = z_part[p2], z3 = z_part[p3];
+        acc += z0;
+        acc += z1;
+        acc += z2;
+        acc += z3;
+    }
+    for (; e < e1; ++e) acc += z_part[d.ray_seg_pos[e]];
+    return acc;
+}
+
 // FP32 hot path.  Rows: r = y - sum_j z and max |r| for the next
 // product pass.  Pixels: g = exact int64 sum of the groups' fixed-point tiles,
 // one rounding to FP32, x' = x + mu g.
@@ -55,10 +75,7 @@ __global__ void __launch_bounds__(kThreads)
         const int64_t ray = (int64_t)blockIdx.x * kThreads + threadIdx.x;
         float rv = 0.f;
         if (ray < d.rows) {
-            const int e0 = d.ray_seg_ptr[ray], e1 = d.ray_seg_ptr[ray + 1];
-            float acc = 0.f;
-            for (int e = e0; e < e1; ++e) acc += z_part[d.ray_seg_pos[e]];
-            rv = y[ray] - acc;
+            rv = y[ray] - row_partial_sum(d, z_part, ray);
             r_out[ray] = rv;
         }
         if (rmax_out) {
@@ -111,10 +128,7 @@ __global__ void __launch_bounds__(kThreads)
         float rv = 0.f;
         if (ray < d.rows) {
             if (sel_i[block_of(rb, d.M, ray)]) {
-                const int e0 = d.ray_seg_ptr[ray], e1 = d.ray_seg_ptr[ray + 1];
-                float acc = 0.f;
-                for (int e = e0; e < e1; ++e) acc += z_part[d.ray_seg_pos[e]];
-                rv = y[ray] - acc;
+                rv = y[ray] - row_partial_sum(d, z_part, ray);
             } else {
                 rv = r_in[ray];
             }
