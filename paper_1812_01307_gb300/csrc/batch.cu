@@ -319,6 +319,8 @@ struct bsgdtv_batch_ctx {
     PassOperand op_r = {}, op_c = {};   // A in CSR / CSC: entries (weight, idx * Bp)
     bool matrix_free = false;           // weights computed on the fly (parallel beam)
     int fgp_chunk = kBatchFgpChunk;     // FGP iterations per launch (autotuned)
+    double *dot_part = nullptr;         // power-iteration partial sums (first use)
+    float *save_x = nullptr, *save_r[2] = {nullptr, nullptr};   // autotuner state copy (first use)
     MfGeometry mfg;
     float *ystage = nullptr;            // [max(rows, cols)] planar staging for one slice
     float *X = nullptr, *Xhat = nullptr, *Y = nullptr, *R[2] = {nullptr, nullptr};   // interleaved
@@ -924,8 +926,8 @@ int bsgdtv_batch_estimate_umax(bsgdtv_batch_t h, int max_iters, double rel_tol, 
     cudaStream_t s = h->stream;
     const int64_t c = h->cols, R = h->rows;
     std::vector<double> part(kDotBlocks);
-    double *d_part = nullptr;
-    BSG_CHECK(balloc(h, &d_part, kDotBlocks));   // kept with the batch's memory
+    if (!h->dot_part) BSG_CHECK(balloc(h, &h->dot_part, kDotBlocks));
+    double *d_part = h->dot_part;
     auto dot = [&](const float *a, const float *b, double *out) -> int {
         slice_dot_kernel<<<kDotBlocks, 256, 0, s>>>(a, b, c, h->Bp, d_part);
         add_launches(1);
@@ -1019,10 +1021,12 @@ int bsgdtv_batch_autotune(bsgdtv_batch_t h, int fgp_iters, int epochs_per_trial,
     cudaStream_t s = h->stream;
     const size_t xb = (size_t)h->cols * h->Bp * sizeof(float), rb = (size_t)h->rows * h->Bp * sizeof(float);
     // the trials run real epochs: keep x^k, r^{k-1} (and r^k's buffer) to restore after each
-    float *sx = nullptr, *sr0 = nullptr, *sr1 = nullptr;
-    BSG_CHECK(balloc(h, &sx, xb / sizeof(float)));
-    BSG_CHECK(balloc(h, &sr0, rb / sizeof(float)));
-    BSG_CHECK(balloc(h, &sr1, rb / sizeof(float)));
+    if (!h->save_x) {
+        BSG_CHECK(balloc(h, &h->save_x, xb / sizeof(float)));
+        BSG_CHECK(balloc(h, &h->save_r[0], rb / sizeof(float)));
+        BSG_CHECK(balloc(h, &h->save_r[1], rb / sizeof(float)));
+    }
+    float *sx = h->save_x, *sr0 = h->save_r[0], *sr1 = h->save_r[1];
     BSG_CUDA(cudaMemcpyAsync(sx, h->X, xb, cudaMemcpyDeviceToDevice, s));
     BSG_CUDA(cudaMemcpyAsync(sr0, h->R[0], rb, cudaMemcpyDeviceToDevice, s));
     BSG_CUDA(cudaMemcpyAsync(sr1, h->R[1], rb, cudaMemcpyDeviceToDevice, s));
