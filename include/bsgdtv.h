@@ -28,6 +28,9 @@
  *     (Neumann) border, the discretisation FGP is defined on.
  *   - Floating point: A values, x, y, r are FP32 with FP32 accumulation on the
  *     hot path; u_max and the objective are computed in FP64.
+ *   - Threads: calls on one handle (bsgdtv_t, bsgdtv_batch_t) must not
+ *     overlap; different handles may be used from different threads.  The
+ *     server (bsgdtv_server_t) accepts calls from any thread at any time.
  */
 #ifndef BSGDTV_H
 #define BSGDTV_H
