@@ -36,10 +36,17 @@ struct FgpShared {
 // makes the joint projection exactly the single-component clip t/max(1,|t|);
 // outside the image both are zeroed.  rsqrtf(max(n2, 1)) is the scale
 // 1/max(1, sqrt(n2)).
-template <int TY, int V>
+//
+// kStepRegs: the dual step 1/(8 tau) is held per pixel and component (cp, cq:
+// 1/(8 tau) where p / q is defined, else 0) instead of testing mask bits; at
+// the undefined places p, q and the momentum point are exactly 0 throughout,
+// so fmaf(d, 0, 0) = 0 gives the same bits as the masked form with two
+// instructions fewer per component (at 2V more registers).
+template <int TY, int V, bool kStepRegs>
 __device__ __forceinline__ void fgp_step(float (&p)[V], float (&pp)[V], float (&q)[V],
                                          float (&qp)[V], const float (&bb)[V], unsigned pmask,
-                                         unsigned qmask, float beta, float tau, float c8,
+                                         unsigned qmask, const float (&cp)[V],
+                                         const float (&cq)[V], float beta, float tau, float c8,
                                          FgpShared<TY, V> &sh, int tx, int ty) {
     float rr[V], ss[V], uu[V];
     // momentum point (r, s) from the last two iterates
@@ -65,8 +72,14 @@ __device__ __forceinline__ void fgp_step(float (&p)[V], float (&pp)[V], float (&
     for (int v = 0; v < V; ++v) {
         const float u_down = (v < V - 1) ? uu[v + 1] : sh.u[ty * V + V][tx + 1];
         const float u_right = sh.u[ty * V + v][tx + 2];
-        const float pt = (pmask & (1u << v)) ? fmaf(uu[v] - u_down, c8, rr[v]) : 0.f;
-        const float qt = (qmask & (1u << v)) ? fmaf(uu[v] - u_right, c8, ss[v]) : 0.f;
+        float pt, qt;
+        if constexpr (kStepRegs) {
+            pt = fmaf(uu[v] - u_down, cp[v], rr[v]);
+            qt = fmaf(uu[v] - u_right, cq[v], ss[v]);
+        } else {
+            pt = (pmask & (1u << v)) ? fmaf(uu[v] - u_down, c8, rr[v]) : 0.f;
+            qt = (qmask & (1u << v)) ? fmaf(uu[v] - u_right, c8, ss[v]) : 0.f;
+        }
         const float inv = rsqrtf(fmaxf(fmaf(pt, pt, qt * qt), 1.f));
         pp[v] = pt * inv;
         qp[v] = qt * inv;
@@ -76,8 +89,9 @@ __device__ __forceinline__ void fgp_step(float (&p)[V], float (&pp)[V], float (&
 // kBatch: blockIdx.z selects one of several images stored `plane` floats
 // apart (b, x_out and the four dual fields alike), each with its own weight
 // tau_z[z]; a weight <= 0 makes that image's prox the identity.
-// TY x V: threads in y x pixels per thread (TY * V = RH).
-template <bool kBatch, int TY, int V>
+// TY x V: threads in y x pixels per thread (TY * V = RH); kStepRegs: see
+// fgp_step.
+template <bool kBatch, int TY, int V, bool kStepRegs>
 __global__ void __launch_bounds__(RW *TY)
     fgp_kernel(const float *__restrict__ b, float *__restrict__ x_out, int H, int W, float tau,
                float c8, const float *__restrict__ mom, int k0, int iters, int HL, int IH, int IW,
@@ -152,13 +166,23 @@ __global__ void __launch_bounds__(RW *TY)
         }
     }
 
+    float cp[V], cq[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        cp[v] = (pmask & (1u << v)) ? c8 : 0.f;
+        cq[v] = (qmask & (1u << v)) ? c8 : 0.f;
+    }
+
     int it = 0;
     for (; it + 2 <= iters; it += 2) {
-        fgp_step<TY, V>(pa, pb, qa, qb, bb, pmask, qmask, mom[k0 + it], tau, c8, sh, tx, ty);
-        fgp_step<TY, V>(pb, pa, qb, qa, bb, pmask, qmask, mom[k0 + it + 1], tau, c8, sh, tx, ty);
+        fgp_step<TY, V, kStepRegs>(pa, pb, qa, qb, bb, pmask, qmask, cp, cq, mom[k0 + it], tau, c8,
+                                   sh, tx, ty);
+        fgp_step<TY, V, kStepRegs>(pb, pa, qb, qa, bb, pmask, qmask, cp, cq, mom[k0 + it + 1], tau,
+                                   c8, sh, tx, ty);
     }
     if (it < iters) {
-        fgp_step<TY, V>(pa, pb, qa, qb, bb, pmask, qmask, mom[k0 + it], tau, c8, sh, tx, ty);
+        fgp_step<TY, V, kStepRegs>(pa, pb, qa, qb, bb, pmask, qmask, cp, cq, mom[k0 + it], tau, c8,
+                                   sh, tx, ty);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const float t0 = pa[v], t1 = qa[v];
@@ -213,7 +237,7 @@ inline bool fits_one_region(int h, int w) { return h <= RH && w <= RW; }
 // 4-pixel strips, <= 64 registers) measured 1-3 % faster than 8 x 8 (512
 // threads, 8-pixel strips, 78 registers): twice the warps per SM hide the two
 // barriers of every iteration better; both give bit-identical iterates.
-template <bool kBatch, int TY = 16, int V = 4>
+template <bool kBatch, int TY = 16, int V = 4, bool kStepRegs = true>
 cudaError_t launch_fgp_regions(const float *b, float *x, int h, int w, float tau,
                                const float *tau_z, int planes, int64_t plane, int iters,
                                const float *mom, FgpScratch sc, cudaStream_t s, bool pdl,
@@ -221,7 +245,7 @@ cudaError_t launch_fgp_regions(const float *b, float *x, int h, int w, float tau
     const dim3 block(RW, TY);
     const float c8 = 1.0f / (8.0f * tau);
     if (fits_one_region(h, w)) {
-        cudaError_t e = launch_kernel(fgp_kernel<kBatch, TY, V>, dim3(1, 1, planes), block, 0, s, pdl, b,
+        cudaError_t e = launch_kernel(fgp_kernel<kBatch, TY, V, kStepRegs>, dim3(1, 1, planes), block, 0, s, pdl, b,
                                       x, h, w, tau, c8, mom, 0, iters, 0, RH, RW, 1, 1, sc.p, sc.q,
                                       sc.pp, sc.qp, tau_z, plane);
         add_launches(1);
@@ -234,7 +258,7 @@ cudaError_t launch_fgp_regions(const float *b, float *x, int h, int w, float tau
         const int IH = RH - 2 * HL, IW = RW - 2 * HL;
         const dim3 grid((w + IW - 1) / IW, (h + IH - 1) / IH, planes);
         const int first = (done == 0), last = (done + chunk == iters);
-        cudaError_t e = launch_kernel(fgp_kernel<kBatch, TY, V>, grid, block, 0, s, pdl || done > 0, b, x,
+        cudaError_t e = launch_kernel(fgp_kernel<kBatch, TY, V, kStepRegs>, grid, block, 0, s, pdl || done > 0, b, x,
                                       h, w, tau, c8, mom, done, chunk, HL, IH, IW, first, last,
                                       sc.p, sc.q, sc.pp, sc.qp, tau_z, plane);
         add_launches(1);
