@@ -31,7 +31,7 @@ if ROOT not in sys.path:
 METRIC = "BSGD-TV epochs/s + HBM GB/s (fused Ax,Aᵀr,TV-prox); served p50/p99 latency"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "products_ellipse512.md")
 TRAFFIC_SOURCES = ["paper_1812_01307_gb300/csrc/products.cu", "paper_1812_01307_gb300/csrc/products_common.cuh",
-                   "paper_1812_01307_gb300/csrc/layout.cpp", "paper_1812_01307_gb300/csrc/bsgdtv_internal.h"]
+                   "paper_1812_01307_gb300/csrc/layout.cpp", "paper_1812_01307_gb300/csrc/layout.h"]
 
 
 def parse():
