@@ -186,7 +186,7 @@ def served_stream(args, B, synth):
         A = synth.parallel_beam_csr(n, na, nb)
         with B.Reconstructor(A, (n, n), 1, 1) as rec:
             u, _ = rec.estimate_umax(300, 1e-9)
-        gid = srv.add_geometry(A, (n, n), 0.9 / (2 * u), slots=32, fmt=B.FMT_F16_I16, prewarm=1)
+        gid = srv.add_geometry(A, (n, n), 0.9 / (2 * u), slots=32, fmt=B.FMT_F16_I16, prewarm=0)
         ys = [synth.noisy_projections(A, synth.phantom(n, ellipses[n], s), s).astype(np.float32)
               for s in range(pool)]
         geoms[n] = (gid, ys, A.nnz)

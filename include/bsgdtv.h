@@ -250,6 +250,24 @@ const char *bsgdtv_strerror(int code);
  * 32, 64 or a multiple of 128. */
 typedef struct bsgdtv_batch_ctx *bsgdtv_batch_t;
 
+/* A, stored once on the device for batches of any size: a reference-counted
+ * operator.  bsgdtv_operator_create_csr validates and uploads a host CSR A
+ * (arguments as for bsgdtv_batch_create_csr_ex, weights in `format`);
+ * bsgdtv_batch_create_from_operator builds a batch that reads it (and holds a
+ * reference, so the creator may call bsgdtv_operator_destroy at any time; the
+ * device arrays go when the last batch using them is destroyed).  A batch from
+ * an operator allocates only its vectors (bsgdtv_batch_device_bytes with
+ * nnz = 0).  Batches on one operator may run concurrently on different
+ * streams: they only read it. */
+typedef struct bsgdtv_operator_ctx *bsgdtv_operator_t;
+
+int bsgdtv_operator_create_csr(bsgdtv_operator_t *out, int64_t rows, int64_t cols, int img_h,
+                               int img_w, const int64_t *row_ptr, const int32_t *col_idx,
+                               const double *vals, int format, void *stream);
+void bsgdtv_operator_destroy(bsgdtv_operator_t op);
+int bsgdtv_batch_create_from_operator(bsgdtv_batch_t *out, bsgdtv_operator_t op, int slices,
+                                      void *stream);
+
 /* Creates a batch of `slices` (1 .. 4096) slices from a host CSR matrix A; the
  * arguments rows .. vals and `stream` mean what they mean for
  * bsgdtv_create_csr (A stored as FP32 weights, 32-bit indices).  Fails with
@@ -361,22 +379,29 @@ int bsgdtv_batch_get_slice_x(bsgdtv_batch_t h, int b, float *x, int out_on_devic
 /* ------------------------------------------------------ continuous batching
  * A reconstruction server: requests (projections of a registered geometry,
  * a TV weight and an epoch budget) are submitted at any time from any host
- * thread and run as slots of batch groups (bsgdtv_batch_*), one group per
- * geometry and more while the HBM budget allows.  A request is admitted into
- * a free slot as soon as one exists (between the group's ticks), keeps its x,
- * r and FGP state on the device, and leaves when its budget of epochs is
- * done; its x is then copied to host memory.  One worker thread inside the
- * server drives the device; groups of different geometries run on their own
- * streams and overlap.  A group's device bytes are those of
- * bsgdtv_batch_device_bytes; admission keeps their sum within the budget,
- * releasing idle groups of other geometries first.  Every request runs
- * Algorithm 1 exactly as a batch slice does, so its result does not depend
- * on the other requests it shares a group with. */
+ * thread and run as slots of batch groups (bsgdtv_batch_*).  A geometry's A
+ * is stored once (an operator) and shared by all its groups; a group is made
+ * when a request finds no free slot, with a power-of-two number of slots
+ * between 4 and the geometry's maximum, sized by the requests of that
+ * geometry then waiting (short queue: small groups with short epochs; long
+ * queue: large groups that read A once for many slices).  A request is
+ * admitted into a free slot as soon as one exists (between the group's
+ * ticks), keeps its x, r and FGP state on the device, and leaves when its
+ * budget of epochs is done; its x is then copied to host memory.  One worker
+ * thread inside the server drives the device; groups run on their own
+ * streams and overlap.  Admission keeps the device bytes (every A plus the
+ * groups' vectors, bsgdtv_batch_device_bytes) within the budget, releasing
+ * idle groups of other geometries first.  Every request runs Algorithm 1
+ * exactly as a batch slice does: its result does not depend on the other
+ * requests, bit for bit within groups of one size and within FP32 rounding
+ * across sizes (the passes sum a slice's products in a grouping set by the
+ * group's slice stride). */
 typedef struct bsgdtv_server_ctx *bsgdtv_server_t;
 
 /* Starts a server on the current device.  hbm_budget_bytes bounds the device
- * bytes of all groups; fgp_iters is the FGP iteration count of every prox;
- * max_tick_epochs caps the epochs a group runs between admissions. */
+ * bytes of all geometries and groups; fgp_iters is the FGP iteration count of
+ * every prox; max_tick_epochs caps the epochs a group runs between
+ * admissions. */
 int bsgdtv_server_create(bsgdtv_server_t *out, int64_t hbm_budget_bytes, int fgp_iters,
                          int max_tick_epochs);
 
@@ -385,11 +410,13 @@ int bsgdtv_server_create(bsgdtv_server_t *out, int64_t hbm_budget_bytes, int fgp
 void bsgdtv_server_destroy(bsgdtv_server_t s);
 
 /* Registers a geometry: host CSR A as for bsgdtv_create_csr (validated and
- * copied), the batch weight format (bsgdtv_batch_create_csr_ex), the slots
- * per group, the step mu > 0 for this A (Theorem 1: mu < 1/(2 u_max), e.g.
- * from bsgdtv_estimate_umax) and how many groups to create now (prewarm, as
- * far as the budget allows; the rest are made on demand).  Writes the
- * geometry id.  Fails with BSGDTV_ERR_OOM if one group exceeds the budget. */
+ * uploaded once as an operator), the batch weight format
+ * (bsgdtv_batch_create_csr_ex), the largest number of slots per group, the
+ * step mu > 0 for this A (Theorem 1: mu < 1/(2 u_max), e.g. from
+ * bsgdtv_estimate_umax) and how many groups of that size to create now
+ * (prewarm, as far as the budget allows; the rest are made on demand).
+ * Writes the geometry id.  Fails with BSGDTV_ERR_OOM if A and one smallest
+ * group exceed what is left of the budget. */
 int bsgdtv_server_add_geometry(bsgdtv_server_t s, int64_t rows, int64_t cols, int img_h, int img_w,
                                const int64_t *row_ptr, const int32_t *col_idx, const double *vals,
                                int format, int slots, double mu, int prewarm, int *geom_id);
@@ -411,7 +438,7 @@ int bsgdtv_server_wait(bsgdtv_server_t s, int64_t request_id, double timeout_s, 
                        double *times);
 
 /* stats [12]: submitted, completed, failed, queued, running, groups, device
- * bytes of the groups, most requests running at once, ticks, epochs run by
+ * bytes in use (operators and groups), most requests running at once, ticks, epochs run by
  * groups, slice-epochs of requests, groups created. */
 int bsgdtv_server_stats(bsgdtv_server_t s, int64_t *stats);
 

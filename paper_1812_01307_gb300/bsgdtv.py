@@ -67,6 +67,9 @@ def load(path: str | None = None):
         "bsgdtv_batch_run_timed": (I32, [P, I32, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "bsgdtv_batch_get_x": (I32, [P, P, I32]),
         "bsgdtv_batch_device_bytes": (I64, [I64, I64, I64, I32, I32]),
+        "bsgdtv_operator_create_csr": (I32, [ctypes.POINTER(P), I64, I64, I32, I32, P, P, P, I32, P]),
+        "bsgdtv_operator_destroy": (None, [P]),
+        "bsgdtv_batch_create_from_operator": (I32, [ctypes.POINTER(P), P, I32, P]),
         "bsgdtv_batch_create_parallel_beam": (I32, [ctypes.POINTER(P), I32, I32, I32, I32, P]),
         "bsgdtv_mf_ray_weights": (I32, [I32, I32, I32, P, I32, I32, P, P, P]),
         "bsgdtv_batch_estimate_umax": (I32, [P, I32, D, ctypes.POINTER(D), ctypes.POINTER(I32)]),
@@ -104,7 +107,8 @@ def exported_symbols():
             "bsgdtv_server_destroy", "bsgdtv_server_add_geometry", "bsgdtv_server_submit",
             "bsgdtv_server_poll", "bsgdtv_server_wait", "bsgdtv_server_stats",
             "bsgdtv_batch_create_parallel_beam", "bsgdtv_mf_ray_weights", "bsgdtv_batch_estimate_umax",
-            "bsgdtv_batch_project", "bsgdtv_batch_autotune",
+            "bsgdtv_batch_project", "bsgdtv_batch_autotune", "bsgdtv_operator_create_csr",
+            "bsgdtv_operator_destroy", "bsgdtv_batch_create_from_operator",
             "bsgdtv_launch_count", "bsgdtv_last_error", "bsgdtv_strerror"]
 
 
@@ -382,6 +386,33 @@ def bsgdtv_batch_create_csr(rows, cols, img_h, img_w, row_ptr, col_idx, vals, sl
     return h
 
 
+def bsgdtv_operator_create_csr(rows, cols, img_h, img_w, row_ptr, col_idx, vals,
+                               fmt=FMT_F32_I32, stream=None):
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    vals = np.ascontiguousarray(vals, dtype=np.float64)
+    op = ctypes.c_void_p()
+    _check(load().bsgdtv_operator_create_csr(ctypes.byref(op), int(rows), int(cols), int(img_h),
+                                             int(img_w), _host_ptr(row_ptr, np.int64),
+                                             _host_ptr(col_idx, np.int32),
+                                             _host_ptr(vals, np.float64), int(fmt),
+                                             stream if stream is not None else current_stream()),
+           "bsgdtv_operator_create_csr")
+    return op
+
+
+def bsgdtv_operator_destroy(op):
+    load().bsgdtv_operator_destroy(op)
+
+
+def bsgdtv_batch_create_from_operator(op, slices, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().bsgdtv_batch_create_from_operator(ctypes.byref(h), op, int(slices),
+                                                    stream if stream is not None else current_stream()),
+           "bsgdtv_batch_create_from_operator")
+    return h
+
+
 def bsgdtv_batch_destroy(h):
     load().bsgdtv_batch_destroy(h)
 
@@ -636,12 +667,18 @@ class BatchReconstructor:
     """Owns one batch handle: B slices sharing the matrix A, each with its own
     y_b and lambda_b; ``set_data(Y, lambdas, mu)`` / ``run`` / ``x()``."""
 
-    def __init__(self, A, img_shape, slices, stream=None, fmt=FMT_F32_I32, parallel_beam=None):
+    def __init__(self, A, img_shape, slices, stream=None, fmt=FMT_F32_I32, parallel_beam=None,
+                 operator=None):
         """`A`: host CSR, or None with parallel_beam = (n_angles, n_bins) for
-        the matrix-free projector of an img_shape = (n, n) image."""
+        the matrix-free projector of an img_shape = (n, n) image, or None with
+        `operator` (from bsgdtv_operator_create_csr) shared with other batches."""
         self.img_shape = tuple(img_shape)
         self.slices = int(slices)
-        if A is None:
+        if operator is not None:
+            n_h, n_w = self.img_shape
+            self.rows, self.cols = None, n_h * n_w
+            self.h = bsgdtv_batch_create_from_operator(operator, slices, stream)
+        elif A is None:
             n = int(img_shape[0])
             na, nb = parallel_beam
             self.rows, self.cols = int(na) * int(nb), n * n

@@ -27,6 +27,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <atomic>
+#include <type_traits>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -44,8 +46,8 @@ constexpr int kPassWarps = 8;       // warps (rows or pixels) per CTA
 constexpr int kPassMinBlocks = 6;   // 48 resident warps per SM (<= 40 registers): the
                                     // gathers are latency-bound, occupancy beats depth
 
-// Packed nonzero of A for the passes: the weight's FP32 bits and the offset
-// (in floats) of the gathered element's slice vector, idx * Bp.
+// Packed nonzero of A for the passes: the weight's FP32 bits and the index of
+// the gathered element (its slice vector starts at idx * Bp floats).
 // Gathered slice vectors are loaded with an L2 evict-last policy so that they
 // stay resident while A streams past them (evict-first).
 __device__ __forceinline__ uint64_t l2_evict_last_policy() {
@@ -79,8 +81,10 @@ __device__ __forceinline__ void fma4(float a, const float4 &x, float4 &acc) {
 // The 32 nonzeros of a round are staged in shared memory once; a partial last
 // round is padded with zero weights aimed at element 0.
 // The nonzeros of A as the passes read them.  kW = 0: packed 8-byte entries
-// (FP32 weight bits, offset); kW = BSGDTV_FMT_F16_I16 / BSGDTV_FMT_BF16_I16:
-// 16-bit weights and 32-bit offsets in two arrays (6 bytes per nonzero).
+// (FP32 weight bits, element index); kW = BSGDTV_FMT_F16_I16 /
+// BSGDTV_FMT_BF16_I16: 16-bit weights and 32-bit element indices in two
+// arrays (6 bytes per nonzero).  Indices do not depend on the slice stride,
+// so one operator serves batches of any size.
 struct PassOperand {
     const int64_t *ptr;
     const int2 *ent;
@@ -110,6 +114,8 @@ __global__ void __launch_bounds__(kPassWarps * 32, kPassMinBlocks)
                 float *__restrict__ out, int64_t n_out, int Bp, float mu) {
     constexpr int G = 32 / LPN;
     constexpr int NB = (32 / G < 4) ? 32 / G : 4;
+    // slice stride: 4 * LPN (a constant) below 128 slices, else Bp
+    const int stride = (LPN < 32) ? 4 * LPN : Bp;
     __shared__ int2 stage[kPassWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = lane / LPN, sl = lane % LPN;
@@ -134,7 +140,12 @@ __global__ void __launch_bounds__(kPassWarps * 32, kPassMinBlocks)
 #pragma unroll
                 for (int q = 0; q < NB; ++q) st[q] = stage[w][(q0 + q) * G + g];
 #pragma unroll
-                for (int q = 0; q < NB; ++q) xv[q] = ld_keep(vl + st[q].y, pol);
+                for (int q = 0; q < NB; ++q) {
+                    if constexpr (LPN < 32)   // element * stride < 2^31: checked at creation
+                        xv[q] = ld_keep(vl + st[q].y * (4 * LPN), pol);
+                    else
+                        xv[q] = ld_keep(vl + (int64_t)st[q].y * stride, pol);
+                }
 #pragma unroll
                 for (int q = 0; q < NB; ++q) fma4(__int_as_float(st[q].x), xv[q], acc);
             }
@@ -308,6 +319,17 @@ void slice_stride(int B, int &Bp, int &lpn) {
 
 using namespace bsgdtv;
 
+// A stored once on the device for any number of batches (reference counted:
+// the creator and every batch built on it hold one reference).
+struct bsgdtv_operator_ctx {
+    int device = 0;
+    int64_t rows = 0, cols = 0, nnz = 0;
+    int img_h = 0, img_w = 0, fmt = BSGDTV_FMT_F32_I32;
+    PassOperand op_r = {}, op_c = {};
+    std::vector<void *> allocs;
+    std::atomic<int> refs{1};
+};
+
 struct bsgdtv_batch_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -316,7 +338,8 @@ struct bsgdtv_batch_ctx {
     int img_h = 0, img_w = 0, B = 0, Bp = 0, lpn = 1;
     std::vector<void *> allocs;
     int fmt = BSGDTV_FMT_F32_I32;
-    PassOperand op_r = {}, op_c = {};   // A in CSR / CSC: entries (weight, idx * Bp)
+    bsgdtv_operator_ctx *op = nullptr;  // shared A (one reference held), null if matrix free
+    PassOperand op_r = {}, op_c = {};   // A in CSR / CSC: entries (weight, element index)
     bool matrix_free = false;           // weights computed on the fly (parallel beam)
     int fgp_chunk = kBatchFgpChunk;     // FGP iterations per launch (autotuned)
     double *dot_part = nullptr;         // power-iteration partial sums (first use)
@@ -495,7 +518,7 @@ int bbuild_graphs(bsgdtv_batch_ctx *h, int fgp_iters) {
 }
 
 // Packed CSR of A and its CSC (rows ascending inside each column): weights
-// as the format stores them, element offsets idx * Bp.
+// as the format stores them, element indices.
 struct PackedOperator {
     std::vector<int64_t> col_ptr;
     std::vector<int2> ent_r, ent_c;                // FP32 weights
@@ -504,12 +527,12 @@ struct PackedOperator {
 };
 
 void pack_operator(int64_t rows, int64_t cols, const int64_t *row_ptr, const int32_t *col_idx,
-                   const double *vals, int Bp, int fmt, PackedOperator &P) {
+                   const double *vals, int fmt, PackedOperator &P) {
     const int64_t nnz = row_ptr[rows];
     const bool f32 = (fmt == BSGDTV_FMT_F32_I32);
     auto put = [&](std::vector<int2> &ent, std::vector<uint16_t> &w, std::vector<int32_t> &off,
                    int64_t k, double a, int64_t idx) {
-        const int32_t o = (int32_t)(idx * Bp);
+        const int32_t o = (int32_t)idx;
         if (f32) {
             const float f = (float)a;
             int bits;
@@ -590,73 +613,145 @@ int alloc_vectors(bsgdtv_batch_ctx *hp) {
 
 extern "C" {
 
-int bsgdtv_batch_create_csr_ex(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int img_h,
+int bsgdtv_operator_create_csr(bsgdtv_operator_t *out, int64_t rows, int64_t cols, int img_h,
                                int img_w, const int64_t *row_ptr, const int32_t *col_idx,
-                               const double *vals, int slices, int format, void *stream) {
+                               const double *vals, int format, void *stream) {
     if (!out) return fail(BSGDTV_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
-    if (slices < 1 || slices > 4096) return fail(BSGDTV_ERR_INVALID_ARG, "slices must be in [1, 4096]");
     if (format != BSGDTV_FMT_F32_I32 && format != BSGDTV_FMT_F16_I16 && format != BSGDTV_FMT_BF16_I16)
         return fail(format == BSGDTV_FMT_F32_I16 ? BSGDTV_ERR_UNSUPPORTED : BSGDTV_ERR_INVALID_ARG,
                     "batch formats: BSGDTV_FMT_F32_I32, BSGDTV_FMT_F16_I16, BSGDTV_FMT_BF16_I16");
     BSG_CHECK(validate_image_csr(rows, cols, img_h, img_w, row_ptr, col_idx, vals));
-    std::unique_ptr<bsgdtv_batch_ctx> h(new (std::nothrow) bsgdtv_batch_ctx());
-    if (!h) return fail(BSGDTV_ERR_OOM, "host allocation");
-    BSG_CUDA(cudaGetDevice(&h->device));
-    h->stream = (cudaStream_t)stream;
-    h->rows = rows;
-    h->cols = cols;
-    h->nnz = row_ptr[rows];
-    h->img_h = img_h;
-    h->img_w = img_w;
-    h->B = slices;
-    h->fmt = format;
-    slice_stride(slices, h->Bp, h->lpn);
-    if (std::max(rows, cols) * h->Bp > INT32_MAX)
-        return fail(BSGDTV_ERR_UNSUPPORTED, "max(rows, cols) * padded slices must fit int32");
-    bsgdtv_batch_ctx *hp = h.get();
+    std::unique_ptr<bsgdtv_operator_ctx> op(new (std::nothrow) bsgdtv_operator_ctx());
+    if (!op) return fail(BSGDTV_ERR_OOM, "host allocation");
+    BSG_CUDA(cudaGetDevice(&op->device));
+    op->rows = rows;
+    op->cols = cols;
+    op->nnz = row_ptr[rows];
+    op->img_h = img_h;
+    op->img_w = img_w;
+    op->fmt = format;
+    cudaStream_t s = (cudaStream_t)stream;
+    bsgdtv_operator_ctx *o = op.get();
+    auto up = [&](auto **dst, const auto *src, size_t count) -> int {
+        void *p = nullptr;
+        const size_t bytes = std::max<size_t>(count, 1) * sizeof(*src);
+        const cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BSGDTV_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) +
+                                            "): " + cudaGetErrorString(e));
+        }
+        o->allocs.push_back(p);
+        *dst = static_cast<std::remove_reference_t<decltype(**dst)> *>(p);
+        if (count)
+            BSG_CUDA(cudaMemcpyAsync(p, src, count * sizeof(*src), cudaMemcpyHostToDevice, s));
+        return BSGDTV_OK;
+    };
     int rc = BSGDTV_OK;
     try {
         PackedOperator P;
-        pack_operator(rows, cols, row_ptr, col_idx, vals, h->Bp, format, P);
+        pack_operator(rows, cols, row_ptr, col_idx, vals, format, P);
         rc = [&]() -> int {
-            BSG_CUDA(cudaStreamCreateWithFlags(&hp->cap_stream, cudaStreamNonBlocking));
             int64_t *rp = nullptr, *cp = nullptr;
-            BSG_CHECK(bupload(hp, &rp, row_ptr, rows + 1));
-            BSG_CHECK(bupload(hp, &cp, P.col_ptr.data(), cols + 1));
-            hp->op_r.ptr = rp;
-            hp->op_c.ptr = cp;
+            BSG_CHECK(up(&rp, row_ptr, (size_t)rows + 1));
+            BSG_CHECK(up(&cp, P.col_ptr.data(), (size_t)cols + 1));
+            o->op_r.ptr = rp;
+            o->op_c.ptr = cp;
             if (format == BSGDTV_FMT_F32_I32) {
                 int2 *er = nullptr, *ec = nullptr;
-                BSG_CHECK(bupload(hp, &er, P.ent_r.data(), hp->nnz));
-                BSG_CHECK(bupload(hp, &ec, P.ent_c.data(), hp->nnz));
-                hp->op_r.ent = er;
-                hp->op_c.ent = ec;
+                BSG_CHECK(up(&er, P.ent_r.data(), (size_t)o->nnz));
+                BSG_CHECK(up(&ec, P.ent_c.data(), (size_t)o->nnz));
+                o->op_r.ent = er;
+                o->op_c.ent = ec;
             } else {
                 uint16_t *wr = nullptr, *wc = nullptr;
                 int32_t *orr = nullptr, *oc = nullptr;
-                BSG_CHECK(bupload(hp, &wr, P.w_r.data(), hp->nnz));
-                BSG_CHECK(bupload(hp, &orr, P.off_r.data(), hp->nnz));
-                BSG_CHECK(bupload(hp, &wc, P.w_c.data(), hp->nnz));
-                BSG_CHECK(bupload(hp, &oc, P.off_c.data(), hp->nnz));
-                hp->op_r.w16 = wr;
-                hp->op_r.off = orr;
-                hp->op_c.w16 = wc;
-                hp->op_c.off = oc;
+                BSG_CHECK(up(&wr, P.w_r.data(), (size_t)o->nnz));
+                BSG_CHECK(up(&orr, P.off_r.data(), (size_t)o->nnz));
+                BSG_CHECK(up(&wc, P.w_c.data(), (size_t)o->nnz));
+                BSG_CHECK(up(&oc, P.off_c.data(), (size_t)o->nnz));
+                o->op_r.w16 = wr;
+                o->op_r.off = orr;
+                o->op_c.w16 = wc;
+                o->op_c.off = oc;
             }
-            BSG_CHECK(alloc_vectors(hp));
-            BSG_CUDA(cudaStreamSynchronize(hp->stream));   // the host vectors die here
+            BSG_CUDA(cudaStreamSynchronize(s));   // the host arrays die here
             return BSGDTV_OK;
         }();
     } catch (const std::bad_alloc &) {
         rc = fail(BSGDTV_ERR_OOM, "host allocation");
     }
     if (rc != BSGDTV_OK) {
+        bsgdtv_operator_destroy(op.release());
+        return rc;
+    }
+    *out = op.release();
+    return BSGDTV_OK;
+}
+
+void bsgdtv_operator_destroy(bsgdtv_operator_t op) {
+    if (!op) return;
+    if (op->refs.fetch_sub(1) != 1) return;   // batches still use it
+    cudaSetDevice(op->device);
+    for (void *p : op->allocs) cudaFree(p);
+    delete op;
+}
+
+int bsgdtv_batch_create_from_operator(bsgdtv_batch_t *out, bsgdtv_operator_t op, int slices,
+                                      void *stream) {
+    if (!out || !op) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (slices < 1 || slices > 4096) return fail(BSGDTV_ERR_INVALID_ARG, "slices must be in [1, 4096]");
+    std::unique_ptr<bsgdtv_batch_ctx> h(new (std::nothrow) bsgdtv_batch_ctx());
+    if (!h) return fail(BSGDTV_ERR_OOM, "host allocation");
+    BSG_CUDA(cudaGetDevice(&h->device));
+    if (h->device != op->device) return fail(BSGDTV_ERR_INVALID_ARG, "operator is on another device");
+    h->stream = (cudaStream_t)stream;
+    h->rows = op->rows;
+    h->cols = op->cols;
+    h->nnz = op->nnz;
+    h->img_h = op->img_h;
+    h->img_w = op->img_w;
+    h->B = slices;
+    h->fmt = op->fmt;
+    h->op_r = op->op_r;
+    h->op_c = op->op_c;
+    op->refs.fetch_add(1);
+    h->op = op;
+    slice_stride(slices, h->Bp, h->lpn);
+    if (h->lpn < 32 && std::max(h->rows, h->cols) * h->Bp > INT32_MAX) {
+        // the passes form element * stride in 32 bits below 128 slices
+        bsgdtv_batch_destroy(h.release());
+        return fail(BSGDTV_ERR_UNSUPPORTED, "max(rows, cols) * padded slices must fit int32");
+    }
+    bsgdtv_batch_ctx *hp = h.get();
+    const int rc = [&]() -> int {
+        BSG_CUDA(cudaStreamCreateWithFlags(&hp->cap_stream, cudaStreamNonBlocking));
+        BSG_CHECK(alloc_vectors(hp));
+        BSG_CUDA(cudaStreamSynchronize(hp->stream));
+        return BSGDTV_OK;
+    }();
+    if (rc != BSGDTV_OK) {
         bsgdtv_batch_destroy(h.release());
         return rc;
     }
     *out = h.release();
     return BSGDTV_OK;
+}
+
+int bsgdtv_batch_create_csr_ex(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int img_h,
+                               int img_w, const int64_t *row_ptr, const int32_t *col_idx,
+                               const double *vals, int slices, int format, void *stream) {
+    if (!out) return fail(BSGDTV_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (slices < 1 || slices > 4096) return fail(BSGDTV_ERR_INVALID_ARG, "slices must be in [1, 4096]");
+    bsgdtv_operator_t op = nullptr;
+    BSG_CHECK(bsgdtv_operator_create_csr(&op, rows, cols, img_h, img_w, row_ptr, col_idx, vals, format,
+                                         stream));
+    const int rc = bsgdtv_batch_create_from_operator(out, op, slices, stream);
+    bsgdtv_operator_destroy(op);   // the batch keeps its own reference
+    return rc;
 }
 
 int64_t bsgdtv_batch_device_bytes(int64_t rows, int64_t cols, int64_t nnz, int slices, int format) {
@@ -774,7 +869,9 @@ void bsgdtv_batch_destroy(bsgdtv_batch_t h) {
         if (ev) cudaEventDestroy(ev);
     for (void *p : h->allocs) cudaFree(p);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    bsgdtv_operator_t op = h->op;
     delete h;
+    bsgdtv_operator_destroy(op);
 }
 
 int bsgdtv_batch_set_data(bsgdtv_batch_t h, const float *y, int y_on_device,

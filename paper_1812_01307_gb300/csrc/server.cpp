@@ -41,6 +41,8 @@ using Clock = std::chrono::steady_clock;
 
 enum ReqState { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
 
+constexpr int kMinSlots = 4;   // smallest group the server makes on demand
+
 struct Request {
     int64_t id = 0;
     int geom = 0;
@@ -70,13 +72,18 @@ struct Group {
 struct Geometry {
     int64_t rows = 0, cols = 0;
     int img_h = 0, img_w = 0;
-    std::vector<int64_t> row_ptr;
-    std::vector<int32_t> col_idx;
-    std::vector<double> vals;
+    bsgdtv_operator_t op = nullptr;   // A on the device, shared by every group
+    int64_t op_bytes = 0;
     int format = BSGDTV_FMT_F32_I32;
-    int slots = 1;
+    int slots = 1;       // slots of the largest group
+    int min_slots = 1;   // slots of the smallest group
     double mu = 0.0;
-    int64_t group_bytes = 0;
+    int64_t nnz = 0;
+    int64_t queued = 0;  // requests of this geometry waiting for a slot
+    // device bytes of a group: its vectors (A is the geometry's, counted once)
+    int64_t bytes_for(int slots_g) const {
+        return bsgdtv_batch_device_bytes(rows, cols, 0, slots_g, format);
+    }
 };
 
 }  // namespace
@@ -125,18 +132,17 @@ int destroy_group(bsgdtv_server_ctx *s, Group *g) {
 
 // Creates a group for geometry gi (caller holds the lock; the A upload runs
 // under it, which only delays submitters).
-int make_group(bsgdtv_server_ctx *s, int gi, Group **out) {
+int make_group(bsgdtv_server_ctx *s, int gi, int slots, Group **out) {
     Geometry &G = *s->geoms[gi];
     std::unique_ptr<Group> g(new Group());
     g->geom = gi;
-    g->bytes = G.group_bytes;
+    g->bytes = G.bytes_for(slots);
     BSG_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
     BSG_CUDA(cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming));
-    int rc = bsgdtv_batch_create_csr_ex(&g->batch, G.rows, G.cols, G.img_h, G.img_w, G.row_ptr.data(),
-                                        G.col_idx.data(), G.vals.data(), G.slots, G.format, g->stream);
+    int rc = bsgdtv_batch_create_from_operator(&g->batch, G.op, slots, g->stream);
     if (rc == BSGDTV_OK) {
-        std::vector<float> zeros((size_t)G.rows * G.slots, 0.f);
-        std::vector<double> lam((size_t)G.slots, 0.0);
+        std::vector<float> zeros((size_t)G.rows * slots, 0.f);
+        std::vector<double> lam((size_t)slots, 0.0);
         rc = bsgdtv_batch_set_data(g->batch, zeros.data(), 0, lam.data(), G.mu);
     }
     if (rc != BSGDTV_OK) {
@@ -145,7 +151,7 @@ int make_group(bsgdtv_server_ctx *s, int gi, Group **out) {
         cudaStreamDestroy(g->stream);
         return rc;
     }
-    g->slot_req.assign(G.slots, -1);
+    g->slot_req.assign(slots, -1);
     g->idle_since = Clock::now();
     s->hbm_used += g->bytes;
     s->groups_made++;
@@ -174,8 +180,8 @@ bool find_slot(bsgdtv_server_ctx *s, int gi, Group **gout, int *slot, int *fatal
                 return true;
             }
     }
-    const int64_t need = s->geoms[gi]->group_bytes;
-    if (need > s->budget) {
+    const Geometry &G = *s->geoms[gi];
+    if (G.op_bytes + G.bytes_for(G.min_slots) > s->budget) {
         *fatal = BSGDTV_ERR_OOM;
         return false;
     }
@@ -184,6 +190,19 @@ bool find_slot(bsgdtv_server_ctx *s, int gi, Group **gout, int *slot, int *fatal
         if (g->geom == gi && g->busy)
             for (int64_t id : g->slot_req)
                 if (id < 0) return false;
+    // a new group sized for the requests of this geometry now waiting
+    // (a power of two between min_slots and slots): few waiting requests get
+    // a small group with short epochs, a long queue a large one that reads A
+    // once for many slices; shrunk if the budget cannot hold it
+    int slots = G.min_slots;
+    while (slots < G.slots && slots < G.queued) slots *= 2;
+    slots = std::min(slots, G.slots);
+    while (slots > G.min_slots && s->hbm_used + G.bytes_for(slots) > s->budget &&
+           !std::any_of(s->groups.begin(), s->groups.end(), [&](const std::unique_ptr<Group> &p) {
+               return p->geom != gi && group_idle(p.get());
+           }))
+        slots = std::max(G.min_slots, slots / 2);
+    const int64_t need = G.bytes_for(slots);
     // release idle groups of other geometries (oldest first) until it fits
     while (s->hbm_used + need > s->budget) {
         Group *victim = nullptr;
@@ -202,7 +221,7 @@ bool find_slot(bsgdtv_server_ctx *s, int gi, Group **gout, int *slot, int *fatal
         return false;
     }
     Group *g = nullptr;
-    const int rc = make_group(s, gi, &g);
+    const int rc = make_group(s, gi, slots, &g);
     if (rc != BSGDTV_OK) {
         *fatal = rc;
         return false;
@@ -222,6 +241,7 @@ void admit(bsgdtv_server_ctx *s) {
                 finish_failed(s, r, fatal, fatal == BSGDTV_ERR_OOM
                                                ? "a group of this geometry exceeds the HBM budget"
                                                : std::string("group creation: ") + bsgdtv_last_error());
+                s->geoms[r.geom]->queued--;
                 it = s->queue.erase(it);
                 s->cv_done.notify_all();
             } else {
@@ -239,6 +259,7 @@ void admit(bsgdtv_server_ctx *s) {
             r.t_admit = Clock::now();
             std::vector<float>().swap(r.y);
         }
+        s->geoms[r.geom]->queued--;
         it = s->queue.erase(it);
     }
 }
@@ -382,6 +403,8 @@ void bsgdtv_server_destroy(bsgdtv_server_t s) {
     cudaSetDevice(s->device);
     for (auto &g : s->groups) destroy_group(s, g.get());
     s->groups.clear();
+    for (auto &G : s->geoms)
+        if (G && G->op) bsgdtv_operator_destroy(G->op);
     s->cv_done.notify_all();
     delete s;
 }
@@ -400,32 +423,44 @@ int bsgdtv_server_add_geometry(bsgdtv_server_t s, int64_t rows, int64_t cols, in
     std::unique_ptr<Geometry> G(new (std::nothrow) Geometry());
     if (!G) return fail(BSGDTV_ERR_OOM, "host allocation");
     const int64_t nnz = row_ptr[rows];
-    try {
-        G->row_ptr.assign(row_ptr, row_ptr + rows + 1);
-        G->col_idx.assign(col_idx, col_idx + nnz);
-        G->vals.assign(vals, vals + nnz);
-    } catch (const std::bad_alloc &) {
-        return fail(BSGDTV_ERR_OOM, "host allocation");
-    }
     G->rows = rows;
     G->cols = cols;
     G->img_h = img_h;
     G->img_w = img_w;
     G->format = format;
     G->slots = slots;
+    G->min_slots = std::min(slots, kMinSlots);
     G->mu = mu;
-    G->group_bytes = bsgdtv_batch_device_bytes(rows, cols, nnz, slots, format);
+    G->nnz = nnz;
+    G->op_bytes = bsgdtv_batch_device_bytes(rows, cols, nnz, 1, format) -
+                  bsgdtv_batch_device_bytes(rows, cols, 0, 1, format);
     std::lock_guard<std::mutex> lock(s->mu);
+    int64_t ops = 0;   // every registered A stays resident; groups can be released
+    for (auto &g : s->geoms)
+        if (g) ops += g->op_bytes;
+    if (ops + G->op_bytes + G->bytes_for(G->min_slots) > s->budget)
+        return fail(BSGDTV_ERR_OOM, "the geometries' A and one group exceed the HBM budget");
+    while (s->hbm_used + G->op_bytes > s->budget) {   // make room: release idle groups
+        auto it = std::find_if(s->groups.begin(), s->groups.end(),
+                               [](const std::unique_ptr<Group> &p) { return group_idle(p.get()); });
+        if (it == s->groups.end()) return fail(BSGDTV_ERR_OOM, "no idle group to release for this A");
+        destroy_group(s, it->get());
+        s->groups.erase(it);
+    }
+    // A goes to the device once, on a private stream; every group reads it
+    cudaStream_t up = nullptr;
+    BSG_CUDA(cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking));
+    const int rc_op = bsgdtv_operator_create_csr(&G->op, rows, cols, img_h, img_w, row_ptr, col_idx,
+                                                 vals, format, up);
+    cudaStreamDestroy(up);
+    if (rc_op != BSGDTV_OK) return rc_op;
+    s->hbm_used += G->op_bytes;
     const int gi = (int)s->geoms.size();
     s->geoms.push_back(std::move(G));
-    if (s->geoms[gi]->group_bytes > s->budget) {
-        s->geoms[gi].reset();
-        return fail(BSGDTV_ERR_OOM, "one group of this geometry exceeds the HBM budget");
-    }
     // prewarm: as many groups as the budget holds now, up to `prewarm`
-    for (int k = 0; k < prewarm && s->hbm_used + s->geoms[gi]->group_bytes <= s->budget; ++k) {
+    for (int k = 0; k < prewarm && s->hbm_used + s->geoms[gi]->bytes_for(slots) <= s->budget; ++k) {
         Group *g = nullptr;
-        const int rc = make_group(s, gi, &g);
+        const int rc = make_group(s, gi, slots, &g);
         if (rc != BSGDTV_OK) return rc;
     }
     *geom_id = gi;
@@ -458,6 +493,7 @@ int bsgdtv_server_submit(bsgdtv_server_t s, int geom_id, const float *y, double 
         r->t_submit = Clock::now();
         *request_id = r->id;
         s->queue.push_back(r->id);
+        s->geoms[geom_id]->queued++;
         s->reqs[r->id] = std::move(r);
         s->submitted++;
     }

@@ -276,3 +276,32 @@ def test_batch_autotune_keeps_results(B):
         bt.run(2, 30)
         X_tuned = bt.x().copy()
     assert np.array_equal(X_plain, X_tuned)
+
+
+def test_batches_share_one_operator(B):
+    """One stored A (an operator) serves batches of different sizes at once;
+    each gives the same bits as a batch that owns its copy of A, and the
+    operator may be released before the batches that use it."""
+    name = "ragged37"
+    n, na, nb, ne, M, N = GEOM[name]
+    A, Y, mu = _setup(name, 40)
+    lam = _lambdas(40)
+    op = B.bsgdtv_operator_create_csr(A.rows, A.cols_n, n, n, A.row_ptr, A.cols, A.vals)
+    small = B.BatchReconstructor(None, (n, n), 3, operator=op)
+    big = B.BatchReconstructor(None, (n, n), 40, operator=op)
+    B.bsgdtv_operator_destroy(op)                   # the batches keep it alive
+    small.set_data(Y[:3], lam[:3], mu)
+    big.set_data(Y, lam, mu)
+    small.run(6, 9)
+    big.run(6, 9)
+    Xs, Xb = small.x(), big.x()
+    small.close()
+    big.close()
+    with B.BatchReconstructor(A, (n, n), 40) as own:
+        own.set_data(Y, lam, mu)
+        own.run(6, 9)
+        Xo = own.x()
+    assert np.array_equal(Xb, Xo)
+    for b in range(3):
+        assert rel(Xs[b], Xo[b]) <= 1e-6
+        assert rel(Xs[b], _oracle_slice(name, A, Y[b], lam[b], mu, 6, 9)) <= 1e-4

@@ -1,7 +1,8 @@
-"""GPU tests of the continuous-batching server: every request's result is
+"""GPU tests of the continuous-batching server: a request's result is
 bit-identical alone and in a mix of geometries, weights, budgets and arrival
-times, and matches the FP64 oracle (relative l2 <= 1e-4); admission keeps the
-groups' device bytes within the HBM budget."""
+times when its group has the same number of slots (within 1e-6 when the
+demand-sized groups differ), and matches the FP64 oracle (relative l2 <=
+1e-4); admission keeps the device bytes within the HBM budget."""
 import threading
 import time
 
@@ -105,22 +106,44 @@ def test_server_alone_equals_mixed_and_oracle(B):
         assert rel(mixed[i], x_ref) <= 1e-4, i
 
 
+def _op_bytes(B, A):
+    return (B.bsgdtv_batch_device_bytes(A.rows, A.cols_n, A.nnz, 1)
+            - B.bsgdtv_batch_device_bytes(A.rows, A.cols_n, 0, 1))
+
+
 def test_server_admission_by_hbm_budget(B):
-    """A budget that holds one group at a time: the two geometries take turns
-    (idle groups are released), every request completes."""
-    A, n, _, _ = geometry("g64")
-    one = B.bsgdtv_batch_device_bytes(A.rows, A.cols_n, A.nnz, 3)
+    """A budget that holds both geometries' A but one group's vectors at a
+    time: the geometries take turns (idle groups are released), every
+    request completes with the same bits."""
+    A64, A37 = geometry("g64")[0], geometry("g37")[0]
+    vec = max(B.bsgdtv_batch_device_bytes(A.rows, A.cols_n, 0, 3) for A in (A64, A37))
+    budget = _op_bytes(B, A64) + _op_bytes(B, A37) + vec + 4096
     reqs = MIX[:6]
-    out, st = _serve(B, reqs, budget=one + 4096)
-    assert st["groups_made"] >= 3 and st["device_bytes"] <= one + 4096
+    out, st = _serve(B, reqs, budget=budget)
+    assert st["groups_made"] >= 3 and st["device_bytes"] <= budget
     ref, _ = _serve(B, reqs)
     for i in out:
         assert np.array_equal(out[i], ref[i])
 
 
+def test_server_groups_sized_by_demand(B):
+    """With up to 16 slots per group, groups are made with as many slots as
+    requests wait (4 .. 16); a request's result then depends on its group's
+    size only through FP32 rounding: alone vs in the mix <= 1e-6, and both
+    match the oracle."""
+    mixed, st = _serve(B, MIX, slots=16, stagger=0)
+    for i in (0, 3, 7):
+        alone, _ = _serve(B, [MIX[i]], slots=16)
+        assert rel(alone[0], mixed[i]) <= 1e-6, i
+        name, seed, lam, ep = MIX[i]
+        A, n, _, mu = geometry(name)
+        x_ref, _ = oracle.run(A, request(name, seed).astype(np.float64), (n, n), 1, 1, lam, mu, ep, K)
+        assert rel(mixed[i], x_ref) <= 1e-4
+
+
 def test_server_errors(B):
     A, n, _, mu = geometry("g64")
-    with pytest.raises(B.BsgdtvError) as e:       # one group exceeds the budget
+    with pytest.raises(B.BsgdtvError) as e:       # A and one group exceed the budget
         with B.Server(1 << 20, K) as srv:
             srv.add_geometry(A, (n, n), mu, slots=3)
     assert e.value.code == -2
