@@ -51,7 +51,7 @@ enum {
     BSGDTV_ERR_STATE = -4,       /* call out of order (e.g. run before set_data) */
     BSGDTV_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
     BSGDTV_ERR_NONFINITE = -6,   /* NaN/Inf in an input */
-    BSGDTV_ERR_UNSUPPORTED = -7  /* valid request this build does not handle */
+    BSGDTV_ERR_UNSUPPORTED = -7  /* valid request the library does not handle */
 };
 
 /* How the device stores A's weights and tile-local column indices.  F32_I32
