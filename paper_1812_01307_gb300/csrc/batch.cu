@@ -42,6 +42,7 @@ namespace {
 
 constexpr int kBatchFgpChunk = 5;   // default FGP iterations per launch (halo = chunk + 1)
 constexpr int kFgpChunkChoices[] = {3, 4, 5, 6, 8};   // what the autotuner tries
+constexpr int64_t kFgpFieldBudget = 48ll << 20;       // bytes of FGP fields per slice group
 constexpr int kPassWarps = 8;       // warps (rows or pixels) per CTA
 constexpr int kPassMinBlocks = 6;   // 48 resident warps per SM (<= 40 registers): the
                                     // gathers are latency-bound, occupancy beats depth
@@ -342,6 +343,7 @@ struct bsgdtv_batch_ctx {
     PassOperand op_r = {}, op_c = {};   // A in CSR / CSC: entries (weight, element index)
     bool matrix_free = false;           // weights computed on the fly (parallel beam)
     int fgp_chunk = kBatchFgpChunk;     // FGP iterations per launch (autotuned)
+    int fgp_group = 0;                  // slices per FGP launch group (0: by the L2 budget)
     double *dot_part = nullptr;         // power-iteration partial sums (first use)
     float *save_x = nullptr, *save_r[2] = {nullptr, nullptr};   // autotuner state copy (first use)
     MfGeometry mfg;
@@ -442,10 +444,20 @@ int benqueue_epoch(bsgdtv_batch_ctx *h, int par, int fgp_iters, cudaStream_t s,
     if (prox) {
         const int64_t c = h->cols;
         BSG_CUDA(launch_transpose(h->Xhat, h->Xhp, c, h->B, h->Bp, true, s));
-        FgpScratch sc{h->fp, h->fq, h->fpp, h->fqp};
-        BSG_CUDA(fgpk::launch_fgp_regions<true>(h->Xhp, h->Xp, h->img_h, h->img_w, 1.f, h->tau,
-                                                h->B, c, fgp_iters, h->mom, sc, s, false,
-                                                h->fgp_chunk));
+        // slices in groups whose FGP fields (b, p, q, p_prev, q_prev) fit in
+        // about half of the L2, so the fields of consecutive chunk launches
+        // come from L2 rather than HBM
+        const int per = std::max<int>(1, (int)std::min<int64_t>(
+                                             h->B, kFgpFieldBudget / std::max<int64_t>(1, 20 * c)));
+        const int sg = h->fgp_group > 0 ? std::min(h->fgp_group, h->B) : per;
+        for (int b0 = 0; b0 < h->B; b0 += sg) {
+            const int nb = std::min(sg, h->B - b0);
+            const size_t o = (size_t)b0 * c;
+            FgpScratch sc{h->fp + o, h->fq + o, h->fpp + o, h->fqp + o};
+            BSG_CUDA(fgpk::launch_fgp_regions<true>(h->Xhp + o, h->Xp + o, h->img_h, h->img_w, 1.f,
+                                                    h->tau + b0, nb, c, fgp_iters, h->mom, sc, s,
+                                                    false, h->fgp_chunk));
+        }
         BSG_CUDA(launch_transpose(h->Xp, h->X, c, h->B, h->Bp, false, s));
     }
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[2], s, cudaEventRecordExternal));
