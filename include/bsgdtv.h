@@ -383,8 +383,9 @@ int bsgdtv_batch_get_slice_x(bsgdtv_batch_t h, int b, float *x, int out_on_devic
  * is stored once (an operator) and shared by all its groups; a group is made
  * when a request finds no free slot, with a power-of-two number of slots
  * between 4 and the geometry's maximum, sized by the requests of that
- * geometry then waiting (short queue: small groups with short epochs; long
- * queue: large groups that read A once for many slices).  A request is
+ * geometry then waiting: a short queue gets small groups with short epochs
+ * (low latency), a long queue large groups that read A once for many slices
+ * (throughput).  A request is
  * admitted into a free slot as soon as one exists (between the group's
  * ticks), keeps its x, r and FGP state on the device, and leaves when its
  * budget of epochs is done; its x is then copied to host memory.  One worker

@@ -344,6 +344,7 @@ struct bsgdtv_batch_ctx {
     bool matrix_free = false;           // weights computed on the fly (parallel beam)
     int fgp_chunk = kBatchFgpChunk;     // FGP iterations per launch (autotuned)
     int fgp_group = 0;                  // slices per FGP launch group (0: by the L2 budget)
+    bool keep_prox = false;             // epochs keep the prox stage even if every lambda is 0
     double *dot_part = nullptr;         // power-iteration partial sums (first use)
     float *save_x = nullptr, *save_r[2] = {nullptr, nullptr};   // autotuner state copy (first use)
     MfGeometry mfg;
@@ -418,6 +419,7 @@ void bdrop_graphs(bsgdtv_batch_ctx *h) {
 
 bool any_prox(const bsgdtv_batch_ctx *h, int fgp_iters) {
     if (fgp_iters <= 0) return false;
+    if (h->keep_prox) return true;
     for (double l : h->lambdas)
         if (l > 0.0) return true;
     return false;
@@ -577,6 +579,13 @@ void pack_operator(int64_t rows, int64_t cols, const int64_t *row_ptr, const int
 }  // namespace
 
 namespace bsgdtv {
+
+void batch_keep_prox(bsgdtv_batch_t h, bool on) {
+    if (h && h->keep_prox != on) {
+        h->keep_prox = on;
+        bdrop_graphs(h);
+    }
+}
 
 int validate_image_csr(int64_t rows, int64_t cols, int img_h, int img_w, const int64_t *row_ptr,
                        const int32_t *col_idx, const double *vals) {

@@ -143,6 +143,11 @@ cudaError_t launch_fgp(const float *b, float *x, int h, int w, float tau, int it
                        int max_chunk = 8);
 void fgp_momentum_host(int iters, std::vector<float> &mom);
 
+// batch.cu: keep the prox stage in a batch's epochs even when every slot has
+// lambda = 0 (slots with lambda = 0 pass through the FGP launch unchanged), so
+// slots that come and go do not force the epoch graphs to be captured again.
+void batch_keep_prox(bsgdtv_batch_t h, bool on);
+
 // batch.cu: host check of a CSR image operator (sizes, sorted in-range
 // columns, finite weights); BSGDTV_* code.
 int validate_image_csr(int64_t rows, int64_t cols, int img_h, int img_w, const int64_t *row_ptr,

@@ -140,6 +140,7 @@ int make_group(bsgdtv_server_ctx *s, int gi, int slots, Group **out) {
     BSG_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
     BSG_CUDA(cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming));
     int rc = bsgdtv_batch_create_from_operator(&g->batch, G.op, slots, g->stream);
+    if (rc == BSGDTV_OK) bsgdtv::batch_keep_prox(g->batch, s->fgp_iters > 0);
     if (rc == BSGDTV_OK) {
         std::vector<float> zeros((size_t)G.rows * slots, 0.f);
         std::vector<double> lam((size_t)slots, 0.0);
@@ -190,10 +191,11 @@ bool find_slot(bsgdtv_server_ctx *s, int gi, Group **gout, int *slot, int *fatal
         if (g->geom == gi && g->busy)
             for (int64_t id : g->slot_req)
                 if (id < 0) return false;
-    // a new group sized for the requests of this geometry now waiting
-    // (a power of two between min_slots and slots): few waiting requests get
-    // a small group with short epochs, a long queue a large one that reads A
-    // once for many slices; shrunk if the budget cannot hold it
+    // a new group sized for the requests of this geometry now waiting (a
+    // power of two between min_slots and slots): a short queue gets a small
+    // group with short epochs (low latency), a long queue a large one that
+    // reads A once for many slices (throughput); shrunk if the budget cannot
+    // hold it
     int slots = G.min_slots;
     while (slots < G.slots && slots < G.queued) slots *= 2;
     slots = std::min(slots, G.slots);
