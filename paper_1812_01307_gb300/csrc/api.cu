@@ -60,6 +60,7 @@ struct bsgdtv_ctx {
     int *flag = nullptr;
     float *rmax = nullptr;   // [3] max |r| of r[0], r[1] and of a test-hook r
     int cur = 0;   // r[cur] holds r^{k-1}
+    bool z_stale = true;   // z partials not yet A x^0 = 0 or computed by an epoch
     bool has_data = false;
     double lambda = 0.0, mu = 0.0, u_max = 0.0;
     int64_t epoch = 0;
@@ -539,8 +540,10 @@ int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, 
     BSG_CHECK(set_device(h));
     cudaStream_t s = h->stream;
     const int64_t R = h->dl.rows, c = h->dl.cols;
+    float y_absmax = 0.f;
     if (!y_on_device) {
-        if (!all_finite(y, R)) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+        if (!all_finite_absmax(y, R, &y_absmax))
+            return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
         BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float), cudaMemcpyHostToDevice, s));
     } else {
         BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -551,13 +554,18 @@ int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, 
         BSG_CUDA(cudaStreamSynchronize(s));
         if (flag) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
     }
-    // x^0 = 0, r^{-1} = y - A x^0 = y; the last block products are A x^0 = 0
-    BSG_CUDA(cudaMemsetAsync(h->x, 0, c * sizeof(float), s));
-    BSG_CUDA(cudaMemsetAsync(h->z_part, 0, (size_t)h->dl.n_slabs * kSlab * sizeof(float), s));
+    // x^0 = 0, r^{-1} = y - A x^0 = y and max |r|; the last block products are
+    // A x^0 = 0 (cleared when the stochastic iteration first needs them)
     h->cur = 0;
-    BSG_CUDA(cudaMemcpyAsync(h->r[0], h->y, R * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    BSG_CUDA(cudaMemsetAsync(h->rmax, 0, sizeof(float), s));
-    BSG_CUDA(launch_absmax(h->r[0], R, h->rmax, s));
+    h->z_stale = true;
+    if (!y_on_device) {
+        BSG_CUDA(launch_init_state(h->y, h->r[0], h->x, R, c, h->rmax, y_absmax, s));
+    } else {
+        BSG_CUDA(cudaMemsetAsync(h->x, 0, c * sizeof(float), s));
+        BSG_CUDA(cudaMemcpyAsync(h->r[0], h->y, R * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        BSG_CUDA(cudaMemsetAsync(h->rmax, 0, sizeof(float), s));
+        BSG_CUDA(launch_absmax(h->r[0], R, h->rmax, s));
+    }
     if (mu <= 0.0) {
         if (h->u_max <= 0.0) {
             double u;
@@ -595,6 +603,7 @@ int bsgdtv_run(bsgdtv_t h, int epochs, int fgp_iters) {
         BSG_CUDA(cudaGraphLaunch(h->gexec[h->cur], h->stream));
         add_launches(h->graph_kernels);
         h->cur ^= 1;
+        h->z_stale = false;   // a full epoch computes every block product
         h->epoch++;
     }
     return BSGDTV_OK;
@@ -623,6 +632,7 @@ int bsgdtv_run_timed(bsgdtv_t h, int epochs, int fgp_iters, double *products_ms,
         BSG_CUDA(cudaGraphLaunch(ex, h->stream));
         add_launches(h->graph_kernels);
         h->cur ^= 1;
+        h->z_stale = false;   // a full epoch computes every block product
         h->epoch++;
     }
     BSG_CUDA(cudaStreamSynchronize(h->stream));
@@ -684,6 +694,10 @@ int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_
     }
     unsigned char *dev = static_cast<unsigned char *>(h->sub_buf);
     BSG_CUDA(cudaMemcpyAsync(dev, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+    if (h->z_stale) {   // undrawn pairs start from the block products of x^0 = 0
+        BSG_CUDA(cudaMemsetAsync(h->z_part, 0, (size_t)h->dl.n_slabs * kSlab * sizeof(float), s));
+        h->z_stale = false;
+    }
     BSG_CHECK(ensure_mom(h, std::max(fgp_iters, 1)));
     const bool prox = h->lambda > 0.0 && fgp_iters > 0;
     for (int k = 0; k < iters; ++k) {

@@ -354,6 +354,26 @@ cudaError_t launch_block_sums(const DevLayout &d, const float *z_part, const int
     return cudaGetLastError();
 }
 
+__global__ void init_state_kernel(const float *__restrict__ y, float *__restrict__ r0,
+                                  float *__restrict__ x, int64_t rows, int64_t cols, float *rmax,
+                                  float rmax_value) {
+    const int64_t n = rows > cols ? rows : cols;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < rows) r0[i] = y[i];
+        if (i < cols) x[i] = 0.f;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *rmax = rmax_value;
+}
+
+cudaError_t launch_init_state(const float *y, float *r0, float *x, int64_t rows, int64_t cols,
+                              float *rmax, float rmax_value, cudaStream_t s) {
+    init_state_kernel<<<grid_for(std::max(rows, cols)), kThreads, 0, s>>>(y, r0, x, rows, cols, rmax,
+                                                                          rmax_value);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_absmax(const float *v, int64_t n, float *out, cudaStream_t s) {
     absmax_kernel<<<grid_for(n), kThreads, 0, s>>>(v, n, out);
     add_launches(1);
