@@ -51,7 +51,8 @@ enum {
     BSGDTV_ERR_STATE = -4,       /* call out of order (e.g. run before set_data) */
     BSGDTV_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
     BSGDTV_ERR_NONFINITE = -6,   /* NaN/Inf in an input */
-    BSGDTV_ERR_UNSUPPORTED = -7  /* valid request the library does not handle */
+    BSGDTV_ERR_UNSUPPORTED = -7, /* valid request the library does not handle */
+    BSGDTV_ERR_CANCELLED = -8    /* a server request was cancelled */
 };
 
 /* How the device stores A's weights and tile-local column indices.  F32_I32
@@ -427,8 +428,17 @@ int bsgdtv_server_add_geometry(bsgdtv_server_t s, int64_t rows, int64_t cols, in
 int bsgdtv_server_submit(bsgdtv_server_t s, int geom_id, const float *y, double lambda, int epochs,
                          int64_t *request_id);
 
-/* Request state: 0 queued, 1 running, 2 done, 3 failed. */
+/* Request state: 0 queued, 1 running, 2 done, 3 failed, 4 cancelled. */
 int bsgdtv_server_poll(bsgdtv_server_t s, int64_t request_id, int *state);
+
+/* Cancels a request that has not ended.  A queued one is cancelled at once;
+ * a running one keeps its state "running" until its group's current tick
+ * (at most max_tick_epochs epochs) ends, then gives up its slot unread.
+ * bsgdtv_server_wait on a cancelled request returns BSGDTV_ERR_CANCELLED and
+ * forgets it.  BSGDTV_ERR_STATE if the request is done, failed or cancelled
+ * (state 2, 3 or 4); BSGDTV_ERR_INVALID_ARG for an unknown (or already waited-for)
+ * id.  Cancellation is a serving feature; Algorithm 1 has no counterpart. */
+int bsgdtv_server_cancel(bsgdtv_server_t s, int64_t request_id);
 
 /* Waits up to timeout_s seconds (< 0: no limit) for the request; on success
  * copies its x [cols] to host memory x (may be NULL) and forgets the request.
@@ -438,9 +448,9 @@ int bsgdtv_server_poll(bsgdtv_server_t s, int64_t request_id, int *state);
 int bsgdtv_server_wait(bsgdtv_server_t s, int64_t request_id, double timeout_s, float *x,
                        double *times);
 
-/* stats [12]: submitted, completed, failed, queued, running, groups, device
+/* stats [13]: submitted, completed, failed, queued, running, groups, device
  * bytes in use (operators and groups), most requests running at once, ticks, epochs run by
- * groups, slice-epochs of requests, groups created. */
+ * groups, slice-epochs of requests, groups created, cancelled. */
 int bsgdtv_server_stats(bsgdtv_server_t s, int64_t *stats);
 
 #ifdef __cplusplus

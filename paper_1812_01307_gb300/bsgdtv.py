@@ -80,6 +80,7 @@ def load(path: str | None = None):
         "bsgdtv_server_add_geometry": (I32, [P, I64, I64, I32, I32, P, P, P, I32, I32, D, I32, ctypes.POINTER(I32)]),
         "bsgdtv_server_submit": (I32, [P, I32, P, D, I32, ctypes.POINTER(I64)]),
         "bsgdtv_server_poll": (I32, [P, I64, ctypes.POINTER(I32)]),
+        "bsgdtv_server_cancel": (I32, [P, I64]),
         "bsgdtv_server_wait": (I32, [P, I64, D, P, P]),
         "bsgdtv_server_stats": (I32, [P, P]),
         "bsgdtv_launch_count": (I64, []),
@@ -105,7 +106,7 @@ def exported_symbols():
             "bsgdtv_batch_get_x", "bsgdtv_batch_create_csr_ex", "bsgdtv_batch_set_slice",
             "bsgdtv_batch_get_slice_x", "bsgdtv_batch_device_bytes", "bsgdtv_server_create",
             "bsgdtv_server_destroy", "bsgdtv_server_add_geometry", "bsgdtv_server_submit",
-            "bsgdtv_server_poll", "bsgdtv_server_wait", "bsgdtv_server_stats",
+            "bsgdtv_server_poll", "bsgdtv_server_cancel", "bsgdtv_server_wait", "bsgdtv_server_stats",
             "bsgdtv_batch_create_parallel_beam", "bsgdtv_mf_ray_weights", "bsgdtv_batch_estimate_umax",
             "bsgdtv_batch_project", "bsgdtv_batch_autotune", "bsgdtv_operator_create_csr",
             "bsgdtv_operator_destroy", "bsgdtv_batch_create_from_operator",
@@ -573,6 +574,12 @@ def bsgdtv_server_poll(h, request_id):
     return st.value
 
 
+def bsgdtv_server_cancel(h, request_id):
+    """Cancels a queued or running request (running: at the end of its
+    group's current tick)."""
+    _check(load().bsgdtv_server_cancel(h, int(request_id)), "bsgdtv_server_cancel")
+
+
 def bsgdtv_server_wait(h, request_id, out=None, timeout_s=-1.0):
     """Waits for a request; fills `out` (float32 numpy, or None) and returns
     (latency_s, queued_s)."""
@@ -584,11 +591,11 @@ def bsgdtv_server_wait(h, request_id, out=None, timeout_s=-1.0):
 
 
 SERVER_STATS = ["submitted", "completed", "failed", "queued", "running", "groups", "device_bytes",
-                "max_running", "ticks", "epochs_run", "slice_epochs", "groups_made"]
+                "max_running", "ticks", "epochs_run", "slice_epochs", "groups_made", "cancelled"]
 
 
 def bsgdtv_server_stats(h):
-    v = np.zeros(12, dtype=np.int64)
+    v = np.zeros(len(SERVER_STATS), dtype=np.int64)
     _check(load().bsgdtv_server_stats(h, _host_ptr(v, np.int64)), "bsgdtv_server_stats")
     return dict(zip(SERVER_STATS, (int(a) for a in v)))
 
@@ -777,6 +784,9 @@ class Server:
 
     def poll(self, request_id):
         return bsgdtv_server_poll(self.h, request_id)
+
+    def cancel(self, request_id):
+        bsgdtv_server_cancel(self.h, request_id)
 
     def wait(self, request_id, geom_id, timeout_s=-1.0):
         """Returns (x, latency_s, queued_s)."""

@@ -285,6 +285,7 @@ const char *bsgdtv_strerror(int code) {
         case BSGDTV_ERR_TIMEOUT: return "device wait timed out";
         case BSGDTV_ERR_NONFINITE: return "non-finite input";
         case BSGDTV_ERR_UNSUPPORTED: return "unsupported";
+        case BSGDTV_ERR_CANCELLED: return "cancelled";
         default: return "unknown error";
     }
 }

@@ -16,7 +16,9 @@
 // ends, finished requests are copied out (x to host memory: the end of their
 // latency) and their slots are emptied; queued requests are admitted between
 // ticks.  A slice's arithmetic never depends on the other slots, so a
-// request's result is the same alone and in any mix.
+// request's result is the same alone and in any mix.  A cancelled request
+// leaves the queue at once, or gives up its slot when its group's current
+// tick ends.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,7 +41,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-enum ReqState { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
+enum ReqState { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3, kCancelled = 4 };
 
 constexpr int kMinSlots = 4;   // smallest group the server makes on demand
 
@@ -51,6 +53,7 @@ struct Request {
     int epochs = 0;
     int remaining = 0;
     int state = kQueued;
+    bool cancel = false;   // running, cancelled: the slot is freed after the tick
     int error = BSGDTV_OK;
     std::string message;
     std::vector<float> x;
@@ -103,9 +106,10 @@ struct bsgdtv_server_ctx {
     int64_t next_id = 1;
     int64_t hbm_used = 0;
     bool stop = false;
+    bool wake = false;   // a cancel for the worker to reap
     std::thread worker;
     // statistics
-    int64_t submitted = 0, completed = 0, failed = 0, ticks = 0, epochs_run = 0, groups_made = 0,
+    int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, ticks = 0, epochs_run = 0, groups_made = 0,
             groups_freed = 0, max_running = 0, slice_epochs = 0;
 };
 
@@ -119,6 +123,22 @@ void finish_failed(bsgdtv_server_ctx *s, Request &r, int code, const std::string
     r.message = msg;
     r.t_done = Clock::now();
     s->failed++;
+}
+
+bool finished(const Request &r) {
+    return r.state == kDone || r.state == kFailed || r.state == kCancelled;
+}
+
+// Empties slot b of g (its state reset to zeros) after its request ended.
+void free_slot(Group *g, int b) {
+    g->slot_req[b] = -1;
+    bsgdtv_batch_set_slice(g->batch, b, nullptr, 0, 0.0);
+}
+
+void finish_cancelled(bsgdtv_server_ctx *s, Request &r) {
+    r.state = kCancelled;
+    r.t_done = Clock::now();
+    s->cancelled++;
 }
 
 int destroy_group(bsgdtv_server_ctx *s, Group *g) {
@@ -319,6 +339,11 @@ bool harvest(bsgdtv_server_ctx *s) {
             }
             r.remaining -= g->tick;
             s->slice_epochs += g->tick;
+            if (r.cancel) {
+                finish_cancelled(s, r);
+                free_slot(g.get(), b);
+                continue;
+            }
             if (r.remaining > 0) continue;
             r.x.resize((size_t)s->geoms[g->geom]->cols);
             int rc = bsgdtv_batch_get_slice_x(g->batch, b, r.x.data(), 0);
@@ -329,8 +354,7 @@ bool harvest(bsgdtv_server_ctx *s) {
             } else {
                 finish_failed(s, r, rc, std::string("get_slice_x: ") + bsgdtv_last_error());
             }
-            g->slot_req[b] = -1;
-            bsgdtv_batch_set_slice(g->batch, b, nullptr, 0, 0.0);   // empty slot: zeros
+            free_slot(g.get(), b);
         }
         if (q != cudaSuccess) cudaGetLastError();
         if (group_idle(g.get())) g->idle_since = Clock::now();
@@ -339,19 +363,41 @@ bool harvest(bsgdtv_server_ctx *s) {
     return any;
 }
 
+// Frees the slots of cancelled requests in groups that are not running a
+// tick (a busy group's are freed when harvest sees its tick end).
+void reap_cancelled(bsgdtv_server_ctx *s) {
+    bool any = false;
+    for (auto &g : s->groups) {
+        if (g->busy) continue;
+        bool freed = false;
+        for (int b = 0; b < (int)g->slot_req.size(); ++b) {
+            const int64_t id = g->slot_req[b];
+            if (id < 0 || !s->reqs[id]->cancel) continue;
+            finish_cancelled(s, *s->reqs[id]);
+            free_slot(g.get(), b);
+            freed = true;
+        }
+        if (freed && group_idle(g.get())) g->idle_since = Clock::now();
+        any = any || freed;
+    }
+    if (any) s->cv_done.notify_all();
+}
+
 void worker_main(bsgdtv_server_ctx *s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lock(s->mu);
     while (true) {
         if (s->stop) break;
         harvest(s);
+        reap_cancelled(s);
         admit(s);
         launch_ticks(s);
         bool busy = false;
         for (auto &g : s->groups) busy = busy || g->busy;
         if (!busy) {
             if (s->queue.empty()) {
-                s->cv_work.wait(lock, [&] { return s->stop || !s->queue.empty(); });
+                s->cv_work.wait(lock, [&] { return s->stop || !s->queue.empty() || s->wake; });
+                s->wake = false;
             } else {
                 // queued requests that cannot be placed yet and nothing running:
                 // wait for a submit, a stop, or retry shortly (memory may free up)
@@ -512,6 +558,29 @@ int bsgdtv_server_poll(bsgdtv_server_t s, int64_t request_id, int *state) {
     return BSGDTV_OK;
 }
 
+int bsgdtv_server_cancel(bsgdtv_server_t s, int64_t request_id) {
+    if (!s) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        auto it = s->reqs.find(request_id);
+        if (it == s->reqs.end()) return fail(BSGDTV_ERR_INVALID_ARG, "unknown request");
+        Request &r = *it->second;
+        if (finished(r)) return fail(BSGDTV_ERR_STATE, "request already ended");
+        if (r.state == kQueued) {
+            s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r.id));
+            s->geoms[r.geom]->queued--;
+            std::vector<float>().swap(r.y);
+            finish_cancelled(s, r);
+            s->cv_done.notify_all();
+            return BSGDTV_OK;
+        }
+        r.cancel = true;   // running: the worker frees its slot
+        s->wake = true;
+    }
+    s->cv_work.notify_all();
+    return BSGDTV_OK;
+}
+
 int bsgdtv_server_wait(bsgdtv_server_t s, int64_t request_id, double timeout_s, float *x,
                        double *times) {
     if (!s) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
@@ -519,15 +588,19 @@ int bsgdtv_server_wait(bsgdtv_server_t s, int64_t request_id, double timeout_s, 
     auto it = s->reqs.find(request_id);
     if (it == s->reqs.end()) return fail(BSGDTV_ERR_INVALID_ARG, "unknown request");
     Request *r = it->second.get();
-    auto finished = [&] { return r->state == kDone || r->state == kFailed; };
+    auto ended = [&] { return finished(*r); };
     if (timeout_s < 0) {
-        s->cv_done.wait(lock, finished);
-    } else if (!s->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), finished)) {
+        s->cv_done.wait(lock, ended);
+    } else if (!s->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), ended)) {
         return fail(BSGDTV_ERR_TIMEOUT, "request not finished within the timeout");
     }
     if (times) {
         times[0] = std::chrono::duration<double>(r->t_done - r->t_submit).count();
         times[1] = r->state == kDone ? std::chrono::duration<double>(r->t_admit - r->t_submit).count() : -1.0;
+    }
+    if (r->state == kCancelled) {
+        s->reqs.erase(it);
+        return fail(BSGDTV_ERR_CANCELLED, "request was cancelled");
     }
     if (r->state == kFailed) {
         const int code = r->error;
@@ -546,9 +619,10 @@ int bsgdtv_server_stats(bsgdtv_server_t s, int64_t *stats) {
     int64_t running = 0;
     for (auto &g : s->groups)
         for (int64_t id : g->slot_req) running += id >= 0;
-    const int64_t v[12] = {s->submitted, s->completed,   s->failed,     (int64_t)s->queue.size(),
+    const int64_t v[13] = {s->submitted, s->completed,   s->failed,     (int64_t)s->queue.size(),
                            running,      (int64_t)s->groups.size(), s->hbm_used, s->max_running,
-                           s->ticks,     s->epochs_run,  s->slice_epochs, s->groups_made};
+                           s->ticks,     s->epochs_run,  s->slice_epochs, s->groups_made,
+                           s->cancelled};
     std::memcpy(stats, v, sizeof(v));
     return BSGDTV_OK;
 }

@@ -165,3 +165,51 @@ def test_server_errors(B):
         assert e.value.code == -5
         x, lat, _ = srv.wait(rid, gid, timeout_s=120)
         assert np.all(np.isfinite(x)) and lat > 0
+
+
+def _poll_until(srv, rid, state, limit_s=60.0):
+    t0 = time.time()
+    while srv.poll(rid) != state:
+        assert time.time() - t0 < limit_s, (rid, srv.poll(rid))
+        time.sleep(0.001)
+
+
+def test_server_cancel(B):
+    """A budget for one group of one slot: a long request runs, a second one
+    queues.  Cancelling the queued one takes effect at once, the running one
+    at the end of its tick; both then wait with BSGDTV_ERR_CANCELLED and are
+    forgotten, and the next request reuses the slot with the bits it gets
+    alone."""
+    A, n, _, mu = geometry("g64")
+    budget = _op_bytes(B, A) + B.bsgdtv_batch_device_bytes(A.rows, A.cols_n, 0, 1) + 4096
+    with B.Server(budget, K, 4) as srv:
+        gid = srv.add_geometry(A, (n, n), mu, slots=1, prewarm=0)
+        long_id = srv.submit(gid, request("g64", 1), 0.05, 1 << 30)
+        queued_id = srv.submit(gid, request("g64", 2), 0.05, 5)
+        _poll_until(srv, long_id, 1)
+        assert srv.poll(queued_id) == 0
+        srv.cancel(queued_id)
+        assert srv.poll(queued_id) == 4
+        with pytest.raises(B.BsgdtvError) as e:
+            srv.cancel(queued_id)                  # already cancelled
+        assert e.value.code == -4
+        with pytest.raises(B.BsgdtvError) as e:
+            srv.wait(queued_id, gid, timeout_s=1.0)
+        assert e.value.code == -8
+        with pytest.raises(B.BsgdtvError) as e:
+            srv.poll(queued_id)                    # forgotten after the wait
+        assert e.value.code == -1
+        srv.cancel(long_id)
+        with pytest.raises(B.BsgdtvError) as e:
+            srv.wait(long_id, gid, timeout_s=60.0)
+        assert e.value.code == -8
+        rid = srv.submit(gid, request("g64", 3), 0.05, 7)
+        x, _, _ = srv.wait(rid, gid, timeout_s=120)
+        with pytest.raises(B.BsgdtvError) as e:
+            srv.cancel(rid)                        # waited for: unknown
+        assert e.value.code == -1
+        st = srv.stats()
+    assert st["cancelled"] == 2 and st["completed"] == 1 and st["failed"] == 0
+    assert st["device_bytes"] <= budget and st["groups_made"] == 1
+    alone, _ = _serve(B, [("g64", 3, 0.05, 7)], slots=1)
+    assert np.array_equal(x, alone[0])
