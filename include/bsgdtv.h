@@ -107,7 +107,10 @@ int bsgdtv_get_partition(bsgdtv_t h, int64_t *row_bounds, int64_t *col_bounds);
  * mu.  mu <= 0 selects mu = 0.9/(2 u_max) (Theorem 1 requires mu < 1/(2 u_max)),
  * estimating u_max first if no estimate exists.  Resets the iteration:
  * x^0 = 0, r^{-1} = y - A x^0 = y, epoch counter 0.  Rejects NaN/Inf in y
- * (BSGDTV_ERR_NONFINITE). */
+ * (BSGDTV_ERR_NONFINITE); once y is being copied, a failure leaves the handle
+ * without data (bsgdtv_run returns BSGDTV_ERR_STATE until a set_data
+ * succeeds).  A host y may be reused as soon as the call returns, pinned or
+ * not (the call waits for the handle's earlier work and the copy). */
 int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, double mu);
 
 /* Largest eigenvalue u_max of A^T A by power iteration in FP64 on the device
@@ -327,8 +330,9 @@ void bsgdtv_batch_destroy(bsgdtv_batch_t h);
  * weights lambdas [slices] (host, each finite and >= 0) and the step mu > 0
  * (finite; Theorem 1 asks mu < 1/(2 u_max), with u_max from
  * bsgdtv_estimate_umax of a single-slice handle on the same A).  Resets every
- * slice: x^0 = 0, r^{-1} = y_b.  Rejects NaN/Inf in y (BSGDTV_ERR_NONFINITE).
- * Synchronises the stream. */
+ * slice: x^0 = 0, r^{-1} = y_b.  Rejects NaN/Inf in y (BSGDTV_ERR_NONFINITE);
+ * once y is being copied a failure leaves the batch without data.  Returns
+ * after y has been read (a host y may be reused at once, pinned or not). */
 int bsgdtv_batch_set_data(bsgdtv_batch_t h, const float *y, int y_on_device,
                           const double *lambdas, double mu);
 
@@ -355,7 +359,9 @@ int bsgdtv_batch_get_x(bsgdtv_batch_t h, float *x, int out_on_device);
  * set_data.  y = NULL empties the slot (y = x = r = 0, lambda = 0).  The other
  * slices are untouched, and since every slice's arithmetic is independent of
  * the others, a slice's iterates do not depend on what the other slots hold.
- * Stream-ordered with run; BSGDTV_ERR_STATE before set_data. */
+ * Stream-ordered with run; BSGDTV_ERR_STATE before set_data.  A host y is
+ * checked for NaN/Inf (BSGDTV_ERR_NONFINITE leaves the slot as it was) and
+ * may be reused when the call returns. */
 int bsgdtv_batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_device, double lambda);
 
 /* Forward projection y_b = A x_b of every slice with the batch's A (stored

@@ -87,6 +87,7 @@ struct bsgdtv_ctx {
     std::vector<cudaEvent_t> tevents;
     int graph_fgp_iters = -1;
     bool graph_prox = false;
+    cudaEvent_t read_done = nullptr;   // set_data's copy has read the caller's host y
     double graph_mu = 0.0, graph_lambda = 0.0;
     int64_t graph_kernels = 0;
 };
@@ -464,6 +465,7 @@ void bsgdtv_destroy(bsgdtv_t h) {
     for (cudaEvent_t ev : h->tevents) cudaEventDestroy(ev);
     for (cudaEvent_t ev : h->tmark)
         if (ev) cudaEventDestroy(ev);
+    if (h->read_done) cudaEventDestroy(h->read_done);
     for (void *p : h->allocs) cudaFree(p);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
@@ -542,10 +544,16 @@ int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, 
     cudaStream_t s = h->stream;
     const int64_t R = h->dl.rows, c = h->dl.cols;
     float y_absmax = 0.f;
+    h->has_data = false;   // y is overwritten from here on: a failure leaves no data
     if (!y_on_device) {
-        if (!all_finite_absmax(y, R, &y_absmax))
-            return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+        // the host scan (NaN/Inf, max |y|) runs while the copy reads y; the
+        // call returns only after the copy has read y, pageable or pinned
+        if (!h->read_done) BSG_CUDA(cudaEventCreateWithFlags(&h->read_done, cudaEventDisableTiming));
         BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float), cudaMemcpyHostToDevice, s));
+        BSG_CUDA(cudaEventRecord(h->read_done, s));
+        const bool finite = all_finite_absmax(y, R, &y_absmax);
+        BSG_CUDA(cudaEventSynchronize(h->read_done));
+        if (!finite) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
     } else {
         BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float), cudaMemcpyDeviceToDevice, s));
         int flag = 0;

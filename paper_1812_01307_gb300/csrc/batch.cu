@@ -367,6 +367,7 @@ struct bsgdtv_batch_ctx {
     cudaGraphNode_t tnode[2][3] = {};
     cudaEvent_t tmark[3] = {nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> tevents;
+    cudaEvent_t read_done = nullptr;   // a caller's host y has been read (see host_upload)
     int graph_fgp_iters = -1;
     int64_t graph_kernels = 0;
 };
@@ -888,12 +889,31 @@ void bsgdtv_batch_destroy(bsgdtv_batch_t h) {
     for (cudaEvent_t ev : h->tevents) cudaEventDestroy(ev);
     for (cudaEvent_t ev : h->tmark)
         if (ev) cudaEventDestroy(ev);
+    if (h->read_done) cudaEventDestroy(h->read_done);
     for (void *p : h->allocs) cudaFree(p);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     bsgdtv_operator_t op = h->op;
     delete h;
     bsgdtv_operator_destroy(op);
 }
+
+namespace {
+
+// Copies n floats of a caller's host array y to dst on the handle's stream,
+// checks y for NaN/Inf on the host while the copy runs, and returns once the
+// copy has read y (stream order: after the handle's earlier work), so the
+// caller may reuse y whether it is pageable or pinned.  *finite: the check.
+int host_upload(bsgdtv_batch_t h, float *dst, const float *y, int64_t n, bool *finite) {
+    cudaStream_t s = h->stream;
+    if (!h->read_done) BSG_CUDA(cudaEventCreateWithFlags(&h->read_done, cudaEventDisableTiming));
+    BSG_CUDA(cudaMemcpyAsync(dst, y, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, s));
+    BSG_CUDA(cudaEventRecord(h->read_done, s));
+    *finite = all_finite(y, n);
+    BSG_CUDA(cudaEventSynchronize(h->read_done));
+    return BSGDTV_OK;
+}
+
+}  // namespace
 
 int bsgdtv_batch_set_data(bsgdtv_batch_t h, const float *y, int y_on_device,
                           const double *lambdas, double mu) {
@@ -905,13 +925,16 @@ int bsgdtv_batch_set_data(bsgdtv_batch_t h, const float *y, int y_on_device,
     BSG_CUDA(cudaSetDevice(h->device));
     cudaStream_t s = h->stream;
     const int64_t rows = h->rows, n_in = rows * h->B;
-    if (!y_on_device && !all_finite(y, n_in))
-        return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
     // y arrives slice-major [B][rows]; it is staged in R[1] (rows * Bp >= rows * B
-    // floats) and interleaved into Y; the first epoch rewrites R[1] in full
-    BSG_CUDA(cudaMemcpyAsync(h->R[1], y, (size_t)n_in * sizeof(float),
-                             y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    if (y_on_device) {
+    // floats) and interleaved into Y; the first epoch rewrites R[1] in full.
+    // From here on the old state is gone: a failure leaves the handle without data.
+    h->has_data = false;
+    if (!y_on_device) {
+        bool finite = false;
+        BSG_CHECK(host_upload(h, h->R[1], y, n_in, &finite));
+        if (!finite) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+    } else {
+        BSG_CUDA(cudaMemcpyAsync(h->R[1], y, (size_t)n_in * sizeof(float), cudaMemcpyDeviceToDevice, s));
         int hflag = 0;
         BSG_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
         BSG_CUDA(launch_check_finite(h->R[1], n_in, h->flag, s));
@@ -1009,19 +1032,18 @@ int bsgdtv_batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_dev
     BSG_CUDA(cudaSetDevice(h->device));
     cudaStream_t s = h->stream;
     const int64_t rows = h->rows;
-    if (y && !y_on_device && !all_finite(y, rows))
-        return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
-    if (y) {
-        BSG_CUDA(cudaMemcpyAsync(h->ystage, y, (size_t)rows * sizeof(float),
-                                 y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-        if (y_on_device) {
-            int hflag = 0;
-            BSG_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
-            BSG_CUDA(launch_check_finite(h->ystage, rows, h->flag, s));
-            BSG_CUDA(cudaMemcpyAsync(&hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-            BSG_CUDA(cudaStreamSynchronize(s));
-            if (hflag) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
-        }
+    if (y && !y_on_device) {   // staged: a bad y leaves the slot as it was
+        bool finite = false;
+        BSG_CHECK(host_upload(h, h->ystage, y, rows, &finite));
+        if (!finite) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+    } else if (y) {
+        BSG_CUDA(cudaMemcpyAsync(h->ystage, y, (size_t)rows * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        int hflag = 0;
+        BSG_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+        BSG_CUDA(launch_check_finite(h->ystage, rows, h->flag, s));
+        BSG_CUDA(cudaMemcpyAsync(&hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BSG_CUDA(cudaStreamSynchronize(s));
+        if (hflag) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
     }
     const double lam = y ? lambda : 0.0;
     const int64_t n = std::max(rows, h->cols);

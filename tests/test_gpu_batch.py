@@ -224,6 +224,43 @@ def test_batch_16bit_weights(B, fmt, bound):
         assert rel(X[b], x_64) <= bound
 
 
+def test_batch_host_y_is_read_before_return(B):
+    """Pinned host buffers passed to set_data and set_slice may be overwritten
+    as soon as the calls return; a NaN in set_slice's y leaves the slot as it
+    was, a NaN in set_data's y leaves the batch without data."""
+    name, slices = "ellipse64", 3
+    n = GEOM[name][0]
+    A, Y, mu = _setup(name, slices)
+    Y = np.ascontiguousarray(Y, dtype=np.float32)
+    lam = np.full(slices, 0.04)
+    with B.BatchReconstructor(A, (n, n), slices) as bt:
+        bt.set_data(Y, lam, mu)
+        bt.set_slice(2, Y[0], 0.04)
+        bt.run(5, 15)
+        X_ref = bt.x().copy()
+        pin = torch.empty(Y.size, dtype=torch.float32).pin_memory()
+        yp = pin.numpy().reshape(Y.shape)
+        yp[:] = Y
+        bt.set_data(yp, lam, mu)
+        yp[:] = np.nan
+        yp[0] = Y[0]
+        bt.set_slice(2, yp[0], 0.04)
+        yp[0] = np.nan
+        bad = Y[1].copy()
+        bad[5] = np.nan
+        with pytest.raises(B.BsgdtvError) as e:
+            bt.set_slice(1, bad, 0.04)       # rejected: slot 1 keeps its data
+        assert e.value.code == -6
+        bt.run(5, 15)
+        assert np.array_equal(bt.x(), X_ref)
+        with pytest.raises(B.BsgdtvError) as e:
+            bt.set_data(yp, lam, mu)          # NaN everywhere now
+        assert e.value.code == -6
+        with pytest.raises(B.BsgdtvError) as e:
+            bt.run(1, 15)
+        assert e.value.code == -4
+
+
 def test_batch_set_slice_restarts_one_slot(B):
     """A slot restarted mid-run follows Algorithm 1 from its own x^0 = 0 while
     the other slots carry on; the restarted slot's iterates are bit-identical

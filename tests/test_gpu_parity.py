@@ -270,6 +270,33 @@ def test_errors_and_state(B):
         assert B.bsgdtv_launch_count() - before == 3 * 3   # products, reduce/update, one FGP launch
 
 
+def test_host_y_is_read_before_set_data_returns(B):
+    """A pinned host y may be overwritten as soon as set_data returns (the
+    copy has read it by then), and a y with NaN leaves the handle without
+    data, even after a successful set_data."""
+    A, _, y, n, na, nb, M, N = _problem("wide130")
+    y32 = y.astype(np.float32)
+    pinned = torch.empty(A.rows, dtype=torch.float32).pin_memory()
+    yp = pinned.numpy()
+    with B.Reconstructor(A, (n, n), M, N, row_unit=nb, col_unit=n) as rec:
+        rec.set_data(y32, 0.05)
+        rec.run(6, 10)
+        x_ref = rec.x().copy()
+        yp[:] = y32
+        rec.set_data(yp, 0.05)
+        yp[:] = np.nan                        # the caller reuses its buffer at once
+        rec.run(6, 10)
+        assert np.array_equal(rec.x(), x_ref)
+        bad = y32.copy()
+        bad[-1] = np.inf
+        with pytest.raises(B.BsgdtvError) as e:
+            rec.set_data(bad, 0.05)
+        assert e.value.code == -6
+        with pytest.raises(B.BsgdtvError) as e:
+            rec.run(1, 10)                    # the rejected y left no data
+        assert e.value.code == -4
+
+
 def test_ellipse512_full_size_epochs(B):
     """The 512x512 workload (360 angles x 727 bins, M = N = 8, lambda 0.02, 50 FGP
     iterations) in the launch configuration bench.py times: 3 epochs vs the oracle."""
