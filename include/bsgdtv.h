@@ -97,6 +97,19 @@ int bsgdtv_create_csr_ex(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, i
                          const int64_t *row_bounds, const int64_t *col_bounds, int format,
                          void *stream);
 
+/* bsgdtv_create_csr_ex for the 2-D parallel-beam geometry of an n x n image
+ * (pixel size 1, centred at the origin), n_angles angles k*pi/n_angles and
+ * n_bins unit detector bins centred on the origin: A (rows k*n_bins + d,
+ * columns s*n + t) holds the exact intersection lengths of ray and pixel,
+ * generated on the device by the matrix-free projector of
+ * bsgdtv_batch_create_parallel_beam (each weight within about 1e-7 of its
+ * FP64 value; half-open pixels, |sin|, |cos| < 1e-15 taken as 0) and stored in
+ * `format`.  Row blocks are M groups of whole angles, column blocks N bands
+ * of whole image rows (the array_split rule).  Needs host memory for the
+ * CSR (12 bytes per nonzero) while the handle is built. */
+int bsgdtv_create_parallel_beam(bsgdtv_t *out, int n, int n_angles, int n_bins, int M, int N,
+                                int format, void *stream);
+
 /* Releases every resource of the handle.  NULL is ignored. */
 void bsgdtv_destroy(bsgdtv_t h);
 

@@ -38,6 +38,7 @@ def load(path: str | None = None):
     sig = {
         "bsgdtv_create_csr": (I32, [ctypes.POINTER(P), I64, I64, I32, I32, P, P, P, I32, I32, I64, I64, P, P, P]),
         "bsgdtv_create_csr_ex": (I32, [ctypes.POINTER(P), I64, I64, I32, I32, P, P, P, I32, I32, I64, I64, P, P, I32, P]),
+        "bsgdtv_create_parallel_beam": (I32, [ctypes.POINTER(P), I32, I32, I32, I32, I32, I32, P]),
         "bsgdtv_stored_weight": (ctypes.c_float, [D, I32]),
         "bsgdtv_destroy": (None, [P]),
         "bsgdtv_get_partition": (I32, [P, P, P]),
@@ -97,7 +98,7 @@ def load(path: str | None = None):
 
 def exported_symbols():
     """Names the binding expects the library to export."""
-    return ["bsgdtv_create_csr", "bsgdtv_create_csr_ex", "bsgdtv_stored_weight", "bsgdtv_destroy", "bsgdtv_get_partition", "bsgdtv_set_data",
+    return ["bsgdtv_create_csr", "bsgdtv_create_csr_ex", "bsgdtv_create_parallel_beam", "bsgdtv_stored_weight", "bsgdtv_destroy", "bsgdtv_get_partition", "bsgdtv_set_data",
             "bsgdtv_estimate_umax", "bsgdtv_get_params", "bsgdtv_run", "bsgdtv_run_timed", "bsgdtv_get_x",
             "bsgdtv_get_state", "bsgdtv_set_state", "bsgdtv_objective", "bsgdtv_block_products",
             "bsgdtv_get_info", "bsgdtv_tv_prox", "bsgdtv_tv_prox_static", "bsgdtv_partition_bounds",
@@ -185,6 +186,15 @@ def bsgdtv_create_csr(rows, cols, img_h, img_w, row_ptr, col_idx, vals, M, N, ro
                                   None if cb is None else _host_ptr(cb, np.int64), int(fmt),
                                   stream if stream is not None else current_stream())
     _check(rc, "bsgdtv_create_csr_ex")
+    return h
+
+
+def bsgdtv_create_parallel_beam(n, n_angles, n_bins, M, N, stream=None, fmt=FMT_F32_I32):
+    h = ctypes.c_void_p()
+    _check(load().bsgdtv_create_parallel_beam(ctypes.byref(h), int(n), int(n_angles), int(n_bins),
+                                              int(M), int(N), int(fmt),
+                                              stream if stream is not None else current_stream()),
+           "bsgdtv_create_parallel_beam")
     return h
 
 
@@ -615,10 +625,20 @@ class Reconstructor:
     vals, rows and cols_n attributes."""
 
     def __init__(self, A, img_shape, M, N, row_unit=1, col_unit=1, row_bounds=None,
-                 col_bounds=None, stream=None, fmt=FMT_F32_I32):
+                 col_bounds=None, stream=None, fmt=FMT_F32_I32, parallel_beam=None):
+        """A = None with parallel_beam = (n_angles, n_bins): A is generated on
+        the device for that geometry of the img_shape = (n, n) image."""
         self.img_shape = tuple(img_shape)
-        self.rows, self.cols = int(A.rows), int(A.cols_n)
         self.M, self.N = int(M), int(N)
+        if A is None:
+            n = int(img_shape[0])
+            if parallel_beam is None or img_shape[1] != n:
+                raise ValueError("A = None needs parallel_beam=(n_angles, n_bins) and a square image")
+            na, nb = (int(v) for v in parallel_beam)
+            self.rows, self.cols = na * nb, n * n
+            self.h = bsgdtv_create_parallel_beam(n, na, nb, M, N, stream, fmt)
+            return
+        self.rows, self.cols = int(A.rows), int(A.cols_n)
         self.h = bsgdtv_create_csr(self.rows, self.cols, img_shape[0], img_shape[1], A.row_ptr,
                                    A.cols, A.vals, M, N, row_unit, col_unit, row_bounds,
                                    col_bounds, stream, fmt)

@@ -457,6 +457,30 @@ int bsgdtv_create_csr_ex(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, i
     return BSGDTV_OK;
 }
 
+int bsgdtv_create_parallel_beam(bsgdtv_t *out, int n, int n_angles, int n_bins, int M, int N,
+                                int format, void *stream) {
+    if (!out) return fail(BSGDTV_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (n < 1 || n > 46340 || n_angles < 1 || n_bins < 1 || (int64_t)n_angles * n_bins > INT32_MAX)
+        return fail(BSGDTV_ERR_INVALID_ARG, "need 1 <= n <= 46340, n_angles, n_bins >= 1, "
+                                            "n_angles * n_bins < 2^31");
+    if (M < 1 || M > n_angles || N < 1 || N > n)
+        return fail(BSGDTV_ERR_INVALID_ARG, "need 1 <= M <= n_angles and 1 <= N <= n");
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col_idx;
+    std::vector<double> vals;
+    try {
+        BSG_CHECK(generate_parallel_beam_csr(n, n_angles, n_bins, (cudaStream_t)stream, row_ptr,
+                                             col_idx, vals));
+    } catch (const std::bad_alloc &) {
+        return fail(BSGDTV_ERR_OOM, "host allocation while generating A");
+    }
+    // blocks of whole angles and whole image rows
+    return bsgdtv_create_csr_ex(out, (int64_t)n_angles * n_bins, (int64_t)n * n, n, n, row_ptr.data(),
+                                col_idx.data(), vals.data(), M, N, n_bins, n, nullptr, nullptr,
+                                format, stream);
+}
+
 void bsgdtv_destroy(bsgdtv_t h) {
     if (!h) return;
     cudaSetDevice(h->device);

@@ -633,6 +633,84 @@ int alloc_vectors(bsgdtv_batch_ctx *hp) {
 
 }  // namespace
 
+namespace bsgdtv {
+
+// The parallel-beam A as a host CSR, weights from the matrix-free projector
+// (mf_weights_kernel, chunks of rays on the device), each row's columns
+// sorted ascending.  Values are the FP32 weights widened to FP64.
+int generate_parallel_beam_csr(int n, int n_angles, int n_bins, cudaStream_t s,
+                               std::vector<int64_t> &row_ptr, std::vector<int32_t> &col_idx,
+                               std::vector<double> &vals) {
+    const int64_t rows = (int64_t)n_angles * n_bins;
+    const int capacity = 2 * n + 2;   // a line meets at most 2n - 1 pixels of an n x n grid
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(rows, ((int64_t)256 << 20) / ((int64_t)capacity * 8)));
+    std::vector<AngleGeo> table;
+    mf_angle_table(n_angles, table);
+    std::vector<int64_t> ray_ids((size_t)chunk);
+    std::vector<int32_t> h_cols((size_t)chunk * capacity);
+    std::vector<float> h_vals((size_t)chunk * capacity);
+    std::vector<int> h_cnt((size_t)chunk);
+    row_ptr.assign(rows + 1, 0);
+    col_idx.clear();
+    vals.clear();
+    void *buf = nullptr;
+    const size_t bytes = table.size() * sizeof(AngleGeo) + chunk * sizeof(int64_t) +
+                         (size_t)chunk * capacity * (sizeof(int32_t) + sizeof(float)) + chunk * sizeof(int) + 1024;
+    BSG_CUDA(cudaMalloc(&buf, bytes));
+    char *p = static_cast<char *>(buf);
+    auto take = [&](size_t b) {
+        char *q = p;
+        p += (b + 255) / 256 * 256;
+        return q;
+    };
+    AngleGeo *geo = reinterpret_cast<AngleGeo *>(take(table.size() * sizeof(AngleGeo)));
+    int64_t *d_rays = reinterpret_cast<int64_t *>(take(chunk * sizeof(int64_t)));
+    int32_t *d_cols = reinterpret_cast<int32_t *>(take((size_t)chunk * capacity * sizeof(int32_t)));
+    float *d_vals = reinterpret_cast<float *>(take((size_t)chunk * capacity * sizeof(float)));
+    int *d_cnt = reinterpret_cast<int *>(take(chunk * sizeof(int)));
+    const int rc = [&]() -> int {
+        BSG_CUDA(cudaMemcpyAsync(geo, table.data(), table.size() * sizeof(AngleGeo), cudaMemcpyHostToDevice, s));
+        MfGeometry G;
+        G.geo = geo;
+        G.n = n;
+        G.n_angles = n_angles;
+        G.n_bins = n_bins;
+        std::vector<std::pair<int32_t, float>> row;
+        for (int64_t r0 = 0; r0 < rows; r0 += chunk) {
+            const int nr = (int)std::min<int64_t>(chunk, rows - r0);
+            for (int i = 0; i < nr; ++i) ray_ids[i] = r0 + i;
+            BSG_CUDA(cudaMemcpyAsync(d_rays, ray_ids.data(), nr * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+            BSG_CUDA(launch_mf_weights(G, d_rays, nr, capacity, d_cols, d_vals, d_cnt, s));
+            BSG_CUDA(cudaMemcpyAsync(h_cnt.data(), d_cnt, nr * sizeof(int), cudaMemcpyDeviceToHost, s));
+            BSG_CUDA(cudaMemcpyAsync(h_cols.data(), d_cols, (size_t)nr * capacity * sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, s));
+            BSG_CUDA(cudaMemcpyAsync(h_vals.data(), d_vals, (size_t)nr * capacity * sizeof(float),
+                                     cudaMemcpyDeviceToHost, s));
+            BSG_CUDA(cudaStreamSynchronize(s));
+            for (int i = 0; i < nr; ++i) {
+                const int c = h_cnt[i];
+                if (c < 0 || c >= capacity) return fail(BSGDTV_ERR_STATE, "ray meets more pixels than a line can");
+                row.clear();
+                for (int k = 0; k < c; ++k)
+                    row.push_back({h_cols[(size_t)i * capacity + k], h_vals[(size_t)i * capacity + k]});
+                std::sort(row.begin(), row.end());
+                for (size_t k = 0; k < row.size(); ++k) {
+                    if (k > 0 && row[k].first == row[k - 1].first)
+                        return fail(BSGDTV_ERR_STATE, "pixel met twice by one ray");
+                    col_idx.push_back(row[k].first);
+                    vals.push_back((double)row[k].second);
+                }
+                row_ptr[r0 + i + 1] = (int64_t)col_idx.size();
+            }
+        }
+        return BSGDTV_OK;
+    }();
+    cudaFree(buf);
+    return rc;
+}
+
+}  // namespace bsgdtv
+
 extern "C" {
 
 int bsgdtv_operator_create_csr(bsgdtv_operator_t *out, int64_t rows, int64_t cols, int img_h,

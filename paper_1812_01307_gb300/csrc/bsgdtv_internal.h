@@ -166,6 +166,13 @@ void fgp_momentum_host(int iters, std::vector<float> &mom);
 // slots that come and go do not force the epoch graphs to be captured again.
 void batch_keep_prox(bsgdtv_batch_t h, bool on);
 
+// batch.cu: the 2-D parallel-beam A of an n x n image (n_angles x n_bins
+// rays) as a host CSR with ascending columns, weights from the matrix-free
+// projector; BSGDTV_* code.
+int generate_parallel_beam_csr(int n, int n_angles, int n_bins, cudaStream_t s,
+                               std::vector<int64_t> &row_ptr, std::vector<int32_t> &col_idx,
+                               std::vector<double> &vals);
+
 // batch.cu: host check of a CSR image operator (sizes, sorted in-range
 // columns, finite weights); BSGDTV_* code.
 int validate_image_csr(int64_t rows, int64_t cols, int img_h, int img_w, const int64_t *row_ptr,

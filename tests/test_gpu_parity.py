@@ -270,6 +270,63 @@ def test_errors_and_state(B):
         assert B.bsgdtv_launch_count() - before == 3 * 3   # products, reduce/update, one FGP launch
 
 
+@pytest.mark.parametrize("name", ["ellipse64", "ragged37", "wide130"])
+def test_parallel_beam_handle_matches_csr_handle(B, name):
+    """bsgdtv_create_parallel_beam builds A on the device for the geometry:
+    same partition as a handle built from the FP64 generator's CSR with whole
+    angles / image rows as units, block products within 1e-6 of it, epochs
+    within 1e-5, and x within 1e-4 of the oracle."""
+    A, _, y, n, na, nb, M, N = _problem(name)
+    y32 = y.astype(np.float32)
+    rng = np.random.default_rng(2)
+    x = torch.tensor(rng.random(A.cols_n), dtype=torch.float32, device="cuda")
+    r = torch.tensor(rng.standard_normal(A.rows), dtype=torch.float32, device="cuda")
+    u, _ = oracle.power_iteration(A)
+    mu = 0.9 / (2 * u)
+    out = []
+    for src in (A, None):
+        with B.Reconstructor(src, (n, n), M, N, row_unit=nb, col_unit=n,
+                             parallel_beam=(na, nb)) as rec:
+            part = rec.partition()
+            info = rec.info()
+            zb = torch.zeros(N * A.rows, device="cuda")
+            gb = torch.zeros(M * A.cols_n, device="cuda")
+            B.bsgdtv_block_products(rec.h, x, r, zb, gb)
+            rec.set_data(y32, 0.05, mu)
+            rec.run(10, 20)
+            out.append((part, info, zb.cpu().numpy(), gb.cpu().numpy(), rec.x().copy()))
+    (pc, ic, zc, gc, xc), (pg, ig, zg, gg, xg) = out
+    assert all(np.array_equal(a, b) for a, b in zip(pc, pg))
+    # the support may differ by weights below 1e-6 (rays grazing pixel corners;
+    # test_gpu_matrix_free checks every weight against the FP64 generator)
+    assert abs(ig["nnz"] - ic["nnz"]) <= 5e-3 * ic["nnz"]
+    assert rel(zg, zc) <= 1e-6 and rel(gg, gc) <= 1e-6
+    assert rel(xg, xc) <= 1e-5
+    x_ref, _ = oracle.run(A, y32.astype(np.float64), (n, n), M, N, 0.05, mu, 10, 20,
+                          row_unit=nb, col_unit=n)
+    assert rel(xg, x_ref) <= 1e-4
+
+
+def test_parallel_beam_handle_512(B):
+    """The 512x512 geometry (360 x 727) generated on the device: 2 epochs in
+    the bench's configuration within 1e-5 of the CSR-built handle."""
+    wl = synth.WORKLOADS["ellipse512"]
+    P = synth.make_problem(wl)
+    y32 = P.y.astype(np.float32)
+    mu = 0.9 / (2 * 1.8e5)
+    xs = []
+    for src in (P.A, None):
+        with B.Reconstructor(src, (wl.n, wl.n), wl.M, wl.N, row_unit=wl.n_bins, col_unit=wl.n,
+                             parallel_beam=(wl.n_angles, wl.n_bins)) as rec:
+            rec.set_data(y32, wl.lam, mu)
+            rec.run(2, wl.fgp_iters)
+            xs.append(rec.x().copy())
+    assert rel(xs[1], xs[0]) <= 1e-5
+    with pytest.raises(B.BsgdtvError) as e:
+        B.bsgdtv_create_parallel_beam(0, 360, 727, 8, 8)
+    assert e.value.code == -1
+
+
 def test_host_y_is_read_before_set_data_returns(B):
     """A pinned host y may be overwritten as soon as set_data returns (the
     copy has read it by then), and a y with NaN leaves the handle without
