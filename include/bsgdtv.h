@@ -176,6 +176,18 @@ int bsgdtv_set_state(bsgdtv_t h, const float *x, const float *r, int64_t epoch, 
  * Synchronises. */
 int bsgdtv_objective(bsgdtv_t h, double *data_term, double *tv);
 
+/* Runs epochs as bsgdtv_run does, in steps of check_every (>= 1) epochs,
+ * evaluating the FP64 objective F = ||y - A x||^2 + lambda TV(x)
+ * (bsgdtv_objective) before the first step and after each one, and stops
+ * after the step where |F_before - F_after| <= rel_tol * F_before, or once
+ * max_epochs have run (the last step may be shorter).  Writes the epochs run
+ * and the last F (either may be NULL).  The iterates are those of
+ * bsgdtv_run for the same number of epochs, bit for bit.  Synchronises at
+ * every check.  The stopping rule is a deployment choice; the paper runs
+ * fixed epoch counts. */
+int bsgdtv_run_until(bsgdtv_t h, int max_epochs, int fgp_iters, int check_every, double rel_tol,
+                     int *epochs_run, double *objective);
+
 /* Test hook: the block products of Algorithm 1 for given x [cols] and r [rows]
  * (device pointers), computed by the same fused kernel the epoch uses.
  *   z_blocks [N*rows]:  z_blocks[j*rows + k] = (A_{I_i}^{J_j} x_{J_j})_k for row

@@ -48,6 +48,7 @@ def load(path: str | None = None):
         "bsgdtv_run": (I32, [P, I32, I32]),
         "bsgdtv_run_timed": (I32, [P, I32, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "bsgdtv_run_subsets": (I32, [P, I32, I32, P, P]),
+        "bsgdtv_run_until": (I32, [P, I32, I32, I32, D, ctypes.POINTER(I32), ctypes.POINTER(D)]),
         "bsgdtv_get_x": (I32, [P, P, I32]),
         "bsgdtv_get_state": (I32, [P, P, P, ctypes.POINTER(I64), I32]),
         "bsgdtv_set_state": (I32, [P, P, P, I64, I32]),
@@ -99,7 +100,8 @@ def load(path: str | None = None):
 def exported_symbols():
     """Names the binding expects the library to export."""
     return ["bsgdtv_create_csr", "bsgdtv_create_csr_ex", "bsgdtv_create_parallel_beam", "bsgdtv_stored_weight", "bsgdtv_destroy", "bsgdtv_get_partition", "bsgdtv_set_data",
-            "bsgdtv_estimate_umax", "bsgdtv_get_params", "bsgdtv_run", "bsgdtv_run_timed", "bsgdtv_get_x",
+            "bsgdtv_estimate_umax", "bsgdtv_get_params", "bsgdtv_run", "bsgdtv_run_timed",
+            "bsgdtv_run_until", "bsgdtv_get_x",
             "bsgdtv_get_state", "bsgdtv_set_state", "bsgdtv_objective", "bsgdtv_block_products",
             "bsgdtv_get_info", "bsgdtv_tv_prox", "bsgdtv_tv_prox_static", "bsgdtv_partition_bounds",
             "bsgdtv_layout_check", "bsgdtv_run_subsets", "bsgdtv_batch_create_csr", "bsgdtv_batch_destroy",
@@ -232,6 +234,15 @@ def bsgdtv_estimate_umax(h, max_iters=5000, rel_tol=1e-12):
     _check(load().bsgdtv_estimate_umax(h, int(max_iters), float(rel_tol), ctypes.byref(u),
                                        ctypes.byref(it)), "bsgdtv_estimate_umax")
     return u.value, it.value
+
+
+def bsgdtv_run_until(h, max_epochs, fgp_iters, check_every=10, rel_tol=1e-6):
+    done = ctypes.c_int()
+    f = ctypes.c_double()
+    _check(load().bsgdtv_run_until(h, int(max_epochs), int(fgp_iters), int(check_every),
+                                   float(rel_tol), ctypes.byref(done), ctypes.byref(f)),
+           "bsgdtv_run_until")
+    return done.value, f.value
 
 
 def bsgdtv_get_params(h):
@@ -677,6 +688,10 @@ class Reconstructor:
 
     def run(self, epochs, fgp_iters):
         bsgdtv_run(self.h, epochs, fgp_iters)
+
+    def run_until(self, max_epochs, fgp_iters, check_every=10, rel_tol=1e-6):
+        """Returns (epochs run, last objective data + lambda TV)."""
+        return bsgdtv_run_until(self.h, max_epochs, fgp_iters, check_every, rel_tol)
 
     def run_subsets(self, row_sel, col_sel, fgp_iters):
         bsgdtv_run_subsets(self.h, row_sel, col_sel, fgp_iters)

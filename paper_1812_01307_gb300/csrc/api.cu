@@ -798,6 +798,37 @@ int bsgdtv_set_state(bsgdtv_t h, const float *x, const float *r, int64_t epoch, 
     return BSGDTV_OK;
 }
 
+int bsgdtv_run_until(bsgdtv_t h, int max_epochs, int fgp_iters, int check_every, double rel_tol,
+                     int *epochs_run, double *objective) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (max_epochs < 0 || fgp_iters < 0 || check_every < 1 || !(rel_tol >= 0.0) ||
+        !std::isfinite(rel_tol))
+        return fail(BSGDTV_ERR_INVALID_ARG, "need max_epochs, fgp_iters >= 0, check_every >= 1, "
+                                            "finite rel_tol >= 0");
+    if (!h->has_data) return fail(BSGDTV_ERR_STATE, "bsgdtv_run_until before bsgdtv_set_data");
+    auto F = [&](double *f) -> int {
+        double data = 0.0, tv = 0.0;
+        BSG_CHECK(bsgdtv_objective(h, &data, &tv));
+        *f = data + h->lambda * tv;
+        return BSGDTV_OK;
+    };
+    double f_before = 0.0, f_after = 0.0;
+    BSG_CHECK(F(&f_before));
+    f_after = f_before;
+    int done = 0;
+    while (done < max_epochs) {
+        const int step = std::min(check_every, max_epochs - done);
+        BSG_CHECK(bsgdtv_run(h, step, fgp_iters));
+        done += step;
+        BSG_CHECK(F(&f_after));
+        if (std::fabs(f_before - f_after) <= rel_tol * std::fabs(f_before)) break;
+        f_before = f_after;
+    }
+    if (epochs_run) *epochs_run = done;
+    if (objective) *objective = f_after;
+    return BSGDTV_OK;
+}
+
 int bsgdtv_objective(bsgdtv_t h, double *data_term, double *tv) {
     if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
     if (!h->has_data) return fail(BSGDTV_ERR_STATE, "no data set");

@@ -221,6 +221,50 @@ def test_objective_fp64(B):
     assert abs(tv - tv_ref) <= 1e-9 * tv_ref
 
 
+def test_run_until_stops_on_the_objective(B):
+    """bsgdtv_run_until: checks F = data + lambda TV every 5 epochs and stops
+    at the first step whose relative decrease is <= rel_tol; the reported F
+    is the handle's FP64 objective at that epoch, the oracle's F of the same
+    iterate agrees to 1e-9 and of the oracle's own iterate to 1e-3 (F is a
+    small residual there), and the iterates equal a plain run of as many
+    epochs, bit for bit."""
+    A, _, y, n, na, nb, M, N = _problem("ellipse64")
+    y32 = y.astype(np.float32)
+    lam, K, c, tol = 0.05, 20, 5, 2e-2   # the oracle's F first moves < 2 % over 5 epochs at 120
+    with B.Reconstructor(A, (n, n), M, N, row_unit=nb, col_unit=n) as rec:
+        rec.set_data(y32, lam)
+        mu = rec.params()[0]
+        k, F = rec.run_until(400, K, check_every=c, rel_tol=tol)
+        x_k = rec.x().copy()
+        d, tv = rec.objective()
+        assert F == d + lam * tv and c <= k < 400 and k % c == 0
+
+        def F_at(e):
+            rec.set_data(y32, lam)
+            rec.run(e, K)
+            d_, tv_ = rec.objective()
+            return d_ + lam * tv_, rec.x().copy()
+
+        f_k, x_again = F_at(k)
+        assert f_k == F and np.array_equal(x_again, x_k)
+        f_prev, _ = F_at(k - c)
+        assert abs(f_prev - f_k) <= tol * f_prev
+        if k >= 2 * c:
+            f_pp, _ = F_at(k - 2 * c)
+            assert abs(f_pp - f_prev) > tol * f_pp
+        rec.set_data(y32, lam)
+        k0, _ = rec.run_until(7, K, check_every=3, rel_tol=0.0)   # runs to the end: 3 + 3 + 1
+        assert k0 == 7
+        with pytest.raises(B.BsgdtvError) as e:
+            rec.run_until(7, K, check_every=0)
+        assert e.value.code == -1
+    Fo, _, _ = oracle.objective(f32(A), y32.astype(np.float64), x_k.astype(np.float64), lam, (n, n))
+    assert abs(Fo - F) <= 1e-9 * F
+    x_ref, _ = oracle.run(A, y32.astype(np.float64), (n, n), M, N, lam, mu, k, K, row_unit=nb, col_unit=n)
+    Fr, _, _ = oracle.objective(A, y32.astype(np.float64), x_ref, lam, (n, n))
+    assert abs(Fr - F) <= 1e-3 * F
+
+
 def test_checkpoint_resume(B):
     A, _, y, n, na, nb, M, N = _problem("ragged37")
     y32 = y.astype(np.float32)
