@@ -425,7 +425,7 @@ def run_ours(args):
         Ys_dev = torch.tensor(Ys, dtype=torch.float32, device=dev)
         bt = B.BatchReconstructor(P.A, (wl.n, wl.n), Bs)
         bt.set_data(Ys_dev, np.full(Bs, wl.lam), mu)
-        chunk, _ = bt.autotune(wl.fgp_iters, 3)
+        chunk, group, _ = bt.autotune(wl.fgp_iters, 3)
         bt.run(max(W, 3), wl.fgp_iters)
         torch.cuda.synchronize()
         D.barrier()
@@ -447,6 +447,7 @@ def run_ours(args):
                              "steps": Kb, "epoch_ms": 1e3 * dt / Kb, "products_ms": pk / Kb,
                              "bytes_per_epoch_products": int(pass_bytes), "achieved_gbs": ach,
                              "autotuned_fgp_iters_per_launch": chunk,
+                             "autotuned_fgp_slices_per_group": group,
                              "frac": ach / peak,
                              "note": "two passes over A (CSR then CSC) per epoch, lanes = slices; "
                                      "x and r gathered from L2"}

@@ -399,11 +399,14 @@ int bsgdtv_batch_project(bsgdtv_batch_t h, const float *x, float *y);
  * data, state restored after every trial) for each candidate launch shape
  * and keeps the fastest.  The candidates are the FGP iterations per launch
  * (3, 4, 5, 6, 8: fewer iterations per launch mean a smaller halo per
- * 64 x 64 region but more launches and field traffic); every candidate gives
- * bit-identical iterates, so tuning never changes results.  Writes the choice
- * and its time per epoch (may be NULL).  Synchronises; needs set_data. */
+ * 64 x 64 region but more launches and field traffic) times the slices per
+ * FGP launch group (half, once and twice the count whose dual fields fill
+ * 48 MB of L2, and all slices: small groups keep the fields in L2, large
+ * ones fill more SMs per launch); every candidate gives bit-identical
+ * iterates, so tuning never changes results.  Writes the choices and the
+ * time per epoch (each may be NULL).  Synchronises; needs set_data. */
 int bsgdtv_batch_autotune(bsgdtv_batch_t h, int fgp_iters, int epochs_per_trial, int *fgp_chunk,
-                          double *epoch_ms);
+                          int *fgp_group, double *epoch_ms);
 
 /* Copies slice b's x [cols] (FP32).  To the host: synchronises the stream. */
 int bsgdtv_batch_get_slice_x(bsgdtv_batch_t h, int b, float *x, int out_on_device);

@@ -76,7 +76,7 @@ def load(path: str | None = None):
         "bsgdtv_mf_ray_weights": (I32, [I32, I32, I32, P, I32, I32, P, P, P]),
         "bsgdtv_batch_estimate_umax": (I32, [P, I32, D, ctypes.POINTER(D), ctypes.POINTER(I32)]),
         "bsgdtv_batch_project": (I32, [P, P, P]),
-        "bsgdtv_batch_autotune": (I32, [P, I32, I32, ctypes.POINTER(I32), ctypes.POINTER(D)]),
+        "bsgdtv_batch_autotune": (I32, [P, I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(D)]),
         "bsgdtv_server_create": (I32, [ctypes.POINTER(P), I64, I32, I32]),
         "bsgdtv_server_destroy": (None, [P]),
         "bsgdtv_server_add_geometry": (I32, [P, I64, I64, I32, I32, P, P, P, I32, I32, D, I32, ctypes.POINTER(I32)]),
@@ -544,11 +544,12 @@ def bsgdtv_batch_project(h, x, y):
 
 
 def bsgdtv_batch_autotune(h, fgp_iters, epochs_per_trial=3):
-    """Picks the batch's FGP iterations per launch by timing; returns (chunk, epoch ms)."""
-    c, ms = ctypes.c_int(), ctypes.c_double()
+    """Picks the batch's FGP iterations per launch and slices per FGP launch
+    group by timing; returns (chunk, group, epoch ms)."""
+    c, g, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _check(load().bsgdtv_batch_autotune(h, int(fgp_iters), int(epochs_per_trial), ctypes.byref(c),
-                                        ctypes.byref(ms)), "bsgdtv_batch_autotune")
-    return c.value, ms.value
+                                        ctypes.byref(g), ctypes.byref(ms)), "bsgdtv_batch_autotune")
+    return c.value, g.value, ms.value
 
 
 def bsgdtv_batch_device_bytes(rows, cols, nnz, slices, fmt=FMT_F32_I32) -> int:

@@ -426,6 +426,14 @@ bool any_prox(const bsgdtv_batch_ctx *h, int fgp_iters) {
     return false;
 }
 
+// Slices per FGP launch group whose fields (b, p, q, p_prev, q_prev) fit in
+// about half of the L2, so the fields of consecutive chunk launches come from
+// L2 rather than HBM.
+int fgp_group_by_budget(const bsgdtv_batch_ctx *h) {
+    return std::max<int>(1, (int)std::min<int64_t>(
+                                h->B, kFgpFieldBudget / std::max<int64_t>(1, 20 * h->cols)));
+}
+
 // One epoch of every slice: reads R[par], writes R[1 - par].
 int benqueue_epoch(bsgdtv_batch_ctx *h, int par, int fgp_iters, cudaStream_t s,
                    cudaEvent_t *marks) {
@@ -447,12 +455,8 @@ int benqueue_epoch(bsgdtv_batch_ctx *h, int par, int fgp_iters, cudaStream_t s,
     if (prox) {
         const int64_t c = h->cols;
         BSG_CUDA(launch_transpose(h->Xhat, h->Xhp, c, h->B, h->Bp, true, s));
-        // slices in groups whose FGP fields (b, p, q, p_prev, q_prev) fit in
-        // about half of the L2, so the fields of consecutive chunk launches
-        // come from L2 rather than HBM
-        const int per = std::max<int>(1, (int)std::min<int64_t>(
-                                             h->B, kFgpFieldBudget / std::max<int64_t>(1, 20 * c)));
-        const int sg = h->fgp_group > 0 ? std::min(h->fgp_group, h->B) : per;
+        // slices in groups (the autotuner's choice, else by the L2 budget)
+        const int sg = h->fgp_group > 0 ? std::min(h->fgp_group, h->B) : fgp_group_by_budget(h);
         for (int b0 = 0; b0 < h->B; b0 += sg) {
             const int nb = std::min(sg, h->B - b0);
             const size_t o = (size_t)b0 * c;
@@ -1231,7 +1235,7 @@ int bsgdtv_batch_project(bsgdtv_batch_t h, const float *x, float *y) {
 }
 
 int bsgdtv_batch_autotune(bsgdtv_batch_t h, int fgp_iters, int epochs_per_trial, int *fgp_chunk,
-                          double *epoch_ms) {
+                          int *fgp_group, double *epoch_ms) {
     if (!h || fgp_iters < 0 || epochs_per_trial < 1)
         return fail(BSGDTV_ERR_INVALID_ARG, "need fgp_iters >= 0 and epochs_per_trial >= 1");
     if (!h->has_data) return fail(BSGDTV_ERR_STATE, "autotune before set_data");
@@ -1258,24 +1262,36 @@ int bsgdtv_batch_autotune(bsgdtv_batch_t h, int fgp_iters, int epochs_per_trial,
         h->epoch = epoch;
         return BSGDTV_OK;
     };
-    int best = h->fgp_chunk;
-    double best_ms = 1e300;
-    for (int chunk : kFgpChunkChoices) {
-        h->fgp_chunk = chunk;
-        bdrop_graphs(h);
-        BSG_CHECK(bsgdtv_batch_run(h, 1, fgp_iters));   // builds the graphs, warms up
-        double pk = 0.0, ep = 0.0;
-        BSG_CHECK(bsgdtv_batch_run_timed(h, epochs_per_trial, fgp_iters, &pk, &ep));
-        BSG_CHECK(restore());
-        if (ep < best_ms) {
-            best_ms = ep;
-            best = chunk;
-        }
+    // slices per FGP launch group: half, once and twice the L2-budget size, all
+    const int per = fgp_group_by_budget(h);
+    std::vector<int> groups;
+    for (int g : {std::max(1, per / 2), per, 2 * per, h->B}) {
+        g = std::min(g, h->B);
+        if (std::find(groups.begin(), groups.end(), g) == groups.end()) groups.push_back(g);
     }
+    int best = h->fgp_chunk, best_g = h->fgp_group;
+    double best_ms = 1e300;
+    for (int g : groups)
+        for (int chunk : kFgpChunkChoices) {
+            h->fgp_chunk = chunk;
+            h->fgp_group = g;
+            bdrop_graphs(h);
+            BSG_CHECK(bsgdtv_batch_run(h, 1, fgp_iters));   // builds the graphs, warms up
+            double pk = 0.0, ep = 0.0;
+            BSG_CHECK(bsgdtv_batch_run_timed(h, epochs_per_trial, fgp_iters, &pk, &ep));
+            BSG_CHECK(restore());
+            if (ep < best_ms) {
+                best_ms = ep;
+                best = chunk;
+                best_g = g;
+            }
+        }
     h->fgp_chunk = best;
+    h->fgp_group = best_g;
     bdrop_graphs(h);
     BSG_CUDA(cudaStreamSynchronize(s));
     if (fgp_chunk) *fgp_chunk = best;
+    if (fgp_group) *fgp_group = best_g > 0 ? best_g : per;
     if (epoch_ms) *epoch_ms = best_ms / epochs_per_trial;
     return BSGDTV_OK;
 }

@@ -308,8 +308,8 @@ def test_batch_autotune_keeps_results(B):
         X_plain = bt.x().copy()
         bt.set_data(Y, lam, mu)
         bt.run(2, 30)
-        chunk, ms = bt.autotune(30, 2)
-        assert chunk in (3, 4, 5, 6, 8) and ms > 0
+        chunk, group, ms = bt.autotune(30, 2)
+        assert chunk in (3, 4, 5, 6, 8) and 1 <= group <= 6 and ms > 0
         bt.run(2, 30)
         X_tuned = bt.x().copy()
     assert np.array_equal(X_plain, X_tuned)
