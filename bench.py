@@ -58,6 +58,9 @@ def parse():
                     help="comma-separated variants to run: f32_i16, f16_i16, bf16_i16, batch, "
                          "matrix_free, stochastic")
     ap.add_argument("--mf-n", type=int, default=2048, help="image size of the matrix-free variant")
+    ap.add_argument("--batch-tuning", default="",
+                    help="FGP iterations per launch and slices per FGP group for the batch, "
+                         "e.g. 5,9 (default: autotune)")
     return ap.parse_args()
 
 
@@ -425,7 +428,11 @@ def run_ours(args):
         Ys_dev = torch.tensor(Ys, dtype=torch.float32, device=dev)
         bt = B.BatchReconstructor(P.A, (wl.n, wl.n), Bs)
         bt.set_data(Ys_dev, np.full(Bs, wl.lam), mu)
-        chunk, group, _ = bt.autotune(wl.fgp_iters, 3)
+        if args.batch_tuning:   # a known tuning: no timing trials (e.g. under a profiler)
+            chunk, group = (int(v) for v in args.batch_tuning.split(","))
+            bt.set_tuning(chunk, group)
+        else:
+            chunk, group, _ = bt.autotune(wl.fgp_iters, 3)
         bt.run(max(W, 3), wl.fgp_iters)
         torch.cuda.synchronize()
         D.barrier()

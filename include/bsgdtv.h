@@ -408,6 +408,12 @@ int bsgdtv_batch_project(bsgdtv_batch_t h, const float *x, float *y);
 int bsgdtv_batch_autotune(bsgdtv_batch_t h, int fgp_iters, int epochs_per_trial, int *fgp_chunk,
                           int *fgp_group, double *epoch_ms);
 
+/* Applies a known tuning without timing (e.g. one bsgdtv_batch_autotune found
+ * earlier): FGP iterations per launch 1..8 (0: the default) and slices per
+ * FGP launch group (0: sized by the 48 MB L2 budget).  Results do not depend
+ * on it.  Synchronises the stream when the tuning changes. */
+int bsgdtv_batch_set_tuning(bsgdtv_batch_t h, int fgp_chunk, int fgp_group);
+
 /* Copies slice b's x [cols] (FP32).  To the host: synchronises the stream. */
 int bsgdtv_batch_get_slice_x(bsgdtv_batch_t h, int b, float *x, int out_on_device);
 

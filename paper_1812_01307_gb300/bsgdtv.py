@@ -77,6 +77,7 @@ def load(path: str | None = None):
         "bsgdtv_batch_estimate_umax": (I32, [P, I32, D, ctypes.POINTER(D), ctypes.POINTER(I32)]),
         "bsgdtv_batch_project": (I32, [P, P, P]),
         "bsgdtv_batch_autotune": (I32, [P, I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(D)]),
+        "bsgdtv_batch_set_tuning": (I32, [P, I32, I32]),
         "bsgdtv_server_create": (I32, [ctypes.POINTER(P), I64, I32, I32]),
         "bsgdtv_server_destroy": (None, [P]),
         "bsgdtv_server_add_geometry": (I32, [P, I64, I64, I32, I32, P, P, P, I32, I32, D, I32, ctypes.POINTER(I32)]),
@@ -111,7 +112,7 @@ def exported_symbols():
             "bsgdtv_server_destroy", "bsgdtv_server_add_geometry", "bsgdtv_server_submit",
             "bsgdtv_server_poll", "bsgdtv_server_cancel", "bsgdtv_server_wait", "bsgdtv_server_stats",
             "bsgdtv_batch_create_parallel_beam", "bsgdtv_mf_ray_weights", "bsgdtv_batch_estimate_umax",
-            "bsgdtv_batch_project", "bsgdtv_batch_autotune", "bsgdtv_operator_create_csr",
+            "bsgdtv_batch_project", "bsgdtv_batch_autotune", "bsgdtv_batch_set_tuning", "bsgdtv_operator_create_csr",
             "bsgdtv_operator_destroy", "bsgdtv_batch_create_from_operator",
             "bsgdtv_launch_count", "bsgdtv_last_error", "bsgdtv_strerror"]
 
@@ -543,6 +544,11 @@ def bsgdtv_batch_project(h, x, y):
     return y
 
 
+def bsgdtv_batch_set_tuning(h, fgp_chunk=0, fgp_group=0):
+    """Applies a known tuning (0 = default for either)."""
+    _check(load().bsgdtv_batch_set_tuning(h, int(fgp_chunk), int(fgp_group)), "bsgdtv_batch_set_tuning")
+
+
 def bsgdtv_batch_autotune(h, fgp_iters, epochs_per_trial=3):
     """Picks the batch's FGP iterations per launch and slices per FGP launch
     group by timing; returns (chunk, group, epoch ms)."""
@@ -770,6 +776,9 @@ class BatchReconstructor:
 
     def autotune(self, fgp_iters, epochs_per_trial=3):
         return bsgdtv_batch_autotune(self.h, fgp_iters, epochs_per_trial)
+
+    def set_tuning(self, fgp_chunk=0, fgp_group=0):
+        bsgdtv_batch_set_tuning(self.h, fgp_chunk, fgp_group)
 
     def project(self, x, y=None):
         """y = A x per slice (CUDA tensors); resets the batch's state."""

@@ -1296,6 +1296,21 @@ int bsgdtv_batch_autotune(bsgdtv_batch_t h, int fgp_iters, int epochs_per_trial,
     return BSGDTV_OK;
 }
 
+int bsgdtv_batch_set_tuning(bsgdtv_batch_t h, int fgp_chunk, int fgp_group) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (fgp_chunk < 0 || fgp_chunk > fgpk::kMaxChunk || fgp_group < 0)
+        return fail(BSGDTV_ERR_INVALID_ARG, "need 0 <= fgp_chunk <= 8 and fgp_group >= 0");
+    const int chunk = fgp_chunk > 0 ? fgp_chunk : kBatchFgpChunk;
+    if (chunk != h->fgp_chunk || fgp_group != h->fgp_group) {
+        BSG_CUDA(cudaSetDevice(h->device));
+        BSG_CUDA(cudaStreamSynchronize(h->stream));
+        h->fgp_chunk = chunk;
+        h->fgp_group = fgp_group;
+        bdrop_graphs(h);
+    }
+    return BSGDTV_OK;
+}
+
 int bsgdtv_batch_get_slice_x(bsgdtv_batch_t h, int b, float *x, int out_on_device) {
     if (!h || !x) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
     if (b < 0 || b >= h->B) return fail(BSGDTV_ERR_INVALID_ARG, "slice index out of range");

@@ -312,7 +312,15 @@ def test_batch_autotune_keeps_results(B):
         assert chunk in (3, 4, 5, 6, 8) and 1 <= group <= 6 and ms > 0
         bt.run(2, 30)
         X_tuned = bt.x().copy()
+        bt.set_tuning(3, 2)                  # a tuning applied by hand: same bits
+        bt.set_data(Y, lam, mu)
+        bt.run(4, 30)
+        X_set = bt.x().copy()
+        with pytest.raises(B.BsgdtvError) as e:
+            bt.set_tuning(9, 0)
+        assert e.value.code == -1
     assert np.array_equal(X_plain, X_tuned)
+    assert np.array_equal(X_plain, X_set)
 
 
 def test_batches_share_one_operator(B):
