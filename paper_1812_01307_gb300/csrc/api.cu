@@ -87,7 +87,6 @@ struct bsgdtv_ctx {
     std::vector<cudaEvent_t> tevents;
     int graph_fgp_iters = -1;
     bool graph_prox = false;
-    cudaEvent_t read_done = nullptr;   // set_data's copy has read the caller's host y
     double graph_mu = 0.0, graph_lambda = 0.0;
     int64_t graph_kernels = 0;
 };
@@ -489,7 +488,6 @@ void bsgdtv_destroy(bsgdtv_t h) {
     for (cudaEvent_t ev : h->tevents) cudaEventDestroy(ev);
     for (cudaEvent_t ev : h->tmark)
         if (ev) cudaEventDestroy(ev);
-    if (h->read_done) cudaEventDestroy(h->read_done);
     for (void *p : h->allocs) cudaFree(p);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
@@ -567,38 +565,21 @@ int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, 
     BSG_CHECK(set_device(h));
     cudaStream_t s = h->stream;
     const int64_t R = h->dl.rows, c = h->dl.cols;
-    float y_absmax = 0.f;
     h->has_data = false;   // y is overwritten from here on: a failure leaves no data
-    if (!y_on_device) {
-        // the host scan (NaN/Inf, max |y|) runs while the copy reads y; the
-        // call returns only after the copy has read y, pageable or pinned
-        if (!h->read_done) BSG_CUDA(cudaEventCreateWithFlags(&h->read_done, cudaEventDisableTiming));
-        BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float), cudaMemcpyHostToDevice, s));
-        BSG_CUDA(cudaEventRecord(h->read_done, s));
-        const bool finite = all_finite_absmax(y, R, &y_absmax);
-        BSG_CUDA(cudaEventSynchronize(h->read_done));
-        if (!finite) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
-    } else {
-        BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float), cudaMemcpyDeviceToDevice, s));
-        int flag = 0;
-        BSG_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
-        BSG_CUDA(launch_check_finite(h->y, R, h->flag, s));
-        BSG_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-        BSG_CUDA(cudaStreamSynchronize(s));
-        if (flag) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
-    }
-    // x^0 = 0, r^{-1} = y - A x^0 = y and max |r|; the last block products are
-    // A x^0 = 0 (cleared when the stochastic iteration first needs them)
+    // copy y, then in one launch r^{-1} = y - A x^0 = y, x^0 = 0 and max |y|
+    // (which is Inf or NaN exactly when y is not finite: the check); the
+    // read-back of max |y| returns after the copy has read y, so a host y may
+    // be reused at once, pageable or pinned.  The last block products are
+    // A x^0 = 0 (cleared when the stochastic iteration first needs them).
+    BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float),
+                             y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    BSG_CUDA(launch_init_state(h->y, h->r[0], h->x, R, c, h->rmax, s));
+    float ymax = 0.f;
+    BSG_CUDA(cudaMemcpyAsync(&ymax, h->rmax, sizeof(float), cudaMemcpyDeviceToHost, s));
+    BSG_CUDA(cudaStreamSynchronize(s));
+    if (!std::isfinite(ymax)) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
     h->cur = 0;
     h->z_stale = true;
-    if (!y_on_device) {
-        BSG_CUDA(launch_init_state(h->y, h->r[0], h->x, R, c, h->rmax, y_absmax, s));
-    } else {
-        BSG_CUDA(cudaMemsetAsync(h->x, 0, c * sizeof(float), s));
-        BSG_CUDA(cudaMemcpyAsync(h->r[0], h->y, R * sizeof(float), cudaMemcpyDeviceToDevice, s));
-        BSG_CUDA(cudaMemsetAsync(h->rmax, 0, sizeof(float), s));
-        BSG_CUDA(launch_absmax(h->r[0], R, h->rmax, s));
-    }
     if (mu <= 0.0) {
         if (h->u_max <= 0.0) {
             double u;

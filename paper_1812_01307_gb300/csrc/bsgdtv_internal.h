@@ -31,21 +31,6 @@ int fail(int code, const std::string &msg);
 
 void add_launches(int64_t n);
 
-// all_finite_absmax: the same test plus max |y| in one pass (the bits of a
-// non-negative float order like the float).
-inline bool all_finite_absmax(const float *y, int64_t n, float *amax) {
-    uint32_t bad = 0, m = 0;
-    for (int64_t i = 0; i < n; ++i) {
-        uint32_t b;
-        std::memcpy(&b, y + i, sizeof(b));
-        bad |= (uint32_t)((b & 0x7f800000u) == 0x7f800000u);
-        const uint32_t a = b & 0x7fffffffu;
-        m = a > m ? a : m;
-    }
-    std::memcpy(amax, &m, sizeof(m));
-    return bad == 0;
-}
-
 // True if no entry of y[0..n) is NaN or +-Inf (exponent bits all ones);
 // branch-free over the whole array so the compiler can vectorise it.
 inline bool all_finite(const float *y, int64_t n) {
@@ -142,9 +127,11 @@ cudaError_t launch_fill64(double *out, double v, int64_t n, cudaStream_t s);
 cudaError_t launch_scale64(const double *in, const double *nrm2, double *out, int64_t n,
                            cudaStream_t s);
 cudaError_t launch_check_finite(const float *v, int64_t n, int *flag, cudaStream_t s);
-// Start of an iteration in one launch: r0 = y [rows], x = 0 [cols], *rmax = value.
+// Start of an iteration: r0 = y [rows], x = 0 [cols] and *rmax = max |y|,
+// which is Inf or NaN exactly when y holds a NaN or +-Inf (a memset and one
+// launch).
 cudaError_t launch_init_state(const float *y, float *r0, float *x, int64_t rows, int64_t cols,
-                              float *rmax, float rmax_value, cudaStream_t s);
+                              float *rmax, cudaStream_t s);
 constexpr int kDotPartials = 1024;
 
 // fgp.cu: K FGP iterations on an h x w image.  `mom` holds the K momentum

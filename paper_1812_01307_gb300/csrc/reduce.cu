@@ -354,22 +354,39 @@ cudaError_t launch_block_sums(const DevLayout &d, const float *z_part, const int
     return cudaGetLastError();
 }
 
+// r^{-1} = y, x^0 = 0 and *rmax = the largest |y| bit pattern with the sign
+// cleared (rmax zeroed beforehand).  Patterns order like the magnitudes, and
+// NaN / +-Inf are exactly those >= 0x7f800000, so *rmax is max |y| when y is
+// finite and reads as Inf or NaN when it is not.
 __global__ void init_state_kernel(const float *__restrict__ y, float *__restrict__ r0,
-                                  float *__restrict__ x, int64_t rows, int64_t cols, float *rmax,
-                                  float rmax_value) {
+                                  float *__restrict__ x, int64_t rows, int64_t cols, float *rmax) {
     const int64_t n = rows > cols ? rows : cols;
+    int m = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < rows) r0[i] = y[i];
+        if (i < rows) {
+            const float v = y[i];
+            r0[i] = v;
+            m = max(m, __float_as_int(v) & 0x7fffffff);
+        }
         if (i < cols) x[i] = 0.f;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *rmax = rmax_value;
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ int wmax[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = (threadIdx.x < (int)(blockDim.x >> 5)) ? wmax[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) atomicMax(reinterpret_cast<int *>(rmax), m);
+    }
 }
 
 cudaError_t launch_init_state(const float *y, float *r0, float *x, int64_t rows, int64_t cols,
-                              float *rmax, float rmax_value, cudaStream_t s) {
-    init_state_kernel<<<grid_for(std::max(rows, cols)), kThreads, 0, s>>>(y, r0, x, rows, cols, rmax,
-                                                                          rmax_value);
+                              float *rmax, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(rmax, 0, sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    init_state_kernel<<<grid_for(std::max(rows, cols)), kThreads, 0, s>>>(y, r0, x, rows, cols, rmax);
     add_launches(1);
     return cudaGetLastError();
 }
