@@ -367,7 +367,6 @@ struct bsgdtv_batch_ctx {
     cudaGraphNode_t tnode[2][3] = {};
     cudaEvent_t tmark[3] = {nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> tevents;
-    cudaEvent_t read_done = nullptr;   // a caller's host y has been read (see host_upload)
     int graph_fgp_iters = -1;
     int64_t graph_kernels = 0;
 };
@@ -971,7 +970,6 @@ void bsgdtv_batch_destroy(bsgdtv_batch_t h) {
     for (cudaEvent_t ev : h->tevents) cudaEventDestroy(ev);
     for (cudaEvent_t ev : h->tmark)
         if (ev) cudaEventDestroy(ev);
-    if (h->read_done) cudaEventDestroy(h->read_done);
     for (void *p : h->allocs) cudaFree(p);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     bsgdtv_operator_t op = h->op;
@@ -981,17 +979,21 @@ void bsgdtv_batch_destroy(bsgdtv_batch_t h) {
 
 namespace {
 
-// Copies n floats of a caller's host array y to dst on the handle's stream,
-// checks y for NaN/Inf on the host while the copy runs, and returns once the
-// copy has read y (stream order: after the handle's earlier work), so the
-// caller may reuse y whether it is pageable or pinned.  *finite: the check.
-int host_upload(bsgdtv_batch_t h, float *dst, const float *y, int64_t n, bool *finite) {
+// Copies n floats of y (host or device) to dst on the handle's stream and
+// checks them for NaN/Inf on the device; returns after the check has been
+// read back, so the copy has read y (a host y may be reused at once, pageable
+// or pinned).  *finite: the check.
+int upload_checked(bsgdtv_batch_t h, float *dst, const float *y, int y_on_device, int64_t n,
+                   bool *finite) {
     cudaStream_t s = h->stream;
-    if (!h->read_done) BSG_CUDA(cudaEventCreateWithFlags(&h->read_done, cudaEventDisableTiming));
-    BSG_CUDA(cudaMemcpyAsync(dst, y, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, s));
-    BSG_CUDA(cudaEventRecord(h->read_done, s));
-    *finite = all_finite(y, n);
-    BSG_CUDA(cudaEventSynchronize(h->read_done));
+    int hflag = 0;
+    BSG_CUDA(cudaMemcpyAsync(dst, y, (size_t)n * sizeof(float),
+                             y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    BSG_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    BSG_CUDA(launch_check_finite(dst, n, h->flag, s));
+    BSG_CUDA(cudaMemcpyAsync(&hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BSG_CUDA(cudaStreamSynchronize(s));
+    *finite = hflag == 0;
     return BSGDTV_OK;
 }
 
@@ -1011,19 +1013,9 @@ int bsgdtv_batch_set_data(bsgdtv_batch_t h, const float *y, int y_on_device,
     // floats) and interleaved into Y; the first epoch rewrites R[1] in full.
     // From here on the old state is gone: a failure leaves the handle without data.
     h->has_data = false;
-    if (!y_on_device) {
-        bool finite = false;
-        BSG_CHECK(host_upload(h, h->R[1], y, n_in, &finite));
-        if (!finite) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
-    } else {
-        BSG_CUDA(cudaMemcpyAsync(h->R[1], y, (size_t)n_in * sizeof(float), cudaMemcpyDeviceToDevice, s));
-        int hflag = 0;
-        BSG_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
-        BSG_CUDA(launch_check_finite(h->R[1], n_in, h->flag, s));
-        BSG_CUDA(cudaMemcpyAsync(&hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-        BSG_CUDA(cudaStreamSynchronize(s));
-        if (hflag) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
-    }
+    bool finite = false;
+    BSG_CHECK(upload_checked(h, h->R[1], y, y_on_device, n_in, &finite));
+    if (!finite) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
     BSG_CUDA(launch_transpose(h->R[1], h->Y, rows, h->B, h->Bp, false, s));
     // x^0 = 0 and r^{-1} = y - A x^0 = y for every slice
     BSG_CUDA(cudaMemsetAsync(h->X, 0, (size_t)h->cols * h->Bp * sizeof(float), s));
@@ -1114,18 +1106,10 @@ int bsgdtv_batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_dev
     BSG_CUDA(cudaSetDevice(h->device));
     cudaStream_t s = h->stream;
     const int64_t rows = h->rows;
-    if (y && !y_on_device) {   // staged: a bad y leaves the slot as it was
+    if (y) {   // staged: a bad y leaves the slot as it was
         bool finite = false;
-        BSG_CHECK(host_upload(h, h->ystage, y, rows, &finite));
+        BSG_CHECK(upload_checked(h, h->ystage, y, y_on_device, rows, &finite));
         if (!finite) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
-    } else if (y) {
-        BSG_CUDA(cudaMemcpyAsync(h->ystage, y, (size_t)rows * sizeof(float), cudaMemcpyDeviceToDevice, s));
-        int hflag = 0;
-        BSG_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
-        BSG_CUDA(launch_check_finite(h->ystage, rows, h->flag, s));
-        BSG_CUDA(cudaMemcpyAsync(&hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-        BSG_CUDA(cudaStreamSynchronize(s));
-        if (hflag) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
     }
     const double lam = y ? lambda : 0.0;
     const int64_t n = std::max(rows, h->cols);
