@@ -343,6 +343,7 @@ int bsgdtv_create_csr_ex(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, i
                          const int64_t *row_ptr, const int32_t *col_idx, const double *vals, int M,
                          int N, int64_t row_unit, int64_t col_unit, const int64_t *row_bounds,
                          const int64_t *col_bounds, int format, void *stream) {
+    BSG_TRACE();
     if (!out) return fail(BSGDTV_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     std::vector<int64_t> rb, cb;
@@ -458,6 +459,7 @@ int bsgdtv_create_csr_ex(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, i
 
 int bsgdtv_create_parallel_beam(bsgdtv_t *out, int n, int n_angles, int n_bins, int M, int N,
                                 int format, void *stream) {
+    BSG_TRACE();
     if (!out) return fail(BSGDTV_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     if (n < 1 || n > 46340 || n_angles < 1 || n_bins < 1 || (int64_t)n_angles * n_bins > INT32_MAX)
@@ -513,6 +515,7 @@ int bsgdtv_get_info(bsgdtv_t h, int64_t *nnz, int64_t *segments, int64_t *work_i
 }
 
 int bsgdtv_estimate_umax(bsgdtv_t h, int max_iters, double rel_tol, double *u_max, int *iters) {
+    BSG_TRACE();
     if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
     if (max_iters < 1 || !(rel_tol >= 0.0)) return fail(BSGDTV_ERR_INVALID_ARG, "bad max_iters / rel_tol");
     BSG_CHECK(set_device(h));
@@ -559,6 +562,7 @@ int bsgdtv_estimate_umax(bsgdtv_t h, int max_iters, double rel_tol, double *u_ma
 }
 
 int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, double mu) {
+    BSG_TRACE();
     if (!h || !y) return fail(BSGDTV_ERR_INVALID_ARG, "null handle or y");
     if (!(lambda >= 0.0) || !std::isfinite(lambda) || !std::isfinite(mu))
         return fail(BSGDTV_ERR_INVALID_ARG, "lambda must be finite and >= 0, mu finite");
@@ -605,6 +609,7 @@ int bsgdtv_get_params(bsgdtv_t h, double *mu, double *lambda, double *u_max) {
 }
 
 int bsgdtv_run(bsgdtv_t h, int epochs, int fgp_iters) {
+    BSG_TRACE();
     if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
     if (!h->has_data) return fail(BSGDTV_ERR_STATE, "bsgdtv_run before bsgdtv_set_data");
     if (epochs < 0 || fgp_iters < 0) return fail(BSGDTV_ERR_INVALID_ARG, "negative epochs / fgp_iters");
@@ -625,6 +630,7 @@ int bsgdtv_run(bsgdtv_t h, int epochs, int fgp_iters) {
 
 int bsgdtv_run_timed(bsgdtv_t h, int epochs, int fgp_iters, double *products_ms,
                      double *epoch_ms) {
+    BSG_TRACE();
     if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
     if (!h->has_data) return fail(BSGDTV_ERR_STATE, "bsgdtv_run_timed before bsgdtv_set_data");
     if (epochs < 0 || fgp_iters < 0) return fail(BSGDTV_ERR_INVALID_ARG, "negative epochs / fgp_iters");
@@ -665,6 +671,7 @@ int bsgdtv_run_timed(bsgdtv_t h, int epochs, int fgp_iters, double *products_ms,
 
 int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_sel,
                        const uint8_t *col_sel) {
+    BSG_TRACE();
     if (!h || !row_sel || !col_sel) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
     if (!h->has_data) return fail(BSGDTV_ERR_STATE, "bsgdtv_run_subsets before bsgdtv_set_data");
     if (iters < 0 || fgp_iters < 0) return fail(BSGDTV_ERR_INVALID_ARG, "negative iters / fgp_iters");
@@ -742,6 +749,7 @@ int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_
 }
 
 int bsgdtv_get_x(bsgdtv_t h, float *out, int out_on_device) {
+    BSG_TRACE();
     if (!h || !out) return fail(BSGDTV_ERR_INVALID_ARG, "null handle or out");
     BSG_CHECK(set_device(h));
     const size_t bytes = h->dl.cols * sizeof(float);
@@ -753,6 +761,7 @@ int bsgdtv_get_x(bsgdtv_t h, float *out, int out_on_device) {
 }
 
 int bsgdtv_get_state(bsgdtv_t h, float *x, float *r, int64_t *epoch, int on_device) {
+    BSG_TRACE();
     if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
     if (!h->has_data) return fail(BSGDTV_ERR_STATE, "no data set");
     BSG_CHECK(set_device(h));
@@ -765,6 +774,7 @@ int bsgdtv_get_state(bsgdtv_t h, float *x, float *r, int64_t *epoch, int on_devi
 }
 
 int bsgdtv_set_state(bsgdtv_t h, const float *x, const float *r, int64_t epoch, int on_device) {
+    BSG_TRACE();
     if (!h || !x || !r) return fail(BSGDTV_ERR_INVALID_ARG, "null handle, x or r");
     if (!h->has_data) return fail(BSGDTV_ERR_STATE, "set_state before set_data");
     if (epoch < 0) return fail(BSGDTV_ERR_INVALID_ARG, "negative epoch");
@@ -781,6 +791,7 @@ int bsgdtv_set_state(bsgdtv_t h, const float *x, const float *r, int64_t epoch, 
 
 int bsgdtv_run_until(bsgdtv_t h, int max_epochs, int fgp_iters, int check_every, double rel_tol,
                      int *epochs_run, double *objective) {
+    BSG_TRACE();
     if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
     if (max_epochs < 0 || fgp_iters < 0 || check_every < 1 || !(rel_tol >= 0.0) ||
         !std::isfinite(rel_tol))
@@ -811,6 +822,7 @@ int bsgdtv_run_until(bsgdtv_t h, int max_epochs, int fgp_iters, int check_every,
 }
 
 int bsgdtv_objective(bsgdtv_t h, double *data_term, double *tv) {
+    BSG_TRACE();
     if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
     if (!h->has_data) return fail(BSGDTV_ERR_STATE, "no data set");
     BSG_CHECK(set_device(h));
@@ -835,6 +847,7 @@ int bsgdtv_objective(bsgdtv_t h, double *data_term, double *tv) {
 
 int bsgdtv_block_products(bsgdtv_t h, const float *x, const float *r, float *z_blocks,
                           float *g_blocks) {
+    BSG_TRACE();
     if (!h || !x || !r || !z_blocks || !g_blocks)
         return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
     BSG_CHECK(set_device(h));
@@ -851,6 +864,7 @@ int bsgdtv_block_products(bsgdtv_t h, const float *x, const float *r, float *z_b
 
 int bsgdtv_tv_prox(const float *b, float *x, int img_h, int img_w, double tau, int iters,
                    void *stream) {
+    BSG_TRACE();
     if (!b || !x || img_h < 1 || img_w < 1 || iters < 0 || !std::isfinite(tau))
         return fail(BSGDTV_ERR_INVALID_ARG, "bad argument");
     if (b == x) return fail(BSGDTV_ERR_INVALID_ARG, "b and x may not alias");

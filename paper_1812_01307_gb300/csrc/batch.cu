@@ -719,6 +719,7 @@ extern "C" {
 int bsgdtv_operator_create_csr(bsgdtv_operator_t *out, int64_t rows, int64_t cols, int img_h,
                                int img_w, const int64_t *row_ptr, const int32_t *col_idx,
                                const double *vals, int format, void *stream) {
+    BSG_TRACE();
     if (!out) return fail(BSGDTV_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     if (format != BSGDTV_FMT_F32_I32 && format != BSGDTV_FMT_F16_I16 && format != BSGDTV_FMT_BF16_I16)
@@ -803,6 +804,7 @@ void bsgdtv_operator_destroy(bsgdtv_operator_t op) {
 
 int bsgdtv_batch_create_from_operator(bsgdtv_batch_t *out, bsgdtv_operator_t op, int slices,
                                       void *stream) {
+    BSG_TRACE();
     if (!out || !op) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
     if (slices < 1 || slices > 4096) return fail(BSGDTV_ERR_INVALID_ARG, "slices must be in [1, 4096]");
@@ -846,6 +848,7 @@ int bsgdtv_batch_create_from_operator(bsgdtv_batch_t *out, bsgdtv_operator_t op,
 int bsgdtv_batch_create_csr_ex(bsgdtv_batch_t *out, int64_t rows, int64_t cols, int img_h,
                                int img_w, const int64_t *row_ptr, const int32_t *col_idx,
                                const double *vals, int slices, int format, void *stream) {
+    BSG_TRACE();
     if (!out) return fail(BSGDTV_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     if (slices < 1 || slices > 4096) return fail(BSGDTV_ERR_INVALID_ARG, "slices must be in [1, 4096]");
@@ -870,6 +873,7 @@ int64_t bsgdtv_batch_device_bytes(int64_t rows, int64_t cols, int64_t nnz, int s
 
 int bsgdtv_batch_create_parallel_beam(bsgdtv_batch_t *out, int n, int n_angles, int n_bins,
                                       int slices, void *stream) {
+    BSG_TRACE();
     if (!out) return fail(BSGDTV_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     if (slices < 1 || slices > 4096) return fail(BSGDTV_ERR_INVALID_ARG, "slices must be in [1, 4096]");
@@ -1001,6 +1005,7 @@ int upload_checked(bsgdtv_batch_t h, float *dst, const float *y, int y_on_device
 
 int bsgdtv_batch_set_data(bsgdtv_batch_t h, const float *y, int y_on_device,
                           const double *lambdas, double mu) {
+    BSG_TRACE();
     if (!h || !y || !lambdas) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
     if (!(mu > 0.0) || !std::isfinite(mu)) return fail(BSGDTV_ERR_INVALID_ARG, "mu must be finite and > 0");
     for (int b = 0; b < h->B; ++b)
@@ -1038,6 +1043,7 @@ int bsgdtv_batch_set_data(bsgdtv_batch_t h, const float *y, int y_on_device,
 
 int bsgdtv_batch_run_timed(bsgdtv_batch_t h, int epochs, int fgp_iters, double *products_ms,
                            double *epoch_ms) {
+    BSG_TRACE();
     if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
     if (!h->has_data) return fail(BSGDTV_ERR_STATE, "run before set_data");
     if (epochs < 0 || fgp_iters < 0) return fail(BSGDTV_ERR_INVALID_ARG, "negative epochs / fgp_iters");
@@ -1082,10 +1088,12 @@ int bsgdtv_batch_run_timed(bsgdtv_batch_t h, int epochs, int fgp_iters, double *
 }
 
 int bsgdtv_batch_run(bsgdtv_batch_t h, int epochs, int fgp_iters) {
+    BSG_TRACE();
     return bsgdtv_batch_run_timed(h, epochs, fgp_iters, nullptr, nullptr);
 }
 
 int bsgdtv_batch_get_x(bsgdtv_batch_t h, float *x, int out_on_device) {
+    BSG_TRACE();
     if (!h || !x) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
     BSG_CUDA(cudaSetDevice(h->device));
     const int64_t c = h->cols;
@@ -1098,6 +1106,7 @@ int bsgdtv_batch_get_x(bsgdtv_batch_t h, float *x, int out_on_device) {
 }
 
 int bsgdtv_batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_device, double lambda) {
+    BSG_TRACE();
     if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
     if (!h->has_data) return fail(BSGDTV_ERR_STATE, "set_slice before set_data");
     if (b < 0 || b >= h->B) return fail(BSGDTV_ERR_INVALID_ARG, "slice index out of range");
@@ -1127,6 +1136,7 @@ int bsgdtv_batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_dev
 
 int bsgdtv_batch_estimate_umax(bsgdtv_batch_t h, int max_iters, double rel_tol, double *u_max,
                                int *iters) {
+    BSG_TRACE();
     if (!h || max_iters < 1 || !(rel_tol >= 0.0)) return fail(BSGDTV_ERR_INVALID_ARG, "bad argument");
     BSG_CUDA(cudaSetDevice(h->device));
     cudaStream_t s = h->stream;
@@ -1193,6 +1203,7 @@ int bsgdtv_batch_estimate_umax(bsgdtv_batch_t h, int max_iters, double rel_tol, 
 }
 
 int bsgdtv_batch_project(bsgdtv_batch_t h, const float *x, float *y) {
+    BSG_TRACE();
     if (!h || !x || !y) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
     BSG_CUDA(cudaSetDevice(h->device));
     cudaStream_t s = h->stream;
@@ -1220,6 +1231,7 @@ int bsgdtv_batch_project(bsgdtv_batch_t h, const float *x, float *y) {
 
 int bsgdtv_batch_autotune(bsgdtv_batch_t h, int fgp_iters, int epochs_per_trial, int *fgp_chunk,
                           int *fgp_group, double *epoch_ms) {
+    BSG_TRACE();
     if (!h || fgp_iters < 0 || epochs_per_trial < 1)
         return fail(BSGDTV_ERR_INVALID_ARG, "need fgp_iters >= 0 and epochs_per_trial >= 1");
     if (!h->has_data) return fail(BSGDTV_ERR_STATE, "autotune before set_data");
@@ -1296,6 +1308,7 @@ int bsgdtv_batch_set_tuning(bsgdtv_batch_t h, int fgp_chunk, int fgp_group) {
 }
 
 int bsgdtv_batch_get_slice_x(bsgdtv_batch_t h, int b, float *x, int out_on_device) {
+    BSG_TRACE();
     if (!h || !x) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
     if (b < 0 || b >= h->B) return fail(BSGDTV_ERR_INVALID_ARG, "slice index out of range");
     BSG_CUDA(cudaSetDevice(h->device));

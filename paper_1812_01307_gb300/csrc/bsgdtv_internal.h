@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cstring>
@@ -30,6 +31,16 @@ int fail(int code, const std::string &msg);
     } while (0)
 
 void add_launches(int64_t n);
+
+// A named NVTX range over a library call, visible to CUDA tools that record
+// NVTX (ncu --nvtx, Nsight Systems); a few nanoseconds when none is attached.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+#define BSG_TRACE() ::bsgdtv::TraceRange bsg_trace_range_(__func__)
 
 // True if no entry of y[0..n) is NaN or +-Inf (exponent bits all ones);
 // branch-free over the whole array so the compiler can vectorise it.
