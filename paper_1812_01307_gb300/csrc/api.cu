@@ -691,9 +691,34 @@ int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_
         BSG_CHECK(upload(h, &h->rb_dev, L.row_bounds));
         BSG_CHECK(upload(h, &h->cb_dev, L.col_bounds));
     }
-    // per iteration: the work items of the drawn pairs (launch order kept), then the masks
+    // per iteration: the work items of the drawn pairs (launch order kept), then
+    // the masks.  A draw leaves fewer items than the persistent CTAs when the
+    // fractions are small, so with FP32 weights and 32-bit indices each item is
+    // split into `shares` ranges of its slabs (the count that minimises
+    // ceil(items * shares / CTAs) / shares, i.e. the item-times of the pass),
+    // which add their g tiles into a zeroed g_part.
+    const bool split = h->dl.fmt == BSGDTV_FMT_F32_I32;
+    const int ctas = 2 * std::max(h->dl.n_sms, 1);
     const int n_items = (int)L.items.size();
-    const size_t item_bytes = (size_t)n_items * sizeof(WorkItem);
+    std::vector<int> drawn(iters, 0), shares(iters, 1);
+    int max_list = 1;
+    for (int k = 0; k < iters; ++k) {
+        const uint8_t *si = row_sel + (size_t)k * M, *sj = col_sel + (size_t)k * N;
+        for (const WorkItem &it : L.items)
+            drawn[k] += si[L.group_block[it.group]] && sj[L.tiles[it.tile].band];
+        if (split) {
+            double best = 1e300;
+            for (int sh = 1; sh <= 8; ++sh) {
+                const double t = (double)((drawn[k] * sh + ctas - 1) / ctas) / sh;
+                if (t < best - 1e-12) {
+                    best = t;
+                    shares[k] = sh;
+                }
+            }
+        }
+        max_list = std::max(max_list, drawn[k] * shares[k]);
+    }
+    const size_t item_bytes = (size_t)std::max(max_list, n_items) * sizeof(WorkItem);
     const size_t stride = (item_bytes + (size_t)M + N + 255) / 256 * 256;
     std::vector<unsigned char> host(stride * iters, 0);
     std::vector<int> count(iters, 0);
@@ -701,8 +726,21 @@ int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_
         unsigned char *base = host.data() + stride * k;
         WorkItem *list = reinterpret_cast<WorkItem *>(base);
         const uint8_t *si = row_sel + (size_t)k * M, *sj = col_sel + (size_t)k * N;
-        for (const WorkItem &it : L.items)
-            if (si[L.group_block[it.group]] && sj[L.tiles[it.tile].band]) list[count[k]++] = it;
+        for (const WorkItem &it : L.items) {
+            if (!si[L.group_block[it.group]] || !sj[L.tiles[it.tile].band]) continue;
+            if (!split) {
+                list[count[k]++] = it;
+                continue;
+            }
+            const int ns = it.slab_end - it.slab_begin;   // an empty item adds nothing
+            const int parts = std::min(shares[k], ns);
+            for (int q = 0; q < parts; ++q) {
+                WorkItem w = it;
+                w.slab_begin = it.slab_begin + (int)((int64_t)ns * q / parts);
+                w.slab_end = it.slab_begin + (int)((int64_t)ns * (q + 1) / parts);
+                list[count[k]++] = w;
+            }
+        }
         for (int i = 0; i < M; ++i) base[item_bytes + i] = si[i] ? 1 : 0;
         for (int j = 0; j < N; ++j) base[item_bytes + M + j] = sj[j] ? 1 : 0;
     }
@@ -727,8 +765,14 @@ int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_
         DevLayout ds = h->dl;
         ds.items = reinterpret_cast<const WorkItem *>(base);
         ds.n_items = count[k];
-        BSG_CUDA(launch_products32(ds, h->x, h->r[par], h->rmax + par, h->rmax + (1 - par), h->z_part,
-                                   reinterpret_cast<int32_t *>(h->g_part), s, false));
+        if (split) {
+            BSG_CUDA(cudaMemsetAsync(h->g_part, 0, (size_t)h->dl.n_groups * h->dl.cols * sizeof(int32_t), s));
+            BSG_CUDA(launch_products32_add(ds, h->x, h->r[par], h->rmax + par, h->rmax + (1 - par),
+                                           h->z_part, reinterpret_cast<int32_t *>(h->g_part), s));
+        } else {
+            BSG_CUDA(launch_products32(ds, h->x, h->r[par], h->rmax + par, h->rmax + (1 - par),
+                                       h->z_part, reinterpret_cast<int32_t *>(h->g_part), s, false));
+        }
         float *xdst = prox ? h->xhat : h->x;
         BSG_CUDA(launch_reduce_subset32(h->dl, h->z_part, reinterpret_cast<const int32_t *>(h->g_part),
                                         h->rmax + par, h->y, h->r[par], h->r[1 - par],

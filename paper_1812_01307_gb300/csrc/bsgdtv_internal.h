@@ -101,6 +101,12 @@ cudaError_t launch_products64(const DevLayout &d, const double *x, const double 
 cudaError_t launch_products32(const DevLayout &d, const float *x, const float *r,
                               const float *rmax_in, float *rmax_clear, float *z_part,
                               int32_t *g_part, cudaStream_t s, bool pdl = false);
+// The same for FMT_F32_I32 work items that may cover part of a (group, tile)
+// pair's slabs: each adds its g tile into g_part (zeroed beforehand) with
+// integer atomics, so the sums stay exact and independent of order.
+cudaError_t launch_products32_add(const DevLayout &d, const float *x, const float *r,
+                                  const float *rmax_in, float *rmax_clear, float *z_part,
+                                  int32_t *g_part, cudaStream_t s);
 
 
 // reduce.cu

@@ -32,10 +32,12 @@ namespace {
 using namespace prod;
 
 // FP32 weights with 32-bit indices.  T: type of x, r, z (float or double); G:
-// shared g tile (int fixed point or double).  The 16-bit formats have their
-// own kernel in products_fmt.cu: sharing this translation unit with it made
-// this kernel about 10 % slower on GB300.
-template <typename T, typename G>
+// shared g tile (int fixed point or double); kAdd: items may be shares of a
+// (group, tile) pair and add their g tile into g_part (int32 atomics) instead
+// of storing it.  The 16-bit formats have their own kernel in products_fmt.cu:
+// sharing this translation unit with it made this kernel about 10 % slower on
+// GB300.
+template <typename T, typename G, bool kAdd>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     products_f32_kernel(const DevLayout d, const T *__restrict__ x, const T *__restrict__ r,
                     const float *__restrict__ rmax_in, float *__restrict__ rmax_clear,
@@ -124,7 +126,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         const int npx = tl.h * tl.w;
         for (int e = threadIdx.x; e < npx; e += kThreads) {
             const int lr = e / tl.w, lc = e - lr * tl.w;
-            gp[(int64_t)(tl.r0 + lr) * d.img_w + tl.c0 + lc] = gs[lr * kTileStride + lc];
+            G *dst = gp + (int64_t)(tl.r0 + lr) * d.img_w + tl.c0 + lc;
+            if constexpr (kAdd) atomicAdd(dst, gs[lr * kTileStride + lc]);
+            else *dst = gs[lr * kTileStride + lc];
         }
         __syncthreads();
     }
@@ -147,7 +151,7 @@ static cudaError_t launch_p32_plain(const DevLayout &d, const float *x, const fl
                                     int32_t *g_part, cudaStream_t s, bool pdl) {
     const size_t smem = kTileWords * (sizeof(float) + sizeof(int));
     const int grid = std::min(d.n_items, kCtasPerSm * std::max(d.n_sms, 1));
-    return launch_kernel(products_f32_kernel<float, int>, dim3(grid), dim3(kThreads), smem, s, pdl,
+    return launch_kernel(products_f32_kernel<float, int, false>, dim3(grid), dim3(kThreads), smem, s, pdl,
                          d, x, r, rmax_in, rmax_clear, z_part, g_part, d.item_ctr);
 }
 
@@ -155,7 +159,7 @@ static cudaError_t launch_p64_plain(const DevLayout &d, const double *x, const d
                                     double *z_part, double *g_part, cudaStream_t s) {
     const size_t smem = 2u * kTileWords * sizeof(double);
     const int grid = std::min(d.n_items, kCtasPerSm * std::max(d.n_sms, 1));
-    return launch_kernel(products_f32_kernel<double, double>, dim3(grid), dim3(kThreads), smem, s,
+    return launch_kernel(products_f32_kernel<double, double, false>, dim3(grid), dim3(kThreads), smem, s,
                          false, d, x, r, (const float *)nullptr, (float *)nullptr, z_part, g_part,
                          d.item_ctr);
 }
@@ -172,6 +176,20 @@ cudaError_t launch_products32(const DevLayout &d, const float *x, const float *r
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+cudaError_t launch_products32_add(const DevLayout &d, const float *x, const float *r,
+                                  const float *rmax_in, float *rmax_clear, float *z_part,
+                                  int32_t *g_part, cudaStream_t s) {
+    if (d.n_items == 0) return cudaSuccess;
+    if (d.fmt != BSGDTV_FMT_F32_I32) return cudaErrorInvalidValue;
+    const size_t smem = kTileWords * (sizeof(float) + sizeof(int));
+    const int grid = std::min(d.n_items, kCtasPerSm * std::max(d.n_sms, 1));
+    const cudaError_t e = launch_kernel(products_f32_kernel<float, int, true>, dim3(grid), dim3(kThreads),
+                                        smem, s, false, d, x, r, rmax_in, rmax_clear, z_part, g_part,
+                                        d.item_ctr);
+    add_launches(1);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 cudaError_t launch_products64(const DevLayout &d, const double *x, const double *r, double *z_part,
                               double *g_part, cudaStream_t s) {
     if (d.n_items == 0) return cudaSuccess;
@@ -183,11 +201,15 @@ cudaError_t launch_products64(const DevLayout &d, const double *x, const double 
 }
 
 cudaError_t prepare_products_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(products_f32_kernel<float, int>,
+    cudaError_t e = cudaFuncSetAttribute(products_f32_kernel<float, int, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kTileWords * (sizeof(float) + sizeof(int))));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(products_f32_kernel<double, double>,
+        e = cudaFuncSetAttribute(products_f32_kernel<float, int, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kTileWords * (sizeof(float) + sizeof(int))));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(products_f32_kernel<double, double, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(2u * kTileWords * sizeof(double)));
     if (e == cudaSuccess) e = prepare_products_fmt_kernels();
