@@ -759,29 +759,34 @@ int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_
     }
     BSG_CHECK(ensure_mom(h, std::max(fgp_iters, 1)));
     const bool prox = h->lambda > 0.0 && fgp_iters > 0;
+    // split items add into g_part: zero it once; each reduction then zeroes
+    // the values it consumes.  Consecutive kernels use programmatic
+    // dependent launch (each waits for its predecessor before reading).
+    if (split)
+        BSG_CUDA(cudaMemsetAsync(h->g_part, 0, (size_t)h->dl.n_groups * h->dl.cols * sizeof(int32_t), s));
     for (int k = 0; k < iters; ++k) {
         const int par = h->cur;
+        const bool pdl = k > 0;   // the first follows copies, not a kernel
         unsigned char *base = dev + stride * k;
         DevLayout ds = h->dl;
         ds.items = reinterpret_cast<const WorkItem *>(base);
         ds.n_items = count[k];
-        if (split) {
-            BSG_CUDA(cudaMemsetAsync(h->g_part, 0, (size_t)h->dl.n_groups * h->dl.cols * sizeof(int32_t), s));
+        int32_t *gp = reinterpret_cast<int32_t *>(h->g_part);
+        if (split)
             BSG_CUDA(launch_products32_add(ds, h->x, h->r[par], h->rmax + par, h->rmax + (1 - par),
-                                           h->z_part, reinterpret_cast<int32_t *>(h->g_part), s));
-        } else {
+                                           h->z_part, gp, s, pdl));
+        else
             BSG_CUDA(launch_products32(ds, h->x, h->r[par], h->rmax + par, h->rmax + (1 - par),
-                                       h->z_part, reinterpret_cast<int32_t *>(h->g_part), s, false));
-        }
+                                       h->z_part, gp, s, pdl));
         float *xdst = prox ? h->xhat : h->x;
-        BSG_CUDA(launch_reduce_subset32(h->dl, h->z_part, reinterpret_cast<const int32_t *>(h->g_part),
-                                        h->rmax + par, h->y, h->r[par], h->r[1 - par],
-                                        h->rmax + (1 - par), h->x, xdst, (float)h->mu, h->rb_dev,
-                                        h->cb_dev, base + item_bytes, base + item_bytes + M, s));
+        BSG_CUDA(launch_reduce_subset32(h->dl, h->z_part, gp, h->rmax + par, h->y, h->r[par],
+                                        h->r[1 - par], h->rmax + (1 - par), h->x, xdst, (float)h->mu,
+                                        h->rb_dev, h->cb_dev, base + item_bytes, base + item_bytes + M,
+                                        split, s, true));
         if (prox) {
             FgpScratch sc{h->fp, h->fq, h->fpp, h->fqp};
             BSG_CUDA(launch_fgp(h->xhat, h->x, h->dl.img_h, h->dl.img_w, (float)(h->mu * h->lambda),
-                                fgp_iters, h->mom, sc, s, false,
+                                fgp_iters, h->mom, sc, s, true,
                                 fgp_chunk_for(h->dl.img_h, h->dl.img_w, fgp_iters, h->dl.n_sms)));
         }
         h->cur ^= 1;

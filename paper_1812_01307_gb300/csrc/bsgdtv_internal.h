@@ -106,7 +106,7 @@ cudaError_t launch_products32(const DevLayout &d, const float *x, const float *r
 // integer atomics, so the sums stay exact and independent of order.
 cudaError_t launch_products32_add(const DevLayout &d, const float *x, const float *r,
                                   const float *rmax_in, float *rmax_clear, float *z_part,
-                                  int32_t *g_part, cudaStream_t s);
+                                  int32_t *g_part, cudaStream_t s, bool pdl = false);
 
 
 // reduce.cu
@@ -123,12 +123,14 @@ cudaError_t launch_reduce_update32(const DevLayout &d, const float *z_part, cons
                                    cudaStream_t s, bool pdl = false);
 // Stochastic variant: the reductions restricted to the drawn row blocks
 // (sel_i [M]) and column blocks (sel_j [N]); rb [M+1], cb [N+1] are the block
-// bounds; rows / pixels outside keep r_in / x.
-cudaError_t launch_reduce_subset32(const DevLayout &d, const float *z_part, const int32_t *g_part,
+// bounds; rows / pixels outside keep r_in / x.  clear_g: the g_part values
+// read are zeroed for a following launch_products32_add.
+cudaError_t launch_reduce_subset32(const DevLayout &d, const float *z_part, int32_t *g_part,
                                    const float *rmax_in, const float *y, const float *r_in,
                                    float *r_out, float *rmax_out, const float *x, float *x_out,
                                    float mu, const int64_t *rb, const int64_t *cb,
-                                   const uint8_t *sel_i, const uint8_t *sel_j, cudaStream_t s);
+                                   const uint8_t *sel_i, const uint8_t *sel_j, bool clear_g,
+                                   cudaStream_t s, bool pdl = false);
 cudaError_t launch_block_sums(const DevLayout &d, const float *z_part, const int32_t *g_part,
                               const float *rmax_in, float *z_blocks, float *g_blocks,
                               cudaStream_t s);

@@ -178,13 +178,13 @@ cudaError_t launch_products32(const DevLayout &d, const float *x, const float *r
 
 cudaError_t launch_products32_add(const DevLayout &d, const float *x, const float *r,
                                   const float *rmax_in, float *rmax_clear, float *z_part,
-                                  int32_t *g_part, cudaStream_t s) {
+                                  int32_t *g_part, cudaStream_t s, bool pdl) {
     if (d.n_items == 0) return cudaSuccess;
     if (d.fmt != BSGDTV_FMT_F32_I32) return cudaErrorInvalidValue;
     const size_t smem = kTileWords * (sizeof(float) + sizeof(int));
     const int grid = std::min(d.n_items, kCtasPerSm * std::max(d.n_sms, 1));
     const cudaError_t e = launch_kernel(products_f32_kernel<float, int, true>, dim3(grid), dim3(kThreads),
-                                        smem, s, false, d, x, r, rmax_in, rmax_clear, z_part, g_part,
+                                        smem, s, pdl, d, x, r, rmax_in, rmax_clear, z_part, g_part,
                                         d.item_ctr);
     add_launches(1);
     return e != cudaSuccess ? e : cudaGetLastError();

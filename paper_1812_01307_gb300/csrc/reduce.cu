@@ -114,15 +114,17 @@ __device__ __forceinline__ int block_of(const int64_t *__restrict__ bounds, int 
 // Rows of drawn row blocks: r = y - sum of all segment partials (partials of
 // undrawn pairs are the last ones computed); other rows keep r_in.  Pixels of
 // drawn column blocks: x' = x + mu * (sum over groups of drawn row blocks of
-// the fixed-point tiles); other pixels keep x.
+// the fixed-point tiles); other pixels keep x.  clear_g: each tile value read
+// is set back to 0, ready for the next pass that adds into g_part.
 __global__ void __launch_bounds__(kThreads)
     reduce_subset32_kernel(const DevLayout d, const float *__restrict__ z_part,
-                           const int32_t *__restrict__ g_part, const float *__restrict__ rmax_in,
+                           int32_t *__restrict__ g_part, const float *__restrict__ rmax_in,
                            const float *__restrict__ y, const float *__restrict__ r_in,
                            float *__restrict__ r_out, float *rmax_out, const float *x,
                            float *x_out, float mu, int nb_rows, const int64_t *__restrict__ rb,
                            const int64_t *__restrict__ cb, const uint8_t *__restrict__ sel_i,
-                           const uint8_t *__restrict__ sel_j) {
+                           const uint8_t *__restrict__ sel_j, bool clear_g) {
+    pdl_wait_and_release();
     if ((int)blockIdx.x < nb_rows) {
         const int64_t ray = (int64_t)blockIdx.x * kThreads + threadIdx.x;
         float rv = 0.f;
@@ -153,7 +155,10 @@ __global__ void __launch_bounds__(kThreads)
         }
         long long acc = 0;
         for (int g = 0; g < d.n_groups; ++g)
-            if (sel_i[d.group_block[g]]) acc += g_part[(int64_t)g * d.cols + p];
+            if (sel_i[d.group_block[g]]) {
+                acc += g_part[(int64_t)g * d.cols + p];
+                if (clear_g) g_part[(int64_t)g * d.cols + p] = 0;
+            }
         const double inv = 1.0 / (double)fixed_scale(*rmax_in, d.colsum_max);
         x_out[p] = x[p] + mu * (float)((double)acc * inv);
     }
@@ -316,18 +321,19 @@ cudaError_t launch_reduce_update64(const DevLayout &d, const double *z_part, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_subset32(const DevLayout &d, const float *z_part, const int32_t *g_part,
+cudaError_t launch_reduce_subset32(const DevLayout &d, const float *z_part, int32_t *g_part,
                                    const float *rmax_in, const float *y, const float *r_in,
                                    float *r_out, float *rmax_out, const float *x, float *x_out,
                                    float mu, const int64_t *rb, const int64_t *cb,
-                                   const uint8_t *sel_i, const uint8_t *sel_j, cudaStream_t s) {
+                                   const uint8_t *sel_i, const uint8_t *sel_j, bool clear_g,
+                                   cudaStream_t s, bool pdl) {
     const int nb_rows = (int)((d.rows + kThreads - 1) / kThreads);
     const int nb_cols = (int)((d.cols + kThreads - 1) / kThreads);
-    reduce_subset32_kernel<<<nb_rows + nb_cols, kThreads, 0, s>>>(
-        d, z_part, g_part, rmax_in, y, r_in, r_out, rmax_out, x, x_out, mu, nb_rows, rb, cb, sel_i,
-        sel_j);
+    const cudaError_t e = launch_kernel(reduce_subset32_kernel, dim3(nb_rows + nb_cols), dim3(kThreads), 0,
+                                        s, pdl, d, z_part, g_part, rmax_in, y, r_in, r_out, rmax_out, x,
+                                        x_out, mu, nb_rows, rb, cb, sel_i, sel_j, clear_g);
     add_launches(1);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_reduce_update32(const DevLayout &d, const float *z_part, const int32_t *g_part,
