@@ -714,6 +714,62 @@ int generate_parallel_beam_csr(int n, int n_angles, int n_bins, cudaStream_t s,
 
 }  // namespace bsgdtv
 
+namespace bsgdtv {
+
+// Copies n floats of y (host or device) to dst on the handle's stream and
+// checks them for NaN/Inf on the device; returns after the check has been
+// read back, so the copy has read y (a host y may be reused at once, pageable
+// or pinned).  *finite: the check.
+int upload_checked(bsgdtv_batch_t h, float *dst, const float *y, int y_on_device, int64_t n,
+                   bool *finite) {
+    cudaStream_t s = h->stream;
+    int hflag = 0;
+    BSG_CUDA(cudaMemcpyAsync(dst, y, (size_t)n * sizeof(float),
+                             y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    BSG_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    BSG_CUDA(launch_check_finite(dst, n, h->flag, s));
+    BSG_CUDA(cudaMemcpyAsync(&hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BSG_CUDA(cudaStreamSynchronize(s));
+    *finite = hflag == 0;
+    return BSGDTV_OK;
+}
+
+// bsgdtv_batch_set_slice; check = false skips the NaN/Inf check of a host y
+// (a caller that has checked it) and with it the wait for the copy: a
+// pageable y is staged by the copy call itself.
+int batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_device, double lambda,
+                    bool check) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (!h->has_data) return fail(BSGDTV_ERR_STATE, "set_slice before set_data");
+    if (b < 0 || b >= h->B) return fail(BSGDTV_ERR_INVALID_ARG, "slice index out of range");
+    if (!(lambda >= 0.0) || !std::isfinite(lambda))
+        return fail(BSGDTV_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+    BSG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    const int64_t rows = h->rows;
+    if (y && (check || y_on_device)) {   // staged: a bad y leaves the slot as it was
+        bool finite = false;
+        BSG_CHECK(upload_checked(h, h->ystage, y, y_on_device, rows, &finite));
+        if (!finite) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+    } else if (y) {
+        BSG_CUDA(cudaMemcpyAsync(h->ystage, y, (size_t)rows * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
+    const double lam = y ? lambda : 0.0;
+    const int64_t n = std::max(rows, h->cols);
+    slice_reset_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y ? h->ystage : nullptr, h->Y, h->X,
+                                                                   h->R[h->cur], rows, h->cols, h->Bp, b);
+    add_launches(1);
+    BSG_CUDA(cudaGetLastError());
+    const float tau = (float)(h->mu * lam);
+    BSG_CUDA(cudaMemcpyAsync(h->tau + b, &tau, sizeof(float), cudaMemcpyHostToDevice, s));
+    const bool prox_before = any_prox(h, 1);
+    h->lambdas[b] = lam;
+    if (any_prox(h, 1) != prox_before) bdrop_graphs(h);   // the epoch gains or loses its prox
+    return BSGDTV_OK;
+}
+
+}  // namespace bsgdtv
+
 extern "C" {
 
 int bsgdtv_operator_create_csr(bsgdtv_operator_t *out, int64_t rows, int64_t cols, int img_h,
@@ -981,27 +1037,6 @@ void bsgdtv_batch_destroy(bsgdtv_batch_t h) {
     bsgdtv_operator_destroy(op);
 }
 
-namespace {
-
-// Copies n floats of y (host or device) to dst on the handle's stream and
-// checks them for NaN/Inf on the device; returns after the check has been
-// read back, so the copy has read y (a host y may be reused at once, pageable
-// or pinned).  *finite: the check.
-int upload_checked(bsgdtv_batch_t h, float *dst, const float *y, int y_on_device, int64_t n,
-                   bool *finite) {
-    cudaStream_t s = h->stream;
-    int hflag = 0;
-    BSG_CUDA(cudaMemcpyAsync(dst, y, (size_t)n * sizeof(float),
-                             y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    BSG_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
-    BSG_CUDA(launch_check_finite(dst, n, h->flag, s));
-    BSG_CUDA(cudaMemcpyAsync(&hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    BSG_CUDA(cudaStreamSynchronize(s));
-    *finite = hflag == 0;
-    return BSGDTV_OK;
-}
-
-}  // namespace
 
 int bsgdtv_batch_set_data(bsgdtv_batch_t h, const float *y, int y_on_device,
                           const double *lambdas, double mu) {
@@ -1107,31 +1142,7 @@ int bsgdtv_batch_get_x(bsgdtv_batch_t h, float *x, int out_on_device) {
 
 int bsgdtv_batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_device, double lambda) {
     BSG_TRACE();
-    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
-    if (!h->has_data) return fail(BSGDTV_ERR_STATE, "set_slice before set_data");
-    if (b < 0 || b >= h->B) return fail(BSGDTV_ERR_INVALID_ARG, "slice index out of range");
-    if (!(lambda >= 0.0) || !std::isfinite(lambda))
-        return fail(BSGDTV_ERR_INVALID_ARG, "lambda must be finite and >= 0");
-    BSG_CUDA(cudaSetDevice(h->device));
-    cudaStream_t s = h->stream;
-    const int64_t rows = h->rows;
-    if (y) {   // staged: a bad y leaves the slot as it was
-        bool finite = false;
-        BSG_CHECK(upload_checked(h, h->ystage, y, y_on_device, rows, &finite));
-        if (!finite) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
-    }
-    const double lam = y ? lambda : 0.0;
-    const int64_t n = std::max(rows, h->cols);
-    slice_reset_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y ? h->ystage : nullptr, h->Y, h->X,
-                                                                   h->R[h->cur], rows, h->cols, h->Bp, b);
-    add_launches(1);
-    BSG_CUDA(cudaGetLastError());
-    const float tau = (float)(h->mu * lam);
-    BSG_CUDA(cudaMemcpyAsync(h->tau + b, &tau, sizeof(float), cudaMemcpyHostToDevice, s));
-    const bool prox_before = any_prox(h, 1);
-    h->lambdas[b] = lam;
-    if (any_prox(h, 1) != prox_before) bdrop_graphs(h);   // the epoch gains or loses its prox
-    return BSGDTV_OK;
+    return bsgdtv::batch_set_slice(h, b, y, y_on_device, lambda, true);
 }
 
 int bsgdtv_batch_estimate_umax(bsgdtv_batch_t h, int max_iters, double rel_tol, double *u_max,

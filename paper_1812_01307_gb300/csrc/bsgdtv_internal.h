@@ -172,6 +172,11 @@ void fgp_momentum_host(int iters, std::vector<float> &mom);
 // slots that come and go do not force the epoch graphs to be captured again.
 void batch_keep_prox(bsgdtv_batch_t h, bool on);
 
+// batch.cu: bsgdtv_batch_set_slice, with check = false for a host y the
+// caller has already checked for NaN/Inf (no device check, no wait).
+int batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_device, double lambda,
+                    bool check);
+
 // batch.cu: the 2-D parallel-beam A of an n x n image (n_angles x n_bins
 // rays) as a host CSR with ascending columns, weights from the matrix-free
 // projector; BSGDTV_* code.

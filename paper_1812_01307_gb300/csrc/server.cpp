@@ -271,7 +271,8 @@ void admit(bsgdtv_server_ctx *s) {
             }
             continue;
         }
-        const int rc = bsgdtv_batch_set_slice(g->batch, slot, r.y.data(), 0, r.lambda);
+        // y was checked at submit: no second check, no wait for the copy
+        const int rc = bsgdtv::batch_set_slice(g->batch, slot, r.y.data(), 0, r.lambda, false);
         if (rc != BSGDTV_OK) {
             finish_failed(s, r, rc, std::string("set_slice: ") + bsgdtv_last_error());
         } else {
