@@ -54,8 +54,8 @@ def parse():
     ap.add_argument("--served-tick", type=int, default=10, help="max epochs between admissions")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip every variant (stored formats and the batch)")
-    ap.add_argument("--variants", default="f32_i16,f16_i16,bf16_i16,batch,matrix_free,stochastic",
-                    help="comma-separated variants to run: f32_i16, f16_i16, bf16_i16, batch, "
+    ap.add_argument("--variants", default="f32_i16,f16_i16,bf16_i16,batch,batch_f16,matrix_free,stochastic",
+                    help="comma-separated variants to run: f32_i16, f16_i16, bf16_i16, batch, batch_f16, "
                          "matrix_free, stochastic")
     ap.add_argument("--mf-n", type=int, default=2048, help="image size of the matrix-free variant")
     ap.add_argument("--batch-tuning", default="",
@@ -422,11 +422,15 @@ def run_ours(args):
                     "bsgdtv_run_subsets, which includes building the work-item lists"}
 
     # many slices sharing one A: B slices of the same geometry, one batch handle
-    if not args.no_variants and args.batch_slices > 0 and "batch" in args.variants.split(","):
+    # (FP32 weights, and binary16 weights with FP32 arithmetic)
+    batch_kinds = [(k, f) for k, f in (("batch", B.FMT_F32_I32), ("batch_f16", B.FMT_F16_I16))
+                   if k in args.variants.split(",")]
+    if not args.no_variants and args.batch_slices > 0 and batch_kinds:
         Bs = args.batch_slices
         _, Ys = synth.slice_stack(P.A, wl.n, wl.n_ellipses, Bs, seed=wl.seed)
         Ys_dev = torch.tensor(Ys, dtype=torch.float32, device=dev)
-        bt = B.BatchReconstructor(P.A, (wl.n, wl.n), Bs)
+    for kind, bfmt in (batch_kinds if not args.no_variants and args.batch_slices > 0 else []):
+        bt = B.BatchReconstructor(P.A, (wl.n, wl.n), Bs, fmt=bfmt)
         bt.set_data(Ys_dev, np.full(Bs, wl.lam), mu)
         if args.batch_tuning:   # a known tuning: no timing trials (e.g. under a profiler)
             chunk, group = (int(v) for v in args.batch_tuning.split(","))
@@ -446,18 +450,20 @@ def run_ours(args):
         dt = D.max_over_ranks(b0.elapsed_time(b1) / 1e3, dev)
         bt.close()
         nnz_b = P.A.row_ptr[-1]
-        # both passes: A once each (4 B weight + 4 B index per nonzero), and
-        # y, x, r, x^ of every slice once per pass they appear in
-        pass_bytes = 16 * nnz_b + 4 * Bs * 3 * (P.A.rows + P.A.cols_n)
+        # both passes: A once each (4 B index + 4 B FP32 or 2 B FP16 weight per
+        # nonzero), and y, x, r, x^ of every slice once per pass they appear in
+        per_nnz = 8 if bfmt == B.FMT_F32_I32 else 6
+        pass_bytes = 2 * per_nnz * nnz_b + 4 * Bs * 3 * (P.A.rows + P.A.cols_n)
         ach = pass_bytes / (pk / 1e3 / Kb) / 1e9
-        variants["batch"] = {"value": world * Bs * Kb / dt, "unit": "slice-epochs/s", "slices": Bs,
-                             "steps": Kb, "epoch_ms": 1e3 * dt / Kb, "products_ms": pk / Kb,
-                             "bytes_per_epoch_products": int(pass_bytes), "achieved_gbs": ach,
-                             "autotuned_fgp_iters_per_launch": chunk,
-                             "autotuned_fgp_slices_per_group": group,
-                             "frac": ach / peak,
-                             "note": "two passes over A (CSR then CSC) per epoch, lanes = slices; "
-                                     "x and r gathered from L2"}
+        variants[kind] = {"value": world * Bs * Kb / dt, "unit": "slice-epochs/s", "slices": Bs,
+                          "steps": Kb, "epoch_ms": 1e3 * dt / Kb, "products_ms": pk / Kb,
+                          "weights": "f32" if bfmt == B.FMT_F32_I32 else "f16",
+                          "bytes_per_epoch_products": int(pass_bytes), "achieved_gbs": ach,
+                          "autotuned_fgp_iters_per_launch": chunk,
+                          "autotuned_fgp_slices_per_group": group,
+                          "frac": ach / peak,
+                          "note": "two passes over A (CSR then CSC) per epoch, lanes = slices; "
+                                  "x and r gathered from L2"}
 
     # large and matrix free: 2048x2048, 60 ellipses, 1440 angles x 2897 bins, 16 slices
     if not args.no_variants and "matrix_free" in args.variants.split(","):
