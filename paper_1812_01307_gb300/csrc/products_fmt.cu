@@ -18,9 +18,10 @@ using namespace prod;
 
 // Stored formats of one column group (four entries of one lane's segment).
 template <int FMT> struct GroupFmt;
-// kDepth: column groups loaded ahead (about 2 KB of A in flight per warp).
+// kDepth: column groups loaded ahead (3 - 4 KB of A in flight per warp; deeper
+// queues measured slower for the 16-bit weights).
 template <> struct GroupFmt<BSGDTV_FMT_F32_I16> {
-    static constexpr int kDepth = 3;
+    static constexpr int kDepth = 4;
     using VT = float4;
     using IT = uint2;   // four 16-bit indices
     static __device__ __forceinline__ void decode(const VT &v, const IT &i, float4 &w, int4 &k) {
