@@ -42,23 +42,25 @@ __device__ __forceinline__ void atomic_max_nonneg(float *dst, float v) {
     atomicMax(reinterpret_cast<int *>(dst), __float_as_int(v));
 }
 
-// Sum of a row's segment partials in segment (ascending tile) order, with
-// four loads in flight.
+// Sum of a row's segment partials in segment (ascending tile) order.  The
+// loads of up to eight segments are issued together (predicated), so a row
+// of up to eight segments (most rows) costs two dependent round trips.
 __device__ __forceinline__ float row_partial_sum(const DevLayout &d, const float *__restrict__ z_part,
                                                  int64_t ray) {
+    constexpr int kU = 8;
     const int e0 = d.ray_seg_ptr[ray], e1 = d.ray_seg_ptr[ray + 1];
     float acc = 0.f;
-    int e = e0;
-    for (; e + 4 <= e1; e += 4) {
-        const int p0 = d.ray_seg_pos[e], p1 = d.ray_seg_pos[e + 1], p2 = d.ray_seg_pos[e + 2],
-                  p3 = d.ray_seg_pos[e + 3];
-        const float z0 = z_part[p0], z1 = z_part[p1], z2 = z_part[p2], z3 = z_part[p3];
-        acc += z0;
-        acc += z1;
-        acc += z2;
-        acc += z3;
+    for (int e = e0; e < e1; e += kU) {
+        int pos[kU];
+        float z[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) pos[k] = (e + k < e1) ? d.ray_seg_pos[e + k] : -1;
+#pragma unroll
+        for (int k = 0; k < kU; ++k) z[k] = (pos[k] >= 0) ? z_part[pos[k]] : 0.f;
+#pragma unroll
+        for (int k = 0; k < kU; ++k)
+            if (e + k < e1) acc += z[k];
     }
-    for (; e < e1; ++e) acc += z_part[d.ray_seg_pos[e]];
     return acc;
 }
 
