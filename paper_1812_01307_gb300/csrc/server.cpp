@@ -568,7 +568,8 @@ int bsgdtv_server_cancel(bsgdtv_server_t s, int64_t request_id) {
         Request &r = *it->second;
         if (finished(r)) return fail(BSGDTV_ERR_STATE, "request already ended");
         if (r.state == kQueued) {
-            s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r.id));
+            auto q = std::find(s->queue.begin(), s->queue.end(), r.id);
+            if (q != s->queue.end()) s->queue.erase(q);
             s->geoms[r.geom]->queued--;
             std::vector<float>().swap(r.y);
             finish_cancelled(s, r);
