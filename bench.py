@@ -271,6 +271,96 @@ def oracle_epochs_per_s(P, mu, seconds, min_epochs=2, max_epochs=10 ** 9):
     return done / dt, done, dt
 
 
+def _pair_worker(conn, blocks_mine, rb, cb, pairs):
+    """Worker of oracle_parallel_epochs_per_s: holds the blocks of its pairs,
+    answers each (x, r) with their block products (oracle.block_products)."""
+    import os
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import oracle
+    M, N = len(rb) - 1, len(cb) - 1
+    blocks = [[None] * N for _ in range(M)]
+    for (i, j), blk in zip(pairs, blocks_mine):
+        blocks[i][j] = blk
+    while True:
+        msg = conn.recv()
+        if msg is None:
+            break
+        x, r = msg
+        z, gh = oracle.block_products(blocks, rb, cb, x, r, pairs)
+        conn.send([(z[i][j], gh[i][j]) for i, j in pairs])
+    conn.close()
+
+
+def oracle_parallel_epochs_per_s(P, mu, seconds, workers, min_epochs=2):
+    """The same oracle epochs with the M x N block products spread over
+    `workers` spawned processes (contiguous runs of pairs in (i, j) order),
+    the residual / gradient sums (ascending j / i), the step and the FGP prox
+    in this process: the oracle's own functions, in the oracle's order.
+    Returns (epochs/s, epochs timed, seconds, workers)."""
+    import multiprocessing as mp
+
+    import numpy as np
+    import oracle
+    wl = P.wl
+    A = oracle.to_scipy(P.A)
+    rb, cb = oracle.partition(A.shape[0], A.shape[1], wl.M, wl.N, wl.n_bins, wl.n)
+    blocks = oracle.split_blocks(A, rb, cb)
+    pairs = [(i, j) for i in range(wl.M) for j in range(wl.N)]
+    workers = max(1, min(workers, len(pairs)))
+    ctx = mp.get_context("spawn")
+    procs, conns, shares = [], [], []
+    for w in range(workers):
+        mine = pairs[len(pairs) * w // workers: len(pairs) * (w + 1) // workers]
+        a, b = ctx.Pipe()
+        pr = ctx.Process(target=_pair_worker, args=(b, [blocks[i][j] for i, j in mine], rb, cb, mine),
+                         daemon=True)
+        pr.start()
+        procs.append(pr)
+        conns.append(a)
+        shares.append(mine)
+    del blocks
+    y = P.y.astype(np.float32).astype(np.float64)
+    x = np.zeros(A.shape[1])
+    r = y.copy()
+    M, N = wl.M, wl.N
+
+    def one_epoch(x, r):
+        for c in conns:
+            c.send((x, r))
+        z = [[None] * N for _ in range(M)]
+        gh = [[None] * N for _ in range(M)]
+        for c, mine in zip(conns, shares):
+            for (i, j), (zz, gg) in zip(mine, c.recv()):
+                z[i][j], gh[i][j] = zz, gg
+        r_new = oracle.reduce_residual(y, z, rb)
+        x_hat = x + mu * oracle.reduce_gradient(gh, cb, x.shape[0])
+        if wl.lam > 0.0 and wl.fgp_iters > 0:
+            x_new = oracle.fgp(x_hat.reshape(wl.n, wl.n), mu * wl.lam, wl.fgp_iters).ravel()
+        else:
+            x_new = x_hat
+        return x_new, r_new
+
+    try:
+        x, r = one_epoch(x, r)     # warm-up: every worker has started and answered
+        done = 0
+        t0 = time.perf_counter()
+        while done < min_epochs or time.perf_counter() - t0 < seconds:
+            x, r = one_epoch(x, r)
+            done += 1
+        dt = time.perf_counter() - t0
+    finally:
+        for c in conns:
+            try:
+                c.send(None)
+            except (OSError, BrokenPipeError):
+                pass
+        for pr in procs:
+            pr.join(timeout=10)
+            if pr.is_alive():
+                pr.terminate()
+    return done / dt, done, dt, workers
+
+
 # ------------------------------------------------------------------ arms
 def run_reference(args):
     from paper_1812_01307_gb300 import dist as D
@@ -374,6 +464,8 @@ def run_ours(args):
            "note": "per step: bsgdtv_set_data(host y) + bsgdtv_run(1 epoch) + bsgdtv_get_x(host x)"}
     rec.close()
     peak, peak_kind = hbm_peak()
+    fp32_scalar, fp32_packed = B.bsgdtv_fp32_fma_peak()
+    fp32_peak = max(fp32_scalar, fp32_packed)
 
     # the same workload with the other stored formats of A (one timed run each)
     variants = {}
@@ -411,15 +503,18 @@ def run_ours(args):
         torch.cuda.synchronize()
         D.barrier()
         t0s = time.perf_counter()
-        rs.run_subsets(R_sel[W:], C_sel[W:], wl.fgp_iters)   # synchronises
-        dts = D.max_over_ranks(time.perf_counter() - t0s, dev)
+        dev_ms, prep_ms = B.bsgdtv_run_subsets_timed(rs.h, R_sel[W:], C_sel[W:], wl.fgp_iters)
+        wall_s = time.perf_counter() - t0s
+        dts = D.max_over_ranks(dev_ms / 1e3, dev)
         rs.close()
         variants["stochastic"] = {
             "value": world * Ks / dts, "unit": "iterations/s", "steps": Ks, "alpha": alpha,
             "gamma": gamma, "block_epochs_per_s": world * Ks * alpha * gamma / dts,
+            "host_prep_ms": prep_ms, "wall_iterations_per_s": Ks / wall_s,
             "note": "per iteration half of the row blocks and half of the column blocks are drawn "
-                    "(Sec. 3); a block-epoch is M*N block products; host wall clock around "
-                    "bsgdtv_run_subsets, which includes building the work-item lists"}
+                    "(Sec. 3); a block-epoch is M*N block products; value: CUDA-event time of the "
+                    "iterations' kernels on the handle's stream (work-item lists already on the "
+                    "device); host_prep_ms: building and uploading those lists, outside it"}
 
     # many slices sharing one A: B slices of the same geometry, one batch handle
     # (FP32 weights, and binary16 weights with FP32 arithmetic)
@@ -429,41 +524,57 @@ def run_ours(args):
         Bs = args.batch_slices
         _, Ys = synth.slice_stack(P.A, wl.n, wl.n_ellipses, Bs, seed=wl.seed)
         Ys_dev = torch.tensor(Ys, dtype=torch.float32, device=dev)
+        lam_b = np.random.default_rng(wl.seed + 3).uniform(0.01, 0.05, Bs)
+        Kfb = 30   # FGP iterations of the batched-volume configuration
     for kind, bfmt in (batch_kinds if not args.no_variants and args.batch_slices > 0 else []):
         bt = B.BatchReconstructor(P.A, (wl.n, wl.n), Bs, fmt=bfmt)
-        bt.set_data(Ys_dev, np.full(Bs, wl.lam), mu)
+        bt.set_data(Ys_dev, lam_b, mu)
         if args.batch_tuning:   # a known tuning: no timing trials (e.g. under a profiler)
             chunk, group = (int(v) for v in args.batch_tuning.split(","))
             bt.set_tuning(chunk, group)
         else:
-            chunk, group, _ = bt.autotune(wl.fgp_iters, 3)
-        bt.run(max(W, 3), wl.fgp_iters)
+            chunk, group, _ = bt.autotune(Kfb, 3)
+        bt.set_data(Ys_dev, lam_b, mu)
+        bt.run(max(W, 3), Kfb)
         torch.cuda.synchronize()
         D.barrier()
-        Kb = max(1, min(K, 200))
+        Kb = max(1, min(K, 150))
         b0 = torch.cuda.Event(enable_timing=True)
         b1 = torch.cuda.Event(enable_timing=True)
         b0.record()
-        pk, ep = bt.run_timed(Kb, wl.fgp_iters)
+        pk, ep = bt.run_timed(Kb, Kfb)
         b1.record()
         torch.cuda.synchronize()
         dt = D.max_over_ranks(b0.elapsed_time(b1) / 1e3, dev)
         bt.close()
-        nnz_b = P.A.row_ptr[-1]
+        nnz_b = int(P.A.row_ptr[-1])
         # both passes: A once each (4 B index + 4 B FP32 or 2 B FP16 weight per
         # nonzero), and y, x, r, x^ of every slice once per pass they appear in
         per_nnz = 8 if bfmt == B.FMT_F32_I32 else 6
         pass_bytes = 2 * per_nnz * nnz_b + 4 * Bs * 3 * (P.A.rows + P.A.cols_n)
         ach = pass_bytes / (pk / 1e3 / Kb) / 1e9
+        prod_s = pk / 1e3 / Kb
+        # ALU roof: 2 FMAs (4 flops) per nonzero and slice, at the measured FP32 peak
+        flops = 4.0 * nnz_b * Bs
+        t_hbm, t_alu = pass_bytes / (peak * 1e9), flops / (fp32_peak * 1e12)
         variants[kind] = {"value": world * Bs * Kb / dt, "unit": "slice-epochs/s", "slices": Bs,
-                          "steps": Kb, "epoch_ms": 1e3 * dt / Kb, "products_ms": pk / Kb,
+                          "steps": Kb, "fgp_iters": Kfb, "lambda": "per slice U(0.01,0.05), seeded",
+                          "epoch_ms": 1e3 * dt / Kb, "products_ms": pk / Kb,
                           "weights": "f32" if bfmt == B.FMT_F32_I32 else "f16",
                           "bytes_per_epoch_products": int(pass_bytes), "achieved_gbs": ach,
                           "autotuned_fgp_iters_per_launch": chunk,
                           "autotuned_fgp_slices_per_group": group,
                           "frac": ach / peak,
+                          "products_tflops": flops / prod_s / 1e12,
+                          "alu_frac": flops / prod_s / 1e12 / fp32_peak,
+                          "binding_roof": "alu" if t_alu > t_hbm else "hbm",
+                          "binding_frac": max(t_hbm, t_alu) / prod_s,
+                          "config": "batched volume: %d slices of %dx%d sharing one A (%d angles x %d "
+                                    "bins), per-slice lambda ~ U(0.01,0.05), %d FGP iterations"
+                                    % (Bs, wl.n, wl.n, wl.n_angles, wl.n_bins, Kfb),
                           "note": "two passes over A (CSR then CSC) per epoch, lanes = slices; "
-                                  "x and r gathered from L2"}
+                                  "x and r gathered from L2; binding_frac = max(HBM time, FP32 "
+                                  "ALU time at the measured peak) / product time"}
 
     # large and matrix free: 2048x2048, 60 ellipses, 1440 angles x 2897 bins, 16 slices
     if not args.no_variants and "matrix_free" in args.variants.split(","):
@@ -492,10 +603,17 @@ def run_ours(args):
         torch.cuda.synchronize()
         dt5 = D.max_over_ranks(m0.elapsed_time(m1) / 1e3, dev)
         mf.close()
+        # the operator's nonzeros (no stored A): 4 flops per nonzero and slice at
+        # least (one FMA in each pass), at the measured FP32 peak
+        nnz5 = synth.parallel_beam_nnz(n5, na5, nb5)
+        flops5 = 4.0 * nnz5 * S5
+        prod5_s = pk5 / 1e3 / Km
         variants["matrix_free"] = {
             "value": world * S5 * Km / dt5, "unit": "slice-epochs/s", "slices": S5, "steps": Km,
             "image": f"{n5}x{n5}", "angles": na5, "bins": nb5, "fgp_iters": K5,
             "epoch_ms": 1e3 * dt5 / Km, "products_ms": pk5 / Km, "u_max": u5, "u_max_iters": it5,
+            "nnz": nnz5, "products_tflops": flops5 / prod5_s / 1e12,
+            "alu_frac": flops5 / prod5_s / 1e12 / fp32_peak,
             "note": "weights computed on the fly in both passes (no stored A); the stored FP32 CSR "
                     "of this geometry would hold about 7.7e9 nonzeros (62 GB)"}
 
@@ -507,27 +625,41 @@ def run_ours(args):
     per_launch = info["min_bytes_per_pass"]
     achieved = per_launch / prod_avg_s / 1e9
     R, c, nnz = P.A.rows, P.A.cols_n, info["nnz"]
+    # per epoch at least: A (8 B per nonzero), y, r^{k-1}, r^k (3R) and x, x^ (2c)
+    # once, and the prox's input and output fields (2c)
     epoch_bytes = 8 * nnz + 4 * (3 * R + 2 * c) + 8 * c
+    epoch_s = elapsed / K
     line = {"metric": METRIC, "value": value, "unit": "epochs/s", "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": 1e3 * elapsed_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(wl), "parallelism": f"independent slices x{world}",
                        "l2": "inputs larger than L2 (A = %.2f GB), no flush" % (8 * nnz / 1e9),
                        "nnz": nnz, "segments": info["segments"], "work_items": info["work_items"]},
-            "hbm_gbs_epoch": epoch_bytes * K / (elapsed / 1.0) / 1e9 if world == 1 else None,
             "products_per_s": 2 * value,
             "roofline": {"bound": "hbm", "kernel": "products_kernel (fused Ax, 2A^T r)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": profiled_traffic(), "bytes_per_launch": per_launch,
                          "avg_launch_ms": prod_avg_s * 1e3,
-                         "share_of_epoch": prod_ms / epoch_ms if epoch_ms > 0 else None},
+                         "share_of_epoch": prod_ms / epoch_ms if epoch_ms > 0 else None,
+                         "epoch_bytes": epoch_bytes,
+                         "epoch_achieved": epoch_bytes / epoch_s / 1e9,
+                         "epoch_frac": epoch_bytes / epoch_s / 1e9 / peak},
+            "fp32_peak_tflops": {"scalar": fp32_scalar, "packed": fp32_packed,
+                                 "kind": "measured in this run: FMA chains at full occupancy, CUDA events"},
             "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
             "served": served, "variants": variants or None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, done, dt = oracle_epochs_per_s(P, mu, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "epochs/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{done} epochs of {wl.name} from x=0 ({dt:.1f} s, FP64 numpy/scipy, one thread)"}
+        ncpu = os.cpu_count() or 1
+        if ncpu > 1:
+            va, done_a, dt_a, wk = oracle_parallel_epochs_per_s(P, mu, args.cpu_seconds, ncpu)
+            line["cpu_baseline"]["all_cores"] = {
+                "value": va, "unit": "epochs/s", "cores": wk, "host_cpus": ncpu, "kind": "oracle",
+                "sample": f"{done_a} epochs of {wl.name} ({dt_a:.1f} s): the {wl.M}x{wl.N} block "
+                          f"products over {wk} processes, sums, step and FGP prox in one"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -155,6 +155,14 @@ int bsgdtv_run(bsgdtv_t h, int epochs, int fgp_iters);
 int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_sel,
                        const uint8_t *col_sel);
 
+/* bsgdtv_run_subsets with its device time: *device_ms receives the CUDA-event
+ * time on the handle's stream from the moment the work-item lists are on the
+ * device to the end of the last iteration's kernels; *prep_ms (may be NULL)
+ * the host time spent validating the draws and building and uploading the
+ * lists.  Same iterates as bsgdtv_run_subsets; synchronises. */
+int bsgdtv_run_subsets_timed(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_sel,
+                             const uint8_t *col_sel, double *device_ms, double *prep_ms);
+
 /* bsgdtv_run that also times, with CUDA events recorded on the handle's
  * stream inside the epoch graphs, every launch of the fused product kernel
  * (the block products) and every whole epoch.  Synchronises.  products_ms / epoch_ms
@@ -206,7 +214,8 @@ int bsgdtv_get_info(bsgdtv_t h, int64_t *nnz, int64_t *segments, int64_t *work_i
 
 /* The TV prox alone: x = FGP(b, tau, iters) for one img_h x img_w image (device
  * pointers b, x; may not alias).  Beck-Teboulle FGP, cold start, isotropic TV,
- * P_C = identity; tau <= 0 or iters <= 0 copies b.  Allocates its scratch (the
+ * P_C = identity; tau <= 0 or iters == 0 copies b; iters < 0 (or a
+ * non-finite tau) is BSGDTV_ERR_INVALID_ARG.  Allocates its scratch (the
  * dual fields) from the device heap for the duration of the call and
  * synchronises `stream` before returning. */
 int bsgdtv_tv_prox(const float *b, float *x, int img_h, int img_w, double tau, int iters,
@@ -219,8 +228,8 @@ int bsgdtv_tv_prox(const float *b, float *x, int img_h, int img_w, double tau, i
  * synchronisation of cudaMalloc/cudaFree, and host runtimes that forbid
  * plugins from allocating.  Same arguments, same result as bsgdtv_tv_prox;
  * it calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
- * (FGP dual fields and momentum table) is one file-scope device array of
- * about 4 MiB that every GPU which loads the library keeps until the process
+ * (two sets of FGP dual fields and the momentum table) is one file-scope
+ * device array of about 8 MiB that every GPU which loads the library keeps until the process
  * exits.  Limits: img_h*img_w <= 262144 (e.g. 512 x 512) and iters <= 4096;
  * larger requests fail with BSGDTV_ERR_INVALID_ARG.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that
@@ -253,6 +262,15 @@ int bsgdtv_layout_check(int64_t rows, int64_t cols, int img_h, int img_w, const 
 /* Host only: the weight as a handle of the given format stores it, widened to
  * FP32 (round to nearest even for the 16-bit formats). */
 float bsgdtv_stored_weight(double v, int format);
+
+/* Measured FP32 CUDA-core throughput of the current device, in TFLOP/s (2
+ * flops per FMA): independent FMA chains at full occupancy, timed with CUDA
+ * events on a private stream, best of three runs after a warm-up, once with
+ * scalar FMAs (*tflops_scalar) and once with packed two-lane FMAs
+ * (*tflops_packed; either may be NULL).  The denominator of the ALU
+ * rooflines of the batched and matrix-free product passes.  Allocates and
+ * frees a small output buffer; synchronises. */
+int bsgdtv_fp32_fma_peak(double *tflops_scalar, double *tflops_packed);
 
 /* Number of kernels this library has launched in the calling process
  * (graph replays count every kernel node). */

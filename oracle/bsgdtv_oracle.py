@@ -42,8 +42,8 @@ import scipy.sparse as sp
 
 __all__ = [
     "split_bounds", "partition", "split_blocks", "block_products", "reduce_residual",
-    "reduce_gradient", "epoch", "run", "L_op", "Lt_op", "proj_iso", "fgp", "fgp_momentum",
-    "tv_iso", "objective", "power_iteration", "descent_condition", "relative_error",
+    "reduce_gradient", "epoch", "run", "L_op", "Lt_op", "proj_iso", "fgp",
+    "tv_iso", "objective", "power_iteration", "descent_condition",
     "to_scipy", "run_subsets",
 ]
 
@@ -173,17 +173,6 @@ def proj_iso(p, q):
     if q.shape[1] > 0:
         q[m1, :] = q[m1, :] / np.maximum(1.0, np.abs(q[m1, :]))
     return p, q
-
-
-def fgp_momentum(K: int):
-    """t_1 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2; returns [(t_k - 1)/t_{k+1}] for k = 1..K."""
-    t = 1.0
-    out = []
-    for _ in range(K):
-        t_next = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
-        out.append((t - 1.0) / t_next)
-        t = t_next
-    return np.asarray(out)
 
 
 def fgp(b, tau: float, K: int, return_dual: bool = False):
@@ -355,9 +344,3 @@ def descent_condition(A, y, x_next, x_cur, x_prev, mu):
     d = x_next - x_cur
     return f(x_next), f(x_cur) + float(d @ grad_prev) + float(d @ d) / (2.0 * mu)
 
-
-def relative_error(x, x_ref) -> float:
-    """||x - x_ref|| / ||x_ref|| (the paper's relative error, Sec. 3)."""
-    x = np.asarray(x, dtype=np.float64).ravel()
-    x_ref = np.asarray(x_ref, dtype=np.float64).ravel()
-    return float(np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref))

@@ -48,6 +48,8 @@ def load(path: str | None = None):
         "bsgdtv_run": (I32, [P, I32, I32]),
         "bsgdtv_run_timed": (I32, [P, I32, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "bsgdtv_run_subsets": (I32, [P, I32, I32, P, P]),
+        "bsgdtv_run_subsets_timed": (I32, [P, I32, I32, P, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "bsgdtv_fp32_fma_peak": (I32, [ctypes.POINTER(D), ctypes.POINTER(D)]),
         "bsgdtv_run_until": (I32, [P, I32, I32, I32, D, ctypes.POINTER(I32), ctypes.POINTER(D)]),
         "bsgdtv_get_x": (I32, [P, P, I32]),
         "bsgdtv_get_state": (I32, [P, P, P, ctypes.POINTER(I64), I32]),
@@ -105,7 +107,8 @@ def exported_symbols():
             "bsgdtv_run_until", "bsgdtv_get_x",
             "bsgdtv_get_state", "bsgdtv_set_state", "bsgdtv_objective", "bsgdtv_block_products",
             "bsgdtv_get_info", "bsgdtv_tv_prox", "bsgdtv_tv_prox_static", "bsgdtv_partition_bounds",
-            "bsgdtv_layout_check", "bsgdtv_run_subsets", "bsgdtv_batch_create_csr", "bsgdtv_batch_destroy",
+            "bsgdtv_layout_check", "bsgdtv_run_subsets", "bsgdtv_run_subsets_timed",
+            "bsgdtv_fp32_fma_peak", "bsgdtv_batch_create_csr", "bsgdtv_batch_destroy",
             "bsgdtv_batch_set_data", "bsgdtv_batch_run", "bsgdtv_batch_run_timed",
             "bsgdtv_batch_get_x", "bsgdtv_batch_create_csr_ex", "bsgdtv_batch_set_slice",
             "bsgdtv_batch_get_slice_x", "bsgdtv_batch_device_bytes", "bsgdtv_server_create",
@@ -273,6 +276,27 @@ def bsgdtv_run_subsets(h, row_sel, col_sel, fgp_iters):
         raise ValueError("row_sel [iters, M] and col_sel [iters, N] with the same iters")
     _check(load().bsgdtv_run_subsets(h, int(rs.shape[0]), int(fgp_iters), _host_ptr(rs, np.uint8),
                                      _host_ptr(cs, np.uint8)), "bsgdtv_run_subsets")
+
+
+def bsgdtv_run_subsets_timed(h, row_sel, col_sel, fgp_iters):
+    """bsgdtv_run_subsets returning (device ms of the iterations' kernels,
+    host ms spent building and uploading the work-item lists)."""
+    rs = np.ascontiguousarray(row_sel, dtype=np.uint8)
+    cs = np.ascontiguousarray(col_sel, dtype=np.uint8)
+    if rs.ndim != 2 or cs.ndim != 2 or rs.shape[0] != cs.shape[0]:
+        raise ValueError("row_sel [iters, M] and col_sel [iters, N] with the same iters")
+    dev, prep = ctypes.c_double(), ctypes.c_double()
+    _check(load().bsgdtv_run_subsets_timed(h, int(rs.shape[0]), int(fgp_iters), _host_ptr(rs, np.uint8),
+                                           _host_ptr(cs, np.uint8), ctypes.byref(dev), ctypes.byref(prep)),
+           "bsgdtv_run_subsets_timed")
+    return dev.value, prep.value
+
+
+def bsgdtv_fp32_fma_peak():
+    """Measured FP32 FMA throughput of the current device: (scalar, packed) TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().bsgdtv_fp32_fma_peak(ctypes.byref(a), ctypes.byref(b)), "bsgdtv_fp32_fma_peak")
+    return a.value, b.value
 
 
 def bsgdtv_get_info(h):

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -54,7 +55,7 @@ struct bsgdtv_ctx {
 
     float *y = nullptr, *r[2] = {nullptr, nullptr}, *x = nullptr, *xhat = nullptr;
     float *z_part = nullptr, *g_part = nullptr;
-    float *fp = nullptr, *fq = nullptr, *fpp = nullptr, *fqp = nullptr;
+    float *fgp = nullptr;   // FGP dual fields: kFgpFieldPlanes planes of cols floats
     float *mom = nullptr;
     int mom_len = 0;
     int *flag = nullptr;
@@ -169,7 +170,7 @@ int enqueue_epoch(bsgdtv_ctx *h, int par, int fgp_iters, cudaStream_t s,
                                     h->rmax + par, h->y, h->r[1 - par], h->rmax + (1 - par), h->x,
                                     xdst, (float)h->mu, s, !marks));
     if (prox) {
-        FgpScratch sc{h->fp, h->fq, h->fpp, h->fqp};
+        const FgpScratch sc = fgp_scratch_planes(h->fgp, h->dl.cols);
         BSG_CUDA(launch_fgp(h->xhat, h->x, h->dl.img_h, h->dl.img_w, (float)(h->mu * h->lambda),
                             fgp_iters, h->mom, sc, s, true,
                             fgp_chunk_for(h->dl.img_h, h->dl.img_w, fgp_iters, h->dl.n_sms)));
@@ -433,9 +434,8 @@ int bsgdtv_create_csr_ex(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, i
     if ((rc = dalloc(hp, &h->y, rows)) || (rc = dalloc(hp, &h->r[0], rows)) ||
         (rc = dalloc(hp, &h->r[1], rows)) || (rc = dalloc(hp, &h->x, cols)) ||
         (rc = dalloc(hp, &h->xhat, cols)) || (rc = dalloc(hp, &h->z_part, d.n_slabs * kSlab)) ||
-        (rc = dalloc(hp, &h->g_part, (size_t)d.n_groups * cols)) || (rc = dalloc(hp, &h->fp, cols)) ||
-        (rc = dalloc(hp, &h->fq, cols)) || (rc = dalloc(hp, &h->fpp, cols)) ||
-        (rc = dalloc(hp, &h->fqp, cols)) || (rc = dalloc(hp, &h->flag, 1)) ||
+        (rc = dalloc(hp, &h->g_part, (size_t)d.n_groups * cols)) || (rc = dalloc(hp, &h->fgp, (size_t)kFgpFieldPlanes * cols)) ||
+        (rc = dalloc(hp, &h->flag, 1)) ||
         (rc = dalloc(hp, &d.item_ctr, 2)) || (rc = dalloc(hp, &h->rmax, 3))) {
         bsgdtv_destroy(h.release());
         return rc;
@@ -669,9 +669,17 @@ int bsgdtv_run_timed(bsgdtv_t h, int epochs, int fgp_iters, double *products_ms,
     return BSGDTV_OK;
 }
 
-int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_sel,
-                       const uint8_t *col_sel) {
-    BSG_TRACE();
+}  // extern "C"
+
+namespace {
+
+// The stochastic iterations; with `marks`, marks[0] is recorded once the
+// work-item lists are on the device (right before the first iteration's
+// kernels) and marks[1] after the last iteration's, and *prep_ms receives the
+// host time spent building and uploading the lists.
+int run_subsets_impl(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_sel,
+                     const uint8_t *col_sel, cudaEvent_t *marks, double *prep_ms) {
+    const auto t_prep = std::chrono::steady_clock::now();
     if (!h || !row_sel || !col_sel) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
     if (!h->has_data) return fail(BSGDTV_ERR_STATE, "bsgdtv_run_subsets before bsgdtv_set_data");
     if (iters < 0 || fgp_iters < 0) return fail(BSGDTV_ERR_INVALID_ARG, "negative iters / fgp_iters");
@@ -764,6 +772,11 @@ int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_
     // dependent launch (each waits for its predecessor before reading).
     if (split)
         BSG_CUDA(cudaMemsetAsync(h->g_part, 0, (size_t)h->dl.n_groups * h->dl.cols * sizeof(int32_t), s));
+    if (marks) {
+        BSG_CUDA(cudaEventRecord(marks[0], s));
+        if (prep_ms)
+            *prep_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_prep).count();
+    }
     for (int k = 0; k < iters; ++k) {
         const int par = h->cur;
         const bool pdl = k > 0;   // the first follows copies, not a kernel
@@ -784,7 +797,7 @@ int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_
                                         h->rb_dev, h->cb_dev, base + item_bytes, base + item_bytes + M,
                                         split, s, true));
         if (prox) {
-            FgpScratch sc{h->fp, h->fq, h->fpp, h->fqp};
+            const FgpScratch sc = fgp_scratch_planes(h->fgp, h->dl.cols);
             BSG_CUDA(launch_fgp(h->xhat, h->x, h->dl.img_h, h->dl.img_w, (float)(h->mu * h->lambda),
                                 fgp_iters, h->mom, sc, s, true,
                                 fgp_chunk_for(h->dl.img_h, h->dl.img_w, fgp_iters, h->dl.n_sms)));
@@ -792,9 +805,48 @@ int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_
         h->cur ^= 1;
         h->epoch++;
     }
+    if (marks) BSG_CUDA(cudaEventRecord(marks[1], s));
     // the host copy of the lists dies here: wait for the upload
     BSG_CUDA(cudaStreamSynchronize(s));
     return BSGDTV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bsgdtv_run_subsets(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_sel,
+                       const uint8_t *col_sel) {
+    BSG_TRACE();
+    return run_subsets_impl(h, iters, fgp_iters, row_sel, col_sel, nullptr, nullptr);
+}
+
+int bsgdtv_run_subsets_timed(bsgdtv_t h, int iters, int fgp_iters, const uint8_t *row_sel,
+                             const uint8_t *col_sel, double *device_ms, double *prep_ms) {
+    BSG_TRACE();
+    if (!device_ms) return fail(BSGDTV_ERR_INVALID_ARG, "device_ms is null");
+    if (h) BSG_CHECK(set_device(h));
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    BSG_CUDA(cudaEventCreate(&ev[0]));
+    cudaError_t e = cudaEventCreate(&ev[1]);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return fail(BSGDTV_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+    }
+    double prep = 0.0;
+    int rc = run_subsets_impl(h, iters, fgp_iters, row_sel, col_sel, iters > 0 ? ev : nullptr, &prep);
+    float ms = 0.f;
+    if (rc == BSGDTV_OK && iters > 0) {
+        e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (e != cudaSuccess) rc = fail(BSGDTV_ERR_CUDA, std::string("cudaEventElapsedTime: ") + cudaGetErrorString(e));
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc == BSGDTV_OK) {
+        *device_ms = ms;
+        if (prep_ms) *prep_ms = prep;
+    }
+    return rc;
 }
 
 int bsgdtv_get_x(bsgdtv_t h, float *out, int out_on_device) {
@@ -927,12 +979,12 @@ int bsgdtv_tv_prox(const float *b, float *x, int img_h, int img_w, double tau, i
     std::vector<float> m;
     fgp_momentum_host(iters, m);
     float *scratch = nullptr;
-    const size_t bytes = (4 * n + m.size()) * sizeof(float);
+    const size_t bytes = (kFgpFieldPlanes * n + m.size()) * sizeof(float);
     BSG_CUDA(cudaMallocAsync((void **)&scratch, bytes, s));
-    float *mom = scratch + 4 * n;
+    float *mom = scratch + kFgpFieldPlanes * n;
     cudaError_t e = cudaMemcpyAsync(mom, m.data(), m.size() * sizeof(float), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
-        FgpScratch sc{scratch, scratch + n, scratch + 2 * n, scratch + 3 * n};
+        const FgpScratch sc = fgp_scratch_planes(scratch, n);
         e = launch_fgp(b, x, img_h, img_w, (float)tau, iters, mom, sc, s);
     }
     cudaError_t e2 = cudaStreamSynchronize(s);   // keeps m alive until the copy is done

@@ -351,7 +351,7 @@ struct bsgdtv_batch_ctx {
     float *ystage = nullptr;            // [max(rows, cols)] planar staging for one slice
     float *X = nullptr, *Xhat = nullptr, *Y = nullptr, *R[2] = {nullptr, nullptr};   // interleaved
     float *Xp = nullptr, *Xhp = nullptr;                                           // planar [B][cols]
-    float *fp = nullptr, *fq = nullptr, *fpp = nullptr, *fqp = nullptr;            // planar FGP duals
+    float *fgp = nullptr;   // planar FGP duals: kFgpFieldPlanes planes of B * cols floats
     float *tau = nullptr;                                                          // [B]
     int *flag = nullptr;
     float *mom = nullptr;
@@ -425,12 +425,12 @@ bool any_prox(const bsgdtv_batch_ctx *h, int fgp_iters) {
     return false;
 }
 
-// Slices per FGP launch group whose fields (b, p, q, p_prev, q_prev) fit in
-// about half of the L2, so the fields of consecutive chunk launches come from
-// L2 rather than HBM.
+// Slices per FGP launch group whose fields (b and the two sets of p, q,
+// p_prev, q_prev: 36 bytes per pixel) fit in about half of the L2, so the
+// fields of consecutive chunk launches come from L2 rather than HBM.
 int fgp_group_by_budget(const bsgdtv_batch_ctx *h) {
     return std::max<int>(1, (int)std::min<int64_t>(
-                                h->B, kFgpFieldBudget / std::max<int64_t>(1, 20 * h->cols)));
+                                h->B, kFgpFieldBudget / std::max<int64_t>(1, 36 * h->cols)));
 }
 
 // One epoch of every slice: reads R[par], writes R[1 - par].
@@ -459,7 +459,7 @@ int benqueue_epoch(bsgdtv_batch_ctx *h, int par, int fgp_iters, cudaStream_t s,
         for (int b0 = 0; b0 < h->B; b0 += sg) {
             const int nb = std::min(sg, h->B - b0);
             const size_t o = (size_t)b0 * c;
-            FgpScratch sc{h->fp + o, h->fq + o, h->fpp + o, h->fqp + o};
+            const FgpScratch sc = fgp_scratch_planes(h->fgp, (int64_t)h->B * c, (int64_t)o);
             BSG_CUDA(fgpk::launch_fgp_regions<true>(h->Xhp + o, h->Xp + o, h->img_h, h->img_w, 1.f,
                                                     h->tau + b0, nb, c, fgp_iters, h->mom, sc, s,
                                                     false, h->fgp_chunk));
@@ -623,8 +623,8 @@ int alloc_vectors(bsgdtv_batch_ctx *hp) {
     BSG_CHECK(balloc(hp, &hp->ystage, (size_t)std::max(hp->rows, hp->cols)));
     for (float **p : {&hp->X, &hp->Xhat}) BSG_CHECK(balloc(hp, p, Ci));
     for (float **p : {&hp->Y, &hp->R[0], &hp->R[1]}) BSG_CHECK(balloc(hp, p, Ri));
-    for (float **p : {&hp->Xp, &hp->Xhp, &hp->fp, &hp->fq, &hp->fpp, &hp->fqp})
-        BSG_CHECK(balloc(hp, p, Cp));
+    for (float **p : {&hp->Xp, &hp->Xhp}) BSG_CHECK(balloc(hp, p, Cp));
+    BSG_CHECK(balloc(hp, &hp->fgp, kFgpFieldPlanes * Cp));
     BSG_CHECK(balloc(hp, &hp->tau, (size_t)hp->B));
     BSG_CHECK(balloc(hp, &hp->flag, 1));
     // padded slices (b >= B) stay zero for good: y = x = r = 0 there
@@ -923,7 +923,7 @@ int64_t bsgdtv_batch_device_bytes(int64_t rows, int64_t cols, int64_t nnz, int s
     const int64_t per_nz = (format == BSGDTV_FMT_F32_I32) ? 8 : 6;
     const int64_t a = 2 * (nnz * per_nz + 8 * (rows + cols + 2));
     const int64_t inter = 4 * (int64_t)Bp * (2 * cols + 3 * rows);
-    const int64_t planar = 4 * (int64_t)slices * 6 * cols;
+    const int64_t planar = 4 * (int64_t)slices * (2 + kFgpFieldPlanes) * cols;
     return a + inter + planar + 4 * (std::max(rows, cols) + slices + 64) + 4 * 4096;
 }
 

@@ -154,10 +154,26 @@ cudaError_t launch_init_state(const float *y, float *r0, float *x, int64_t rows,
 constexpr int kDotPartials = 1024;
 
 // fgp.cu: K FGP iterations on an h x w image.  `mom` holds the K momentum
-// coefficients (iteration k uses mom[k-1]); p,q,pp,qp are h*w scratch fields.
-struct FgpScratch {
+// coefficients (iteration k uses mom[k-1]).  The dual state passes between
+// the launches of a tiled FGP through two sets of h*w fields (p, q, p_prev,
+// q_prev), read from one and written to the other by turns.
+struct FgpFields {
     float *p, *q, *pp, *qp;
 };
+struct FgpScratch {
+    FgpFields set[2];
+};
+constexpr int kFgpFieldPlanes = 8;   // h*w floats of scratch per image
+// The two sets carved out of kFgpFieldPlanes consecutive planes of `plane`
+// floats starting at base (+ offset within each plane).
+inline FgpScratch fgp_scratch_planes(float *base, int64_t plane, int64_t offset = 0) {
+    FgpScratch sc;
+    for (int k = 0; k < 2; ++k) {
+        float *b = base + offset + (int64_t)4 * k * plane;
+        sc.set[k] = FgpFields{b, b + plane, b + 2 * plane, b + 3 * plane};
+    }
+    return sc;
+}
 // Iterations per launch for an h x w image on n_sms SMs (a cost model of
 // halo recomputation, waves and launches; every choice gives the same iterates).
 int fgp_chunk_for(int h, int w, int iters, int n_sms);

@@ -18,7 +18,7 @@
 // otherwise regions overlap by a halo of (iterations per launch + 1) pixels
 // (temporal blocking), so each launch runs several iterations with no global
 // synchronisation, and the dual fields persist in global memory (L2) between
-// launches.  Pixels outside the image hold exact zeros (b = p = q = 0), which
+// launches, in two sets that the launches read and write by turns.  Pixels outside the image hold exact zeros (b = p = q = 0), which
 // is the operator's own boundary condition, so no halo is needed there.
 #include <cuda_runtime.h>
 

@@ -86,8 +86,15 @@ __device__ __forceinline__ void fgp_step(float (&p)[V], float (&pp)[V], float (&
     }
 }
 
+// The dual state (p, q, p_prev, q_prev) of a tiled FGP passes between
+// launches through global memory.  A launch reads the set the previous launch
+// wrote (*_in; not read when `first`) and writes its regions' interiors to the
+// other set (*_out; not written when `last`): a region's halo is a neighbour's
+// interior, and CTAs of one grid run in no fixed order, so reading and
+// writing one set in place would let a neighbour that finished first hand
+// this region iterates that are a whole launch ahead.
 // kBatch: blockIdx.z selects one of several images stored `plane` floats
-// apart (b, x_out and the four dual fields alike), each with its own weight
+// apart (b, x_out and the dual fields alike), each with its own weight
 // tau_z[z]; a weight <= 0 makes that image's prox the identity.
 // TY x V: threads in y x pixels per thread (TY * V = RH); kStepRegs: see
 // fgp_step.
@@ -95,8 +102,10 @@ template <bool kBatch, int TY, int V, bool kStepRegs>
 __global__ void __launch_bounds__(RW *TY)
     fgp_kernel(const float *__restrict__ b, float *__restrict__ x_out, int H, int W, float tau,
                float c8, const float *__restrict__ mom, int k0, int iters, int HL, int IH, int IW,
-               int first, int last, float *__restrict__ p_g, float *__restrict__ q_g,
-               float *__restrict__ pp_g, float *__restrict__ qp_g,
+               int first, int last, const float *__restrict__ p_in,
+               const float *__restrict__ q_in, const float *__restrict__ pp_in,
+               const float *__restrict__ qp_in, float *__restrict__ p_out,
+               float *__restrict__ q_out, float *__restrict__ pp_out, float *__restrict__ qp_out,
                const float *__restrict__ tau_z, int64_t plane) {
     __shared__ FgpShared<TY, V> sh;
 
@@ -124,10 +133,14 @@ __global__ void __launch_bounds__(RW *TY)
         const int64_t off = (int64_t)blockIdx.z * plane;
         b += off;
         x_out += off;
-        p_g += off;
-        q_g += off;
-        pp_g += off;
-        qp_g += off;
+        p_in += off;
+        q_in += off;
+        pp_in += off;
+        qp_in += off;
+        p_out += off;
+        q_out += off;
+        pp_out += off;
+        qp_out += off;
         tau = tau_z[blockIdx.z];
         c8 = 1.0f / (8.0f * tau);
     }
@@ -159,10 +172,10 @@ __global__ void __launch_bounds__(RW *TY)
         if (first || !in) {
             pa[v] = qa[v] = pb[v] = qb[v] = 0.f;
         } else {
-            pa[v] = p_g[o];
-            qa[v] = q_g[o];
-            pb[v] = pp_g[o];
-            qb[v] = qp_g[o];
+            pa[v] = p_in[o];
+            qa[v] = q_in[o];
+            pb[v] = pp_in[o];
+            qb[v] = qp_in[o];
         }
     }
 
@@ -219,16 +232,23 @@ __global__ void __launch_bounds__(RW *TY)
             const bool interior = rr_ >= HL && rr_ < HL + IH && tx >= HL && tx < HL + IW;
             if (!(interior && col_in && i >= 0 && i < H)) continue;
             const int64_t o = (int64_t)i * W + j;
-            p_g[o] = pa[v];
-            q_g[o] = qa[v];
-            pp_g[o] = pb[v];
-            qp_g[o] = qb[v];
+            p_out[o] = pa[v];
+            q_out[o] = qa[v];
+            pp_out[o] = pb[v];
+            qp_out[o] = qb[v];
         }
     }
 }
 
 
 inline bool fits_one_region(int h, int w) { return h <= RH && w <= RW; }
+
+// Launch `launch` of a tiled FGP reads field set (launch + 1) & 1 and writes
+// set launch & 1.
+inline const FgpFields &fgp_read_set(const FgpScratch &sc, int launch) {
+    return sc.set[(launch + 1) & 1];
+}
+inline const FgpFields &fgp_write_set(const FgpScratch &sc, int launch) { return sc.set[launch & 1]; }
 
 // K FGP iterations: one launch when the image fits one region, else one
 // launch per chunk of <= kMaxChunk iterations over overlapping regions.
@@ -245,22 +265,26 @@ cudaError_t launch_fgp_regions(const float *b, float *x, int h, int w, float tau
     const dim3 block(RW, TY);
     const float c8 = 1.0f / (8.0f * tau);
     if (fits_one_region(h, w)) {
+        // one launch, no field traffic (first and last)
+        const FgpFields &f = sc.set[0];
         cudaError_t e = launch_kernel(fgp_kernel<kBatch, TY, V, kStepRegs>, dim3(1, 1, planes), block, 0, s, pdl, b,
-                                      x, h, w, tau, c8, mom, 0, iters, 0, RH, RW, 1, 1, sc.p, sc.q,
-                                      sc.pp, sc.qp, tau_z, plane);
+                                      x, h, w, tau, c8, mom, 0, iters, 0, RH, RW, 1, 1, f.p, f.q,
+                                      f.pp, f.qp, f.p, f.q, f.pp, f.qp, tau_z, plane);
         add_launches(1);
         return e != cudaSuccess ? e : cudaGetLastError();
     }
     int done = 0;
-    while (done < iters) {
+    for (int launch = 0; done < iters; ++launch) {
         const int chunk = std::min(max_chunk, iters - done);
         const int HL = chunk + 1;
         const int IH = RH - 2 * HL, IW = RW - 2 * HL;
         const dim3 grid((w + IW - 1) / IW, (h + IH - 1) / IH, planes);
         const int first = (done == 0), last = (done + chunk == iters);
+        const FgpFields &fi = fgp_read_set(sc, launch), &fo = fgp_write_set(sc, launch);
         cudaError_t e = launch_kernel(fgp_kernel<kBatch, TY, V, kStepRegs>, grid, block, 0, s, pdl || done > 0, b, x,
                                       h, w, tau, c8, mom, done, chunk, HL, IH, IW, first, last,
-                                      sc.p, sc.q, sc.pp, sc.qp, tau_z, plane);
+                                      fi.p, fi.q, fi.pp, fi.qp, fo.p, fo.q, fo.pp, fo.qp, tau_z,
+                                      plane);
         add_launches(1);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -8,7 +8,7 @@
 // allocating at all.  This entry point serves them: its scratch (the FGP dual
 // fields and the momentum table) lives in one file-scope device array that is
 // part of the loaded library.  Every GPU that loads the library holds that
-// array (about 4 MiB) until the process exits.
+// array (about 8 MiB) until the process exits.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -21,9 +21,10 @@ namespace {
 
 constexpr int64_t kStaticMaxPixels = 512 * 512;   // largest img_h * img_w accepted
 constexpr int kStaticMaxIters = 4096;             // largest FGP iteration count accepted
-constexpr int64_t kStaticFloats = 4 * kStaticMaxPixels + kStaticMaxIters;
+constexpr int64_t kStaticFloats = kFgpFieldPlanes * kStaticMaxPixels + kStaticMaxIters;
 
-// p, q, p_prev, q_prev (kStaticMaxPixels floats each) then the momentum table.
+// Two sets of p, q, p_prev, q_prev (kStaticMaxPixels floats each; the tiled
+// FGP's launches read one set and write the other) then the momentum table.
 static __device__ __align__(256) float g_static_scratch[kStaticFloats];
 
 // Device address of g_static_scratch, looked up once per device.  In host
@@ -77,7 +78,7 @@ extern "C" int bsgdtv_tv_prox_static(const float *b, float *x, int img_h, int im
     // The dual fields need no clearing: the first FGP launch starts from zero
     // in registers and every later launch reads only values an earlier launch
     // of this call wrote.  The momentum table is rewritten in full below.
-    float *mom_dev = base + 4 * kStaticMaxPixels;
+    float *mom_dev = base + kFgpFieldPlanes * kStaticMaxPixels;
     float mom[kStaticMaxIters];
     double t = 1.0;
     mom[0] = 0.f;
@@ -87,8 +88,7 @@ extern "C" int bsgdtv_tv_prox_static(const float *b, float *x, int img_h, int im
         t = tn;
     }
     BSG_CUDA(cudaMemcpyAsync(mom_dev, mom, iters * sizeof(float), cudaMemcpyHostToDevice, s));
-    FgpScratch sc{base, base + kStaticMaxPixels, base + 2 * kStaticMaxPixels,
-                  base + 3 * kStaticMaxPixels};
+    const FgpScratch sc = fgp_scratch_planes(base, kStaticMaxPixels);
     BSG_CUDA(launch_fgp(b, x, img_h, img_w, (float)tau, iters, mom_dev, sc, s));
     BSG_CUDA(cudaStreamSynchronize(s));
     return BSGDTV_OK;

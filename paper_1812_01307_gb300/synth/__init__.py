@@ -116,6 +116,14 @@ def parallel_beam_csr(n: int, n_angles: int, n_bins: int) -> CSR:
     return CSR(rows, n * n, row_ptr, cols, vals)
 
 
+def parallel_beam_nnz(n: int, n_angles: int, n_bins: int) -> int:
+    """Nonzeros of the parallel-beam A, counted without storing it."""
+    lib = _load()
+    row_nnz = np.zeros(n_angles * n_bins, dtype=np.int64)
+    lib.siddon_count(int(n), int(n_angles), int(n_bins), _ptr(row_nnz, ctypes.c_int64))
+    return int(row_nnz.sum())
+
+
 def ellipse_params(n_ellipses: int, seed: int, scale: float) -> np.ndarray:
     """[n_ellipses, 6] array of (cx, cy, a, b, phi, intensity)."""
     rng = np.random.default_rng(seed)

@@ -89,6 +89,31 @@ def test_batch_matches_oracle_per_slice(B, name, slices, epochs, K, check):
         assert rel(X[b], x_ref) <= 1e-4, (b, rel(X[b], x_ref))
 
 
+def test_batch_prox_multiwave_large_weight(B):
+    """40 slices of 130x130 in one FGP launch group: 9 overlapping regions per
+    slice, 360 CTAs per launch (several waves), with lambda so large that
+    tau = mu * lambda is 0.3 .. 1.2: the duals move far in every iteration,
+    so a region reading its halo from a neighbour that already stored the
+    next launch's iterates would show.  Every slice vs the oracle."""
+    n, na, nb = 130, 12, 185
+    A = synth.parallel_beam_csr(n, na, nb)
+    slices = 40
+    _, Y = synth.slice_stack(A, n, 8, slices, seed=5)
+    Y = Y.astype(np.float32)
+    u, _ = oracle.power_iteration(A)
+    mu = 0.9 / (2 * u)
+    lam = (0.3 + 0.9 * np.arange(slices) / (slices - 1)) / mu
+    epochs, K = 3, 30
+    with B.BatchReconstructor(A, (n, n), slices) as bt:
+        bt.set_data(Y, lam, mu)
+        bt.run(epochs, K)
+        X = bt.x()
+    for b in range(slices):
+        x_ref, _ = oracle.run(A, Y[b].astype(np.float64), (n, n), 2, 3, lam[b], mu, epochs, K,
+                              row_unit=nb, col_unit=n)
+        assert rel(X[b], x_ref) <= 1e-4, (b, rel(X[b], x_ref))
+
+
 def test_batch_without_prox_and_device_inputs(B):
     """lambda = 0 everywhere (no prox in the epoch), y and x passed as device tensors."""
     name, slices = "ellipse64", 3

@@ -191,6 +191,23 @@ def test_tv_prox_512_full_size(B):
     assert rel(xt.cpu().numpy(), ref) <= 1e-5
 
 
+def test_tv_prox_multiwave_large_tau(B):
+    """1024x1024 with a large weight: each launch of the tiled FGP covers 576
+    overlapping 64x64 regions (several waves of CTAs on the GPU), and with
+    tau = 0.5 every iteration moves the duals a long way, so a region that
+    read a neighbour's halo after that neighbour had already stored the next
+    launch's iterates would stand out.  Two weights, 40 and 23 iterations."""
+    rng = np.random.default_rng(9)
+    b = synth.phantom(1024, 40, 5) + 0.2 * rng.standard_normal((1024, 1024))
+    b = b.astype(np.float32)
+    bt = torch.from_numpy(b).cuda()
+    xt = torch.empty_like(bt)
+    for tau, K in ((0.5, 40), (2.0, 23)):
+        B.bsgdtv_tv_prox(bt, xt, tau, K)
+        ref = oracle.fgp(b.astype(np.float64), tau, K)
+        assert rel(xt.cpu().numpy(), ref) <= 1e-5, (tau, K)
+
+
 def test_tv_prox_degenerate_cases(B):
     b = torch.full((33, 70), -1.25, device="cuda")
     x = torch.empty_like(b)

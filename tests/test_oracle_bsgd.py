@@ -138,6 +138,32 @@ def test_theorem2_descent_condition_implies_decrease():
     assert held >= 10
 
 
+def test_theorem2_condition_sides_closed_form():
+    """The two sides of Theorem 2's condition, pinned without the oracle's own
+    expression: f is the quadratic ||y - Ax||^2, so f(x_cur + d) expands
+    exactly to f(x_cur) + 2 d^T A^T A x_cur - 2 d^T A^T y + ||A d||^2, and
+    lhs - rhs = 2 d^T A^T A (x_cur - x_prev) + ||A d||^2 - ||d||^2 / (2 mu)
+    (the gradient grad f(v) = -2 A^T (y - A v) taken at x_prev, not x_cur).
+    A dropped term, a wrong sign or the gradient taken at x_cur moves the
+    difference by one of these terms, which the random points make nonzero."""
+    A, D, y = _problem(6, 14, 11, seed=3)
+    rng = np.random.default_rng(7)
+    mu = 1.7e-3
+    for _ in range(5):
+        x_prev, x_cur, x_next = (rng.standard_normal(36) for _ in range(3))
+        lhs, rhs = oracle.descent_condition(A, y, x_next, x_cur, x_prev, mu)
+        d = x_next - x_cur
+        f_cur = float(np.sum((y - D @ x_cur) ** 2))
+        f_next = f_cur + 2 * d @ (D.T @ (D @ x_cur)) - 2 * d @ (D.T @ y) + float(np.sum((D @ d) ** 2))
+        diff = 2 * d @ (D.T @ (D @ (x_cur - x_prev))) + float(np.sum((D @ d) ** 2)) - d @ d / (2 * mu)
+        scale = abs(f_cur) + abs(d @ d / (2 * mu)) + 1.0
+        assert abs(lhs - f_next) <= 1e-11 * scale
+        assert abs((lhs - rhs) - diff) <= 1e-11 * scale
+    # at x_next = x_cur both sides equal f(x_cur): the strict condition fails
+    lhs, rhs = oracle.descent_condition(A, y, x_cur, x_cur, x_prev, mu)
+    assert lhs == rhs
+
+
 def test_fixed_point_solves_tv_problem_independently():
     """lambda > 0: the limit of Algorithm 1 (prox weight 2 mu lambda) minimises
     ||y-Ax||^2 + lambda TV(x); checked against Chambolle-Pock."""

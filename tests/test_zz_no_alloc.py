@@ -9,8 +9,12 @@ so that a second call sees the shared scratch exactly as the first left it.
 
 This file is named to be collected last.
 """
+import ctypes
+
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -52,6 +56,69 @@ def test_static_prox_matches_allocating_prox_two_calls(B):
         B.bsgdtv_tv_prox_static(b, out, tau, iters)
         assert torch.isfinite(out).all()
         assert _rel(out, ref) <= 1e-5
+
+
+def test_static_prox_matches_oracle_and_degenerate_paths(B):
+    """One call straight against the FP64 oracle (a tiled 300x211 image with a
+    large weight), the single-region path (<= 64x64, one launch) and the
+    branch that copies b (tau <= 0 or zero iterations)."""
+    for shape, tau, iters, seed in [((300, 211), 1.5, 37, 2), ((64, 64), 0.6, 19, 3), ((17, 45), 0.3, 8, 4)]:
+        b = _image(shape, seed)
+        out = torch.full_like(b, float("nan"))
+        B.bsgdtv_tv_prox_static(b, out, tau, iters)
+        ref = oracle.fgp(b.cpu().numpy().astype(np.float64), tau, iters)
+        assert _rel(out, torch.from_numpy(ref).cuda()) <= 1e-5, shape
+    b = _image((40, 33), 5)
+    for tau, iters in [(0.0, 10), (-1.0, 10), (0.5, 0)]:
+        out = torch.full_like(b, float("nan"))
+        B.bsgdtv_tv_prox_static(b, out, tau, iters)
+        assert torch.equal(out, b), (tau, iters)
+
+
+class _DefaultPool:
+    """High-water mark of the device's default stream-ordered memory pool
+    (the pool cudaMallocAsync draws from), read through the driver API."""
+    USED_MEM_HIGH = 8          # CU_MEMPOOL_ATTR_USED_MEM_HIGH
+
+    def __init__(self, device):
+        self.cu = ctypes.CDLL("libcuda.so.1")
+        dev = ctypes.c_int()
+        assert self.cu.cuDeviceGet(ctypes.byref(dev), device) == 0
+        self.pool = ctypes.c_void_p()
+        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+
+    def reset_high(self):
+        zero = ctypes.c_uint64(0)
+        assert self.cu.cuMemPoolSetAttribute(self.pool, self.USED_MEM_HIGH, ctypes.byref(zero)) == 0
+
+    def high(self):
+        v = ctypes.c_uint64()
+        assert self.cu.cuMemPoolGetAttribute(self.pool, self.USED_MEM_HIGH, ctypes.byref(v)) == 0
+        return v.value
+
+
+def test_static_prox_allocates_nothing(B):
+    """The defining property: after a first call (which may load the library's
+    device code, array included), further calls change neither the device's
+    free memory nor the default pool's high-water mark, while the allocating
+    entry point does raise that mark (so the probe can see an allocation)."""
+    b = _image((512, 512), 6)
+    out = torch.empty_like(b)
+    B.bsgdtv_tv_prox_static(b, out, 0.4, 30)
+    torch.cuda.synchronize()
+    pool = _DefaultPool(torch.cuda.current_device())
+    pool.reset_high()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        B.bsgdtv_tv_prox_static(b, out, 0.4, 30)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert pool.high() == 0
+    ref = torch.empty_like(b)
+    B.bsgdtv_tv_prox(b, ref, 0.4, 30)
+    assert pool.high() >= 8 * 512 * 512 * 4
+    assert torch.equal(out, ref)
 
 
 def test_static_prox_rejects_oversize(B):
