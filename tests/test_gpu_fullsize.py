@@ -78,7 +78,7 @@ def test_ellipse512_every_block_product(B, ellipse512):
     A = P.A
     M, N = wl.M, wl.N
     rng = np.random.default_rng(11)
-    x = (P.x_true + 0.1 * rng.standard_normal(A.cols_n)).astype(np.float32)
+    x = (P.x_true.ravel() + 0.1 * rng.standard_normal(A.cols_n)).astype(np.float32)
     r = (P.y - synth.csr_matvec(A, x.astype(np.float64))).astype(np.float32)
     with B.Reconstructor(A, (wl.n, wl.n), M, N, row_unit=wl.n_bins, col_unit=wl.n) as rec:
         zb = torch.zeros(N * A.rows, device="cuda")
