@@ -16,73 +16,107 @@ constexpr int RW = 64;      // region width  = threads in x
 constexpr int RH = 64;      // region height = TY threads in y x V pixels per thread
 constexpr int kMaxChunk = 8;  // iterations per launch when tiled (halo = chunk + 1)
 
-// Shared buffers are padded with a zero border so that neighbour reads need
-// no bounds tests: column c of the region is stored at c + 1, row -1 of the
-// strip-edge buffer and row RH of u are zero.
+// The neighbour values pass through shared buffers stored column by column
+// ([column + 1][row], column stride SC): a thread's strip of V = 4 pixels is
+// one 16-byte word, written and read with single 128-bit accesses.  SC = 68
+// floats makes 8 consecutive columns' words fall on distinct bank groups (no
+// conflicts).  Column 0 (left of the region) and RW + 1 (right of it) are
+// zero, as are row 0 of the strip-edge buffer and row TY of the strip-top
+// buffer, so neighbour reads need no bounds tests.
+constexpr int SC = RH + 4;
+static_assert(SC % 8 == 4, "column stride: 16-byte words of consecutive columns on distinct banks");
+
 template <int TY, int V>
 struct FgpShared {
-    static_assert(TY * V == RH, "a region is RH pixels high");
-    float s[RH][RW + 2];        // s of the momentum point, read by the right neighbour
-    float u[RH + 1][RW + 2];    // u, read by the left and upper neighbours
+    static_assert(TY * V == RH && V == 4, "a region is RH pixels high, 4 per thread");
+    float s[RW + 2][SC];        // s of the momentum point, read by the right neighbour
+    float u[RW + 2][SC];        // u, read by the left neighbour
     float r_edge[TY + 1][RW];   // r of each strip's last pixel, read by the strip below
+    float u_top[TY + 1][RW];    // u of each strip's first pixel, read by the strip above
+};
+
+// Two-lane FP32 arithmetic (one instruction for two pixels; each lane rounds
+// exactly as the scalar operation would).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// A thread's 4 pixels as two pairs: pixels (0, 1) and (2, 3) of the strip.
+struct Strip {
+    float2 h[2];
+    __device__ __forceinline__ float get(int v) const { return (v & 1) ? h[v >> 1].y : h[v >> 1].x; }
+    __device__ __forceinline__ void set(int v, float a) {
+        if (v & 1)
+            h[v >> 1].y = a;
+        else
+            h[v >> 1].x = a;
+    }
 };
 
 // One FGP iteration for this thread's strip.  (p, q) hold the current dual
 // iterate and (pp, qp) the previous one; the new iterate is written over
 // (pp, qp), so the caller swaps the roles of the two register sets.
 //
-// The projection is applied jointly everywhere: where only p (last column) or
-// only q (last row) is defined, the other component is zeroed first, which
-// makes the joint projection exactly the single-component clip t/max(1,|t|);
-// outside the image both are zeroed.  rsqrtf(max(n2, 1)) is the scale
-// 1/max(1, sqrt(n2)).
-//
-// kStepRegs: the dual step 1/(8 tau) is held per pixel and component (cp, cq:
-// 1/(8 tau) where p / q is defined, else 0) instead of testing mask bits; at
-// the undefined places p, q and the momentum point are exactly 0 throughout,
-// so fmaf(d, 0, 0) = 0 gives the same bits as the masked form with two
-// instructions fewer per component (at 2V more registers).
-template <int TY, int V, bool kStepRegs>
-__device__ __forceinline__ void fgp_step(float (&p)[V], float (&pp)[V], float (&q)[V],
-                                         float (&qp)[V], const float (&bb)[V], unsigned pmask,
-                                         unsigned qmask, const float (&cp)[V],
-                                         const float (&cq)[V], float beta, float tau, float c8,
-                                         FgpShared<TY, V> &sh, int tx, int ty) {
-    float rr[V], ss[V], uu[V];
+// The projection is applied jointly everywhere: where only p (last row of the
+// image has no p) or only q is defined, the other component is exactly 0
+// throughout, because its dual step (cp or cq: 1/(8 tau) where the component
+// exists, else 0) keeps it there, and the joint projection then equals the
+// single-component clip t/max(1,|t|); outside the image b, p and q are all 0.
+// rsqrtf(max(n2, 1)) is the scale 1/max(1, sqrt(n2)).
+template <int TY, int V>
+__device__ __forceinline__ void fgp_step(Strip &p, Strip &pp, Strip &q, Strip &qp,
+                                         const Strip &bb, const Strip &cp, const Strip &cq,
+                                         float beta, float tau, FgpShared<TY, V> &sh, int tx,
+                                         int ty) {
+    const float2 beta2 = make_float2(beta, beta), ntau2 = make_float2(-tau, -tau);
+    Strip rr, ss, uu;
     // momentum point (r, s) from the last two iterates
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        rr[v] = fmaf(beta, p[v] - pp[v], p[v]);
-        ss[v] = fmaf(beta, q[v] - qp[v], q[v]);
-        sh.s[ty * V + v][tx + 1] = ss[v];
+    for (int k = 0; k < 2; ++k) {
+        rr.h[k] = fma2(beta2, sub2(p.h[k], pp.h[k]), p.h[k]);
+        ss.h[k] = fma2(beta2, sub2(q.h[k], qp.h[k]), q.h[k]);
     }
-    sh.r_edge[ty + 1][tx] = rr[V - 1];
+    *reinterpret_cast<float4 *>(&sh.s[tx + 1][ty * V]) =
+        make_float4(ss.h[0].x, ss.h[0].y, ss.h[1].x, ss.h[1].y);
+    sh.r_edge[ty + 1][tx] = rr.h[1].y;
     __syncthreads();
-    // u = b - tau L(r, s)
+    // u = b - tau L(r, s): r one row up, s one column left
+    {
+        const float4 sl = *reinterpret_cast<const float4 *>(&sh.s[tx][ty * V]);
+        const float r_up0 = sh.r_edge[ty][tx];
+        const float2 rup[2] = {make_float2(r_up0, rr.h[0].x), make_float2(rr.h[0].y, rr.h[1].x)};
+        const float2 sleft[2] = {make_float2(sl.x, sl.y), make_float2(sl.z, sl.w)};
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        const float r_up = (v > 0) ? rr[v - 1] : sh.r_edge[ty][tx];
-        const float s_left = sh.s[ty * V + v][tx];
-        uu[v] = fmaf(-tau, (rr[v] - r_up) + (ss[v] - s_left), bb[v]);
-        sh.u[ty * V + v][tx + 1] = uu[v];
+        for (int k = 0; k < 2; ++k)
+            uu.h[k] = fma2(ntau2, add2(sub2(rr.h[k], rup[k]), sub2(ss.h[k], sleft[k])), bb.h[k]);
     }
+    *reinterpret_cast<float4 *>(&sh.u[tx + 1][ty * V]) =
+        make_float4(uu.h[0].x, uu.h[0].y, uu.h[1].x, uu.h[1].y);
+    sh.u_top[ty][tx] = uu.h[0].x;
     __syncthreads();
-    // (P, Q) = L^T u, gradient step on the dual, projection onto the unit ball
+    // (P, Q) = L^T u (u one row down, one column right), gradient step on the
+    // dual, projection onto the unit ball
+    const float4 ur = *reinterpret_cast<const float4 *>(&sh.u[tx + 2][ty * V]);
+    const float u_dn3 = sh.u_top[ty + 1][tx];
+    const float2 udn[2] = {make_float2(uu.h[0].y, uu.h[1].x), make_float2(uu.h[1].y, u_dn3)};
+    const float2 urt[2] = {make_float2(ur.x, ur.y), make_float2(ur.z, ur.w)};
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        const float u_down = (v < V - 1) ? uu[v + 1] : sh.u[ty * V + V][tx + 1];
-        const float u_right = sh.u[ty * V + v][tx + 2];
-        float pt, qt;
-        if constexpr (kStepRegs) {
-            pt = fmaf(uu[v] - u_down, cp[v], rr[v]);
-            qt = fmaf(uu[v] - u_right, cq[v], ss[v]);
-        } else {
-            pt = (pmask & (1u << v)) ? fmaf(uu[v] - u_down, c8, rr[v]) : 0.f;
-            qt = (qmask & (1u << v)) ? fmaf(uu[v] - u_right, c8, ss[v]) : 0.f;
-        }
-        const float inv = rsqrtf(fmaxf(fmaf(pt, pt, qt * qt), 1.f));
-        pp[v] = pt * inv;
-        qp[v] = qt * inv;
+    for (int k = 0; k < 2; ++k) {
+        const float2 pt = fma2(sub2(uu.h[k], udn[k]), cp.h[k], rr.h[k]);
+        const float2 qt = fma2(sub2(uu.h[k], urt[k]), cq.h[k], ss.h[k]);
+        const float2 n2 = fma2(pt, pt, mul2(qt, qt));
+        const float2 inv = make_float2(rsqrtf(fmaxf(n2.x, 1.f)), rsqrtf(fmaxf(n2.y, 1.f)));
+        pp.h[k] = mul2(pt, inv);
+        qp.h[k] = mul2(qt, inv);
     }
 }
 
@@ -96,9 +130,8 @@ __device__ __forceinline__ void fgp_step(float (&p)[V], float (&pp)[V], float (&
 // kBatch: blockIdx.z selects one of several images stored `plane` floats
 // apart (b, x_out and the dual fields alike), each with its own weight
 // tau_z[z]; a weight <= 0 makes that image's prox the identity.
-// TY x V: threads in y x pixels per thread (TY * V = RH); kStepRegs: see
-// fgp_step.
-template <bool kBatch, int TY, int V, bool kStepRegs>
+// TY x V: threads in y x pixels per thread (TY * V = RH, V = 4).
+template <bool kBatch, int TY, int V>
 __global__ void __launch_bounds__(RW *TY)
     fgp_kernel(const float *__restrict__ b, float *__restrict__ x_out, int H, int W, float tau,
                float c8, const float *__restrict__ mom, int k0, int iters, int HL, int IH, int IW,
@@ -107,27 +140,25 @@ __global__ void __launch_bounds__(RW *TY)
                const float *__restrict__ qp_in, float *__restrict__ p_out,
                float *__restrict__ q_out, float *__restrict__ pp_out, float *__restrict__ qp_out,
                const float *__restrict__ tau_z, int64_t plane) {
-    __shared__ FgpShared<TY, V> sh;
+    __shared__ __align__(16) FgpShared<TY, V> sh;
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int R0 = blockIdx.y * IH - HL, C0 = blockIdx.x * IW - HL;
     const int j = C0 + tx;
     const bool col_in = (j >= 0 && j < W);
 
-    // zero borders (never written afterwards) and the masks
-    if (ty == 0) {
-        sh.r_edge[0][tx] = 0.f;
-        sh.u[RH][tx + 1] = 0.f;
-        if (tx == 0) sh.u[RH][0] = sh.u[RH][RW + 1] = 0.f;
-    }
-    if (tx == 0) {
+    // zero borders (never written afterwards): columns 0 and RW + 1, row 0
+    // of the strip-edge buffer, row TY of the strip-top buffer
+    if (tx < 2) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            sh.s[ty * V + v][0] = 0.f;
-            sh.u[ty * V + v][RW + 1] = 0.f;
-            sh.s[ty * V + v][RW + 1] = 0.f;
-            sh.u[ty * V + v][0] = 0.f;
+            sh.s[tx * (RW + 1)][ty * V + v] = 0.f;
+            sh.u[tx * (RW + 1)][ty * V + v] = 0.f;
         }
+    }
+    if (ty == 0) {
+        sh.r_edge[0][tx] = 0.f;
+        sh.u_top[TY][tx] = 0.f;
     }
     if constexpr (kBatch) {
         const int64_t off = (int64_t)blockIdx.z * plane;
@@ -144,7 +175,25 @@ __global__ void __launch_bounds__(RW *TY)
         tau = tau_z[blockIdx.z];
         c8 = 1.0f / (8.0f * tau);
     }
+    // b and the dual steps.  Every launch of one prox after the first starts
+    // only once the first has passed its wait on the kernel that wrote b, so
+    // those launches read b before their own wait (overlapping the previous
+    // launch's tail); the first reads it after.
+    Strip bb, cp, cq;
+    auto load_b = [&]() {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int i = R0 + ty * V + v;
+            const bool in = col_in && i >= 0 && i < H;
+            bb.set(v, in ? b[(int64_t)i * W + j] : 0.f);
+            // per-pixel dual steps: 1/(8 tau) where p (i < H-1) / q (j < W-1) exists
+            cp.set(v, (in && i < H - 1) ? c8 : 0.f);
+            cq.set(v, (in && j < W - 1) ? c8 : 0.f);
+        }
+    };
+    if (!first) load_b();
     pdl_wait_and_release();
+    if (first) load_b();
     if constexpr (kBatch) {
         if (!(tau > 0.f)) {   // block-uniform: zero weight, x = b
             if (!last) return;
@@ -159,60 +208,53 @@ __global__ void __launch_bounds__(RW *TY)
         }
     }
 
-    float bb[V], pa[V], pb[V], qa[V], qb[V];
-    unsigned pmask = 0u, qmask = 0u;   // bit v: p / q defined at this strip's pixel v
+    Strip pa, pb, qa, qb;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         const int i = R0 + ty * V + v;
         const bool in = col_in && i >= 0 && i < H;
-        if (in && i < H - 1) pmask |= 1u << v;
-        if (in && j < W - 1) qmask |= 1u << v;
         const int64_t o = (int64_t)i * W + j;
-        bb[v] = in ? b[o] : 0.f;
         if (first || !in) {
-            pa[v] = qa[v] = pb[v] = qb[v] = 0.f;
+            pa.set(v, 0.f);
+            qa.set(v, 0.f);
+            pb.set(v, 0.f);
+            qb.set(v, 0.f);
         } else {
-            pa[v] = p_in[o];
-            qa[v] = q_in[o];
-            pb[v] = pp_in[o];
-            qb[v] = qp_in[o];
+            pa.set(v, p_in[o]);
+            qa.set(v, q_in[o]);
+            pb.set(v, pp_in[o]);
+            qb.set(v, qp_in[o]);
         }
     }
 
-    float cp[V], cq[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-        cp[v] = (pmask & (1u << v)) ? c8 : 0.f;
-        cq[v] = (qmask & (1u << v)) ? c8 : 0.f;
-    }
-
+    // momentum coefficients are loaded one pair of iterations ahead, so the
+    // load's latency hides behind the iterations
     int it = 0;
+    float m0 = iters > 0 ? mom[k0] : 0.f, m1 = iters > 1 ? mom[k0 + 1] : 0.f;
     for (; it + 2 <= iters; it += 2) {
-        fgp_step<TY, V, kStepRegs>(pa, pb, qa, qb, bb, pmask, qmask, cp, cq, mom[k0 + it], tau, c8,
-                                   sh, tx, ty);
-        fgp_step<TY, V, kStepRegs>(pb, pa, qb, qa, bb, pmask, qmask, cp, cq, mom[k0 + it + 1], tau,
-                                   c8, sh, tx, ty);
+        const float n0 = it + 2 < iters ? mom[k0 + it + 2] : 0.f;
+        const float n1 = it + 3 < iters ? mom[k0 + it + 3] : 0.f;
+        fgp_step<TY, V>(pa, pb, qa, qb, bb, cp, cq, m0, tau, sh, tx, ty);
+        fgp_step<TY, V>(pb, pa, qb, qa, bb, cp, cq, m1, tau, sh, tx, ty);
+        m0 = n0;
+        m1 = n1;
     }
     if (it < iters) {
-        fgp_step<TY, V, kStepRegs>(pa, pb, qa, qb, bb, pmask, qmask, cp, cq, mom[k0 + it], tau, c8,
-                                   sh, tx, ty);
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const float t0 = pa[v], t1 = qa[v];
-            pa[v] = pb[v];
-            qa[v] = qb[v];
-            pb[v] = t0;
-            qb[v] = t1;
-        }
+        fgp_step<TY, V>(pa, pb, qa, qb, bb, cp, cq, m0, tau, sh, tx, ty);
+        const Strip t0 = pa, t1 = qa;
+        pa = pb;
+        qa = qb;
+        pb = t0;
+        qb = t1;
     }
     // (pa, qa): current iterate, (pb, qb): previous one
 
     if (last) {
         // x = b - tau L(p, q) with the final iterate
         __syncthreads();
-#pragma unroll
-        for (int v = 0; v < V; ++v) sh.s[ty * V + v][tx + 1] = qa[v];
-        sh.r_edge[ty + 1][tx] = pa[V - 1];
+        *reinterpret_cast<float4 *>(&sh.s[tx + 1][ty * V]) =
+            make_float4(qa.h[0].x, qa.h[0].y, qa.h[1].x, qa.h[1].y);
+        sh.r_edge[ty + 1][tx] = pa.get(V - 1);
         __syncthreads();
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -220,9 +262,9 @@ __global__ void __launch_bounds__(RW *TY)
             const int i = R0 + rr_;
             const bool interior = rr_ >= HL && rr_ < HL + IH && tx >= HL && tx < HL + IW;
             if (!(interior && col_in && i >= 0 && i < H)) continue;
-            const float p_up = (v > 0) ? pa[v - 1] : sh.r_edge[ty][tx];
-            const float q_left = sh.s[rr_][tx];
-            x_out[(int64_t)i * W + j] = bb[v] - tau * (pa[v] + qa[v] - p_up - q_left);
+            const float p_up = (v > 0) ? pa.get(v - 1) : sh.r_edge[ty][tx];
+            const float q_left = sh.s[tx][rr_];
+            x_out[(int64_t)i * W + j] = bb.get(v) - tau * (pa.get(v) + qa.get(v) - p_up - q_left);
         }
     } else {
 #pragma unroll
@@ -232,10 +274,10 @@ __global__ void __launch_bounds__(RW *TY)
             const bool interior = rr_ >= HL && rr_ < HL + IH && tx >= HL && tx < HL + IW;
             if (!(interior && col_in && i >= 0 && i < H)) continue;
             const int64_t o = (int64_t)i * W + j;
-            p_out[o] = pa[v];
-            q_out[o] = qa[v];
-            pp_out[o] = pb[v];
-            qp_out[o] = qb[v];
+            p_out[o] = pa.get(v);
+            q_out[o] = qa.get(v);
+            pp_out[o] = pb.get(v);
+            qp_out[o] = qb.get(v);
         }
     }
 }
@@ -253,11 +295,11 @@ inline const FgpFields &fgp_write_set(const FgpScratch &sc, int launch) { return
 // K FGP iterations: one launch when the image fits one region, else one
 // launch per chunk of <= kMaxChunk iterations over overlapping regions.
 // kBatch: `planes` images `plane` floats apart, weights tau_z[0 .. planes).
-// TY x V: the kernel's thread shape (see fgp_kernel).  16 x 4 (1024 threads,
-// 4-pixel strips, <= 64 registers) measured 1-3 % faster than 8 x 8 (512
-// threads, 8-pixel strips, 78 registers): twice the warps per SM hide the two
-// barriers of every iteration better; both give bit-identical iterates.
-template <bool kBatch, int TY = 16, int V = 4, bool kStepRegs = true>
+// TY x V: the kernel's thread shape (see fgp_kernel): 16 x 4, 1024 threads
+// with 4-pixel strips (an earlier 8 x 8 shape with 512 threads ran 1-3 %
+// slower: twice the warps per SM hide the two barriers of every iteration
+// better).
+template <bool kBatch, int TY = 16, int V = 4>
 cudaError_t launch_fgp_regions(const float *b, float *x, int h, int w, float tau,
                                const float *tau_z, int planes, int64_t plane, int iters,
                                const float *mom, FgpScratch sc, cudaStream_t s, bool pdl,
@@ -267,7 +309,7 @@ cudaError_t launch_fgp_regions(const float *b, float *x, int h, int w, float tau
     if (fits_one_region(h, w)) {
         // one launch, no field traffic (first and last)
         const FgpFields &f = sc.set[0];
-        cudaError_t e = launch_kernel(fgp_kernel<kBatch, TY, V, kStepRegs>, dim3(1, 1, planes), block, 0, s, pdl, b,
+        cudaError_t e = launch_kernel(fgp_kernel<kBatch, TY, V>, dim3(1, 1, planes), block, 0, s, pdl, b,
                                       x, h, w, tau, c8, mom, 0, iters, 0, RH, RW, 1, 1, f.p, f.q,
                                       f.pp, f.qp, f.p, f.q, f.pp, f.qp, tau_z, plane);
         add_launches(1);
@@ -281,7 +323,7 @@ cudaError_t launch_fgp_regions(const float *b, float *x, int h, int w, float tau
         const dim3 grid((w + IW - 1) / IW, (h + IH - 1) / IH, planes);
         const int first = (done == 0), last = (done + chunk == iters);
         const FgpFields &fi = fgp_read_set(sc, launch), &fo = fgp_write_set(sc, launch);
-        cudaError_t e = launch_kernel(fgp_kernel<kBatch, TY, V, kStepRegs>, grid, block, 0, s, pdl || done > 0, b, x,
+        cudaError_t e = launch_kernel(fgp_kernel<kBatch, TY, V>, grid, block, 0, s, pdl || done > 0, b, x,
                                       h, w, tau, c8, mom, done, chunk, HL, IH, IW, first, last,
                                       fi.p, fi.q, fi.pp, fi.qp, fo.p, fo.q, fo.pp, fo.qp, tau_z,
                                       plane);
