@@ -261,7 +261,9 @@ int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w
     };
 
     // ---------------------------------------------- pass 1: counts per pair
-    // pair_nnz: stored elements (each segment padded to a multiple of kGroup)
+    // pair_nnz: stored elements (each segment padded to a multiple of G)
+    const int G = group_size(fmt);
+    L.group = G;
     std::vector<int64_t> pair_nnz(n_pairs, 0), pair_seg(n_pairs, 0), pair_real(n_pairs, 0);
     // largest column sum of |a| (FP32 weights) within one row group: bounds the
     // fixed-point accumulation of the A^T r tile
@@ -286,7 +288,7 @@ int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w
             for (int32_t t : touched) {
                 ps[t]++;
                 pr[t] += cnt[t];
-                pn[t] += (int64_t)kGroup * ((cnt[t] + kGroup - 1) / kGroup);
+                pn[t] += (int64_t)G * ((cnt[t] + G - 1) / G);
                 cnt[t] = 0;
             }
             touched.clear();
@@ -366,17 +368,17 @@ int build_layout(HostLayout &L, int64_t rows, int64_t cols, int img_h, int img_w
                     L.seg_len[sl * kSlab + l] = (int32_t)slen[t][s0 + l];
                     maxlen = std::max<int>(maxlen, (int)slen[t][s0 + l]);
                 }
-                // column groups of kGroup elements: group kk holds elements
-                // [kGroup*kk, kGroup*kk + kGroup) of every lane whose segment is
-                // longer than kGroup*kk, in lane order; short tails are padded
-                // with zero weights aimed at the lane's private dummy word
-                const int maxg = (maxlen + kGroup - 1) / kGroup;
+                // column groups of G elements: group kk holds elements
+                // [G*kk, G*kk + G) of every lane whose segment is longer than
+                // G*kk, in lane order; short tails are padded with zero
+                // weights aimed at the lane's private dummy word
+                const int maxg = (maxlen + G - 1) / G;
                 for (int kk = 0; kk < maxg; ++kk)
                     for (int l = 0; l < lanes; ++l) {
                         const int64_t len = slen[t][s0 + l];
-                        if (len <= (int64_t)kGroup * kk) continue;
-                        for (int j = 0; j < kGroup; ++j) {
-                            const int64_t k = (int64_t)kGroup * kk + j;
+                        if (len <= (int64_t)G * kk) continue;
+                        for (int j = 0; j < G; ++j) {
+                            const int64_t k = (int64_t)G * kk + j;
                             if (k < len) {
                                 const int64_t src = sstart[t][s0 + l] + k;
                                 L.vals[out] = tv[src];
@@ -465,14 +467,15 @@ int verify_layout(const HostLayout &L, const int64_t *row_ptr, const int32_t *co
             maxlen = std::max(maxlen, len);
         }
         int64_t pos = L.slab_off[sl];
-        const int maxg = (maxlen + kGroup - 1) / kGroup;
+        const int G = L.group;
+        const int maxg = (maxlen + G - 1) / G;
         for (int kk = 0; kk < maxg; ++kk)
             for (int l = 0; l < kSlab; ++l) {
                 const int len = L.seg_len[sl * kSlab + l];
-                if (len <= kGroup * kk) continue;
-                for (int j = 0; j < kGroup; ++j, ++pos) {
+                if (len <= G * kk) continue;
+                for (int j = 0; j < G; ++j, ++pos) {
                     const int32_t loc = L.idx[pos];
-                    if (kGroup * kk + j >= len) {
+                    if (G * kk + j >= len) {
                         if (loc != kPadBase + l || L.vals[pos] != 0.0f)
                             return fail(BSGDTV_ERR_STATE, "bad padding entry");
                         continue;
@@ -483,7 +486,7 @@ int verify_layout(const HostLayout &L, const int64_t *row_ptr, const int32_t *co
                     per_row[L.seg_ray[sl * kSlab + l]].push_back({col, L.vals[pos]});
                 }
             }
-        if (pos % kGroup) return fail(BSGDTV_ERR_STATE, "slab not aligned");
+        if (pos % G) return fail(BSGDTV_ERR_STATE, "slab not aligned");
         if (pos != L.slab_off[sl + 1]) return fail(BSGDTV_ERR_STATE, "slab size mismatch");
     }
     for (int64_t r = 0; r < L.rows; ++r) {

@@ -16,15 +16,19 @@ namespace bsgdtv {
 // column-block band J_j) and the rows into groups (sub-ranges of the row blocks
 // I_i).  A work item is one (group, tile) pair.  Inside a work item every row
 // that touches the tile contributes one segment (its nonzeros in that tile).
-// Segments are packed 32 to a slab; a slab is stored in column groups of
-// kGroup elements (elements [4kk, 4kk+4) of every segment longer than 4kk, in
+// Segments are packed 32 to a slab; a slab is stored in column groups of G
+// elements (elements [G kk, G kk + G) of every segment longer than G kk, in
 // lane order, tails padded with zero weights), so that a warp reads it with
-// coalesced 16-byte loads, one lane per segment.
+// coalesced 16-byte loads, one lane per segment: G = 4 for FP32 weights,
+// G = 8 for 16-bit weights with 16-bit indices (16 bytes of weights and 16 of
+// indices per lane and group, the same registers per group as FP32 with
+// 32-bit indices and twice the nonzeros).
 constexpr int kTileH = 64;
 constexpr int kTileW = 64;
 constexpr int kTileStride = kTileW + 1;   // padded shared-memory row stride (floats)
 constexpr int kSlab = 32;
-constexpr int kGroup = 4;                            // elements per lane per vector load
+constexpr int kGroup = 4;                            // elements per lane per load (FP32 weights)
+constexpr int kGroup16 = 8;                          // the same for 16-bit weights
 constexpr int kPadBase = kTileH * kTileStride;        // per-lane dummy words for padding
 constexpr int kTileWords = kPadBase + kSlab;          // shared-memory words per tile array
 
@@ -56,6 +60,7 @@ struct HostLayout {
     std::vector<int32_t> slab_item;                 // [n_slabs] item index (storage order)
     std::vector<int32_t> seg_ray, seg_len;          // [n_slabs*32]
     int fmt = 0;                                    // BSGDTV_FMT_*
+    int group = kGroup;                             // elements per column group (group_size(fmt))
     std::vector<float> vals;                        // [stored] slab-ordered (as stored, in FP32)
     std::vector<int32_t> idx;                       // [stored] tile-local shared-memory word
     std::vector<uint16_t> vals16;                   // binary16 / bfloat16 bits (16-bit formats)
@@ -76,6 +81,8 @@ uint16_t double_to_half_bits(double v);
 uint16_t double_to_bf16_bits(double v);
 float stored_weight(double v, int fmt);
 int bytes_per_entry(int fmt);
+// Elements per column group of a slab for a stored format.
+inline int group_size(int fmt) { return (fmt == 2 || fmt == 3) ? kGroup16 : kGroup; }
 
 // Decodes the layout back into CSR and compares with the input (host check).
 int verify_layout(const HostLayout &L, const int64_t *row_ptr, const int32_t *col_idx,

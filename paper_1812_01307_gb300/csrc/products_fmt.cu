@@ -1,7 +1,8 @@
 // Fused block products of Algorithm 1 for A stored with 16-bit tile-local
 // indices and FP32, binary16 or bfloat16 weights (see products.cu for the
-// work decomposition; this kernel differs only in how a column group of four
-// entries is loaded and decoded, and in a deeper prefetch).
+// work decomposition; this kernel differs only in how a column group is
+// loaded and decoded: four entries with FP32 weights, eight with 16-bit
+// weights).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -16,46 +17,94 @@ namespace {
 
 using namespace prod;
 
-// Stored formats of one column group (four entries of one lane's segment).
+// Stored formats of one column group (kN entries of one lane's segment):
+// FP32 weights with 16-bit indices in groups of 4 (16 + 8 bytes per lane),
+// 16-bit weights with 16-bit indices in groups of 8 (16 + 16 bytes per lane:
+// the registers of one FP32 + 32-bit-index group for twice the entries).
+// kDepth: column groups loaded ahead of the one in use.
 template <int FMT> struct GroupFmt;
-// kDepth: column groups loaded ahead (3 - 4 KB of A in flight per warp; deeper
-// queues measured slower for the 16-bit weights).
 template <> struct GroupFmt<BSGDTV_FMT_F32_I16> {
+    static constexpr int kN = 4;
     static constexpr int kDepth = 4;
     using VT = float4;
     using IT = uint2;   // four 16-bit indices
-    static __device__ __forceinline__ void decode(const VT &v, const IT &i, float4 &w, int4 &k) {
-        w = v;
-        k = make_int4((int)(i.x & 0xFFFFu), (int)(i.x >> 16), (int)(i.y & 0xFFFFu), (int)(i.y >> 16));
+    static __device__ __forceinline__ void decode(const VT &v, const IT &i, float (&w)[kN], int (&k)[kN]) {
+        w[0] = v.x;
+        w[1] = v.y;
+        w[2] = v.z;
+        w[3] = v.w;
+        k[0] = (int)(i.x & 0xFFFFu);
+        k[1] = (int)(i.x >> 16);
+        k[2] = (int)(i.y & 0xFFFFu);
+        k[3] = (int)(i.y >> 16);
     }
 };
+__device__ __forceinline__ void unpack_idx8(const uint4 &i, int (&k)[8]) {
+    const unsigned u[4] = {i.x, i.y, i.z, i.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        k[2 * t] = (int)(u[t] & 0xFFFFu);
+        k[2 * t + 1] = (int)(u[t] >> 16);
+    }
+}
 template <> struct GroupFmt<BSGDTV_FMT_F16_I16> {
+    static constexpr int kN = 8;
     static constexpr int kDepth = 4;
-    using VT = uint2;   // four binary16 weights
-    using IT = uint2;
-    static __device__ __forceinline__ void decode(const VT &v, const IT &i, float4 &w, int4 &k) {
-        w = make_float4(__half2float(__ushort_as_half((unsigned short)(v.x & 0xFFFFu))),
-                        __half2float(__ushort_as_half((unsigned short)(v.x >> 16))),
-                        __half2float(__ushort_as_half((unsigned short)(v.y & 0xFFFFu))),
-                        __half2float(__ushort_as_half((unsigned short)(v.y >> 16))));
-        k = make_int4((int)(i.x & 0xFFFFu), (int)(i.x >> 16), (int)(i.y & 0xFFFFu), (int)(i.y >> 16));
+    using VT = uint4;   // eight binary16 weights
+    using IT = uint4;   // eight 16-bit indices
+    static __device__ __forceinline__ void decode(const VT &v, const IT &i, float (&w)[kN], int (&k)[kN]) {
+        const unsigned u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&u[t]));
+            w[2 * t] = f.x;
+            w[2 * t + 1] = f.y;
+        }
+        unpack_idx8(i, k);
     }
 };
 template <> struct GroupFmt<BSGDTV_FMT_BF16_I16> {
+    static constexpr int kN = 8;
     static constexpr int kDepth = 4;
-    using VT = uint2;   // four bfloat16 weights: the upper halves of FP32 values
-    using IT = uint2;
-    static __device__ __forceinline__ void decode(const VT &v, const IT &i, float4 &w, int4 &k) {
-        w = make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xFFFF0000u),
-                        __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xFFFF0000u));
-        k = make_int4((int)(i.x & 0xFFFFu), (int)(i.x >> 16), (int)(i.y & 0xFFFFu), (int)(i.y >> 16));
+    using VT = uint4;   // eight bfloat16 weights: the upper halves of FP32 values
+    using IT = uint4;
+    static __device__ __forceinline__ void decode(const VT &v, const IT &i, float (&w)[kN], int (&k)[kN]) {
+        const unsigned u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            w[2 * t] = __uint_as_float(u[t] << 16);
+            w[2 * t + 1] = __uint_as_float(u[t] & 0xFFFF0000u);
+        }
+        unpack_idx8(i, k);
     }
 };
+
+// Accumulation of one column group (see products_common.cuh): z partial in a
+// register, the A^T r contributions into the shared g tile.
+template <int N>
+__device__ __forceinline__ void use_entries(const float (&w)[N], const int (&k)[N], const float r2s,
+                                            const float *xs, int *gs, float &acc) {
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+        acc = fmaf(w[t], xs[k[t]], acc);
+        atomicAdd(gs + k[t], __float2int_rn(w[t] * r2s));
+    }
+}
+template <int N>
+__device__ __forceinline__ void use_entries(const float (&w)[N], const int (&k)[N], const double r2,
+                                            const double *xs, double *gs, double &acc) {
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+        acc += (double)w[t] * xs[k[t]];
+        atomicAdd(gs + k[t], (double)w[t] * r2);
+    }
+}
 
 template <typename X>
 __device__ __forceinline__ X zero_of();
 template <> __device__ __forceinline__ float4 zero_of<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 template <> __device__ __forceinline__ uint2 zero_of<uint2>() { return make_uint2(0u, 0u); }
+template <> __device__ __forceinline__ uint4 zero_of<uint4>() { return make_uint4(0u, 0u, 0u, 0u); }
 
 // T: type of x, r, z (float or double); G: shared g tile (int fixed point or
 // double); FMT: stored weight / index format.
@@ -104,14 +153,15 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             const int64_t seg = (int64_t)sl * kSlab + lane;
             const int len = d.seg_len[seg];
             const int ray = d.seg_ray[seg];
-            const int ng = (len + kGroup - 1) / kGroup;
+            constexpr int kN = GroupFmt<FMT>::kN;
+            const int ng = (len + kN - 1) / kN;
             const T r2 = (len > 0) ? T(2) * r[ray] * scale : T(0);
-            const int64_t base = d.slab_off[sl] / kGroup;
+            const int64_t base = d.slab_off[sl] / kN;
             const VT *V = V4 + base;
             const IT *I = I4 + base;
             const int maxg = __reduce_max_sync(0xffffffffu, ng);
             // kDepth column groups in flight ahead of the one in use
-            constexpr int kDepth = GroupFmt<FMT>::kDepth;
+            constexpr int kDepth = sizeof(T) == 4 ? GroupFmt<FMT>::kDepth : 2;   // FP64: setup only
             int off = 0;
             T acc = T(0);
             {
@@ -134,10 +184,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                     off += __popc(a);
                     if (ng > kk + kDepth) { vn = __ldcs(V + p); in_ = __ldcs(I + p); }
                     if (ng > kk) {
-                        float4 w;
-                        int4 k4;
-                        GroupFmt<FMT>::decode(vq[0], iq[0], w, k4);
-                        use_group(w, k4, r2, xs, gs, acc);
+                        float w[kN];
+                        int k[kN];
+                        GroupFmt<FMT>::decode(vq[0], iq[0], w, k);
+                        use_entries<kN>(w, k, r2, xs, gs, acc);
                     }
 #pragma unroll
                     for (int t = 0; t + 1 < kDepth; ++t) {
