@@ -46,10 +46,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-slices", type=int, default=64,
                     help="slices of the batched variant (many slices sharing one A); 0 skips it")
-    ap.add_argument("--served-requests", type=int, default=200,
-                    help="requests of the served stream (0 skips it)")
-    ap.add_argument("--served-full", action="store_true",
-                    help="include 1024x1024 requests (p = 0.1) in the served stream")
+    ap.add_argument("--served-requests", type=int, default=400,
+                    help="requests of the served stream (0 skips it); the configuration's stream has "
+                         "2000, the default times its first 400")
+    ap.add_argument("--served-small", action="store_true",
+                    help="leave the 1024x1024 requests (p = 0.1) out of the served stream")
     ap.add_argument("--served-budget-gb", type=float, default=64.0)
     ap.add_argument("--served-tick", type=int, default=10, help="max epochs between admissions")
     ap.add_argument("--no-variants", action="store_true",
@@ -164,18 +165,19 @@ def kernel_source_hash():
 # ------------------------------------------------------------- served stream
 def served_stream(args, B, synth):
     """Continuous batching under a Poisson stream of reconstruction requests:
-    image n in {128, 256, 512} (p = .4, .3, .2, renormalised; 1024 with p = .1
-    under --served-full), angles = round(0.7 n), bins = ceil(sqrt(2) n) + 1,
-    lambda ~ U(0.01, 0.1), epochs ~ U{100..300}, 30 FGP iterations, FP16
-    weights, A cached per geometry.  Phase 1 submits every request at once
-    (saturated throughput); phase 2 replays them with Poisson arrivals at 0.7x
-    that rate.  Latency = submit -> x in host memory."""
+    image n in {128, 256, 512, 1024} with p = .4, .3, .2, .1 (1024 left out,
+    the rest renormalised, under --served-small), angles = round(0.7 n), bins =
+    ceil(sqrt(2) n) + 1, lambda ~ U(0.01, 0.1), epochs ~ U{100..300}, 30 FGP
+    iterations, FP16 weights, A cached per geometry.  Phase 1 submits every
+    request at once (saturated throughput); phase 2 replays them with Poisson
+    arrivals at 0.7x that rate.  Latency = submit -> x in host memory."""
     import math
     import threading
 
     import numpy as np
-    sizes = [128, 256, 512] + ([1024] if args.served_full else [])
-    probs = np.array([0.4, 0.3, 0.2] + ([0.1] if args.served_full else []))
+    full = not getattr(args, "served_small", False)
+    sizes = [128, 256, 512] + ([1024] if full else [])
+    probs = np.array([0.4, 0.3, 0.2] + ([0.1] if full else []))
     probs = probs / probs.sum()
     ellipses = {128: 10, 256: 20, 512: 30, 1024: 40}
     K, N, pool = 30, args.served_requests, 8
@@ -187,8 +189,10 @@ def served_stream(args, B, synth):
     for n in sizes:
         na, nb = int(round(0.7 * n)), int(math.ceil(math.sqrt(2) * n)) + 1
         A = synth.parallel_beam_csr(n, na, nb)
-        with B.Reconstructor(A, (n, n), 1, 1) as rec:
-            u, _ = rec.estimate_umax(300, 1e-9)
+        # u_max of this geometry by the batch power iteration with the
+        # on-the-fly projector (no second stored copy of A)
+        with B.BatchReconstructor(None, (n, n), 1, parallel_beam=(na, nb)) as one:
+            u, _ = one.estimate_umax(300, 1e-9)
         gid = srv.add_geometry(A, (n, n), 0.9 / (2 * u), slots=32, fmt=B.FMT_F16_I16, prewarm=0)
         ys = [synth.noisy_projections(A, synth.phantom(n, ellipses[n], s), s).astype(np.float32)
               for s in range(pool)]
@@ -232,7 +236,9 @@ def served_stream(args, B, synth):
     srv.close()
     slice_epochs = sum(r[3] for r in reqs)
     mix = {str(n): int(sum(1 for r in reqs if r[0] == n)) for n in sizes}
-    return {"requests": N, "mix": mix, "fgp_iters": K, "epochs": "U{100..300}", "lambda": "U(0.01,0.1)",
+    return {"requests": N, "stream": ("the first %d requests of the 2000-request served stream" % N
+                                       if full else "%d requests without the 1024x1024 ones" % N),
+            "mix": mix, "fgp_iters": K, "epochs": "U{100..300}", "lambda": "U(0.01,0.1)",
             "weights": "f16", "slots_per_group": 32, "hbm_budget_gb": args.served_budget_gb,
             "max_tick_epochs": args.served_tick,
             "saturated": {"requests_per_s": sat_rps, "slice_epochs_per_s": slice_epochs / span_sat,

@@ -444,12 +444,14 @@ int bsgdtv_batch_get_slice_x(bsgdtv_batch_t h, int b, float *x, int out_on_devic
  * between 4 and the geometry's maximum, sized by the requests of that
  * geometry then waiting: a short queue gets small groups with short epochs
  * (low latency), a long queue large groups that read A once for many slices
- * (throughput).  A request is
- * admitted into a free slot as soon as one exists (between the group's
- * ticks), keeps its x, r and FGP state on the device, and leaves when its
- * budget of epochs is done; its x is then copied to host memory.  One worker
- * thread inside the server drives the device; groups run on their own
- * streams and overlap.  Admission keeps the device bytes (every A plus the
+ * (throughput).  A request is admitted into a free slot as soon as one
+ * exists, also while its group runs: the worker posts it in the slot's
+ * mailbox (host-mapped memory) and a slot scheduler kernel at the start of
+ * every epoch admits it on the device, counts its epochs, and when its budget
+ * is done writes its x to host memory and publishes a completion record.
+ * Its x, r and FGP state stay on the device meanwhile.  One worker thread
+ * inside the server keeps every busy group's stream fed with runs of epochs;
+ * groups run on their own streams and overlap.  Admission keeps the device bytes (every A plus the
  * groups' vectors, bsgdtv_batch_device_bytes) within the budget, releasing
  * idle groups of other geometries first.  Every request runs Algorithm 1
  * exactly as a batch slice does: its result does not depend on the other
@@ -460,8 +462,9 @@ typedef struct bsgdtv_server_ctx *bsgdtv_server_t;
 
 /* Starts a server on the current device.  hbm_budget_bytes bounds the device
  * bytes of all geometries and groups; fgp_iters is the FGP iteration count of
- * every prox; max_tick_epochs caps the epochs a group runs between
- * admissions. */
+ * every prox; max_tick_epochs caps the epochs of one run the worker enqueues
+ * on a group (admissions and completions happen at every epoch boundary on
+ * the device, whatever the run length). */
 int bsgdtv_server_create(bsgdtv_server_t *out, int64_t hbm_budget_bytes, int fgp_iters,
                          int max_tick_epochs);
 
@@ -490,8 +493,9 @@ int bsgdtv_server_submit(bsgdtv_server_t s, int geom_id, const float *y, double 
 int bsgdtv_server_poll(bsgdtv_server_t s, int64_t request_id, int *state);
 
 /* Cancels a request that has not ended.  A queued one is cancelled at once;
- * a running one keeps its state "running" until its group's current tick
- * (at most max_tick_epochs epochs) ends, then gives up its slot unread.
+ * a running one keeps its state "running" until the device's slot scheduler
+ * sees the cancellation at its group's next epoch boundary and empties the
+ * slot (its x is not returned).
  * bsgdtv_server_wait on a cancelled request returns BSGDTV_ERR_CANCELLED and
  * forgets it.  BSGDTV_ERR_STATE if the request is done, failed or cancelled
  * (state 2, 3 or 4); BSGDTV_ERR_INVALID_ARG for an unknown (or already waited-for)
@@ -506,9 +510,20 @@ int bsgdtv_server_cancel(bsgdtv_server_t s, int64_t request_id);
 int bsgdtv_server_wait(bsgdtv_server_t s, int64_t request_id, double timeout_s, float *x,
                        double *times);
 
-/* stats [13]: submitted, completed, failed, queued, running, groups, device
- * bytes in use (operators and groups), most requests running at once, ticks, epochs run by
- * groups, slice-epochs of requests, groups created, cancelled. */
+/* Arms an idle group of the geometry (made if none exists and the budget
+ * allows): one epoch is launched at once whose slot scheduler waits on the
+ * device, polling the group's mailboxes, for up to wait_s seconds (0 <=
+ * wait_s <= 1) for a request to be posted, so that a request submitted
+ * meanwhile starts without waiting for a host launch.  Blocks until that
+ * device-side wait has ended: BSGDTV_OK if a request arrived (it then runs as
+ * usual), BSGDTV_ERR_TIMEOUT if the wait ran out with no request (the epoch
+ * then ran on empty slots).  A serving feature; the paper has none. */
+int bsgdtv_server_arm(bsgdtv_server_t s, int geom_id, double wait_s);
+
+/* stats [15]: submitted, completed, failed, queued, running, groups, device
+ * bytes in use (operators and groups), most requests running at once, runs
+ * of epochs launched, epochs run by groups, slice-epochs of requests, groups
+ * created, cancelled, armed epochs, armed waits that timed out. */
 int bsgdtv_server_stats(bsgdtv_server_t s, int64_t *stats);
 
 #ifdef __cplusplus

@@ -88,6 +88,7 @@ def load(path: str | None = None):
         "bsgdtv_server_cancel": (I32, [P, I64]),
         "bsgdtv_server_wait": (I32, [P, I64, D, P, P]),
         "bsgdtv_server_stats": (I32, [P, P]),
+        "bsgdtv_server_arm": (I32, [P, I32, D]),
         "bsgdtv_launch_count": (I64, []),
         "bsgdtv_last_error": (ctypes.c_char_p, []),
         "bsgdtv_strerror": (ctypes.c_char_p, [I32]),
@@ -114,6 +115,7 @@ def exported_symbols():
             "bsgdtv_batch_get_slice_x", "bsgdtv_batch_device_bytes", "bsgdtv_server_create",
             "bsgdtv_server_destroy", "bsgdtv_server_add_geometry", "bsgdtv_server_submit",
             "bsgdtv_server_poll", "bsgdtv_server_cancel", "bsgdtv_server_wait", "bsgdtv_server_stats",
+            "bsgdtv_server_arm",
             "bsgdtv_batch_create_parallel_beam", "bsgdtv_mf_ray_weights", "bsgdtv_batch_estimate_umax",
             "bsgdtv_batch_project", "bsgdtv_batch_autotune", "bsgdtv_batch_set_tuning", "bsgdtv_operator_create_csr",
             "bsgdtv_operator_destroy", "bsgdtv_batch_create_from_operator",
@@ -643,7 +645,8 @@ def bsgdtv_server_wait(h, request_id, out=None, timeout_s=-1.0):
 
 
 SERVER_STATS = ["submitted", "completed", "failed", "queued", "running", "groups", "device_bytes",
-                "max_running", "ticks", "epochs_run", "slice_epochs", "groups_made", "cancelled"]
+                "max_running", "ticks", "epochs_run", "slice_epochs", "groups_made", "cancelled",
+                "armed_epochs", "wait_timeouts"]
 
 
 def bsgdtv_server_stats(h):
@@ -865,3 +868,9 @@ class Server:
 
     def stats(self):
         return bsgdtv_server_stats(self.h)
+
+    def arm(self, geom_id, wait_s):
+        """Arms an idle group of the geometry for wait_s seconds (device-side
+        wait); raises BsgdtvError with code BSGDTV_ERR_TIMEOUT if no request
+        arrived meanwhile."""
+        _check(load().bsgdtv_server_arm(self.h, int(geom_id), float(wait_s)), "bsgdtv_server_arm")

@@ -274,6 +274,176 @@ cudaError_t launch_transpose(const float *in, float *out, int64_t n, int B, int 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------ served mode: slot scheduler
+// Loads and stores of host-mapped memory with system scope.
+__device__ __forceinline__ int ld_acquire_sys(const int *p) {
+    int v;
+    asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed_sys(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ long long ld_relaxed_sys64(const long long *p) {
+    long long v;
+    asm volatile("ld.relaxed.sys.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(int *p, int v) {
+    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Device slot state, [4][B] + 1: admitted seq, epochs still to run, live
+// flag, epochs run so far; then the count of epochs the group has run.  acts [B + 1]: this epoch's actions (slot | kind << 24),
+// their count last.
+enum ServeAct { kActAdmit = 1, kActRetire = 2 };
+constexpr int kServeThreads = 256;
+
+// One CTA at the start of every served epoch.  (1) An armed epoch with no
+// live slot and no posted admission waits, bounded by ctrl->wait_ns, for a
+// mailbox to change.  (2) Per slot: a new seq admits (state latched from the
+// mailbox); a live slot whose budget is spent or that was cancelled retires
+// (tau = 0 from here on); every live slot then counts this epoch.
+__global__ void __launch_bounds__(kServeThreads)
+    serve_decide_kernel(const ServeSlot *mb, ServeDone *done, ServeCtrl *ctrl, int *state,
+                        int *acts, float *tau, int *arm_seen, int B) {
+    int *seq_s = state, *rem = state + B, *live = state + 2 * B, *ran = state + 3 * B;
+    const int epoch = state[4 * B];   // index of this epoch in the group's sequence
+    __shared__ int n_act;
+    if (threadIdx.x == 0) {
+        n_act = 0;
+        const int arm = ld_relaxed_sys(&ctrl->arm_seq);
+        if (arm != *arm_seen) {
+            *arm_seen = arm;
+            long long wait = ld_relaxed_sys64(&ctrl->wait_ns);
+            wait = wait < 0 ? 0 : (wait > kServeMaxWaitNs ? kServeMaxWaitNs : wait);
+            const unsigned long long t0 = global_ns();
+            int status = 1;
+            for (;;) {
+                bool work = false;
+                for (int b = 0; b < B && !work; ++b)
+                    work = live[b] || ld_relaxed_sys(&mb[b].seq) != seq_s[b];
+                if (work) {
+                    status = 0;
+                    break;
+                }
+                if ((long long)(global_ns() - t0) > wait) break;   // bounded: the wait ran out
+                __nanosleep(2000);
+            }
+            ctrl->status = status;
+            __threadfence_system();
+            st_release_sys(&ctrl->status_seq, arm);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        const int seq = ld_acquire_sys(&mb[b].seq);
+        int act = 0;
+        if (seq != seq_s[b]) {
+            seq_s[b] = seq;
+            rem[b] = ld_relaxed_sys(&mb[b].epochs);
+            tau[b] = __int_as_float(ld_relaxed_sys(reinterpret_cast<const int *>(&mb[b].tau)));
+            live[b] = 1;
+            ran[b] = 0;
+            act = kActAdmit;
+            done[b].picked_epoch = epoch;
+            __threadfence_system();
+            st_release_sys(&done[b].picked_seq, seq);
+        } else if (live[b] && (rem[b] <= 0 || ld_relaxed_sys(&mb[b].cancel) == seq)) {
+            live[b] = 0;
+            tau[b] = 0.f;
+            act = kActRetire;
+        }
+        if (live[b]) {
+            rem[b]--;
+            ran[b]++;
+        }
+        if (act) acts[atomicAdd(&n_act, 1)] = b | (act << 24);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        acts[B] = n_act;
+        state[4 * B] = epoch + 1;
+    }
+}
+
+constexpr int kServeUnroll = 8;                               // elements per thread per unit
+constexpr int kServeChunk = kServeThreads * kServeUnroll;    // vector elements per work unit
+
+// Applies this epoch's actions, work units (action, chunk of the slot's
+// vectors) spread over a fixed grid.  Admit: Y_b = R_b = y (from the slot's
+// pinned staging row in host memory; each thread issues all its loads before
+// its stores, so a unit has kServeChunk reads in flight), X_b = 0.  Retire:
+// the slot's x to its pinned result row, then Y_b = X_b = R_b = 0; the last
+// unit of a retiring slot publishes the completion record (after every
+// unit's stores are visible to the host).
+__global__ void __launch_bounds__(kServeThreads)
+    serve_apply_kernel(const int *__restrict__ acts, const int *__restrict__ state,
+                       const float *__restrict__ ypin, float *__restrict__ xpin, ServeDone *done,
+                       int *unit_cnt, float *__restrict__ Y, float *__restrict__ X,
+                       float *__restrict__ R, int64_t rows, int64_t cols, int Bp, int B) {
+    const int n_act = acts[B];
+    if (n_act == 0) return;
+    const int64_t n = rows > cols ? rows : cols;
+    const int chunks = (int)((n + kServeChunk - 1) / kServeChunk);
+    for (int64_t w = blockIdx.x; w < (int64_t)n_act * chunks; w += gridDim.x) {
+        const int a = acts[w / chunks];
+        const int b = a & 0xFFFFFF, kind = a >> 24;
+        const int64_t i0 = (w % chunks) * (int64_t)kServeChunk + threadIdx.x;
+        float v[kServeUnroll];
+        if (kind == kActAdmit) {
+#pragma unroll
+            for (int k = 0; k < kServeUnroll; ++k) {
+                const int64_t i = i0 + (int64_t)k * kServeThreads;
+                v[k] = i < rows ? __ldcv(ypin + (int64_t)b * rows + i) : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < kServeUnroll; ++k) {
+                const int64_t i = i0 + (int64_t)k * kServeThreads;
+                if (i < rows) {
+                    Y[i * Bp + b] = v[k];
+                    R[i * Bp + b] = v[k];
+                }
+                if (i < cols) X[i * Bp + b] = 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kServeUnroll; ++k) {
+                const int64_t i = i0 + (int64_t)k * kServeThreads;
+                v[k] = i < cols ? X[i * Bp + b] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < kServeUnroll; ++k) {
+                const int64_t i = i0 + (int64_t)k * kServeThreads;
+                if (i < cols) {
+                    xpin[(int64_t)b * cols + i] = v[k];
+                    X[i * Bp + b] = 0.f;
+                }
+                if (i < rows) {
+                    Y[i * Bp + b] = 0.f;
+                    R[i * Bp + b] = 0.f;
+                }
+            }
+            __threadfence_system();
+            __syncthreads();
+            if (threadIdx.x == 0 && atomicAdd(unit_cnt + b, 1) == chunks - 1) {
+                unit_cnt[b] = 0;
+                done[b].epochs_run = state[3 * B + b];
+                __threadfence_system();
+                st_release_sys(&done[b].seq, state[b]);
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // Power iteration helpers on slice 0 of interleaved [n][Bp] vectors:
 // per-block FP64 partial sums of a*b (fixed grid, summed on the host in block
 // order), and v = s * w written to slice 0 (the other slices stay zero).
@@ -369,6 +539,18 @@ struct bsgdtv_batch_ctx {
     std::vector<cudaEvent_t> tevents;
     int graph_fgp_iters = -1;
     int64_t graph_kernels = 0;
+    // served mode (batch_serve_enable): host-mapped mailboxes, completion
+    // records, control block and staging rows (host / device addresses; the
+    // memory is the caller's), device slot state, action list, per-slot unit
+    // counters
+    bool served = false;
+    ServeView view = {};
+    ServeSlot *mb_d = nullptr;
+    ServeDone *done_d = nullptr;
+    ServeCtrl *ctrl_d = nullptr;
+    float *ypin_d = nullptr, *xpin_d = nullptr;
+    int *slot_state = nullptr, *acts = nullptr, *unit_cnt = nullptr, *arm_seen = nullptr;
+    int serve_grid = 1;   // CTAs of the apply kernel (2 per SM)
 };
 
 namespace {
@@ -437,6 +619,16 @@ int fgp_group_by_budget(const bsgdtv_batch_ctx *h) {
 int benqueue_epoch(bsgdtv_batch_ctx *h, int par, int fgp_iters, cudaStream_t s,
                    cudaEvent_t *marks) {
     const bool prox = any_prox(h, fgp_iters);
+    if (h->served) {
+        // the slot scheduler: admissions and retirements at this epoch boundary
+        serve_decide_kernel<<<1, kServeThreads, 0, s>>>(h->mb_d, h->done_d, h->ctrl_d, h->slot_state,
+                                                        h->acts, h->tau, h->arm_seen, h->B);
+        serve_apply_kernel<<<h->serve_grid, kServeThreads, 0, s>>>(
+            h->acts, h->slot_state, h->ypin_d, h->xpin_d, h->done_d, h->unit_cnt, h->Y, h->X,
+            h->R[par], h->rows, h->cols, h->Bp, h->B);
+        add_launches(2);
+        BSG_CUDA(cudaGetLastError());
+    }
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[0], s, cudaEventRecordExternal));
     if (h->matrix_free) {
         BSG_CUDA(launch_mf_pass(true, h->Bp, h->mfg, h->X, h->Y, h->R[1 - par], 0.f, s));
@@ -765,6 +957,71 @@ int batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_device, do
     const bool prox_before = any_prox(h, 1);
     h->lambdas[b] = lam;
     if (any_prox(h, 1) != prox_before) bdrop_graphs(h);   // the epoch gains or loses its prox
+    return BSGDTV_OK;
+}
+
+namespace {
+struct ServeLayout {
+    size_t mb, done, ctrl, y, x, total;
+};
+ServeLayout serve_layout(int B, int64_t rows, int64_t cols) {
+    auto up256 = [](size_t v) { return (v + 255) / 256 * 256; };
+    ServeLayout L;
+    L.mb = 0;
+    L.done = up256(L.mb + (size_t)B * sizeof(ServeSlot));
+    L.ctrl = up256(L.done + (size_t)B * sizeof(ServeDone));
+    L.y = up256(L.ctrl + sizeof(ServeCtrl));
+    L.x = up256(L.y + (size_t)B * rows * sizeof(float));
+    L.total = up256(L.x + (size_t)B * cols * sizeof(float));
+    return L;
+}
+}  // namespace
+
+size_t batch_serve_host_bytes(int B, int64_t rows, int64_t cols) {
+    return serve_layout(B, rows, cols).total;
+}
+
+int batch_serve_enable(bsgdtv_batch_t h, ServeView *view, void *host_block) {
+    if (!h || !view || !host_block) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    if (!h->has_data) return fail(BSGDTV_ERR_STATE, "served mode before set_data");
+    if (h->served) return fail(BSGDTV_ERR_STATE, "batch already served");
+    if (h->B > 0xFFFFFF) return fail(BSGDTV_ERR_INVALID_ARG, "too many slots for served mode");
+    BSG_CUDA(cudaSetDevice(h->device));
+    const int B = h->B;
+    const ServeLayout lay = serve_layout(B, h->rows, h->cols);
+    void *hp = host_block;
+    std::memset(hp, 0, lay.y);   // mailboxes, records and control start at zero
+    void *dp = nullptr;
+    BSG_CUDA(cudaHostGetDevicePointer(&dp, hp, 0));
+    unsigned char *hb = static_cast<unsigned char *>(hp), *db = static_cast<unsigned char *>(dp);
+    h->view.mb = reinterpret_cast<ServeSlot *>(hb + lay.mb);
+    h->view.done = reinterpret_cast<ServeDone *>(hb + lay.done);
+    h->view.ctrl = reinterpret_cast<ServeCtrl *>(hb + lay.ctrl);
+    h->view.ypin = reinterpret_cast<float *>(hb + lay.y);
+    h->view.xpin = reinterpret_cast<float *>(hb + lay.x);
+    h->view.rows = h->rows;
+    h->view.cols = h->cols;
+    h->view.B = B;
+    h->mb_d = reinterpret_cast<ServeSlot *>(db + lay.mb);
+    h->done_d = reinterpret_cast<ServeDone *>(db + lay.done);
+    h->ctrl_d = reinterpret_cast<ServeCtrl *>(db + lay.ctrl);
+    h->ypin_d = reinterpret_cast<float *>(db + lay.y);
+    h->xpin_d = reinterpret_cast<float *>(db + lay.x);
+    BSG_CHECK(balloc(h, &h->slot_state, (size_t)4 * B + 1));
+    BSG_CHECK(balloc(h, &h->acts, (size_t)B + 1));
+    BSG_CHECK(balloc(h, &h->unit_cnt, (size_t)B));
+    BSG_CHECK(balloc(h, &h->arm_seen, 1));
+    BSG_CUDA(cudaMemsetAsync(h->slot_state, 0, ((size_t)4 * B + 1) * sizeof(int), h->stream));
+    BSG_CUDA(cudaMemsetAsync(h->acts, 0, ((size_t)B + 1) * sizeof(int), h->stream));
+    BSG_CUDA(cudaMemsetAsync(h->unit_cnt, 0, (size_t)B * sizeof(int), h->stream));
+    BSG_CUDA(cudaMemsetAsync(h->arm_seen, 0, sizeof(int), h->stream));
+    BSG_CUDA(cudaStreamSynchronize(h->stream));
+    int sms = 1;
+    BSG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    h->serve_grid = 2 * std::max(sms, 1);
+    h->served = true;
+    bdrop_graphs(h);   // the epochs gain the scheduler
+    *view = h->view;
     return BSGDTV_OK;
 }
 

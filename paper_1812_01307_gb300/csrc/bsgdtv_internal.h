@@ -188,6 +188,66 @@ void fgp_momentum_host(int iters, std::vector<float> &mom);
 // slots that come and go do not force the epoch graphs to be captured again.
 void batch_keep_prox(bsgdtv_batch_t h, bool on);
 
+// ------------------------------------------------ served mode of a batch
+// A batch in served mode runs, at the start of every epoch, a device-side
+// slot scheduler: it reads per-slot mailboxes in host-mapped memory that the
+// host fills at any time (an admission: y in the slot's pinned staging row,
+// tau = mu*lambda, an epoch budget; or a cancellation), resets admitted slots
+// (y, r^{-1} = y, x = 0), counts every live slot's epochs, and when a slot's
+// budget is spent writes its x to the slot's pinned result row and publishes
+// a completion record.  Requests therefore join and leave at epoch
+// boundaries while the host keeps the group's stream fed with epochs.
+// Host-written mailbox of one slot (host-mapped).  The host fills epochs and
+// tau (and y) first, then publishes by storing a new seq.
+struct ServeSlot {
+    int seq;      // bumped by the host for every admission into this slot
+    int epochs;   // epoch budget of the admitted request
+    float tau;    // mu * lambda of the admitted request
+    int cancel;   // == seq: end the request at the next epoch boundary
+};
+// Device-written records of one slot (host-mapped): seq of the request whose
+// x is in the slot's result row and the epochs it ran; seq of the last
+// admission the device picked up and the index of the epoch that picked it
+// up (the group's epochs count from 0), from which the host knows exactly
+// how many more epochs the request needs.
+struct ServeDone {
+    int seq;
+    int epochs_run;
+    int picked_seq;
+    int picked_epoch;
+};
+// Control block (host-mapped).  An armed epoch (arm_seq changed) whose slots
+// are all idle waits on the device, polling the mailboxes, up to wait_ns for
+// an admission; it then stores status (0: work arrived, 1: the wait ran out)
+// and status_seq = arm_seq.
+struct ServeCtrl {
+    long long wait_ns;
+    int arm_seq;
+    int status_seq;
+    int status;
+    int pad_[3];
+};
+constexpr long long kServeMaxWaitNs = 1000000000ll;   // longest device-side wait (1 s)
+// Host view of a served batch's mapped memory.
+struct ServeView {
+    ServeSlot *mb;
+    ServeDone *done;
+    ServeCtrl *ctrl;
+    float *ypin;   // [B][rows] staging rows of admitted y
+    float *xpin;   // [B][cols] result rows of retired slots
+    int64_t rows, cols;
+    int B;
+};
+// Bytes of host-mapped memory a served batch of B slots needs (mailboxes,
+// records, control block, staging and result rows).
+size_t batch_serve_host_bytes(int B, int64_t rows, int64_t cols);
+// Switches a batch (which has data, e.g. all-zero slots) into served mode:
+// host_block is mapped pinned memory (cudaHostAlloc with
+// cudaHostAllocMapped) of at least batch_serve_host_bytes bytes, owned by
+// the caller and kept until the batch is destroyed; allocates the device slot
+// state; the epoch graphs gain the scheduler.  Slots start empty.
+int batch_serve_enable(bsgdtv_batch_t h, ServeView *view, void *host_block);
+
 // batch.cu: bsgdtv_batch_set_slice, with check = false for a host y the
 // caller has already checked for NaN/Inf (no device check, no wait).
 int batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_device, double lambda,

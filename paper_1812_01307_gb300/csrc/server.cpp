@@ -2,23 +2,31 @@
 //
 // Requests (projections y of a registered geometry, a TV weight lambda and an
 // epoch budget) arrive at any time.  Each geometry owns one or more batch
-// groups: a batch handle (one shared A, `slots` slices) on its own stream.  A
-// request is admitted into a free slot of a group of its geometry as soon as
-// one exists; a new group is created only while the device bytes of all
-// groups stay within the HBM budget, and an idle group of another geometry
-// is released to make room.  Admitted requests keep their x, r and FGP state
-// on the device in their slot.
+// groups: a batch handle (one shared A, `slots` slices) in served mode on its
+// own stream.  A geometry's A is stored once; a new group is created only
+// while the device bytes of all groups stay within the HBM budget, and an
+// idle group of another geometry is released to make room.
 //
-// One worker thread drives the device.  Every group with occupied slots runs
-// a "tick" of E epochs, E = the smallest remaining budget among its slots
-// (capped), as one sequence of captured epoch graphs on the group's stream,
-// so the groups of different geometries overlap on the GPU.  When a tick
-// ends, finished requests are copied out (x to host memory: the end of their
-// latency) and their slots are emptied; queued requests are admitted between
-// ticks.  A slice's arithmetic never depends on the other slots, so a
-// request's result is the same alone and in any mix.  A cancelled request
-// leaves the queue at once, or gives up its slot when its group's current
-// tick ends.
+// Admission, epoch counting and retirement run on the device.  Every epoch of
+// a served group starts with a slot scheduler kernel that reads the group's
+// mailboxes in host-mapped memory: the worker thread admits a request by
+// copying y into the slot's pinned staging row and posting (tau, epochs, a
+// new sequence number) in the slot's mailbox, at any time, also while the
+// group is running; the device resets the slot at the next epoch boundary,
+// counts the request's epochs, and after the last one writes x into the
+// slot's pinned result row and publishes a completion record, which the
+// worker picks up (x in host memory: the end of the request's latency) to
+// free the slot.  So requests join and leave at epoch boundaries while the
+// worker only keeps each busy group's stream fed with runs of epochs (at
+// most two runs in flight per group).  Groups of different geometries run
+// concurrently on their streams.  A slice's arithmetic never depends on the
+// other slots, so a request's result is the same alone and in any mix.
+//
+// An armed epoch (bsgdtv_server_arm) is launched on an idle group before any
+// request is there: its scheduler waits on the device, polling the
+// mailboxes, for at most the requested time; a request submitted meanwhile
+// starts at once without a host launch, and a wait that runs out ends the
+// epoch with a timeout status.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -60,14 +68,24 @@ struct Request {
     Clock::time_point t_submit, t_admit, t_done;
 };
 
+constexpr int kMaxRuns = 2;     // runs of epochs in flight per group
+
 struct Group {
     int geom = 0;
     bsgdtv_batch_t batch = nullptr;
     cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
+    bsgdtv::ServeView view = {};     // host-mapped mailboxes, records, staging rows
+    void *pinned = nullptr;          // the block behind view (from the server's pool)
     std::vector<int64_t> slot_req;   // request id per slot, -1 = free
-    bool busy = false;
-    int tick = 0;
+    std::vector<int> slot_seq;       // last sequence number posted per slot
+    std::vector<int64_t> slot_end;   // epochs the group must have run to retire the slot's
+                                     // request (known once the device picked it up; -1 before)
+    int64_t enq = 0;                 // epochs enqueued on the group since it was made
+    cudaEvent_t run_ev[kMaxRuns] = {};
+    int run_len[kMaxRuns] = {};
+    int runs = 0;                    // runs in flight (run_ev[0 .. runs) in launch order)
+    int arm_seq = 0;                 // last armed epoch's sequence number
+    bool armed = false;              // an armed epoch's wait has not been reported yet
     int64_t bytes = 0;
     Clock::time_point idle_since;
 };
@@ -108,9 +126,26 @@ struct bsgdtv_server_ctx {
     bool stop = false;
     bool wake = false;   // a cancel for the worker to reap
     std::thread worker;
+    // armed epochs asked for by bsgdtv_server_arm: geometry, wait, result
+    struct Arm {
+        int geom = 0;
+        long long wait_ns = 0;
+        bool launched = false, finished = false;
+        int result = BSGDTV_OK;
+        Group *group = nullptr;
+    };
+    std::vector<Arm *> arms;
+    // mapped pinned host blocks of served groups, kept for reuse: pinning
+    // memory costs milliseconds per group, groups come and go often
+    struct Pinned {
+        void *p = nullptr;
+        size_t bytes = 0;
+        bool used = false;
+    };
+    std::vector<Pinned> pinned;
     // statistics
     int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, ticks = 0, epochs_run = 0, groups_made = 0,
-            groups_freed = 0, max_running = 0, slice_epochs = 0;
+            groups_freed = 0, max_running = 0, slice_epochs = 0, wait_timeouts = 0, armed_epochs = 0;
 };
 
 namespace {
@@ -129,10 +164,10 @@ bool finished(const Request &r) {
     return r.state == kDone || r.state == kFailed || r.state == kCancelled;
 }
 
-// Empties slot b of g (its state reset to zeros) after its request ended.
+// Slot b of g is free again (the device emptied it when it retired).
 void free_slot(Group *g, int b) {
     g->slot_req[b] = -1;
-    bsgdtv_batch_set_slice(g->batch, b, nullptr, 0, 0.0);
+    g->slot_end[b] = -1;
 }
 
 void finish_cancelled(bsgdtv_server_ctx *s, Request &r) {
@@ -141,9 +176,33 @@ void finish_cancelled(bsgdtv_server_ctx *s, Request &r) {
     s->cancelled++;
 }
 
+// A mapped pinned block of at least `bytes` (a free one of at most twice
+// that size is reused), or null.
+void *pinned_acquire(bsgdtv_server_ctx *s, size_t bytes) {
+    for (auto &b : s->pinned)
+        if (!b.used && b.bytes >= bytes && b.bytes <= 2 * bytes) {
+            b.used = true;
+            return b.p;
+        }
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    s->pinned.push_back({p, bytes, true});
+    return p;
+}
+
+void pinned_release(bsgdtv_server_ctx *s, void *p) {
+    for (auto &b : s->pinned)
+        if (b.p == p) b.used = false;
+}
+
 int destroy_group(bsgdtv_server_ctx *s, Group *g) {
     if (g->batch) bsgdtv_batch_destroy(g->batch);
-    if (g->done) cudaEventDestroy(g->done);
+    if (g->pinned) pinned_release(s, g->pinned);
+    for (cudaEvent_t &ev : g->run_ev)
+        if (ev) cudaEventDestroy(ev);
     if (g->stream) cudaStreamDestroy(g->stream);
     s->hbm_used -= g->bytes;
     s->groups_freed++;
@@ -158,21 +217,33 @@ int make_group(bsgdtv_server_ctx *s, int gi, int slots, Group **out) {
     g->geom = gi;
     g->bytes = G.bytes_for(slots);
     BSG_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
-    BSG_CUDA(cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming));
-    int rc = bsgdtv_batch_create_from_operator(&g->batch, G.op, slots, g->stream);
+    int rc = BSGDTV_OK;
+    for (cudaEvent_t &ev : g->run_ev)
+        if (rc == BSGDTV_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+            rc = fail(BSGDTV_ERR_CUDA, "event creation");
+    if (rc == BSGDTV_OK) rc = bsgdtv_batch_create_from_operator(&g->batch, G.op, slots, g->stream);
     if (rc == BSGDTV_OK) bsgdtv::batch_keep_prox(g->batch, s->fgp_iters > 0);
     if (rc == BSGDTV_OK) {
         std::vector<float> zeros((size_t)G.rows * slots, 0.f);
         std::vector<double> lam((size_t)slots, 0.0);
         rc = bsgdtv_batch_set_data(g->batch, zeros.data(), 0, lam.data(), G.mu);
     }
+    if (rc == BSGDTV_OK) {
+        g->pinned = pinned_acquire(s, bsgdtv::batch_serve_host_bytes(slots, G.rows, G.cols));
+        rc = g->pinned ? bsgdtv::batch_serve_enable(g->batch, &g->view, g->pinned)
+                       : fail(BSGDTV_ERR_OOM, "pinned host memory for a served group");
+    }
     if (rc != BSGDTV_OK) {
         if (g->batch) bsgdtv_batch_destroy(g->batch);
-        cudaEventDestroy(g->done);
+        if (g->pinned) pinned_release(s, g->pinned);
+        for (cudaEvent_t &ev : g->run_ev)
+            if (ev) cudaEventDestroy(ev);
         cudaStreamDestroy(g->stream);
         return rc;
     }
     g->slot_req.assign(slots, -1);
+    g->slot_seq.assign(slots, 0);
+    g->slot_end.assign(slots, -1);
     g->idle_since = Clock::now();
     s->hbm_used += g->bytes;
     s->groups_made++;
@@ -182,7 +253,7 @@ int make_group(bsgdtv_server_ctx *s, int gi, int slots, Group **out) {
 }
 
 bool group_idle(const Group *g) {
-    if (g->busy) return false;
+    if (g->runs > 0 || g->armed) return false;
     for (int64_t id : g->slot_req)
         if (id >= 0) return false;
     return true;
@@ -192,32 +263,41 @@ bool group_idle(const Group *g) {
 // had now (the request waits); sets *fatal if the geometry can never fit.
 bool find_slot(bsgdtv_server_ctx *s, int gi, Group **gout, int *slot, int *fatal) {
     *fatal = BSGDTV_OK;
+    // any free slot of this geometry, running group or not (admission is
+    // posted to the slot's mailbox; an armed group first)
+    Group *best = nullptr;
+    int best_slot = -1;
     for (auto &g : s->groups) {
-        if (g->geom != gi || g->busy) continue;
+        if (g->geom != gi) continue;
         for (int b = 0; b < (int)g->slot_req.size(); ++b)
             if (g->slot_req[b] < 0) {
-                *gout = g.get();
-                *slot = b;
-                return true;
+                if (!best || (g->armed && !best->armed)) {
+                    best = g.get();
+                    best_slot = b;
+                }
+                break;
             }
+    }
+    if (best) {
+        *gout = best;
+        *slot = best_slot;
+        return true;
     }
     const Geometry &G = *s->geoms[gi];
     if (G.op_bytes + G.bytes_for(G.min_slots) > s->budget) {
         *fatal = BSGDTV_ERR_OOM;
         return false;
     }
-    // a group of this geometry is busy with free slots: wait for its tick
+    // every group of this geometry is full: a new group (a power of two
+    // between min_slots and slots) is sized by the geometry's demand, the
+    // requests waiting plus those running, so light load gets small groups
+    // with short epochs (low latency) and sustained load large ones that read
+    // A once for many slices (throughput); shrunk if the budget cannot hold it
+    int slots = G.min_slots, running_g = 0;
     for (auto &g : s->groups)
-        if (g->geom == gi && g->busy)
-            for (int64_t id : g->slot_req)
-                if (id < 0) return false;
-    // a new group sized for the requests of this geometry now waiting (a
-    // power of two between min_slots and slots): a short queue gets a small
-    // group with short epochs (low latency), a long queue a large one that
-    // reads A once for many slices (throughput); shrunk if the budget cannot
-    // hold it
-    int slots = G.min_slots;
-    while (slots < G.slots && slots < G.queued) slots *= 2;
+        if (g->geom == gi)
+            for (int64_t id : g->slot_req) running_g += id >= 0;
+    while (slots < G.slots && slots < G.queued + running_g) slots *= 2;
     slots = std::min(slots, G.slots);
     while (slots > G.min_slots && s->hbm_used + G.bytes_for(slots) > s->budget &&
            !std::any_of(s->groups.begin(), s->groups.end(), [&](const std::unique_ptr<Group> &p) {
@@ -271,117 +351,192 @@ void admit(bsgdtv_server_ctx *s) {
             }
             continue;
         }
-        // y was checked at submit: no second check, no wait for the copy
-        const int rc = bsgdtv::batch_set_slice(g->batch, slot, r.y.data(), 0, r.lambda, false);
-        if (rc != BSGDTV_OK) {
-            finish_failed(s, r, rc, std::string("set_slice: ") + bsgdtv_last_error());
-        } else {
-            g->slot_req[slot] = r.id;
-            r.state = kRunning;
-            r.remaining = r.epochs;
-            r.t_admit = Clock::now();
-            std::vector<float>().swap(r.y);
-        }
+        // y was checked at submit.  Post the admission: staging row and
+        // fields first, then the new sequence number (release)
+        const Geometry &G = *s->geoms[r.geom];
+        bsgdtv::ServeSlot &m = g->view.mb[slot];
+        std::memcpy(g->view.ypin + (size_t)slot * G.rows, r.y.data(), (size_t)G.rows * sizeof(float));
+        m.epochs = r.epochs;
+        m.tau = (float)(G.mu * r.lambda);
+        const int seq = ++g->slot_seq[slot];
+        __atomic_store_n(&m.seq, seq, __ATOMIC_RELEASE);
+        g->slot_req[slot] = r.id;
+        g->slot_end[slot] = -1;   // set when the device reports the pickup
+        r.state = kRunning;
+        r.remaining = r.epochs;
+        r.t_admit = Clock::now();
+        std::vector<float>().swap(r.y);
         s->geoms[r.geom]->queued--;
         it = s->queue.erase(it);
     }
 }
 
-// Launches a tick on every group that has occupied slots and is not running.
-void launch_ticks(bsgdtv_server_ctx *s) {
+// Keeps every group with occupied slots fed with runs of epochs (at most
+// kMaxRuns in flight), each as long as the longest remaining budget there
+// (capped at max_tick), and launches the armed epochs asked for.
+void feed_groups(bsgdtv_server_ctx *s) {
     int64_t running = 0;
     for (auto &g : s->groups) {
-        int tick = 0;
-        for (int64_t id : g->slot_req)
-            if (id >= 0) {
+        // epochs still to enqueue: exact for requests the device has picked
+        // up (their end epoch is known), one for the others while nothing is
+        // in flight (so the device picks them up)
+        int64_t need = 0;
+        bool occupied = false;
+        for (size_t b = 0; b < g->slot_req.size(); ++b)
+            if (g->slot_req[b] >= 0) {
                 running++;
-                const int rem = s->reqs[id]->remaining;
-                tick = tick ? std::min(tick, rem) : rem;
+                occupied = true;
+                if (g->slot_end[b] >= 0) need = std::max(need, g->slot_end[b] - g->enq);
             }
-        if (g->busy || tick == 0) continue;
-        tick = std::min(tick, s->max_tick);
-        int rc = bsgdtv_batch_run(g->batch, tick, s->fgp_iters);
-        if (rc == BSGDTV_OK && cudaEventRecord(g->done, g->stream) != cudaSuccess) rc = BSGDTV_ERR_CUDA;
-        if (rc != BSGDTV_OK) {
-            const std::string msg = std::string("run: ") + bsgdtv_last_error();
-            for (int64_t &id : g->slot_req)
-                if (id >= 0) {
-                    finish_failed(s, *s->reqs[id], rc, msg);
-                    id = -1;
+        if (occupied && need <= 0 && g->runs == 0) need = 1;
+        while (need > 0 && g->runs < kMaxRuns) {
+            const int len = (int)std::max<int64_t>(1, std::min<int64_t>(need, s->max_tick));
+            int rc = bsgdtv_batch_run(g->batch, len, s->fgp_iters);
+            if (rc == BSGDTV_OK && cudaEventRecord(g->run_ev[g->runs], g->stream) != cudaSuccess)
+                rc = BSGDTV_ERR_CUDA;
+            if (rc != BSGDTV_OK) {
+                const std::string msg = std::string("run: ") + bsgdtv_last_error();
+                for (int64_t &id : g->slot_req)
+                    if (id >= 0) {
+                        finish_failed(s, *s->reqs[id], rc, msg);
+                        id = -1;
+                    }
+                s->cv_done.notify_all();
+                break;
+            }
+            g->run_len[g->runs++] = len;
+            g->enq += len;
+            s->ticks++;
+            s->epochs_run += len;
+            need -= len;
+        }
+    }
+    s->max_running = std::max(s->max_running, running);
+    // armed epochs: one epoch on an idle group (made if the budget allows)
+    for (bsgdtv_server_ctx::Arm *a : s->arms) {
+        if (a->launched) continue;
+        Group *g = nullptr;
+        for (auto &p : s->groups)
+            if (p->geom == a->geom && group_idle(p.get())) {
+                g = p.get();
+                break;
+            }
+        if (!g) {
+            int slot = -1, fatal = BSGDTV_OK;
+            if (!find_slot(s, a->geom, &g, &slot, &fatal) || !group_idle(g)) {
+                if (fatal != BSGDTV_OK) {
+                    a->launched = a->finished = true;
+                    a->result = fatal;
+                    s->cv_done.notify_all();
                 }
+                continue;
+            }
+        }
+        bsgdtv::ServeCtrl &c = *g->view.ctrl;
+        c.wait_ns = a->wait_ns;
+        g->arm_seq++;
+        __atomic_store_n(&c.arm_seq, g->arm_seq, __ATOMIC_RELEASE);
+        int rc = bsgdtv_batch_run(g->batch, 1, s->fgp_iters);
+        if (rc == BSGDTV_OK && cudaEventRecord(g->run_ev[g->runs], g->stream) != cudaSuccess)
+            rc = BSGDTV_ERR_CUDA;
+        a->launched = true;
+        if (rc != BSGDTV_OK) {
+            a->finished = true;
+            a->result = rc;
             s->cv_done.notify_all();
             continue;
         }
-        g->busy = true;
-        g->tick = tick;
+        g->run_len[g->runs++] = 1;
+        g->enq += 1;
+        g->armed = true;
+        a->group = g;
         s->ticks++;
-        s->epochs_run += tick;
+        s->epochs_run += 1;
+        s->armed_epochs++;
     }
-    s->max_running = std::max(s->max_running, running);
 }
 
-// Harvests finished ticks.  Returns true if any group finished.
+// Retires finished runs, picks up completion records (x copied from the
+// slot's result row; the slot is free again), posts cancellations, and
+// reports armed epochs whose device-side wait has ended.  Returns true if
+// anything changed.
 bool harvest(bsgdtv_server_ctx *s) {
     bool any = false;
     for (auto &g : s->groups) {
-        if (!g->busy) continue;
-        const cudaError_t q = cudaEventQuery(g->done);
-        if (q == cudaErrorNotReady) continue;
-        g->busy = false;
-        any = true;
+        // runs complete in launch order
+        while (g->runs > 0) {
+            const cudaError_t q = cudaEventQuery(g->run_ev[0]);
+            if (q == cudaErrorNotReady) break;
+            if (q != cudaSuccess) {
+                cudaGetLastError();
+                for (int64_t &id : g->slot_req)
+                    if (id >= 0) {
+                        finish_failed(s, *s->reqs[id], BSGDTV_ERR_CUDA,
+                                      std::string("run: ") + cudaGetErrorString(q));
+                        id = -1;
+                    }
+                any = true;
+            }
+            // the oldest run is done: its event moves to the free end
+            cudaEvent_t ev0 = g->run_ev[0];
+            for (int k = 0; k + 1 < kMaxRuns; ++k) {
+                g->run_ev[k] = g->run_ev[k + 1];
+                g->run_len[k] = g->run_len[k + 1];
+            }
+            g->run_ev[kMaxRuns - 1] = ev0;
+            g->runs--;
+            any = true;
+        }
+        const Geometry &G = *s->geoms[g->geom];
         for (int b = 0; b < (int)g->slot_req.size(); ++b) {
             const int64_t id = g->slot_req[b];
             if (id < 0) continue;
             Request &r = *s->reqs[id];
-            if (q != cudaSuccess) {
-                finish_failed(s, r, BSGDTV_ERR_CUDA, std::string("tick: ") + cudaGetErrorString(q));
-                g->slot_req[b] = -1;
+            const bsgdtv::ServeDone &d = g->view.done[b];
+            if (g->slot_end[b] < 0 &&
+                __atomic_load_n(&d.picked_seq, __ATOMIC_ACQUIRE) == g->slot_seq[b])
+                // picked up at epoch e: runs epochs e .. e + E - 1, retired at e + E
+                g->slot_end[b] = (int64_t)d.picked_epoch + r.epochs + 1;
+            if (__atomic_load_n(&d.seq, __ATOMIC_ACQUIRE) != g->slot_seq[b]) {
+                // still running: post a cancellation once
+                if (r.cancel && __atomic_load_n(&g->view.mb[b].cancel, __ATOMIC_RELAXED) != g->slot_seq[b])
+                    __atomic_store_n(&g->view.mb[b].cancel, g->slot_seq[b], __ATOMIC_RELEASE);
                 continue;
             }
-            r.remaining -= g->tick;
-            s->slice_epochs += g->tick;
+            const int ran = d.epochs_run;
+            s->slice_epochs += ran;
+            r.remaining = r.epochs - ran;
             if (r.cancel) {
                 finish_cancelled(s, r);
-                free_slot(g.get(), b);
-                continue;
-            }
-            if (r.remaining > 0) continue;
-            r.x.resize((size_t)s->geoms[g->geom]->cols);
-            int rc = bsgdtv_batch_get_slice_x(g->batch, b, r.x.data(), 0);
-            if (rc == BSGDTV_OK) {
-                r.state = kDone;
-                r.t_done = Clock::now();
-                s->completed++;
             } else {
-                finish_failed(s, r, rc, std::string("get_slice_x: ") + bsgdtv_last_error());
+                try {
+                    r.x.assign(g->view.xpin + (size_t)b * G.cols, g->view.xpin + (size_t)(b + 1) * G.cols);
+                    r.state = kDone;
+                    r.t_done = Clock::now();
+                    s->completed++;
+                } catch (const std::bad_alloc &) {
+                    finish_failed(s, r, BSGDTV_ERR_OOM, "host allocation for x");
+                }
             }
             free_slot(g.get(), b);
+            any = true;
         }
-        if (q != cudaSuccess) cudaGetLastError();
-        if (group_idle(g.get())) g->idle_since = Clock::now();
+        if (g->armed &&
+            __atomic_load_n(&g->view.ctrl->status_seq, __ATOMIC_ACQUIRE) == g->arm_seq) {
+            const int timed_out = g->view.ctrl->status;
+            g->armed = false;
+            if (timed_out) s->wait_timeouts++;
+            for (bsgdtv_server_ctx::Arm *a : s->arms)
+                if (a->group == g.get() && !a->finished) {
+                    a->finished = true;
+                    a->result = timed_out ? BSGDTV_ERR_TIMEOUT : BSGDTV_OK;
+                }
+            any = true;
+        }
+        if (group_idle(g.get()) && any) g->idle_since = Clock::now();
     }
     if (any) s->cv_done.notify_all();
     return any;
-}
-
-// Frees the slots of cancelled requests in groups that are not running a
-// tick (a busy group's are freed when harvest sees its tick end).
-void reap_cancelled(bsgdtv_server_ctx *s) {
-    bool any = false;
-    for (auto &g : s->groups) {
-        if (g->busy) continue;
-        bool freed = false;
-        for (int b = 0; b < (int)g->slot_req.size(); ++b) {
-            const int64_t id = g->slot_req[b];
-            if (id < 0 || !s->reqs[id]->cancel) continue;
-            finish_cancelled(s, *s->reqs[id]);
-            free_slot(g.get(), b);
-            freed = true;
-        }
-        if (freed && group_idle(g.get())) g->idle_since = Clock::now();
-        any = any || freed;
-    }
-    if (any) s->cv_done.notify_all();
 }
 
 void worker_main(bsgdtv_server_ctx *s) {
@@ -390,11 +545,10 @@ void worker_main(bsgdtv_server_ctx *s) {
     while (true) {
         if (s->stop) break;
         harvest(s);
-        reap_cancelled(s);
         admit(s);
-        launch_ticks(s);
+        feed_groups(s);
         bool busy = false;
-        for (auto &g : s->groups) busy = busy || g->busy;
+        for (auto &g : s->groups) busy = busy || g->runs > 0;
         if (!busy) {
             if (s->queue.empty()) {
                 s->cv_work.wait(lock, [&] { return s->stop || !s->queue.empty() || s->wake; });
@@ -454,6 +608,7 @@ void bsgdtv_server_destroy(bsgdtv_server_t s) {
     s->groups.clear();
     for (auto &G : s->geoms)
         if (G && G->op) bsgdtv_operator_destroy(G->op);
+    for (auto &b : s->pinned) cudaFreeHost(b.p);
     s->cv_done.notify_all();
     delete s;
 }
@@ -576,7 +731,7 @@ int bsgdtv_server_cancel(bsgdtv_server_t s, int64_t request_id) {
             s->cv_done.notify_all();
             return BSGDTV_OK;
         }
-        r.cancel = true;   // running: the worker frees its slot
+        r.cancel = true;   // running: the worker posts it to the slot's mailbox
         s->wake = true;
     }
     s->cv_work.notify_all();
@@ -615,16 +770,42 @@ int bsgdtv_server_wait(bsgdtv_server_t s, int64_t request_id, double timeout_s, 
     return BSGDTV_OK;
 }
 
+int bsgdtv_server_arm(bsgdtv_server_t s, int geom_id, double wait_s) {
+    if (!s) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    if (!(wait_s >= 0.0) || wait_s * 1e9 > (double)bsgdtv::kServeMaxWaitNs)
+        return fail(BSGDTV_ERR_INVALID_ARG, "need 0 <= wait_s <= 1");
+    bsgdtv_server_ctx::Arm a;
+    a.geom = geom_id;
+    a.wait_ns = (long long)(wait_s * 1e9);
+    std::unique_lock<std::mutex> lock(s->mu);
+    if (geom_id < 0 || geom_id >= (int)s->geoms.size() || !s->geoms[geom_id])
+        return fail(BSGDTV_ERR_INVALID_ARG, "unknown geometry");
+    if (s->stop) return fail(BSGDTV_ERR_STATE, "server is stopping");
+    s->arms.push_back(&a);
+    s->wake = true;
+    s->cv_work.notify_all();
+    // the device wait is bounded by wait_s; the host allows it that long plus
+    // the launch and a margin before giving up on the report
+    const bool ok = s->cv_done.wait_for(lock, std::chrono::duration<double>(wait_s + 30.0),
+                                        [&] { return a.finished || s->stop; });
+    s->arms.erase(std::find(s->arms.begin(), s->arms.end(), &a));
+    if (!ok || !a.finished) return fail(BSGDTV_ERR_STATE, "armed epoch not reported (server stopping)");
+    if (a.result == BSGDTV_ERR_TIMEOUT)
+        return fail(BSGDTV_ERR_TIMEOUT, "no request arrived during the device-side wait");
+    if (a.result != BSGDTV_OK) return fail(a.result, "armed epoch failed");
+    return BSGDTV_OK;
+}
+
 int bsgdtv_server_stats(bsgdtv_server_t s, int64_t *stats) {
     if (!s || !stats) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
     std::lock_guard<std::mutex> lock(s->mu);
     int64_t running = 0;
     for (auto &g : s->groups)
         for (int64_t id : g->slot_req) running += id >= 0;
-    const int64_t v[13] = {s->submitted, s->completed,   s->failed,     (int64_t)s->queue.size(),
+    const int64_t v[15] = {s->submitted, s->completed,   s->failed,     (int64_t)s->queue.size(),
                            running,      (int64_t)s->groups.size(), s->hbm_used, s->max_running,
                            s->ticks,     s->epochs_run,  s->slice_epochs, s->groups_made,
-                           s->cancelled};
+                           s->cancelled, s->armed_epochs, s->wait_timeouts};
     std::memcpy(stats, v, sizeof(v));
     return BSGDTV_OK;
 }

@@ -177,9 +177,10 @@ def _poll_until(srv, rid, state, limit_s=60.0):
 def test_server_cancel(B):
     """A budget for one group of one slot: a long request runs, a second one
     queues.  Cancelling the queued one takes effect at once, the running one
-    at the end of its tick; both then wait with BSGDTV_ERR_CANCELLED and are
-    forgotten, and the next request reuses the slot with the bits it gets
-    alone."""
+    at its group's next epoch boundary (the device's slot scheduler reads the
+    cancellation from the slot's mailbox); both then wait with
+    BSGDTV_ERR_CANCELLED and are forgotten, and the next request reuses the
+    slot with the bits it gets alone."""
     A, n, _, mu = geometry("g64")
     budget = _op_bytes(B, A) + B.bsgdtv_batch_device_bytes(A.rows, A.cols_n, 0, 1) + 4096
     with B.Server(budget, K, 4) as srv:
@@ -212,4 +213,83 @@ def test_server_cancel(B):
     assert st["cancelled"] == 2 and st["completed"] == 1 and st["failed"] == 0
     assert st["device_bytes"] <= budget and st["groups_made"] == 1
     alone, _ = _serve(B, [("g64", 3, 0.05, 7)], slots=1)
+    assert np.array_equal(x, alone[0])
+
+
+def test_server_admits_and_retires_between_epochs_of_a_running_group(B):
+    """Admission and retirement happen on the device at epoch boundaries: a
+    short request submitted while a long one keeps its group running (runs of
+    up to 200 epochs) joins that group and completes while the long one is
+    still running; its result equals the same request served alone."""
+    A, n, _, mu = geometry("g64")
+    with B.Server(1 << 34, K, 200) as srv:
+        gid = srv.add_geometry(A, (n, n), mu, slots=4, prewarm=1)
+        long_id = srv.submit(gid, request("g64", 1), 0.05, 1 << 30)
+        _poll_until(srv, long_id, 1)
+        time.sleep(0.05)                           # the group is mid-run now
+        short_id = srv.submit(gid, request("g64", 4), 0.03, 9)
+        x, lat, _ = srv.wait(short_id, gid, timeout_s=120)
+        assert srv.poll(long_id) == 1               # the long request is still running
+        st = srv.stats()
+        assert st["groups_made"] == 1 and st["max_running"] == 2
+        srv.cancel(long_id)
+        with pytest.raises(B.BsgdtvError) as e:
+            srv.wait(long_id, gid, timeout_s=60.0)
+        assert e.value.code == -8
+    alone, _ = _serve(B, [("g64", 4, 0.03, 9)], slots=4)
+    assert np.array_equal(x, alone[0])
+    x_ref, _ = oracle.run(A, request("g64", 4).astype(np.float64), (n, n), 1, 1, 0.03, mu, 9, K)
+    assert rel(x, x_ref) <= 1e-4
+
+
+def test_server_armed_wait_times_out(B):
+    """An armed epoch whose device-side wait sees no request ends it after the
+    limit and reports BSGDTV_ERR_TIMEOUT; the server stays usable."""
+    A, n, _, mu = geometry("g37")
+    with B.Server(1 << 34, K, 4) as srv:
+        gid = srv.add_geometry(A, (n, n), mu, slots=4, prewarm=1)
+        t0 = time.time()
+        with pytest.raises(B.BsgdtvError) as e:
+            srv.arm(gid, 0.05)
+        assert e.value.code == -5
+        assert time.time() - t0 >= 0.05
+        st = srv.stats()
+        assert st["armed_epochs"] == 1 and st["wait_timeouts"] == 1
+        with pytest.raises(B.BsgdtvError) as e:
+            srv.arm(gid, 2.0)                       # beyond the 1 s limit
+        assert e.value.code == -1
+        rid = srv.submit(gid, request("g37", 2), 0.02, 9)
+        x, _, _ = srv.wait(rid, gid, timeout_s=120)
+    alone, _ = _serve(B, [("g37", 2, 0.02, 9)], slots=4)
+    assert np.array_equal(x, alone[0])
+
+
+def test_server_armed_wait_admits_a_request(B):
+    """A request submitted while an armed epoch waits on the device starts in
+    that epoch: the arm reports success, and the result equals the request
+    served alone."""
+    A, n, _, mu = geometry("g37")
+    with B.Server(1 << 34, K, 4) as srv:
+        gid = srv.add_geometry(A, (n, n), mu, slots=4, prewarm=1)
+        res = {}
+
+        def arm():
+            try:
+                srv.arm(gid, 0.9)
+                res["rc"] = 0
+            except B.BsgdtvError as err:
+                res["rc"] = err.code
+
+        th = threading.Thread(target=arm)
+        th.start()
+        t0 = time.time()
+        while srv.stats()["armed_epochs"] < 1:     # the armed epoch is on the device
+            assert time.time() - t0 < 30
+            time.sleep(0.001)
+        rid = srv.submit(gid, request("g37", 5), 0.05, 11)
+        th.join()
+        x, _, _ = srv.wait(rid, gid, timeout_s=120)
+        assert res["rc"] == 0
+        assert srv.stats()["wait_timeouts"] == 0
+    alone, _ = _serve(B, [("g37", 5, 0.05, 11)], slots=4)
     assert np.array_equal(x, alone[0])
