@@ -435,6 +435,40 @@ int bsgdtv_batch_set_tuning(bsgdtv_batch_t h, int fgp_chunk, int fgp_group);
 /* Copies slice b's x [cols] (FP32).  To the host: synchronises the stream. */
 int bsgdtv_batch_get_slice_x(bsgdtv_batch_t h, int b, float *x, int out_on_device);
 
+/* ------------------------------------------------------ packed batches
+ * Several geometries (operators of one weight format, any sizes) with
+ * `slices` slots each, whose epochs run together: each stage of an epoch --
+ * the row pass r = y - A x, the column pass x^ = x + 2 mu A^T r_prev, the
+ * transposes around the prox and every FGP launch -- is one kernel launch
+ * over all parts (Algorithm 1 per slot, exactly as a batch slice of its
+ * geometry), captured in one CUDA graph per epoch.  Uneven requests (images
+ * of different sizes, angle and bin counts) thus share launches instead of
+ * running one set per geometry.  Part k has its own y, lambdas and mu. */
+typedef struct bsgdtv_packed_ctx *bsgdtv_packed_t;
+
+/* Creates a packed batch of n_parts (1 .. 8) operators, `slices` slots each
+ * (1 .. 4096), on `stream`.  Every part starts without data. */
+int bsgdtv_packed_create(bsgdtv_packed_t *out, const bsgdtv_operator_t *ops, int n_parts, int slices,
+                         void *stream);
+
+/* Data of part `part`: as bsgdtv_batch_set_data for that part's geometry
+ * (y [slices][rows of the part], lambdas [slices], mu for its A); restarts
+ * the part's slots from x^0 = 0.  Every part needs data before a run. */
+int bsgdtv_packed_set_part(bsgdtv_packed_t h, int part, const float *y, int y_on_device,
+                           const double *lambdas, double mu);
+
+/* Runs `epochs` epochs of every part (asynchronous on the handle's stream). */
+int bsgdtv_packed_run(bsgdtv_packed_t h, int epochs, int fgp_iters);
+
+/* x of part `part`, [slices][cols of the part] (synchronises for a host x). */
+int bsgdtv_packed_get_x(bsgdtv_packed_t h, int part, float *x, int out_on_device);
+
+/* Kernel launches in one epoch of the packed batch with fgp_iters FGP
+ * iterations (builds the epoch graphs if needed). */
+int bsgdtv_packed_launches_per_epoch(bsgdtv_packed_t h, int fgp_iters, int64_t *launches);
+
+void bsgdtv_packed_destroy(bsgdtv_packed_t h);
+
 /* ------------------------------------------------------ continuous batching
  * A reconstruction server: requests (projections of a registered geometry,
  * a TV weight and an epoch budget) are submitted at any time from any host

@@ -80,6 +80,12 @@ def load(path: str | None = None):
         "bsgdtv_batch_project": (I32, [P, P, P]),
         "bsgdtv_batch_autotune": (I32, [P, I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(D)]),
         "bsgdtv_batch_set_tuning": (I32, [P, I32, I32]),
+        "bsgdtv_packed_create": (I32, [ctypes.POINTER(P), P, I32, I32, P]),
+        "bsgdtv_packed_set_part": (I32, [P, I32, P, I32, P, D]),
+        "bsgdtv_packed_run": (I32, [P, I32, I32]),
+        "bsgdtv_packed_get_x": (I32, [P, I32, P, I32]),
+        "bsgdtv_packed_launches_per_epoch": (I32, [P, I32, ctypes.POINTER(I64)]),
+        "bsgdtv_packed_destroy": (None, [P]),
         "bsgdtv_server_create": (I32, [ctypes.POINTER(P), I64, I32, I32]),
         "bsgdtv_server_destroy": (None, [P]),
         "bsgdtv_server_add_geometry": (I32, [P, I64, I64, I32, I32, P, P, P, I32, I32, D, I32, ctypes.POINTER(I32)]),
@@ -119,6 +125,8 @@ def exported_symbols():
             "bsgdtv_batch_create_parallel_beam", "bsgdtv_mf_ray_weights", "bsgdtv_batch_estimate_umax",
             "bsgdtv_batch_project", "bsgdtv_batch_autotune", "bsgdtv_batch_set_tuning", "bsgdtv_operator_create_csr",
             "bsgdtv_operator_destroy", "bsgdtv_batch_create_from_operator",
+            "bsgdtv_packed_create", "bsgdtv_packed_set_part", "bsgdtv_packed_run",
+            "bsgdtv_packed_get_x", "bsgdtv_packed_launches_per_epoch", "bsgdtv_packed_destroy",
             "bsgdtv_launch_count", "bsgdtv_last_error", "bsgdtv_strerror"]
 
 
@@ -818,6 +826,79 @@ class BatchReconstructor:
         if out is None:
             out = np.empty(self.cols, dtype=np.float32)
         return bsgdtv_batch_get_slice_x(self.h, b, out)
+
+
+class PackedBatch:
+    """Several geometries with `slices` slots each, every epoch stage one
+    launch over all of them: ``PackedBatch([A1, A2], [(n1, n1), (n2, n2)],
+    slices)``, ``set_part(k, Y_k, lambdas_k, mu_k)``, ``run``, ``x(k)``."""
+
+    def __init__(self, As, img_shapes, slices, fmt=FMT_F32_I32, stream=None):
+        import torch
+        self.slices = int(slices)
+        self.rows = [int(A.rows) for A in As]
+        self.cols = [int(A.cols_n) for A in As]
+        ops = [bsgdtv_operator_create_csr(A.rows, A.cols_n, shp[0], shp[1], A.row_ptr, A.cols,
+                                          A.vals, fmt)
+               for A, shp in zip(As, img_shapes)]
+        arr = (ctypes.c_void_p * len(ops))(*[op.value for op in ops])
+        h = ctypes.c_void_p()
+        try:
+            _check(load().bsgdtv_packed_create(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p),
+                                               len(ops), self.slices,
+                                               stream if stream is not None else current_stream()),
+                   "bsgdtv_packed_create")
+        finally:
+            for op in ops:                      # the parts keep their own references
+                bsgdtv_operator_destroy(op)
+        self.h = h.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            load().bsgdtv_packed_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_part(self, k, Y, lambdas, mu):
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        if lam.size != self.slices:
+            raise ValueError("one lambda per slot")
+        if _is_tensor(Y):
+            import torch
+            ptr, dev = _dev_ptr(Y, torch.float32, self.slices * self.rows[k]), 1
+        else:
+            Y = np.ascontiguousarray(Y, dtype=np.float32)
+            if Y.size != self.slices * self.rows[k]:
+                raise ValueError("Y must hold slices x rows of the part")
+            ptr, dev = _host_ptr(Y, np.float32), 0
+        _check(load().bsgdtv_packed_set_part(self.h, int(k), ptr, dev, _host_ptr(lam, np.float64),
+                                             float(mu)), "bsgdtv_packed_set_part")
+
+    def run(self, epochs, fgp_iters):
+        _check(load().bsgdtv_packed_run(self.h, int(epochs), int(fgp_iters)), "bsgdtv_packed_run")
+
+    def x(self, k):
+        out = np.empty((self.slices, self.cols[k]), dtype=np.float32)
+        _check(load().bsgdtv_packed_get_x(self.h, int(k), _host_ptr(out, np.float32), 0),
+               "bsgdtv_packed_get_x")
+        return out
+
+    def launches_per_epoch(self, fgp_iters):
+        n = ctypes.c_int64()
+        _check(load().bsgdtv_packed_launches_per_epoch(self.h, int(fgp_iters), ctypes.byref(n)),
+               "bsgdtv_packed_launches_per_epoch")
+        return n.value
 
 
 class Server:

@@ -109,19 +109,45 @@ __device__ __forceinline__ int2 load_entry(const PassOperand &A, int64_t e) {
     }
 }
 
+// One pass launch covers up to kMaxPassParts parts (operators with their own
+// vectors, one slice stride Bp for all): CTA blockIdx.x belongs to the last
+// part whose cta_begin it has reached.
+struct PassPart {
+    PassOperand A;
+    const float *v, *base;
+    float *out;
+    int64_t n_out;
+    float mu;
+    int cta_begin;
+};
+constexpr int kMaxPassParts = 8;
+struct PassLaunch {
+    PassPart part[kMaxPassParts];
+    int n_parts;
+    int Bp;
+};
+
 template <int LPN, bool kRowPass, int kW>
 __global__ void __launch_bounds__(kPassWarps * 32, kPassMinBlocks)
-    pass_kernel(const PassOperand A, const float *__restrict__ v, const float *__restrict__ base,
-                float *__restrict__ out, int64_t n_out, int Bp, float mu) {
+    pass_kernel(const __grid_constant__ PassLaunch L) {
     constexpr int G = 32 / LPN;
     constexpr int NB = (32 / G < 4) ? 32 / G : 4;
+    int pi = 0;
+    while (pi + 1 < L.n_parts && (int)blockIdx.x >= L.part[pi + 1].cta_begin) ++pi;
+    const PassPart &P = L.part[pi];
+    const PassOperand &A = P.A;
+    const float *__restrict__ v = P.v;
+    const float *__restrict__ base = P.base;
+    float *__restrict__ out = P.out;
+    const int Bp = L.Bp;
+    const float mu = P.mu;
     // slice stride: 4 * LPN (a constant) below 128 slices, else Bp
     const int stride = (LPN < 32) ? 4 * LPN : Bp;
     __shared__ int2 stage[kPassWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = lane / LPN, sl = lane % LPN;
-    const int64_t k = (int64_t)blockIdx.x * kPassWarps + w;
-    if (k >= n_out) return;   // warp-uniform
+    const int64_t k = (int64_t)((int)blockIdx.x - P.cta_begin) * kPassWarps + w;
+    if (k >= P.n_out) return;   // warp-uniform
     const uint64_t pol = l2_evict_last_policy();
     const int64_t e0 = A.ptr[k], e1 = A.ptr[k + 1];
     for (int c0 = 0; c0 < Bp; c0 += 4 * LPN) {
@@ -175,13 +201,11 @@ __global__ void __launch_bounds__(kPassWarps * 32, kPassMinBlocks)
 }
 
 template <bool kRowPass, int kW>
-cudaError_t launch_pass_w(int lpn, const PassOperand &A, const float *v, const float *base,
-                          float *out, int64_t n_out, int Bp, float mu, cudaStream_t s) {
-    const dim3 grid((unsigned)((n_out + kPassWarps - 1) / kPassWarps));
-    const dim3 block(kPassWarps * 32);
-#define BSG_PASS(L)                                                                          \
-    case L:                                                                                  \
-        pass_kernel<L, kRowPass, kW><<<grid, block, 0, s>>>(A, v, base, out, n_out, Bp, mu); \
+cudaError_t launch_pass_w(int lpn, const PassLaunch &L, int ctas, cudaStream_t s) {
+    const dim3 grid((unsigned)ctas), block(kPassWarps * 32);
+#define BSG_PASS(LP)                                                     \
+    case LP:                                                             \
+        pass_kernel<LP, kRowPass, kW><<<grid, block, 0, s>>>(L);         \
         break;
     switch (lpn) {
         BSG_PASS(1)
@@ -198,19 +222,35 @@ cudaError_t launch_pass_w(int lpn, const PassOperand &A, const float *v, const f
     return cudaGetLastError();
 }
 
+// One pass over the parts' operators (all of format fmt, slice stride Bp):
+// row pass out = base - A v, column pass out = base + 2 mu A^T v, per part.
+template <bool kRowPass>
+cudaError_t launch_pass_parts(int fmt, int lpn, const PassPart *parts, int n_parts, int Bp,
+                              cudaStream_t s) {
+    if (n_parts < 1 || n_parts > kMaxPassParts) return cudaErrorInvalidValue;
+    PassLaunch L = {};
+    L.n_parts = n_parts;
+    L.Bp = Bp;
+    int ctas = 0;
+    for (int k = 0; k < n_parts; ++k) {
+        L.part[k] = parts[k];
+        L.part[k].cta_begin = ctas;
+        ctas += (int)((parts[k].n_out + kPassWarps - 1) / kPassWarps);
+    }
+    if (ctas == 0) return cudaSuccess;
+    switch (fmt) {
+        case BSGDTV_FMT_F32_I32: return launch_pass_w<kRowPass, 0>(lpn, L, ctas, s);
+        case BSGDTV_FMT_F16_I16: return launch_pass_w<kRowPass, BSGDTV_FMT_F16_I16>(lpn, L, ctas, s);
+        case BSGDTV_FMT_BF16_I16: return launch_pass_w<kRowPass, BSGDTV_FMT_BF16_I16>(lpn, L, ctas, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <bool kRowPass>
 cudaError_t launch_pass(int fmt, int lpn, const PassOperand &A, const float *v, const float *base,
                         float *out, int64_t n_out, int Bp, float mu, cudaStream_t s) {
-    switch (fmt) {
-        case BSGDTV_FMT_F32_I32:
-            return launch_pass_w<kRowPass, 0>(lpn, A, v, base, out, n_out, Bp, mu, s);
-        case BSGDTV_FMT_F16_I16:
-            return launch_pass_w<kRowPass, BSGDTV_FMT_F16_I16>(lpn, A, v, base, out, n_out, Bp, mu, s);
-        case BSGDTV_FMT_BF16_I16:
-            return launch_pass_w<kRowPass, BSGDTV_FMT_BF16_I16>(lpn, A, v, base, out, n_out, Bp, mu, s);
-        default:
-            return cudaErrorInvalidValue;
-    }
+    const PassPart p = {A, v, base, out, n_out, mu, 0};
+    return launch_pass_parts<kRowPass>(fmt, lpn, &p, 1, Bp, s);
 }
 
 // Slot reset: slice b of the interleaved Y, X and R becomes (y_b, 0, y_b),
@@ -234,11 +274,29 @@ __global__ void slice_gather_kernel(const float *__restrict__ in, float *__restr
     if (i < n) out[i] = in[i * Bp + b];
 }
 
-// Planar [B][n] <-> interleaved [n][Bp] (only slices b < B are touched).
-__global__ void transpose_kernel(const float *__restrict__ in, float *__restrict__ out, int64_t n,
-                                 int B, int Bp, int to_planar) {
+// Planar [B][n] <-> interleaved [n][Bp] (only slices b < B are touched), for
+// up to kMaxTransParts parts (arrays of different n, one B and Bp): CTA
+// column blockIdx.x belongs to the last part whose x_begin it has reached.
+struct TransPart {
+    const float *in;
+    float *out;
+    int64_t n;
+    int x_begin;
+};
+constexpr int kMaxTransParts = 8;
+struct TransLaunch {
+    TransPart part[kMaxTransParts];
+    int n_parts;
+};
+
+__global__ void transpose_kernel(const __grid_constant__ TransLaunch L, int B, int Bp, int to_planar) {
     __shared__ float t[32][33];
-    const int64_t k0 = (int64_t)blockIdx.x * 32;
+    int pi = 0;
+    while (pi + 1 < L.n_parts && (int)blockIdx.x >= L.part[pi + 1].x_begin) ++pi;
+    const float *__restrict__ in = L.part[pi].in;
+    float *__restrict__ out = L.part[pi].out;
+    const int64_t n = L.part[pi].n;
+    const int64_t k0 = (int64_t)((int)blockIdx.x - L.part[pi].x_begin) * 32;
     const int b0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8 threads
     for (int yy = ty; yy < 32; yy += 8) {
@@ -266,12 +324,27 @@ __global__ void transpose_kernel(const float *__restrict__ in, float *__restrict
     }
 }
 
-cudaError_t launch_transpose(const float *in, float *out, int64_t n, int B, int Bp, bool to_planar,
-                             cudaStream_t s) {
-    const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((B + 31) / 32));
-    transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(in, out, n, B, Bp, to_planar ? 1 : 0);
+cudaError_t launch_transpose_parts(const TransPart *parts, int n_parts, int B, int Bp,
+                                   bool to_planar, cudaStream_t s) {
+    if (n_parts < 1 || n_parts > kMaxTransParts) return cudaErrorInvalidValue;
+    TransLaunch L = {};
+    L.n_parts = n_parts;
+    int xs = 0;
+    for (int k = 0; k < n_parts; ++k) {
+        L.part[k] = parts[k];
+        L.part[k].x_begin = xs;
+        xs += (int)((parts[k].n + 31) / 32);
+    }
+    const dim3 grid((unsigned)xs, (unsigned)((B + 31) / 32));
+    transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(L, B, Bp, to_planar ? 1 : 0);
     add_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const float *in, float *out, int64_t n, int B, int Bp, bool to_planar,
+                             cudaStream_t s) {
+    const TransPart p = {in, out, n, 0};
+    return launch_transpose_parts(&p, 1, B, Bp, to_planar, s);
 }
 
 // ------------------------------------------------ served mode: slot scheduler
@@ -652,9 +725,9 @@ int benqueue_epoch(bsgdtv_batch_ctx *h, int par, int fgp_iters, cudaStream_t s,
             const int nb = std::min(sg, h->B - b0);
             const size_t o = (size_t)b0 * c;
             const FgpScratch sc = fgp_scratch_planes(h->fgp, (int64_t)h->B * c, (int64_t)o);
-            BSG_CUDA(fgpk::launch_fgp_regions<true>(h->Xhp + o, h->Xp + o, h->img_h, h->img_w, 1.f,
-                                                    h->tau + b0, nb, c, fgp_iters, h->mom, sc, s,
-                                                    false, h->fgp_chunk));
+            BSG_CUDA(fgpk::launch_fgp_regions(h->Xhp + o, h->Xp + o, h->img_h, h->img_w,
+                                              h->tau + b0, nb, c, fgp_iters, h->mom, sc, s, false,
+                                              h->fgp_chunk));
         }
         BSG_CUDA(launch_transpose(h->Xp, h->X, c, h->B, h->Bp, false, s));
     }
@@ -1588,6 +1661,220 @@ int bsgdtv_batch_get_slice_x(bsgdtv_batch_t h, int b, float *x, int out_on_devic
                              out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              h->stream));
     if (!out_on_device) BSG_CUDA(cudaStreamSynchronize(h->stream));
+    return BSGDTV_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------- packed batches
+// Several geometries' batches (parts) whose epochs run together: each stage
+// of an epoch (row pass, column pass, the transposes around the prox and
+// every FGP launch) is one kernel launch over all parts, captured in one
+// graph per parity of the residual double buffer.
+struct bsgdtv_packed_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<bsgdtv_batch_t> parts;   // one batch per operator, on `stream`
+    std::vector<bool> part_data;         // set_part called for the part
+    int fmt = BSGDTV_FMT_F32_I32, B = 0, Bp = 0, lpn = 1;
+    int fgp_chunk = bsgdtv::kBatchFgpChunk;
+    float *mom = nullptr;
+    int mom_len = 0;
+    int cur = 0;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int graph_fgp_iters = -1;
+    bool graph_prox = false;
+    int64_t graph_kernels = 0;
+};
+
+namespace {
+
+void pdrop_graphs(bsgdtv_packed_ctx *h) {
+    for (auto &g : h->gexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    h->graph_fgp_iters = -1;
+}
+
+bool packed_prox(const bsgdtv_packed_ctx *h, int fgp_iters) {
+    if (fgp_iters <= 0) return false;
+    for (bsgdtv_batch_t p : h->parts)
+        if (any_prox(p, fgp_iters)) return true;
+    return false;
+}
+
+// One epoch of every part: reads R[par], writes R[1 - par] of each.
+int penqueue_epoch(bsgdtv_packed_ctx *h, int par, int fgp_iters, cudaStream_t s) {
+    const int n = (int)h->parts.size();
+    const bool prox = packed_prox(h, fgp_iters);
+    PassPart rowp[kMaxPassParts], colp[kMaxPassParts];
+    TransPart tin[kMaxTransParts], tout[kMaxTransParts];
+    fgpk::FgpImages img[fgpk::kMaxFgpParts];
+    for (int k = 0; k < n; ++k) {
+        const bsgdtv_batch_ctx *p = h->parts[k];
+        rowp[k] = {p->op_r, p->X, p->Y, p->R[1 - par], p->rows, 0.f, 0};
+        colp[k] = {p->op_c, p->R[par], p->X, prox ? p->Xhat : p->X, p->cols, (float)p->mu, 0};
+        tin[k] = {p->Xhat, p->Xhp, p->cols, 0};
+        tout[k] = {p->Xp, p->X, p->cols, 0};
+        img[k] = {p->Xhp, p->Xp, p->tau, 1.f, fgp_scratch_planes(p->fgp, (int64_t)p->B * p->cols),
+                  p->cols, p->img_h, p->img_w, p->B};
+    }
+    // r^k = y - A x^k for every part (reads x before the column pass updates it)
+    BSG_CUDA(launch_pass_parts<true>(h->fmt, h->lpn, rowp, n, h->Bp, s));
+    // x^ = x^k + mu_part * 2 A^T r^{k-1}
+    BSG_CUDA(launch_pass_parts<false>(h->fmt, h->lpn, colp, n, h->Bp, s));
+    if (prox) {
+        BSG_CUDA(launch_transpose_parts(tin, n, h->B, h->Bp, true, s));
+        BSG_CUDA(fgpk::launch_fgp_parts(img, n, fgp_iters, h->mom, s, false, h->fgp_chunk));
+        BSG_CUDA(launch_transpose_parts(tout, n, h->B, h->Bp, false, s));
+    }
+    return BSGDTV_OK;
+}
+
+int pbuild_graphs(bsgdtv_packed_ctx *h, int fgp_iters) {
+    pdrop_graphs(h);
+    if (fgp_iters > h->mom_len) {
+        std::vector<float> m;
+        fgp_momentum_host(fgp_iters, m);
+        float *d = nullptr;
+        BSG_CHECK(balloc(h->parts[0], &d, m.size()));   // freed with part 0
+        BSG_CUDA(cudaMemcpy(d, m.data(), m.size() * sizeof(float), cudaMemcpyHostToDevice));
+        h->mom = d;
+        h->mom_len = fgp_iters;
+    }
+    const int64_t before = bsgdtv_launch_count();
+    for (int par = 0; par < 2; ++par) {
+        cudaGraph_t g = nullptr;
+        BSG_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = penqueue_epoch(h, par, fgp_iters, h->cap_stream);
+        const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (rc != BSGDTV_OK) {
+            if (g) cudaGraphDestroy(g);
+            add_launches(before - bsgdtv_launch_count());
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(BSGDTV_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        const cudaError_t ei = cudaGraphInstantiate(&h->gexec[par], g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess)
+            return fail(BSGDTV_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    }
+    const int64_t captured = bsgdtv_launch_count() - before;
+    add_launches(-captured);
+    h->graph_kernels = captured / 2;
+    h->graph_fgp_iters = fgp_iters;
+    h->graph_prox = packed_prox(h, fgp_iters);
+    return BSGDTV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bsgdtv_packed_create(bsgdtv_packed_t *out, const bsgdtv_operator_t *ops, int n_parts, int slices,
+                         void *stream) {
+    BSG_TRACE();
+    if (!out || !ops) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (n_parts < 1 || n_parts > kMaxPassParts)
+        return fail(BSGDTV_ERR_INVALID_ARG, "need 1 <= n_parts <= 8");
+    for (int k = 0; k < n_parts; ++k) {
+        if (!ops[k]) return fail(BSGDTV_ERR_INVALID_ARG, "null operator");
+        if (ops[k]->fmt != ops[0]->fmt) return fail(BSGDTV_ERR_INVALID_ARG, "parts must share one weight format");
+    }
+    std::unique_ptr<bsgdtv_packed_ctx> h(new (std::nothrow) bsgdtv_packed_ctx());
+    if (!h) return fail(BSGDTV_ERR_OOM, "host allocation");
+    BSG_CUDA(cudaGetDevice(&h->device));
+    h->stream = (cudaStream_t)stream;
+    h->fmt = ops[0]->fmt;
+    h->B = slices;
+    bsgdtv_packed_ctx *hp = h.get();
+    auto cleanup = [&](int rc) {
+        bsgdtv_packed_destroy(h.release());
+        return rc;
+    };
+    BSG_CUDA(cudaStreamCreateWithFlags(&hp->cap_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < n_parts; ++k) {
+        bsgdtv_batch_t b = nullptr;
+        const int rc = bsgdtv_batch_create_from_operator(&b, ops[k], slices, stream);
+        if (rc != BSGDTV_OK) return cleanup(rc);
+        hp->parts.push_back(b);
+        hp->part_data.push_back(false);
+    }
+    hp->Bp = hp->parts[0]->Bp;
+    hp->lpn = hp->parts[0]->lpn;
+    *out = h.release();
+    return BSGDTV_OK;
+}
+
+void bsgdtv_packed_destroy(bsgdtv_packed_t h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    pdrop_graphs(h);
+    for (bsgdtv_batch_t p : h->parts) bsgdtv_batch_destroy(p);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+}
+
+int bsgdtv_packed_set_part(bsgdtv_packed_t h, int part, const float *y, int y_on_device,
+                           const double *lambdas, double mu) {
+    BSG_TRACE();
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (part < 0 || part >= (int)h->parts.size()) return fail(BSGDTV_ERR_INVALID_ARG, "part out of range");
+    h->part_data[part] = false;
+    BSG_CHECK(bsgdtv_batch_set_data(h->parts[part], y, y_on_device, lambdas, mu));
+    bsgdtv_batch_ctx *p = h->parts[part];
+    // the packed epochs read r^{k-1} from R[cur] of every part
+    if (h->cur != p->cur) {
+        BSG_CUDA(cudaMemcpyAsync(p->R[h->cur], p->R[p->cur], (size_t)p->rows * p->Bp * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, h->stream));
+        BSG_CUDA(cudaStreamSynchronize(h->stream));
+        p->cur = h->cur;
+    }
+    pdrop_graphs(h);   // mu and the weights are baked into the epochs
+    h->part_data[part] = true;
+    return BSGDTV_OK;
+}
+
+int bsgdtv_packed_run(bsgdtv_packed_t h, int epochs, int fgp_iters) {
+    BSG_TRACE();
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    for (bool d : h->part_data)
+        if (!d) return fail(BSGDTV_ERR_STATE, "run before every part has data");
+    if (epochs < 0 || fgp_iters < 0) return fail(BSGDTV_ERR_INVALID_ARG, "negative epochs / fgp_iters");
+    if (epochs == 0) return BSGDTV_OK;
+    BSG_CUDA(cudaSetDevice(h->device));
+    if (!h->gexec[0] || h->graph_fgp_iters != fgp_iters) BSG_CHECK(pbuild_graphs(h, fgp_iters));
+    for (int e = 0; e < epochs; ++e) {
+        BSG_CUDA(cudaGraphLaunch(h->gexec[h->cur], h->stream));
+        add_launches(h->graph_kernels);
+        h->cur ^= 1;
+        for (bsgdtv_batch_t p : h->parts) {
+            p->cur = h->cur;
+            p->epoch++;
+        }
+    }
+    return BSGDTV_OK;
+}
+
+int bsgdtv_packed_get_x(bsgdtv_packed_t h, int part, float *x, int out_on_device) {
+    BSG_TRACE();
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (part < 0 || part >= (int)h->parts.size()) return fail(BSGDTV_ERR_INVALID_ARG, "part out of range");
+    return bsgdtv_batch_get_x(h->parts[part], x, out_on_device);
+}
+
+int bsgdtv_packed_launches_per_epoch(bsgdtv_packed_t h, int fgp_iters, int64_t *launches) {
+    if (!h || !launches) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    for (bool d : h->part_data)
+        if (!d) return fail(BSGDTV_ERR_STATE, "every part needs data first");
+    BSG_CUDA(cudaSetDevice(h->device));
+    if (!h->gexec[0] || h->graph_fgp_iters != fgp_iters) BSG_CHECK(pbuild_graphs(h, fgp_iters));
+    *launches = h->graph_kernels;
     return BSGDTV_OK;
 }
 

@@ -72,8 +72,8 @@ int fgp_plan_launches(int h, int w, int iters, int max_chunk) {
 
 cudaError_t launch_fgp(const float *b, float *x, int h, int w, float tau, int iters,
                        const float *mom, FgpScratch sc, cudaStream_t s, bool pdl, int max_chunk) {
-    return launch_fgp_regions<false>(b, x, h, w, tau, nullptr, 1, 0, iters, mom, sc, s, pdl,
-                                     max_chunk);
+    const FgpImages p = {b, x, nullptr, tau, sc, 0, h, w, 1};
+    return launch_fgp_parts(&p, 1, iters, mom, s, pdl, max_chunk);
 }
 
 }  // namespace bsgdtv

@@ -120,30 +120,65 @@ __device__ __forceinline__ void fgp_step(Strip &p, Strip &pp, Strip &q, Strip &q
     }
 }
 
+// One launch of the FGP covers the images of up to kMaxFgpParts parts (a
+// part: `slices` images of H x W, `plane` floats apart, with their own
+// weights).  CTA blockIdx.x belongs to the last part whose cta_begin it has
+// reached and takes, within it, image z and region (bx, by) of the rx x ry
+// regions of that image.
+struct FgpPart {
+    const float *b;       // inputs, image z at + z * plane
+    float *x;             // outputs
+    const float *tau_z;   // per-image weights, or null: every image uses tau
+    float tau;
+    FgpFields in, out;    // dual field sets read / written (image z at + z * plane)
+    int64_t plane;
+    int H, W, rx, ry;     // image size; regions across and down
+    int cta_begin;        // first CTA of this part
+};
+constexpr int kMaxFgpParts = 8;
+struct FgpLaunch {
+    FgpPart part[kMaxFgpParts];
+    int n_parts;
+};
+
 // The dual state (p, q, p_prev, q_prev) of a tiled FGP passes between
 // launches through global memory.  A launch reads the set the previous launch
-// wrote (*_in; not read when `first`) and writes its regions' interiors to the
-// other set (*_out; not written when `last`): a region's halo is a neighbour's
+// wrote (in; not read when `first`) and writes its regions' interiors to the
+// other set (out; not written when `last`): a region's halo is a neighbour's
 // interior, and CTAs of one grid run in no fixed order, so reading and
 // writing one set in place would let a neighbour that finished first hand
-// this region iterates that are a whole launch ahead.
-// kBatch: blockIdx.z selects one of several images stored `plane` floats
-// apart (b, x_out and the dual fields alike), each with its own weight
-// tau_z[z]; a weight <= 0 makes that image's prox the identity.
+// this region iterates that are a whole launch ahead.  A weight <= 0 makes an
+// image's prox the identity (x = b).
 // TY x V: threads in y x pixels per thread (TY * V = RH, V = 4).
-template <bool kBatch, int TY, int V>
+template <int TY, int V>
 __global__ void __launch_bounds__(RW *TY)
-    fgp_kernel(const float *__restrict__ b, float *__restrict__ x_out, int H, int W, float tau,
-               float c8, const float *__restrict__ mom, int k0, int iters, int HL, int IH, int IW,
-               int first, int last, const float *__restrict__ p_in,
-               const float *__restrict__ q_in, const float *__restrict__ pp_in,
-               const float *__restrict__ qp_in, float *__restrict__ p_out,
-               float *__restrict__ q_out, float *__restrict__ pp_out, float *__restrict__ qp_out,
-               const float *__restrict__ tau_z, int64_t plane) {
+    fgp_kernel(const __grid_constant__ FgpLaunch L, const float *__restrict__ mom, int k0, int iters,
+               int HL, int IH, int IW, int first, int last) {
     __shared__ __align__(16) FgpShared<TY, V> sh;
 
+    int pi = 0;
+    while (pi + 1 < L.n_parts && (int)blockIdx.x >= L.part[pi + 1].cta_begin) ++pi;
+    const FgpPart &P = L.part[pi];
+    const int per = P.rx * P.ry, local = (int)blockIdx.x - P.cta_begin;
+    const int z = local / per, reg = local - z * per;
+    const int by = reg / P.rx, bx = reg - by * P.rx;
+    const int H = P.H, W = P.W;
+    const int64_t off = (int64_t)z * P.plane;
+    const float *__restrict__ b = P.b + off;
+    float *__restrict__ x_out = P.x + off;
+    const float *__restrict__ p_in = P.in.p + off;
+    const float *__restrict__ q_in = P.in.q + off;
+    const float *__restrict__ pp_in = P.in.pp + off;
+    const float *__restrict__ qp_in = P.in.qp + off;
+    float *__restrict__ p_out = P.out.p + off;
+    float *__restrict__ q_out = P.out.q + off;
+    float *__restrict__ pp_out = P.out.pp + off;
+    float *__restrict__ qp_out = P.out.qp + off;
+    const float tau = P.tau_z ? P.tau_z[z] : P.tau;
+    const float c8 = 1.0f / (8.0f * tau);
+
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int R0 = blockIdx.y * IH - HL, C0 = blockIdx.x * IW - HL;
+    const int R0 = by * IH - HL, C0 = bx * IW - HL;
     const int j = C0 + tx;
     const bool col_in = (j >= 0 && j < W);
 
@@ -159,21 +194,6 @@ __global__ void __launch_bounds__(RW *TY)
     if (ty == 0) {
         sh.r_edge[0][tx] = 0.f;
         sh.u_top[TY][tx] = 0.f;
-    }
-    if constexpr (kBatch) {
-        const int64_t off = (int64_t)blockIdx.z * plane;
-        b += off;
-        x_out += off;
-        p_in += off;
-        q_in += off;
-        pp_in += off;
-        qp_in += off;
-        p_out += off;
-        q_out += off;
-        pp_out += off;
-        qp_out += off;
-        tau = tau_z[blockIdx.z];
-        c8 = 1.0f / (8.0f * tau);
     }
     // b and the dual steps.  Every launch of one prox after the first starts
     // only once the first has passed its wait on the kernel that wrote b, so
@@ -194,18 +214,16 @@ __global__ void __launch_bounds__(RW *TY)
     if (!first) load_b();
     pdl_wait_and_release();
     if (first) load_b();
-    if constexpr (kBatch) {
-        if (!(tau > 0.f)) {   // block-uniform: zero weight, x = b
-            if (!last) return;
+    if (!(tau > 0.f)) {   // block-uniform: zero weight, x = b
+        if (!last) return;
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const int rr_ = ty * V + v;
-                const int i = R0 + rr_;
-                const bool interior = rr_ >= HL && rr_ < HL + IH && tx >= HL && tx < HL + IW;
-                if (interior && col_in && i >= 0 && i < H) x_out[(int64_t)i * W + j] = b[(int64_t)i * W + j];
-            }
-            return;
+        for (int v = 0; v < V; ++v) {
+            const int rr_ = ty * V + v;
+            const int i = R0 + rr_;
+            const bool interior = rr_ >= HL && rr_ < HL + IH && tx >= HL && tx < HL + IW;
+            if (interior && col_in && i >= 0 && i < H) x_out[(int64_t)i * W + j] = b[(int64_t)i * W + j];
         }
+        return;
     }
 
     Strip pa, pb, qa, qb;
@@ -292,26 +310,61 @@ inline const FgpFields &fgp_read_set(const FgpScratch &sc, int launch) {
 }
 inline const FgpFields &fgp_write_set(const FgpScratch &sc, int launch) { return sc.set[launch & 1]; }
 
-// K FGP iterations: one launch when the image fits one region, else one
-// launch per chunk of <= kMaxChunk iterations over overlapping regions.
-// kBatch: `planes` images `plane` floats apart, weights tau_z[0 .. planes).
-// TY x V: the kernel's thread shape (see fgp_kernel): 16 x 4, 1024 threads
-// with 4-pixel strips (an earlier 8 x 8 shape with 512 threads ran 1-3 %
-// slower: twice the warps per SM hide the two barriers of every iteration
-// better).
-template <bool kBatch, int TY = 16, int V = 4>
-cudaError_t launch_fgp_regions(const float *b, float *x, int h, int w, float tau,
-                               const float *tau_z, int planes, int64_t plane, int iters,
-                               const float *mom, FgpScratch sc, cudaStream_t s, bool pdl,
-                               int max_chunk = kMaxChunk) {
+// Host description of one part of an FGP launch: `slices` images of h x w,
+// `plane` floats apart (b in, x out), weights tau_z[0 .. slices) or, with
+// tau_z null, tau for all; sc: the part's two dual field sets.
+struct FgpImages {
+    const float *b;
+    float *x;
+    const float *tau_z;
+    float tau;
+    FgpScratch sc;
+    int64_t plane;
+    int h, w, slices;
+};
+
+// K FGP iterations on every image of n_parts parts, each launch covering all
+// of them: one launch when every image fits one region, else one launch per
+// chunk of <= max_chunk iterations over overlapping regions (halo = chunk +
+// 1).  TY x V: the kernel's thread shape (see fgp_kernel): 16 x 4, 1024
+// threads with 4-pixel strips (an earlier 8 x 8 shape with 512 threads ran
+// 1-3 % slower: twice the warps per SM hide the two barriers of every
+// iteration better).
+template <int TY = 16, int V = 4>
+cudaError_t launch_fgp_parts(const FgpImages *parts, int n_parts, int iters, const float *mom,
+                             cudaStream_t s, bool pdl, int max_chunk = kMaxChunk) {
+    if (n_parts < 1 || n_parts > kMaxFgpParts) return cudaErrorInvalidValue;
     const dim3 block(RW, TY);
-    const float c8 = 1.0f / (8.0f * tau);
-    if (fits_one_region(h, w)) {
+    bool single = true;
+    for (int k = 0; k < n_parts; ++k) single = single && fits_one_region(parts[k].h, parts[k].w);
+    auto build = [&](int launch, int HL, int IH, int IW, FgpLaunch &L) -> int {
+        int ctas = 0;
+        L.n_parts = n_parts;
+        for (int k = 0; k < n_parts; ++k) {
+            const FgpImages &q = parts[k];
+            FgpPart &P = L.part[k];
+            P.b = q.b;
+            P.x = q.x;
+            P.tau_z = q.tau_z;
+            P.tau = q.tau;
+            P.in = fgp_read_set(q.sc, launch);
+            P.out = fgp_write_set(q.sc, launch);
+            P.plane = q.plane;
+            P.H = q.h;
+            P.W = q.w;
+            P.rx = (q.w + IW - 1) / IW;
+            P.ry = (q.h + IH - 1) / IH;
+            P.cta_begin = ctas;
+            ctas += P.rx * P.ry * q.slices;
+        }
+        return ctas;
+    };
+    FgpLaunch L = {};
+    if (single) {
         // one launch, no field traffic (first and last)
-        const FgpFields &f = sc.set[0];
-        cudaError_t e = launch_kernel(fgp_kernel<kBatch, TY, V>, dim3(1, 1, planes), block, 0, s, pdl, b,
-                                      x, h, w, tau, c8, mom, 0, iters, 0, RH, RW, 1, 1, f.p, f.q,
-                                      f.pp, f.qp, f.p, f.q, f.pp, f.qp, tau_z, plane);
+        const int ctas = build(0, 0, RH, RW, L);
+        cudaError_t e = launch_kernel(fgp_kernel<TY, V>, dim3(ctas), block, 0, s, pdl, L, mom, 0,
+                                      iters, 0, RH, RW, 1, 1);
         add_launches(1);
         return e != cudaSuccess ? e : cudaGetLastError();
     }
@@ -320,19 +373,26 @@ cudaError_t launch_fgp_regions(const float *b, float *x, int h, int w, float tau
         const int chunk = std::min(max_chunk, iters - done);
         const int HL = chunk + 1;
         const int IH = RH - 2 * HL, IW = RW - 2 * HL;
-        const dim3 grid((w + IW - 1) / IW, (h + IH - 1) / IH, planes);
+        const int ctas = build(launch, HL, IH, IW, L);
         const int first = (done == 0), last = (done + chunk == iters);
-        const FgpFields &fi = fgp_read_set(sc, launch), &fo = fgp_write_set(sc, launch);
-        cudaError_t e = launch_kernel(fgp_kernel<kBatch, TY, V>, grid, block, 0, s, pdl || done > 0, b, x,
-                                      h, w, tau, c8, mom, done, chunk, HL, IH, IW, first, last,
-                                      fi.p, fi.q, fi.pp, fi.qp, fo.p, fo.q, fo.pp, fo.qp, tau_z,
-                                      plane);
+        cudaError_t e = launch_kernel(fgp_kernel<TY, V>, dim3(ctas), block, 0, s, pdl || done > 0, L,
+                                      mom, done, chunk, HL, IH, IW, first, last);
         add_launches(1);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         done += chunk;
     }
     return cudaSuccess;
+}
+
+// The batched form of one part: `planes` images `plane` floats apart with
+// weights tau_z.
+inline cudaError_t launch_fgp_regions(const float *b, float *x, int h, int w, const float *tau_z,
+                                      int planes, int64_t plane, int iters, const float *mom,
+                                      FgpScratch sc, cudaStream_t s, bool pdl,
+                                      int max_chunk = kMaxChunk) {
+    const FgpImages p = {b, x, tau_z, 1.f, sc, plane, h, w, planes};
+    return launch_fgp_parts(&p, 1, iters, mom, s, pdl, max_chunk);
 }
 
 }  // namespace fgpk

@@ -375,3 +375,40 @@ def test_batches_share_one_operator(B):
     for b in range(3):
         assert rel(Xs[b], Xo[b]) <= 1e-6
         assert rel(Xs[b], _oracle_slice(name, A, Y[b], lam[b], mu, 6, 9)) <= 1e-4
+
+
+def test_packed_batch_of_three_geometries(B):
+    """Requests of three geometries (64x64, ragged 37x37 with rays missing the
+    image, 130x130 over several FGP regions) packed into one handle: every
+    epoch stage is one launch over all parts (2 passes, 2 transposes and one
+    launch per chunk of FGP iterations, whatever the number of parts), and
+    each slot equals the same slot of a batch of its geometry alone bit for
+    bit and the oracle within 1e-4."""
+    geoms = [(64, 60, 91, 10), (37, 11, 55, 4), (130, 12, 185, 8)]
+    slices, epochs, K = 4, 12, 15
+    As, Ys, mus, lams = [], [], [], []
+    for gi, (n, na, nb, ne) in enumerate(geoms):
+        A = synth.parallel_beam_csr(n, na, nb)
+        _, Y = synth.slice_stack(A, n, ne, slices, seed=11 + gi)
+        u, _ = oracle.power_iteration(A)
+        As.append(A)
+        Ys.append(Y.astype(np.float32))
+        mus.append(0.9 / (2 * u))
+        lams.append(np.array([0.05, 0.0, 0.02, 0.1]) * (1 + gi))
+    shapes = [(g[0], g[0]) for g in geoms]
+    with B.PackedBatch(As, shapes, slices) as pk:
+        for k in range(3):
+            pk.set_part(k, Ys[k], lams[k], mus[k])
+        pk.run(epochs, K)
+        Xs = [pk.x(k) for k in range(3)]
+        launches = pk.launches_per_epoch(K)
+    assert launches == 2 + 2 + (K + 4) // 5           # 5 FGP iterations per launch
+    for k, (n, na, nb, ne) in enumerate(geoms):
+        with B.BatchReconstructor(As[k], shapes[k], slices) as bt:
+            bt.set_data(Ys[k], lams[k], mus[k])
+            bt.run(epochs, K)
+            assert np.array_equal(bt.x(), Xs[k]), k
+        for b in range(slices):
+            x_ref, _ = oracle.run(As[k], Ys[k][b].astype(np.float64), (n, n), 1, 1, lams[k][b], mus[k],
+                                  epochs, K)
+            assert rel(Xs[k][b], x_ref) <= 1e-4, (k, b)
