@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--served-small", action="store_true",
                     help="leave the 1024x1024 requests (p = 0.1) out of the served stream")
     ap.add_argument("--served-budget-gb", type=float, default=64.0)
+    ap.add_argument("--served-pack", type=int, default=1,
+                    help="geometries a server group may pack into one set of launches (1: none)")
+    ap.add_argument("--served-pack-ratio", type=float, default=4.0,
+                    help="largest ratio of nonzeros between geometries packed into one group")
     ap.add_argument("--served-tick", type=int, default=10, help="max epochs between admissions")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip every variant (stored formats and the batch)")
@@ -185,7 +189,14 @@ def served_stream(args, B, synth):
     budget = int(args.served_budget_gb * 2 ** 30)
     t_setup = time.perf_counter()
     geoms = {}
+
+    def slot_cap(n):
+        return 32
+
     srv = B.Server(budget, K, args.served_tick)
+    pack = getattr(args, "served_pack", 1)
+    if pack > 1:
+        srv.set_packing(pack, getattr(args, "served_pack_ratio", 4.0))
     for n in sizes:
         na, nb = int(round(0.7 * n)), int(math.ceil(math.sqrt(2) * n)) + 1
         A = synth.parallel_beam_csr(n, na, nb)
@@ -193,7 +204,8 @@ def served_stream(args, B, synth):
         # on-the-fly projector (no second stored copy of A)
         with B.BatchReconstructor(None, (n, n), 1, parallel_beam=(na, nb)) as one:
             u, _ = one.estimate_umax(300, 1e-9)
-        gid = srv.add_geometry(A, (n, n), 0.9 / (2 * u), slots=32, fmt=B.FMT_F16_I16, prewarm=0)
+        gid = srv.add_geometry(A, (n, n), 0.9 / (2 * u), slots=slot_cap(n), fmt=B.FMT_F16_I16,
+                               prewarm=0)
         ys = [synth.noisy_projections(A, synth.phantom(n, ellipses[n], s), s).astype(np.float32)
               for s in range(pool)]
         geoms[n] = (gid, ys, A.nnz)
@@ -239,7 +251,10 @@ def served_stream(args, B, synth):
     return {"requests": N, "stream": ("the first %d requests of the 2000-request served stream" % N
                                        if full else "%d requests without the 1024x1024 ones" % N),
             "mix": mix, "fgp_iters": K, "epochs": "U{100..300}", "lambda": "U(0.01,0.1)",
-            "weights": "f16", "slots_per_group": 32, "hbm_budget_gb": args.served_budget_gb,
+            "weights": "f16", "slots_per_group": 32,
+            "hbm_budget_gb": args.served_budget_gb, "packing_max_parts": pack,
+            "packed_groups": st2["packed_groups"], "max_parts_per_group": st2["max_parts"],
+            "launches_per_epoch_of_a_packed_group": st2["packed_launches"] or None,
             "max_tick_epochs": args.served_tick,
             "saturated": {"requests_per_s": sat_rps, "slice_epochs_per_s": slice_epochs / span_sat,
                           "p50_ms": 1e3 * float(np.percentile(lat_sat, 50)),

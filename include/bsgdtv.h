@@ -554,10 +554,27 @@ int bsgdtv_server_wait(bsgdtv_server_t s, int64_t request_id, double timeout_s, 
  * then ran on empty slots).  A serving feature; the paper has none. */
 int bsgdtv_server_arm(bsgdtv_server_t s, int geom_id, double wait_s);
 
-/* stats [15]: submitted, completed, failed, queued, running, groups, device
+/* hold != 0: requests submitted from now on (and those queued) wait in the
+ * queue without being admitted, while running ones carry on; hold = 0
+ * admits them again, a burst of them together (which lets packing see every
+ * geometry of the burst at once).  A serving feature; the paper has none. */
+int bsgdtv_server_hold(bsgdtv_server_t s, int hold);
+
+/* Packing of uneven requests: a group the server makes for a geometry also
+ * takes, as further parts of one packed batch (bsgdtv_packed_*), up to
+ * max_parts - 1 other geometries that have requests waiting and no free
+ * slot, need the same slot count, share the weight format and whose
+ * operators hold within cost_ratio times the nonzeros of each other; every
+ * epoch stage of the group is then one launch for all of them.  max_parts = 1
+ * (the default) packs nothing.  Applies to groups made afterwards. */
+int bsgdtv_server_set_packing(bsgdtv_server_t s, int max_parts, double cost_ratio);
+
+/* stats [18]: submitted, completed, failed, queued, running, groups, device
  * bytes in use (operators and groups), most requests running at once, runs
  * of epochs launched, epochs run by groups, slice-epochs of requests, groups
- * created, cancelled, armed epochs, armed waits that timed out. */
+ * created, cancelled, armed epochs, armed waits that timed out, packed groups
+ * created (more than one geometry), most geometries in one group, kernel
+ * launches per epoch of the last packed group made. */
 int bsgdtv_server_stats(bsgdtv_server_t s, int64_t *stats);
 
 #ifdef __cplusplus

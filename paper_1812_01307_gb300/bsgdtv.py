@@ -95,6 +95,8 @@ def load(path: str | None = None):
         "bsgdtv_server_wait": (I32, [P, I64, D, P, P]),
         "bsgdtv_server_stats": (I32, [P, P]),
         "bsgdtv_server_arm": (I32, [P, I32, D]),
+        "bsgdtv_server_set_packing": (I32, [P, I32, D]),
+        "bsgdtv_server_hold": (I32, [P, I32]),
         "bsgdtv_launch_count": (I64, []),
         "bsgdtv_last_error": (ctypes.c_char_p, []),
         "bsgdtv_strerror": (ctypes.c_char_p, [I32]),
@@ -121,7 +123,7 @@ def exported_symbols():
             "bsgdtv_batch_get_slice_x", "bsgdtv_batch_device_bytes", "bsgdtv_server_create",
             "bsgdtv_server_destroy", "bsgdtv_server_add_geometry", "bsgdtv_server_submit",
             "bsgdtv_server_poll", "bsgdtv_server_cancel", "bsgdtv_server_wait", "bsgdtv_server_stats",
-            "bsgdtv_server_arm",
+            "bsgdtv_server_arm", "bsgdtv_server_set_packing", "bsgdtv_server_hold",
             "bsgdtv_batch_create_parallel_beam", "bsgdtv_mf_ray_weights", "bsgdtv_batch_estimate_umax",
             "bsgdtv_batch_project", "bsgdtv_batch_autotune", "bsgdtv_batch_set_tuning", "bsgdtv_operator_create_csr",
             "bsgdtv_operator_destroy", "bsgdtv_batch_create_from_operator",
@@ -654,7 +656,7 @@ def bsgdtv_server_wait(h, request_id, out=None, timeout_s=-1.0):
 
 SERVER_STATS = ["submitted", "completed", "failed", "queued", "running", "groups", "device_bytes",
                 "max_running", "ticks", "epochs_run", "slice_epochs", "groups_made", "cancelled",
-                "armed_epochs", "wait_timeouts"]
+                "armed_epochs", "wait_timeouts", "packed_groups", "max_parts", "packed_launches"]
 
 
 def bsgdtv_server_stats(h):
@@ -949,6 +951,13 @@ class Server:
 
     def stats(self):
         return bsgdtv_server_stats(self.h)
+
+    def hold(self, on=True):
+        _check(load().bsgdtv_server_hold(self.h, 1 if on else 0), "bsgdtv_server_hold")
+
+    def set_packing(self, max_parts, cost_ratio=4.0):
+        _check(load().bsgdtv_server_set_packing(self.h, int(max_parts), float(cost_ratio)),
+               "bsgdtv_server_set_packing")
 
     def arm(self, geom_id, wait_s):
         """Arms an idle group of the geometry for wait_s seconds (device-side

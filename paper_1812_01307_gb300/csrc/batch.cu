@@ -379,14 +379,42 @@ __device__ __forceinline__ unsigned long long global_ns() {
 enum ServeAct { kActAdmit = 1, kActRetire = 2 };
 constexpr int kServeThreads = 256;
 
-// One CTA at the start of every served epoch.  (1) An armed epoch with no
-// live slot and no posted admission waits, bounded by ctrl->wait_ns, for a
-// mailbox to change.  (2) Per slot: a new seq admits (state latched from the
-// mailbox); a live slot whose budget is spent or that was cancelled retires
-// (tau = 0 from here on); every live slot then counts this epoch.
-__global__ void __launch_bounds__(kServeThreads)
-    serve_decide_kernel(const ServeSlot *mb, ServeDone *done, ServeCtrl *ctrl, int *state,
-                        int *acts, float *tau, int *arm_seen, int B) {
+// The served state of one part (a batch in served mode) as the scheduler
+// kernels see it; a launch covers up to kMaxServeParts parts.
+struct ServePart {
+    const ServeSlot *mb;
+    ServeDone *done;
+    ServeCtrl *ctrl;
+    int *state;      // [4 * B + 1]
+    int *acts;       // [B + 1]
+    float *tau;      // [B]
+    int *arm_seen;
+    const float *ypin;
+    float *xpin;
+    int *unit_cnt;   // [B]
+    float *Y, *X, *R;   // R: the r^{k-1} buffer the epoch reads
+    int64_t rows, cols;
+    int B, Bp;
+};
+constexpr int kMaxServeParts = 8;
+struct ServeLaunch {
+    ServePart part[kMaxServeParts];
+    int n_parts;
+};
+
+// One CTA per part at the start of every served epoch.  (1) An armed epoch
+// with no live slot and no posted admission waits, bounded by ctrl->wait_ns,
+// for a mailbox to change.  (2) Per slot: a new seq admits (state latched
+// from the mailbox); a live slot whose budget is spent or that was cancelled
+// retires (tau = 0 from here on); every live slot then counts this epoch.
+__global__ void __launch_bounds__(kServeThreads) serve_decide_kernel(const __grid_constant__ ServeLaunch L) {
+    const ServePart &P = L.part[blockIdx.x];
+    const ServeSlot *mb = P.mb;
+    ServeDone *done = P.done;
+    ServeCtrl *ctrl = P.ctrl;
+    int *state = P.state, *acts = P.acts, *arm_seen = P.arm_seen;
+    float *tau = P.tau;
+    const int B = P.B;
     int *seq_s = state, *rem = state + B, *live = state + 2 * B, *ran = state + 3 * B;
     const int epoch = state[4 * B];   // index of this epoch in the group's sequence
     __shared__ int n_act;
@@ -450,69 +478,75 @@ __global__ void __launch_bounds__(kServeThreads)
 constexpr int kServeUnroll = 8;                               // elements per thread per unit
 constexpr int kServeChunk = kServeThreads * kServeUnroll;    // vector elements per work unit
 
-// Applies this epoch's actions, work units (action, chunk of the slot's
-// vectors) spread over a fixed grid.  Admit: Y_b = R_b = y (from the slot's
-// pinned staging row in host memory; each thread issues all its loads before
-// its stores, so a unit has kServeChunk reads in flight), X_b = 0.  Retire:
-// the slot's x to its pinned result row, then Y_b = X_b = R_b = 0; the last
-// unit of a retiring slot publishes the completion record (after every
-// unit's stores are visible to the host).
-__global__ void __launch_bounds__(kServeThreads)
-    serve_apply_kernel(const int *__restrict__ acts, const int *__restrict__ state,
-                       const float *__restrict__ ypin, float *__restrict__ xpin, ServeDone *done,
-                       int *unit_cnt, float *__restrict__ Y, float *__restrict__ X,
-                       float *__restrict__ R, int64_t rows, int64_t cols, int Bp, int B) {
-    const int n_act = acts[B];
-    if (n_act == 0) return;
-    const int64_t n = rows > cols ? rows : cols;
-    const int chunks = (int)((n + kServeChunk - 1) / kServeChunk);
-    for (int64_t w = blockIdx.x; w < (int64_t)n_act * chunks; w += gridDim.x) {
-        const int a = acts[w / chunks];
-        const int b = a & 0xFFFFFF, kind = a >> 24;
-        const int64_t i0 = (w % chunks) * (int64_t)kServeChunk + threadIdx.x;
-        float v[kServeUnroll];
-        if (kind == kActAdmit) {
+// Applies this epoch's actions of every part, work units (action, chunk of
+// the slot's vectors) spread over a fixed grid.  Admit: Y_b = R_b = y (from
+// the slot's pinned staging row in host memory; each thread issues all its
+// loads before its stores, so a unit has kServeChunk reads in flight), X_b =
+// 0.  Retire: the slot's x to its pinned result row, then Y_b = X_b = R_b =
+// 0; the last unit of a retiring slot publishes the completion record (after
+// every unit's stores are visible to the host).
+__global__ void __launch_bounds__(kServeThreads) serve_apply_kernel(const __grid_constant__ ServeLaunch L) {
+    for (int pi = 0; pi < L.n_parts; ++pi) {
+        const ServePart &P = L.part[pi];
+        const int B = P.B, Bp = P.Bp;
+        const int n_act = P.acts[B];
+        if (n_act == 0) continue;
+        const int64_t rows = P.rows, cols = P.cols;
+        const float *__restrict__ ypin = P.ypin;
+        float *__restrict__ xpin = P.xpin;
+        float *__restrict__ Y = P.Y;
+        float *__restrict__ X = P.X;
+        float *__restrict__ R = P.R;
+        const int64_t n = rows > cols ? rows : cols;
+        const int chunks = (int)((n + kServeChunk - 1) / kServeChunk);
+        for (int64_t w = blockIdx.x; w < (int64_t)n_act * chunks; w += gridDim.x) {
+            const int a = P.acts[w / chunks];
+            const int b = a & 0xFFFFFF, kind = a >> 24;
+            const int64_t i0 = (w % chunks) * (int64_t)kServeChunk + threadIdx.x;
+            float v[kServeUnroll];
+            if (kind == kActAdmit) {
 #pragma unroll
-            for (int k = 0; k < kServeUnroll; ++k) {
-                const int64_t i = i0 + (int64_t)k * kServeThreads;
-                v[k] = i < rows ? __ldcv(ypin + (int64_t)b * rows + i) : 0.f;
-            }
-#pragma unroll
-            for (int k = 0; k < kServeUnroll; ++k) {
-                const int64_t i = i0 + (int64_t)k * kServeThreads;
-                if (i < rows) {
-                    Y[i * Bp + b] = v[k];
-                    R[i * Bp + b] = v[k];
+                for (int k = 0; k < kServeUnroll; ++k) {
+                    const int64_t i = i0 + (int64_t)k * kServeThreads;
+                    v[k] = i < rows ? __ldcv(ypin + (int64_t)b * rows + i) : 0.f;
                 }
-                if (i < cols) X[i * Bp + b] = 0.f;
-            }
-        } else {
 #pragma unroll
-            for (int k = 0; k < kServeUnroll; ++k) {
-                const int64_t i = i0 + (int64_t)k * kServeThreads;
-                v[k] = i < cols ? X[i * Bp + b] : 0.f;
-            }
+                for (int k = 0; k < kServeUnroll; ++k) {
+                    const int64_t i = i0 + (int64_t)k * kServeThreads;
+                    if (i < rows) {
+                        Y[i * Bp + b] = v[k];
+                        R[i * Bp + b] = v[k];
+                    }
+                    if (i < cols) X[i * Bp + b] = 0.f;
+                }
+            } else {
 #pragma unroll
-            for (int k = 0; k < kServeUnroll; ++k) {
-                const int64_t i = i0 + (int64_t)k * kServeThreads;
-                if (i < cols) {
-                    xpin[(int64_t)b * cols + i] = v[k];
-                    X[i * Bp + b] = 0.f;
+                for (int k = 0; k < kServeUnroll; ++k) {
+                    const int64_t i = i0 + (int64_t)k * kServeThreads;
+                    v[k] = i < cols ? X[i * Bp + b] : 0.f;
                 }
-                if (i < rows) {
-                    Y[i * Bp + b] = 0.f;
-                    R[i * Bp + b] = 0.f;
+#pragma unroll
+                for (int k = 0; k < kServeUnroll; ++k) {
+                    const int64_t i = i0 + (int64_t)k * kServeThreads;
+                    if (i < cols) {
+                        xpin[(int64_t)b * cols + i] = v[k];
+                        X[i * Bp + b] = 0.f;
+                    }
+                    if (i < rows) {
+                        Y[i * Bp + b] = 0.f;
+                        R[i * Bp + b] = 0.f;
+                    }
                 }
-            }
-            __threadfence_system();
-            __syncthreads();
-            if (threadIdx.x == 0 && atomicAdd(unit_cnt + b, 1) == chunks - 1) {
-                unit_cnt[b] = 0;
-                done[b].epochs_run = state[3 * B + b];
                 __threadfence_system();
-                st_release_sys(&done[b].seq, state[b]);
+                __syncthreads();
+                if (threadIdx.x == 0 && atomicAdd(P.unit_cnt + b, 1) == chunks - 1) {
+                    P.unit_cnt[b] = 0;
+                    P.done[b].epochs_run = P.state[3 * B + b];
+                    __threadfence_system();
+                    st_release_sys(&P.done[b].seq, P.state[b]);
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
 }
@@ -688,19 +722,33 @@ int fgp_group_by_budget(const bsgdtv_batch_ctx *h) {
                                 h->B, kFgpFieldBudget / std::max<int64_t>(1, 36 * h->cols)));
 }
 
+// The slot scheduler of served parts at the start of an epoch reading
+// R[par]: admissions and retirements at this epoch boundary (one launch of
+// each scheduler kernel for all parts).
+int enqueue_serve_prologue(bsgdtv_batch_ctx *const *parts, int n, int par, cudaStream_t s) {
+    if (n < 1 || n > kMaxServeParts) return fail(BSGDTV_ERR_INVALID_ARG, "too many served parts");
+    ServeLaunch L = {};
+    L.n_parts = n;
+    for (int k = 0; k < n; ++k) {
+        const bsgdtv_batch_ctx *h = parts[k];
+        L.part[k] = {h->mb_d, h->done_d, h->ctrl_d, h->slot_state, h->acts, h->tau, h->arm_seen,
+                     h->ypin_d, h->xpin_d, h->unit_cnt, h->Y, h->X, h->R[par], h->rows, h->cols,
+                     h->B, h->Bp};
+    }
+    serve_decide_kernel<<<n, kServeThreads, 0, s>>>(L);
+    serve_apply_kernel<<<parts[0]->serve_grid, kServeThreads, 0, s>>>(L);
+    add_launches(2);
+    BSG_CUDA(cudaGetLastError());
+    return BSGDTV_OK;
+}
+
 // One epoch of every slice: reads R[par], writes R[1 - par].
 int benqueue_epoch(bsgdtv_batch_ctx *h, int par, int fgp_iters, cudaStream_t s,
                    cudaEvent_t *marks) {
     const bool prox = any_prox(h, fgp_iters);
     if (h->served) {
-        // the slot scheduler: admissions and retirements at this epoch boundary
-        serve_decide_kernel<<<1, kServeThreads, 0, s>>>(h->mb_d, h->done_d, h->ctrl_d, h->slot_state,
-                                                        h->acts, h->tau, h->arm_seen, h->B);
-        serve_apply_kernel<<<h->serve_grid, kServeThreads, 0, s>>>(
-            h->acts, h->slot_state, h->ypin_d, h->xpin_d, h->done_d, h->unit_cnt, h->Y, h->X,
-            h->R[par], h->rows, h->cols, h->Bp, h->B);
-        add_launches(2);
-        BSG_CUDA(cudaGetLastError());
+        bsgdtv_batch_ctx *one[1] = {h};
+        BSG_CHECK(enqueue_serve_prologue(one, 1, par, s));
     }
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[0], s, cudaEventRecordExternal));
     if (h->matrix_free) {
@@ -1710,6 +1758,7 @@ bool packed_prox(const bsgdtv_packed_ctx *h, int fgp_iters) {
 int penqueue_epoch(bsgdtv_packed_ctx *h, int par, int fgp_iters, cudaStream_t s) {
     const int n = (int)h->parts.size();
     const bool prox = packed_prox(h, fgp_iters);
+    if (h->parts[0]->served) BSG_CHECK(enqueue_serve_prologue(h->parts.data(), n, par, s));
     PassPart rowp[kMaxPassParts], colp[kMaxPassParts];
     TransPart tin[kMaxTransParts], tout[kMaxTransParts];
     fgpk::FgpImages img[fgpk::kMaxFgpParts];
@@ -1728,7 +1777,35 @@ int penqueue_epoch(bsgdtv_packed_ctx *h, int par, int fgp_iters, cudaStream_t s)
     BSG_CUDA(launch_pass_parts<false>(h->fmt, h->lpn, colp, n, h->Bp, s));
     if (prox) {
         BSG_CUDA(launch_transpose_parts(tin, n, h->B, h->Bp, true, s));
-        BSG_CUDA(fgpk::launch_fgp_parts(img, n, fgp_iters, h->mom, s, false, h->fgp_chunk));
+        // the prox over groups of images whose fields (b and both dual sets,
+        // 36 bytes per pixel) fit about half of the L2, so consecutive chunk
+        // launches of a group find them there; a group may span parts
+        fgpk::FgpImages grp[fgpk::kMaxFgpParts];
+        int ng = 0;
+        int64_t used = 0;
+        for (int k = 0; k < n; ++k) {
+            const bsgdtv_batch_ctx *p = h->parts[k];
+            const int64_t per = 36 * p->cols;
+            for (int b0 = 0; b0 < p->B;) {
+                if (ng == fgpk::kMaxFgpParts || (ng > 0 && used + per > kFgpFieldBudget)) {
+                    BSG_CUDA(fgpk::launch_fgp_parts(grp, ng, fgp_iters, h->mom, s, false, h->fgp_chunk));
+                    ng = 0;
+                    used = 0;
+                }
+                const int fit = (int)std::max<int64_t>(1, (kFgpFieldBudget - used) / per);
+                const int nb = std::min(p->B - b0, fit);
+                fgpk::FgpImages q = img[k];
+                q.b = img[k].b + (int64_t)b0 * p->cols;
+                q.x = img[k].x + (int64_t)b0 * p->cols;
+                q.tau_z = p->tau + b0;
+                q.sc = fgp_scratch_planes(p->fgp, (int64_t)p->B * p->cols, (int64_t)b0 * p->cols);
+                q.slices = nb;
+                grp[ng++] = q;
+                used += per * nb;
+                b0 += nb;
+            }
+        }
+        if (ng > 0) BSG_CUDA(fgpk::launch_fgp_parts(grp, ng, fgp_iters, h->mom, s, false, h->fgp_chunk));
         BSG_CUDA(launch_transpose_parts(tout, n, h->B, h->Bp, false, s));
     }
     return BSGDTV_OK;
@@ -1771,6 +1848,21 @@ int pbuild_graphs(bsgdtv_packed_ctx *h, int fgp_iters) {
 }
 
 }  // namespace
+
+namespace bsgdtv {
+
+bsgdtv_batch_t packed_part(bsgdtv_packed_t h, int k) {
+    return (h && k >= 0 && k < (int)h->parts.size()) ? h->parts[k] : nullptr;
+}
+
+int packed_serve_enable(bsgdtv_packed_t h, int k, ServeView *view, void *host_block) {
+    if (!h || k < 0 || k >= (int)h->parts.size()) return fail(BSGDTV_ERR_INVALID_ARG, "part out of range");
+    BSG_CHECK(batch_serve_enable(h->parts[k], view, host_block));
+    pdrop_graphs(h);   // the epochs gain the scheduler
+    return BSGDTV_OK;
+}
+
+}  // namespace bsgdtv
 
 extern "C" {
 

@@ -248,6 +248,13 @@ size_t batch_serve_host_bytes(int B, int64_t rows, int64_t cols);
 // state; the epoch graphs gain the scheduler.  Slots start empty.
 int batch_serve_enable(bsgdtv_batch_t h, ServeView *view, void *host_block);
 
+// Part k of a packed batch (a batch handle owned by it), or null.
+bsgdtv_batch_t packed_part(bsgdtv_packed_t h, int k);
+// batch_serve_enable for part k of a packed batch (every part of a packed
+// batch is served or none is); its epochs gain one scheduler launch pair
+// for all parts.
+int packed_serve_enable(bsgdtv_packed_t h, int k, ServeView *view, void *host_block);
+
 // batch.cu: bsgdtv_batch_set_slice, with check = false for a host y the
 // caller has already checked for NaN/Inf (no device check, no wait).
 int batch_set_slice(bsgdtv_batch_t h, int b, const float *y, int y_on_device, double lambda,

@@ -69,25 +69,40 @@ struct Request {
 };
 
 constexpr int kMaxRuns = 2;     // runs of epochs in flight per group
+constexpr int kMaxParts = 8;    // geometries packed into one group at most
 
-struct Group {
+// One geometry's slots inside a group (a part of the group's packed batch).
+struct Part {
     int geom = 0;
-    bsgdtv_batch_t batch = nullptr;
-    cudaStream_t stream = nullptr;
     bsgdtv::ServeView view = {};     // host-mapped mailboxes, records, staging rows
     void *pinned = nullptr;          // the block behind view (from the server's pool)
     std::vector<int64_t> slot_req;   // request id per slot, -1 = free
     std::vector<int> slot_seq;       // last sequence number posted per slot
     std::vector<int64_t> slot_end;   // epochs the group must have run to retire the slot's
                                      // request (known once the device picked it up; -1 before)
-    int64_t enq = 0;                 // epochs enqueued on the group since it was made
+    int arm_seq = 0;                 // last armed epoch's sequence number (this part's control)
+};
+
+// A group: a packed batch of one or more geometries' parts with a common slot
+// count, on its own stream; every epoch stage is one launch over all parts.
+struct Group {
+    bsgdtv_packed_t packed = nullptr;
+    cudaStream_t stream = nullptr;
+    std::vector<Part> parts;
+    int slots = 0;
     cudaEvent_t run_ev[kMaxRuns] = {};
     int run_len[kMaxRuns] = {};
     int runs = 0;                    // runs in flight (run_ev[0 .. runs) in launch order)
-    int arm_seq = 0;                 // last armed epoch's sequence number
-    bool armed = false;              // an armed epoch's wait has not been reported yet
+    int64_t enq = 0;                 // epochs enqueued on the group since it was made
+    int armed_part = -1;             // part whose armed wait has not been reported yet
     int64_t bytes = 0;
+    int64_t launches_per_epoch = 0;
     Clock::time_point idle_since;
+    Part *part_of(int geom) {
+        for (Part &p : parts)
+            if (p.geom == geom) return &p;
+        return nullptr;
+    }
 };
 
 struct Geometry {
@@ -144,8 +159,15 @@ struct bsgdtv_server_ctx {
     };
     std::vector<Pinned> pinned;
     // statistics
+    // packing: a new group also takes other waiting geometries of the same
+    // slot count whose operators are within cost_ratio (nonzeros) of each
+    // other, up to max_parts geometries
+    bool hold = false;   // admissions held (bsgdtv_server_hold)
+    int pack_max_parts = 1;
+    double pack_cost_ratio = 4.0;
     int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, ticks = 0, epochs_run = 0, groups_made = 0,
-            groups_freed = 0, max_running = 0, slice_epochs = 0, wait_timeouts = 0, armed_epochs = 0;
+            groups_freed = 0, max_running = 0, slice_epochs = 0, wait_timeouts = 0, armed_epochs = 0,
+            packed_groups = 0, max_parts = 0, packed_launches = 0;
 };
 
 namespace {
@@ -164,10 +186,10 @@ bool finished(const Request &r) {
     return r.state == kDone || r.state == kFailed || r.state == kCancelled;
 }
 
-// Slot b of g is free again (the device emptied it when it retired).
-void free_slot(Group *g, int b) {
-    g->slot_req[b] = -1;
-    g->slot_end[b] = -1;
+// Slot b of a part is free again (the device emptied it when it retired).
+void free_slot(Part *p, int b) {
+    p->slot_req[b] = -1;
+    p->slot_end[b] = -1;
 }
 
 void finish_cancelled(bsgdtv_server_ctx *s, Request &r) {
@@ -199,8 +221,9 @@ void pinned_release(bsgdtv_server_ctx *s, void *p) {
 }
 
 int destroy_group(bsgdtv_server_ctx *s, Group *g) {
-    if (g->batch) bsgdtv_batch_destroy(g->batch);
-    if (g->pinned) pinned_release(s, g->pinned);
+    if (g->packed) bsgdtv_packed_destroy(g->packed);
+    for (Part &p : g->parts)
+        if (p.pinned) pinned_release(s, p.pinned);
     for (cudaEvent_t &ev : g->run_ev)
         if (ev) cudaEventDestroy(ev);
     if (g->stream) cudaStreamDestroy(g->stream);
@@ -209,77 +232,129 @@ int destroy_group(bsgdtv_server_ctx *s, Group *g) {
     return BSGDTV_OK;
 }
 
-// Creates a group for geometry gi (caller holds the lock; the A upload runs
-// under it, which only delays submitters).
-int make_group(bsgdtv_server_ctx *s, int gi, int slots, Group **out) {
-    Geometry &G = *s->geoms[gi];
+// Creates a group of the geometries `gis` with `slots` slots each (caller
+// holds the lock).
+int make_group(bsgdtv_server_ctx *s, const std::vector<int> &gis, int slots, Group **out) {
     std::unique_ptr<Group> g(new Group());
-    g->geom = gi;
-    g->bytes = G.bytes_for(slots);
+    g->slots = slots;
+    int64_t bytes = 0;
+    std::vector<bsgdtv_operator_t> ops;
+    for (int gi : gis) {
+        bytes += s->geoms[gi]->bytes_for(slots);
+        ops.push_back(s->geoms[gi]->op);
+    }
+    g->bytes = bytes;
     BSG_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
     int rc = BSGDTV_OK;
     for (cudaEvent_t &ev : g->run_ev)
         if (rc == BSGDTV_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
             rc = fail(BSGDTV_ERR_CUDA, "event creation");
-    if (rc == BSGDTV_OK) rc = bsgdtv_batch_create_from_operator(&g->batch, G.op, slots, g->stream);
-    if (rc == BSGDTV_OK) bsgdtv::batch_keep_prox(g->batch, s->fgp_iters > 0);
-    if (rc == BSGDTV_OK) {
+    if (rc == BSGDTV_OK)
+        rc = bsgdtv_packed_create(&g->packed, ops.data(), (int)ops.size(), slots, g->stream);
+    g->parts.resize(gis.size());
+    for (size_t k = 0; k < gis.size() && rc == BSGDTV_OK; ++k) {
+        const Geometry &G = *s->geoms[gis[k]];
+        Part &p = g->parts[k];
+        p.geom = gis[k];
+        bsgdtv::batch_keep_prox(bsgdtv::packed_part(g->packed, (int)k), s->fgp_iters > 0);
         std::vector<float> zeros((size_t)G.rows * slots, 0.f);
         std::vector<double> lam((size_t)slots, 0.0);
-        rc = bsgdtv_batch_set_data(g->batch, zeros.data(), 0, lam.data(), G.mu);
+        rc = bsgdtv_packed_set_part(g->packed, (int)k, zeros.data(), 0, lam.data(), G.mu);
+        if (rc == BSGDTV_OK) {
+            p.pinned = pinned_acquire(s, bsgdtv::batch_serve_host_bytes(slots, G.rows, G.cols));
+            rc = p.pinned ? bsgdtv::packed_serve_enable(g->packed, (int)k, &p.view, p.pinned)
+                          : fail(BSGDTV_ERR_OOM, "pinned host memory for a served group");
+        }
+        p.slot_req.assign(slots, -1);
+        p.slot_seq.assign(slots, 0);
+        p.slot_end.assign(slots, -1);
     }
-    if (rc == BSGDTV_OK) {
-        g->pinned = pinned_acquire(s, bsgdtv::batch_serve_host_bytes(slots, G.rows, G.cols));
-        rc = g->pinned ? bsgdtv::batch_serve_enable(g->batch, &g->view, g->pinned)
-                       : fail(BSGDTV_ERR_OOM, "pinned host memory for a served group");
-    }
+    if (rc == BSGDTV_OK)
+        rc = bsgdtv_packed_launches_per_epoch(g->packed, s->fgp_iters, &g->launches_per_epoch);
     if (rc != BSGDTV_OK) {
-        if (g->batch) bsgdtv_batch_destroy(g->batch);
-        if (g->pinned) pinned_release(s, g->pinned);
+        if (g->packed) bsgdtv_packed_destroy(g->packed);
+        for (Part &p : g->parts)
+            if (p.pinned) pinned_release(s, p.pinned);
         for (cudaEvent_t &ev : g->run_ev)
             if (ev) cudaEventDestroy(ev);
         cudaStreamDestroy(g->stream);
         return rc;
     }
-    g->slot_req.assign(slots, -1);
-    g->slot_seq.assign(slots, 0);
-    g->slot_end.assign(slots, -1);
     g->idle_since = Clock::now();
     s->hbm_used += g->bytes;
     s->groups_made++;
+    if (gis.size() > 1) {
+        s->packed_groups++;
+        s->packed_launches = g->launches_per_epoch;
+    }
+    s->max_parts = std::max<int64_t>(s->max_parts, (int64_t)gis.size());
     *out = g.get();
     s->groups.push_back(std::move(g));
     return BSGDTV_OK;
 }
 
 bool group_idle(const Group *g) {
-    if (g->runs > 0 || g->armed) return false;
-    for (int64_t id : g->slot_req)
-        if (id >= 0) return false;
+    if (g->runs > 0 || g->armed_part >= 0) return false;
+    for (const Part &p : g->parts)
+        for (int64_t id : p.slot_req)
+            if (id >= 0) return false;
     return true;
+}
+
+int running_of(const bsgdtv_server_ctx *s, int gi) {
+    int n = 0;
+    for (auto &g : s->groups)
+        for (const Part &p : g->parts)
+            if (p.geom == gi)
+                for (int64_t id : p.slot_req) n += id >= 0;
+    return n;
+}
+
+bool has_free_slot(const bsgdtv_server_ctx *s, int gi) {
+    for (auto &g : s->groups)
+        for (const Part &p : g->parts)
+            if (p.geom == gi)
+                for (int64_t id : p.slot_req)
+                    if (id < 0) return true;
+    return false;
+}
+
+// Slots of a new group for geometry gi: a power of two between min_slots
+// and slots covering the geometry's demand (requests waiting plus running).
+int demand_slots(const bsgdtv_server_ctx *s, int gi) {
+    const Geometry &G = *s->geoms[gi];
+    int slots = G.min_slots;
+    const int64_t demand = G.queued + running_of(s, gi);
+    while (slots < G.slots && slots < demand) slots *= 2;
+    return std::min(slots, G.slots);
 }
 
 // Finds or makes a free slot for geometry gi.  Returns false if none can be
 // had now (the request waits); sets *fatal if the geometry can never fit.
-bool find_slot(bsgdtv_server_ctx *s, int gi, Group **gout, int *slot, int *fatal) {
+bool find_slot(bsgdtv_server_ctx *s, int gi, Group **gout, int *part, int *slot, int *fatal) {
     *fatal = BSGDTV_OK;
     // any free slot of this geometry, running group or not (admission is
     // posted to the slot's mailbox; an armed group first)
     Group *best = nullptr;
-    int best_slot = -1;
-    for (auto &g : s->groups) {
-        if (g->geom != gi) continue;
-        for (int b = 0; b < (int)g->slot_req.size(); ++b)
-            if (g->slot_req[b] < 0) {
-                if (!best || (g->armed && !best->armed)) {
-                    best = g.get();
-                    best_slot = b;
+    int best_part = -1, best_slot = -1;
+    for (auto &g : s->groups)
+        for (int k = 0; k < (int)g->parts.size(); ++k) {
+            const Part &p = g->parts[k];
+            if (p.geom != gi) continue;
+            for (int b = 0; b < (int)p.slot_req.size(); ++b)
+                if (p.slot_req[b] < 0) {
+                    const bool armed = g->armed_part == k;
+                    if (!best || (armed && best->armed_part < 0)) {
+                        best = g.get();
+                        best_part = k;
+                        best_slot = b;
+                    }
+                    break;
                 }
-                break;
-            }
-    }
+        }
     if (best) {
         *gout = best;
+        *part = best_part;
         *slot = best_slot;
         return true;
     }
@@ -288,29 +363,41 @@ bool find_slot(bsgdtv_server_ctx *s, int gi, Group **gout, int *slot, int *fatal
         *fatal = BSGDTV_ERR_OOM;
         return false;
     }
-    // every group of this geometry is full: a new group (a power of two
-    // between min_slots and slots) is sized by the geometry's demand, the
-    // requests waiting plus those running, so light load gets small groups
-    // with short epochs (low latency) and sustained load large ones that read
-    // A once for many slices (throughput); shrunk if the budget cannot hold it
-    int slots = G.min_slots, running_g = 0;
-    for (auto &g : s->groups)
-        if (g->geom == gi)
-            for (int64_t id : g->slot_req) running_g += id >= 0;
-    while (slots < G.slots && slots < G.queued + running_g) slots *= 2;
-    slots = std::min(slots, G.slots);
-    while (slots > G.min_slots && s->hbm_used + G.bytes_for(slots) > s->budget &&
+    // every group of this geometry is full: a new group sized by the
+    // geometry's demand (requests waiting plus running), so light load gets
+    // small groups with short epochs (low latency) and sustained load large
+    // ones that read A once for many slices (throughput); shrunk if the
+    // budget cannot hold it.  With packing, other geometries with requests
+    // waiting and no free slot, the same slot count and operators of a
+    // similar size join it as parts (one launch per epoch stage for all).
+    int slots = demand_slots(s, gi);
+    std::vector<int> gis = {gi};
+    if (s->pack_max_parts > 1) {
+        for (int h = 0; h < (int)s->geoms.size() && (int)gis.size() < s->pack_max_parts; ++h) {
+            if (h == gi || !s->geoms[h] || s->geoms[h]->queued <= 0 || has_free_slot(s, h)) continue;
+            const Geometry &H = *s->geoms[h];
+            if (H.format != G.format || demand_slots(s, h) != slots) continue;
+            const double r = (double)std::max(H.nnz, G.nnz) / (double)std::max<int64_t>(1, std::min(H.nnz, G.nnz));
+            if (r <= s->pack_cost_ratio) gis.push_back(h);
+        }
+    }
+    auto bytes_of = [&](int sl) {
+        int64_t b = 0;
+        for (int k : gis) b += s->geoms[k]->bytes_for(sl);
+        return b;
+    };
+    while (slots > G.min_slots && s->hbm_used + bytes_of(slots) > s->budget &&
            !std::any_of(s->groups.begin(), s->groups.end(), [&](const std::unique_ptr<Group> &p) {
-               return p->geom != gi && group_idle(p.get());
+               return !p->part_of(gi) && group_idle(p.get());
            }))
         slots = std::max(G.min_slots, slots / 2);
-    const int64_t need = G.bytes_for(slots);
-    // release idle groups of other geometries (oldest first) until it fits
+    while (gis.size() > 1 && s->hbm_used + bytes_of(slots) > s->budget) gis.pop_back();
+    const int64_t need = bytes_of(slots);
+    // release idle groups without this geometry (oldest first) until it fits
     while (s->hbm_used + need > s->budget) {
         Group *victim = nullptr;
         for (auto &g : s->groups)
-            if (g->geom != gi && group_idle(g.get()) &&
-                (!victim || g->idle_since < victim->idle_since))
+            if (!g->part_of(gi) && group_idle(g.get()) && (!victim || g->idle_since < victim->idle_since))
                 victim = g.get();
         if (!victim) return false;
         destroy_group(s, victim);
@@ -323,22 +410,24 @@ bool find_slot(bsgdtv_server_ctx *s, int gi, Group **gout, int *slot, int *fatal
         return false;
     }
     Group *g = nullptr;
-    const int rc = make_group(s, gi, slots, &g);
+    const int rc = make_group(s, gis, slots, &g);
     if (rc != BSGDTV_OK) {
         *fatal = rc;
         return false;
     }
     *gout = g;
+    *part = 0;
     *slot = 0;
     return true;
 }
 
 void admit(bsgdtv_server_ctx *s) {
+    if (s->hold) return;
     for (auto it = s->queue.begin(); it != s->queue.end();) {
         Request &r = *s->reqs[*it];
         Group *g = nullptr;
-        int slot = -1, fatal = BSGDTV_OK;
-        if (!find_slot(s, r.geom, &g, &slot, &fatal)) {
+        int part = -1, slot = -1, fatal = BSGDTV_OK;
+        if (!find_slot(s, r.geom, &g, &part, &slot, &fatal)) {
             if (fatal != BSGDTV_OK) {
                 finish_failed(s, r, fatal, fatal == BSGDTV_ERR_OOM
                                                ? "a group of this geometry exceeds the HBM budget"
@@ -354,14 +443,15 @@ void admit(bsgdtv_server_ctx *s) {
         // y was checked at submit.  Post the admission: staging row and
         // fields first, then the new sequence number (release)
         const Geometry &G = *s->geoms[r.geom];
-        bsgdtv::ServeSlot &m = g->view.mb[slot];
-        std::memcpy(g->view.ypin + (size_t)slot * G.rows, r.y.data(), (size_t)G.rows * sizeof(float));
+        Part &pt = g->parts[part];
+        bsgdtv::ServeSlot &m = pt.view.mb[slot];
+        std::memcpy(pt.view.ypin + (size_t)slot * G.rows, r.y.data(), (size_t)G.rows * sizeof(float));
         m.epochs = r.epochs;
         m.tau = (float)(G.mu * r.lambda);
-        const int seq = ++g->slot_seq[slot];
+        const int seq = ++pt.slot_seq[slot];
         __atomic_store_n(&m.seq, seq, __ATOMIC_RELEASE);
-        g->slot_req[slot] = r.id;
-        g->slot_end[slot] = -1;   // set when the device reports the pickup
+        pt.slot_req[slot] = r.id;
+        pt.slot_end[slot] = -1;   // set when the device reports the pickup
         r.state = kRunning;
         r.remaining = r.epochs;
         r.t_admit = Clock::now();
@@ -382,25 +472,27 @@ void feed_groups(bsgdtv_server_ctx *s) {
         // in flight (so the device picks them up)
         int64_t need = 0;
         bool occupied = false;
-        for (size_t b = 0; b < g->slot_req.size(); ++b)
-            if (g->slot_req[b] >= 0) {
-                running++;
-                occupied = true;
-                if (g->slot_end[b] >= 0) need = std::max(need, g->slot_end[b] - g->enq);
-            }
+        for (Part &p : g->parts)
+            for (size_t b = 0; b < p.slot_req.size(); ++b)
+                if (p.slot_req[b] >= 0) {
+                    running++;
+                    occupied = true;
+                    if (p.slot_end[b] >= 0) need = std::max(need, p.slot_end[b] - g->enq);
+                }
         if (occupied && need <= 0 && g->runs == 0) need = 1;
         while (need > 0 && g->runs < kMaxRuns) {
             const int len = (int)std::max<int64_t>(1, std::min<int64_t>(need, s->max_tick));
-            int rc = bsgdtv_batch_run(g->batch, len, s->fgp_iters);
+            int rc = bsgdtv_packed_run(g->packed, len, s->fgp_iters);
             if (rc == BSGDTV_OK && cudaEventRecord(g->run_ev[g->runs], g->stream) != cudaSuccess)
                 rc = BSGDTV_ERR_CUDA;
             if (rc != BSGDTV_OK) {
                 const std::string msg = std::string("run: ") + bsgdtv_last_error();
-                for (int64_t &id : g->slot_req)
-                    if (id >= 0) {
-                        finish_failed(s, *s->reqs[id], rc, msg);
-                        id = -1;
-                    }
+                for (Part &p : g->parts)
+                    for (int64_t &id : p.slot_req)
+                        if (id >= 0) {
+                            finish_failed(s, *s->reqs[id], rc, msg);
+                            id = -1;
+                        }
                 s->cv_done.notify_all();
                 break;
             }
@@ -412,18 +504,19 @@ void feed_groups(bsgdtv_server_ctx *s) {
         }
     }
     s->max_running = std::max(s->max_running, running);
-    // armed epochs: one epoch on an idle group (made if the budget allows)
+    // armed epochs: one epoch on an idle group of the geometry (made if the
+    // budget allows)
     for (bsgdtv_server_ctx::Arm *a : s->arms) {
         if (a->launched) continue;
         Group *g = nullptr;
         for (auto &p : s->groups)
-            if (p->geom == a->geom && group_idle(p.get())) {
+            if (p->part_of(a->geom) && group_idle(p.get())) {
                 g = p.get();
                 break;
             }
         if (!g) {
-            int slot = -1, fatal = BSGDTV_OK;
-            if (!find_slot(s, a->geom, &g, &slot, &fatal) || !group_idle(g)) {
+            int part = -1, slot = -1, fatal = BSGDTV_OK;
+            if (!find_slot(s, a->geom, &g, &part, &slot, &fatal) || !group_idle(g)) {
                 if (fatal != BSGDTV_OK) {
                     a->launched = a->finished = true;
                     a->result = fatal;
@@ -432,11 +525,14 @@ void feed_groups(bsgdtv_server_ctx *s) {
                 continue;
             }
         }
-        bsgdtv::ServeCtrl &c = *g->view.ctrl;
+        int k = 0;
+        while (g->parts[k].geom != a->geom) ++k;
+        Part &p = g->parts[k];
+        bsgdtv::ServeCtrl &c = *p.view.ctrl;
         c.wait_ns = a->wait_ns;
-        g->arm_seq++;
-        __atomic_store_n(&c.arm_seq, g->arm_seq, __ATOMIC_RELEASE);
-        int rc = bsgdtv_batch_run(g->batch, 1, s->fgp_iters);
+        p.arm_seq++;
+        __atomic_store_n(&c.arm_seq, p.arm_seq, __ATOMIC_RELEASE);
+        int rc = bsgdtv_packed_run(g->packed, 1, s->fgp_iters);
         if (rc == BSGDTV_OK && cudaEventRecord(g->run_ev[g->runs], g->stream) != cudaSuccess)
             rc = BSGDTV_ERR_CUDA;
         a->launched = true;
@@ -448,7 +544,7 @@ void feed_groups(bsgdtv_server_ctx *s) {
         }
         g->run_len[g->runs++] = 1;
         g->enq += 1;
-        g->armed = true;
+        g->armed_part = k;
         a->group = g;
         s->ticks++;
         s->epochs_run += 1;
@@ -469,13 +565,13 @@ bool harvest(bsgdtv_server_ctx *s) {
             if (q == cudaErrorNotReady) break;
             if (q != cudaSuccess) {
                 cudaGetLastError();
-                for (int64_t &id : g->slot_req)
-                    if (id >= 0) {
-                        finish_failed(s, *s->reqs[id], BSGDTV_ERR_CUDA,
-                                      std::string("run: ") + cudaGetErrorString(q));
-                        id = -1;
-                    }
-                any = true;
+                for (Part &p : g->parts)
+                    for (int64_t &id : p.slot_req)
+                        if (id >= 0) {
+                            finish_failed(s, *s->reqs[id], BSGDTV_ERR_CUDA,
+                                          std::string("run: ") + cudaGetErrorString(q));
+                            id = -1;
+                        }
             }
             // the oldest run is done: its event moves to the free end
             cudaEvent_t ev0 = g->run_ev[0];
@@ -487,51 +583,55 @@ bool harvest(bsgdtv_server_ctx *s) {
             g->runs--;
             any = true;
         }
-        const Geometry &G = *s->geoms[g->geom];
-        for (int b = 0; b < (int)g->slot_req.size(); ++b) {
-            const int64_t id = g->slot_req[b];
-            if (id < 0) continue;
-            Request &r = *s->reqs[id];
-            const bsgdtv::ServeDone &d = g->view.done[b];
-            if (g->slot_end[b] < 0 &&
-                __atomic_load_n(&d.picked_seq, __ATOMIC_ACQUIRE) == g->slot_seq[b])
-                // picked up at epoch e: runs epochs e .. e + E - 1, retired at e + E
-                g->slot_end[b] = (int64_t)d.picked_epoch + r.epochs + 1;
-            if (__atomic_load_n(&d.seq, __ATOMIC_ACQUIRE) != g->slot_seq[b]) {
-                // still running: post a cancellation once
-                if (r.cancel && __atomic_load_n(&g->view.mb[b].cancel, __ATOMIC_RELAXED) != g->slot_seq[b])
-                    __atomic_store_n(&g->view.mb[b].cancel, g->slot_seq[b], __ATOMIC_RELEASE);
-                continue;
-            }
-            const int ran = d.epochs_run;
-            s->slice_epochs += ran;
-            r.remaining = r.epochs - ran;
-            if (r.cancel) {
-                finish_cancelled(s, r);
-            } else {
-                try {
-                    r.x.assign(g->view.xpin + (size_t)b * G.cols, g->view.xpin + (size_t)(b + 1) * G.cols);
-                    r.state = kDone;
-                    r.t_done = Clock::now();
-                    s->completed++;
-                } catch (const std::bad_alloc &) {
-                    finish_failed(s, r, BSGDTV_ERR_OOM, "host allocation for x");
+        for (Part &p : g->parts) {
+            const Geometry &G = *s->geoms[p.geom];
+            for (int b = 0; b < (int)p.slot_req.size(); ++b) {
+                const int64_t id = p.slot_req[b];
+                if (id < 0) continue;
+                Request &r = *s->reqs[id];
+                const bsgdtv::ServeDone &d = p.view.done[b];
+                if (p.slot_end[b] < 0 &&
+                    __atomic_load_n(&d.picked_seq, __ATOMIC_ACQUIRE) == p.slot_seq[b])
+                    // picked up at epoch e: runs epochs e .. e + E - 1, retired at e + E
+                    p.slot_end[b] = (int64_t)d.picked_epoch + r.epochs + 1;
+                if (__atomic_load_n(&d.seq, __ATOMIC_ACQUIRE) != p.slot_seq[b]) {
+                    // still running: post a cancellation once
+                    if (r.cancel && __atomic_load_n(&p.view.mb[b].cancel, __ATOMIC_RELAXED) != p.slot_seq[b])
+                        __atomic_store_n(&p.view.mb[b].cancel, p.slot_seq[b], __ATOMIC_RELEASE);
+                    continue;
                 }
+                const int ran = d.epochs_run;
+                s->slice_epochs += ran;
+                r.remaining = r.epochs - ran;
+                if (r.cancel) {
+                    finish_cancelled(s, r);
+                } else {
+                    try {
+                        r.x.assign(p.view.xpin + (size_t)b * G.cols, p.view.xpin + (size_t)(b + 1) * G.cols);
+                        r.state = kDone;
+                        r.t_done = Clock::now();
+                        s->completed++;
+                    } catch (const std::bad_alloc &) {
+                        finish_failed(s, r, BSGDTV_ERR_OOM, "host allocation for x");
+                    }
+                }
+                free_slot(&p, b);
+                any = true;
             }
-            free_slot(g.get(), b);
-            any = true;
         }
-        if (g->armed &&
-            __atomic_load_n(&g->view.ctrl->status_seq, __ATOMIC_ACQUIRE) == g->arm_seq) {
-            const int timed_out = g->view.ctrl->status;
-            g->armed = false;
-            if (timed_out) s->wait_timeouts++;
-            for (bsgdtv_server_ctx::Arm *a : s->arms)
-                if (a->group == g.get() && !a->finished) {
-                    a->finished = true;
-                    a->result = timed_out ? BSGDTV_ERR_TIMEOUT : BSGDTV_OK;
-                }
-            any = true;
+        if (g->armed_part >= 0) {
+            const Part &p = g->parts[g->armed_part];
+            if (__atomic_load_n(&p.view.ctrl->status_seq, __ATOMIC_ACQUIRE) == p.arm_seq) {
+                const int timed_out = p.view.ctrl->status;
+                g->armed_part = -1;
+                if (timed_out) s->wait_timeouts++;
+                for (bsgdtv_server_ctx::Arm *a : s->arms)
+                    if (a->group == g.get() && !a->finished) {
+                        a->finished = true;
+                        a->result = timed_out ? BSGDTV_ERR_TIMEOUT : BSGDTV_OK;
+                    }
+                any = true;
+            }
         }
         if (group_idle(g.get()) && any) g->idle_since = Clock::now();
     }
@@ -664,7 +764,7 @@ int bsgdtv_server_add_geometry(bsgdtv_server_t s, int64_t rows, int64_t cols, in
     // prewarm: as many groups as the budget holds now, up to `prewarm`
     for (int k = 0; k < prewarm && s->hbm_used + s->geoms[gi]->bytes_for(slots) <= s->budget; ++k) {
         Group *g = nullptr;
-        const int rc = make_group(s, gi, slots, &g);
+        const int rc = make_group(s, {gi}, slots, &g);
         if (rc != BSGDTV_OK) return rc;
     }
     *geom_id = gi;
@@ -770,6 +870,27 @@ int bsgdtv_server_wait(bsgdtv_server_t s, int64_t request_id, double timeout_s, 
     return BSGDTV_OK;
 }
 
+int bsgdtv_server_hold(bsgdtv_server_t s, int hold) {
+    if (!s) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->hold = hold != 0;
+        s->wake = true;
+    }
+    s->cv_work.notify_all();
+    return BSGDTV_OK;
+}
+
+int bsgdtv_server_set_packing(bsgdtv_server_t s, int max_parts, double cost_ratio) {
+    if (!s) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    if (max_parts < 1 || max_parts > kMaxParts || !(cost_ratio >= 1.0))
+        return fail(BSGDTV_ERR_INVALID_ARG, "need 1 <= max_parts <= 8 and cost_ratio >= 1");
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->pack_max_parts = max_parts;
+    s->pack_cost_ratio = cost_ratio;
+    return BSGDTV_OK;
+}
+
 int bsgdtv_server_arm(bsgdtv_server_t s, int geom_id, double wait_s) {
     if (!s) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
     if (!(wait_s >= 0.0) || wait_s * 1e9 > (double)bsgdtv::kServeMaxWaitNs)
@@ -801,11 +922,13 @@ int bsgdtv_server_stats(bsgdtv_server_t s, int64_t *stats) {
     std::lock_guard<std::mutex> lock(s->mu);
     int64_t running = 0;
     for (auto &g : s->groups)
-        for (int64_t id : g->slot_req) running += id >= 0;
-    const int64_t v[15] = {s->submitted, s->completed,   s->failed,     (int64_t)s->queue.size(),
+        for (const Part &p : g->parts)
+            for (int64_t id : p.slot_req) running += id >= 0;
+    const int64_t v[18] = {s->submitted, s->completed,   s->failed,     (int64_t)s->queue.size(),
                            running,      (int64_t)s->groups.size(), s->hbm_used, s->max_running,
                            s->ticks,     s->epochs_run,  s->slice_epochs, s->groups_made,
-                           s->cancelled, s->armed_epochs, s->wait_timeouts};
+                           s->cancelled, s->armed_epochs, s->wait_timeouts, s->packed_groups,
+                           s->max_parts, s->packed_launches};
     std::memcpy(stats, v, sizeof(v));
     return BSGDTV_OK;
 }

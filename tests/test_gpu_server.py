@@ -61,14 +61,18 @@ MIX = [("g64", 1, 0.05, 14), ("g37", 2, 0.02, 9), ("g64", 3, 0.1, 23), ("g64", 4
        ("g64", 9, 0.02, 8), ("g37", 10, 0.06, 12)]
 
 
-def _serve(B, reqs, slots=3, max_tick=4, budget=1 << 34, stagger=0):
+def _serve(B, reqs, slots=3, max_tick=4, budget=1 << 34, stagger=0, pack=1):
     """Runs the requests through one server; submits `stagger` at a time from
-    a second thread while the first ones run.  Returns {index: x}."""
+    a second thread while the first ones run; pack > 1 lets groups take that
+    many geometries.  Returns {index: x}."""
     with B.Server(budget, K, max_tick) as srv:
+        if pack > 1:
+            srv.set_packing(pack, 1e9)
+            srv.hold(True)   # the whole burst is queued before the first group is made
         gid = {}
         for name in sorted({r[0] for r in reqs}):
             A, n, _, mu = geometry(name)
-            gid[name] = srv.add_geometry(A, (n, n), mu, slots=slots)
+            gid[name] = srv.add_geometry(A, (n, n), mu, slots=slots, prewarm=0 if pack > 1 else 1)
         ids = {}
 
         def submit(lo, hi):
@@ -77,12 +81,15 @@ def _serve(B, reqs, slots=3, max_tick=4, budget=1 << 34, stagger=0):
                 ids[i] = srv.submit(gid[name], request(name, seed), lam, ep)
 
         if stagger:
+            assert pack == 1
             submit(0, stagger)
             t = threading.Thread(target=lambda: (time.sleep(0.01), submit(stagger, len(reqs))))
             t.start()
             t.join()
         else:
             submit(0, len(reqs))
+        if pack > 1:
+            srv.hold(False)
         out = {}
         for i, rid in ids.items():
             x, lat, q = srv.wait(rid, gid[reqs[i][0]], timeout_s=120)
@@ -293,3 +300,23 @@ def test_server_armed_wait_admits_a_request(B):
         assert srv.stats()["wait_timeouts"] == 0
     alone, _ = _serve(B, [("g37", 5, 0.05, 11)], slots=4)
     assert np.array_equal(x, alone[0])
+
+
+def test_server_packs_two_geometries_into_one_group(B):
+    """With packing, requests of two geometries waiting together share one
+    group (one packed batch): every epoch stage is one launch for both
+    (scheduler pair, two passes, two transposes, one FGP launch), and each
+    result is bit-identical to the request served alone in an unpacked group
+    of the same slot count, and within 1e-4 of the oracle."""
+    reqs = MIX[:6]
+    mixed, st = _serve(B, reqs, slots=3, pack=2)
+    assert st["packed_groups"] >= 1 and st["max_parts"] == 2
+    assert st["packed_launches"] == 2 + 2 + 2 + 1
+    for i in range(len(reqs)):
+        alone, _ = _serve(B, [reqs[i]], slots=3)
+        assert np.array_equal(alone[0], mixed[i]), i
+    for i in (0, 1):
+        name, seed, lam, ep = reqs[i]
+        A, n, _, mu = geometry(name)
+        x_ref, _ = oracle.run(A, request(name, seed).astype(np.float64), (n, n), 1, 1, lam, mu, ep, K)
+        assert rel(mixed[i], x_ref) <= 1e-4, i
