@@ -555,6 +555,7 @@ def run_ours(args):
             bt.set_tuning(chunk, group)
         else:
             chunk, group, _ = bt.autotune(Kfb, 3)
+        lanes = bt.tuning()[2:]
         bt.set_data(Ys_dev, lam_b, mu)
         bt.run(max(W, 3), Kfb)
         torch.cuda.synchronize()
@@ -585,6 +586,7 @@ def run_ours(args):
                           "bytes_per_epoch_products": int(pass_bytes), "achieved_gbs": ach,
                           "autotuned_fgp_iters_per_launch": chunk,
                           "autotuned_fgp_slices_per_group": group,
+                          "pass_lanes_per_nonzero": {"row": lanes[0], "column": lanes[1]},
                           "frac": ach / peak,
                           "products_tflops": flops / prod_s / 1e12,
                           "alu_frac": flops / prod_s / 1e12 / fp32_peak,

@@ -415,14 +415,17 @@ int bsgdtv_batch_project(bsgdtv_batch_t h, const float *x, float *y);
 
 /* Autotuner: times epochs_per_trial epochs of this batch (on its current
  * data, state restored after every trial) for each candidate launch shape
- * and keeps the fastest.  The candidates are the FGP iterations per launch
- * (3, 4, 5, 6, 8: fewer iterations per launch mean a smaller halo per
+ * and keeps the fastest.  First the lanes per nonzero of each product pass
+ * (the batch's own count, half and a quarter of it: slices per warp step,
+ * see bsgdtv_batch_set_pass_lanes; these change the order of FP32 sums, so
+ * results may move within FP32 rounding), then the FGP iterations per
+ * launch (3, 4, 5, 6, 8: fewer iterations per launch mean a smaller halo per
  * 64 x 64 region but more launches and field traffic) times the slices per
  * FGP launch group (half, once and twice the count whose dual fields fill
  * 48 MB of L2, and all slices: small groups keep the fields in L2, large
- * ones fill more SMs per launch); every candidate gives bit-identical
- * iterates, so tuning never changes results.  Writes the choices and the
- * time per epoch (each may be NULL).  Synchronises; needs set_data. */
+ * ones fill more SMs per launch; these give bit-identical iterates).  Writes
+ * the FGP choices and the time per epoch (each may be NULL;
+ * bsgdtv_batch_get_tuning has all choices).  Synchronises; needs set_data. */
 int bsgdtv_batch_autotune(bsgdtv_batch_t h, int fgp_iters, int epochs_per_trial, int *fgp_chunk,
                           int *fgp_group, double *epoch_ms);
 
@@ -431,6 +434,23 @@ int bsgdtv_batch_autotune(bsgdtv_batch_t h, int fgp_iters, int epochs_per_trial,
  * FGP launch group (0: sized by the 48 MB L2 budget).  Results do not depend
  * on it.  Synchronises the stream when the tuning changes. */
 int bsgdtv_batch_set_tuning(bsgdtv_batch_t h, int fgp_chunk, int fgp_group);
+
+/* The tuning in force: FGP iterations per launch, slices per FGP launch
+ * group, and the lanes per nonzero of the row and column passes (any output
+ * may be NULL). */
+int bsgdtv_batch_get_tuning(bsgdtv_batch_t h, int *fgp_chunk, int *fgp_group, int *lanes_row,
+                            int *lanes_col);
+
+/* Lanes per nonzero of the row and column passes: each lane carries 4
+ * slices, so with L lanes a warp applies 32 / L nonzeros per step to 4 L
+ * slices and takes the padded slices in Bp / (4 L) chunks.  0 restores the
+ * batch's own count (the smallest with 4 L >= slices, at most 32); otherwise
+ * that count or, below 32, a smaller power of two >= 2.  Fewer lanes change the order of a slice's FP32
+ * sums (results within FP32 rounding, deterministic for a given choice).
+ * bsgdtv_batch_autotune times the batch's count, half and a quarter of it
+ * for each pass (keeping fewer lanes only when measurably faster) before its
+ * FGP search. */
+int bsgdtv_batch_set_pass_lanes(bsgdtv_batch_t h, int lanes_row, int lanes_col);
 
 /* Copies slice b's x [cols] (FP32).  To the host: synchronises the stream. */
 int bsgdtv_batch_get_slice_x(bsgdtv_batch_t h, int b, float *x, int out_on_device);

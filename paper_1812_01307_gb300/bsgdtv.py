@@ -80,6 +80,8 @@ def load(path: str | None = None):
         "bsgdtv_batch_project": (I32, [P, P, P]),
         "bsgdtv_batch_autotune": (I32, [P, I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(D)]),
         "bsgdtv_batch_set_tuning": (I32, [P, I32, I32]),
+        "bsgdtv_batch_get_tuning": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "bsgdtv_batch_set_pass_lanes": (I32, [P, I32, I32]),
         "bsgdtv_packed_create": (I32, [ctypes.POINTER(P), P, I32, I32, P]),
         "bsgdtv_packed_set_part": (I32, [P, I32, P, I32, P, D]),
         "bsgdtv_packed_run": (I32, [P, I32, I32]),
@@ -125,7 +127,8 @@ def exported_symbols():
             "bsgdtv_server_poll", "bsgdtv_server_cancel", "bsgdtv_server_wait", "bsgdtv_server_stats",
             "bsgdtv_server_arm", "bsgdtv_server_set_packing", "bsgdtv_server_hold",
             "bsgdtv_batch_create_parallel_beam", "bsgdtv_mf_ray_weights", "bsgdtv_batch_estimate_umax",
-            "bsgdtv_batch_project", "bsgdtv_batch_autotune", "bsgdtv_batch_set_tuning", "bsgdtv_operator_create_csr",
+            "bsgdtv_batch_project", "bsgdtv_batch_autotune", "bsgdtv_batch_set_tuning",
+            "bsgdtv_batch_get_tuning", "bsgdtv_batch_set_pass_lanes", "bsgdtv_operator_create_csr",
             "bsgdtv_operator_destroy", "bsgdtv_batch_create_from_operator",
             "bsgdtv_packed_create", "bsgdtv_packed_set_part", "bsgdtv_packed_run",
             "bsgdtv_packed_get_x", "bsgdtv_packed_launches_per_epoch", "bsgdtv_packed_destroy",
@@ -816,6 +819,17 @@ class BatchReconstructor:
 
     def set_tuning(self, fgp_chunk=0, fgp_group=0):
         bsgdtv_batch_set_tuning(self.h, fgp_chunk, fgp_group)
+
+    def tuning(self):
+        """(FGP iterations per launch, slices per FGP group, row-pass lanes, column-pass lanes)."""
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(load().bsgdtv_batch_get_tuning(self.h, *[ctypes.byref(a) for a in v]),
+               "bsgdtv_batch_get_tuning")
+        return tuple(a.value for a in v)
+
+    def set_pass_lanes(self, lanes_row=0, lanes_col=0):
+        _check(load().bsgdtv_batch_set_pass_lanes(self.h, int(lanes_row), int(lanes_col)),
+               "bsgdtv_batch_set_pass_lanes")
 
     def project(self, x, y=None):
         """y = A x per slice (CUDA tensors); resets the batch's state."""

@@ -74,8 +74,9 @@ __device__ __forceinline__ void fma4(float a, const float4 &x, float4 &acc) {
 
 // One warp per output element k (a row of A in the row pass, a column in the
 // column pass).  Each lane owns 4 consecutive slices; LPN lanes cover the 4*LPN
-// slices of one chunk, so the warp applies G = 32/LPN nonzeros at a time
-// (group g takes the nonzeros j = g, g + G, ...).  acc = sum_e a_e v[idx_e][slices]
+// slices of one chunk (the warp takes the Bp / (4 LPN) chunks in turn), so the
+// warp applies G = 32/LPN nonzeros at a time (group g takes the nonzeros j = g,
+// g + G, ...).  acc = sum_e a_e v[idx_e][slices]
 // in that fixed order, the G group sums are added by a fixed butterfly, then
 //   row pass:    out[k] = base[k] - acc       (base = y, v = x)
 //   column pass: out[k] = base[k] + mu*2*acc  (base = x, v = r_prev)
@@ -127,36 +128,37 @@ struct PassLaunch {
     int Bp;
 };
 
-template <int LPN, bool kRowPass, int kW>
+// kOwnStride: the padded slice stride is 4 * LPN (the batch's own lanes per
+// nonzero, one chunk), a compile-time constant; else L.Bp (fewer lanes than
+// that, several chunks).
+// kMulti: the launch has several parts (a packed batch); with one part the
+// descriptor's fields are read at fixed offsets of the kernel arguments.
+template <int LPN, bool kRowPass, int kW, bool kOwnStride = true, bool kMulti = false>
 __global__ void __launch_bounds__(kPassWarps * 32, kPassMinBlocks)
     pass_kernel(const __grid_constant__ PassLaunch L) {
     constexpr int G = 32 / LPN;
     constexpr int NB = (32 / G < 4) ? 32 / G : 4;
     int pi = 0;
-    while (pi + 1 < L.n_parts && (int)blockIdx.x >= L.part[pi + 1].cta_begin) ++pi;
+    if constexpr (kMulti)
+        while (pi + 1 < L.n_parts && (int)blockIdx.x >= L.part[pi + 1].cta_begin) ++pi;
+    // the part's fields are used where needed (read from the kernel
+    // arguments), not held in registers across the gather loop
     const PassPart &P = L.part[pi];
-    const PassOperand &A = P.A;
-    const float *__restrict__ v = P.v;
-    const float *__restrict__ base = P.base;
-    float *__restrict__ out = P.out;
-    const int Bp = L.Bp;
-    const float mu = P.mu;
-    // slice stride: 4 * LPN (a constant) below 128 slices, else Bp
-    const int stride = (LPN < 32) ? 4 * LPN : Bp;
+    const int Bp = (kOwnStride && LPN < 32) ? 4 * LPN : L.Bp;
     __shared__ int2 stage[kPassWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = lane / LPN, sl = lane % LPN;
-    const int64_t k = (int64_t)((int)blockIdx.x - P.cta_begin) * kPassWarps + w;
+    const int64_t k = (int64_t)(kMulti ? (int)blockIdx.x - P.cta_begin : (int)blockIdx.x) * kPassWarps + w;
     if (k >= P.n_out) return;   // warp-uniform
     const uint64_t pol = l2_evict_last_policy();
-    const int64_t e0 = A.ptr[k], e1 = A.ptr[k + 1];
+    const int64_t e0 = P.A.ptr[k], e1 = P.A.ptr[k + 1];
     for (int c0 = 0; c0 < Bp; c0 += 4 * LPN) {
-        const float *vl = v + c0 + sl * 4;
+        const float *vl = P.v + c0 + sl * 4;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int64_t r0 = e0; r0 < e1; r0 += 32) {
             const int64_t e = r0 + lane;
             int2 t = make_int2(0, 0);
-            if (e < e1) t = load_entry<kW>(A, e);
+            if (e < e1) t = load_entry<kW>(P.A, e);
             stage[w][lane] = t;
             __syncwarp();
             // NB gathers issued per lane before their FMAs
@@ -168,10 +170,12 @@ __global__ void __launch_bounds__(kPassWarps * 32, kPassMinBlocks)
                 for (int q = 0; q < NB; ++q) st[q] = stage[w][(q0 + q) * G + g];
 #pragma unroll
                 for (int q = 0; q < NB; ++q) {
-                    if constexpr (LPN < 32)   // element * stride < 2^31: checked at creation
-                        xv[q] = ld_keep(vl + st[q].y * (4 * LPN), pol);
+                    // below 32 lanes per nonzero the batch has Bp <= 128 and
+                    // element * Bp < 2^31 (checked at creation)
+                    if constexpr (LPN < 32)
+                        xv[q] = ld_keep(vl + st[q].y * Bp, pol);
                     else
-                        xv[q] = ld_keep(vl + (int64_t)st[q].y * stride, pol);
+                        xv[q] = ld_keep(vl + (int64_t)st[q].y * Bp, pol);
                 }
 #pragma unroll
                 for (int q = 0; q < NB; ++q) fma4(__int_as_float(st[q].x), xv[q], acc);
@@ -187,15 +191,16 @@ __global__ void __launch_bounds__(kPassWarps * 32, kPassMinBlocks)
         }
         if (g == 0) {
             const int64_t o = k * Bp + c0 + sl * 4;
-            const float4 b = __ldcs(reinterpret_cast<const float4 *>(base + o));
+            const float4 b = __ldcs(reinterpret_cast<const float4 *>(P.base + o));
             float4 res;
             if (kRowPass) {
                 res = make_float4(b.x - acc.x, b.y - acc.y, b.z - acc.z, b.w - acc.w);
             } else {
+                const float mu = P.mu;
                 res = make_float4(b.x + mu * (2.f * acc.x), b.y + mu * (2.f * acc.y),
                                   b.z + mu * (2.f * acc.z), b.w + mu * (2.f * acc.w));
             }
-            *reinterpret_cast<float4 *>(out + o) = res;
+            *reinterpret_cast<float4 *>(P.out + o) = res;
         }
     }
 }
@@ -203,21 +208,41 @@ __global__ void __launch_bounds__(kPassWarps * 32, kPassMinBlocks)
 template <bool kRowPass, int kW>
 cudaError_t launch_pass_w(int lpn, const PassLaunch &L, int ctas, cudaStream_t s) {
     const dim3 grid((unsigned)ctas), block(kPassWarps * 32);
-#define BSG_PASS(LP)                                                     \
-    case LP:                                                             \
-        pass_kernel<LP, kRowPass, kW><<<grid, block, 0, s>>>(L);         \
+    const bool own = lpn == 32 || 4 * lpn == L.Bp;
+#define BSG_PASS(LP)                                                                   \
+    case LP:                                                                           \
+        if (L.n_parts > 1)                                                             \
+            pass_kernel<LP, kRowPass, kW, true, true><<<grid, block, 0, s>>>(L);       \
+        else                                                                           \
+            pass_kernel<LP, kRowPass, kW><<<grid, block, 0, s>>>(L);                   \
         break;
-    switch (lpn) {
-        BSG_PASS(1)
-        BSG_PASS(2)
-        BSG_PASS(4)
-        BSG_PASS(8)
-        BSG_PASS(16)
-        BSG_PASS(32)
-        default:
-            return cudaErrorInvalidValue;
+#define BSG_PASS_N(LP)                                                   \
+    case LP:                                                             \
+        pass_kernel<LP, kRowPass, kW, false><<<grid, block, 0, s>>>(L);  \
+        break;
+    if (own) {
+        switch (lpn) {
+            BSG_PASS(1)
+            BSG_PASS(2)
+            BSG_PASS(4)
+            BSG_PASS(8)
+            BSG_PASS(16)
+            BSG_PASS(32)
+            default:
+                return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (lpn) {   // fewer lanes than the batch's own count (2 .. 16)
+            BSG_PASS_N(2)
+            BSG_PASS_N(4)
+            BSG_PASS_N(8)
+            BSG_PASS_N(16)
+            default:
+                return cudaErrorInvalidValue;
+        }
     }
 #undef BSG_PASS
+#undef BSG_PASS_N
     add_launches(1);
     return cudaGetLastError();
 }
@@ -614,6 +639,7 @@ struct bsgdtv_batch_ctx {
     cudaStream_t cap_stream = nullptr;
     int64_t rows = 0, cols = 0, nnz = 0;
     int img_h = 0, img_w = 0, B = 0, Bp = 0, lpn = 1;
+    int lpn_row = 0, lpn_col = 0;       // lanes per nonzero of the passes (0: lpn; autotuned)
     std::vector<void *> allocs;
     int fmt = BSGDTV_FMT_F32_I32;
     bsgdtv_operator_ctx *op = nullptr;  // shared A (one reference held), null if matrix free
@@ -757,10 +783,10 @@ int benqueue_epoch(bsgdtv_batch_ctx *h, int par, int fgp_iters, cudaStream_t s,
                                 (float)h->mu, s));
     } else {
         // r^k = y - A x^k (reads x before the column pass updates it)
-        BSG_CUDA(launch_pass<true>(h->fmt, h->lpn, h->op_r, h->X, h->Y, h->R[1 - par], h->rows,
+        BSG_CUDA(launch_pass<true>(h->fmt, h->lpn_row ? h->lpn_row : h->lpn, h->op_r, h->X, h->Y, h->R[1 - par], h->rows,
                                    h->Bp, 0.f, s));
         // x^ = x^k + mu * 2 A^T r^{k-1}
-        BSG_CUDA(launch_pass<false>(h->fmt, h->lpn, h->op_c, h->R[par], h->X, prox ? h->Xhat : h->X,
+        BSG_CUDA(launch_pass<false>(h->fmt, h->lpn_col ? h->lpn_col : h->lpn, h->op_c, h->R[par], h->X, prox ? h->Xhat : h->X,
                                     h->cols, h->Bp, (float)h->mu, s));
     }
     if (marks) BSG_CUDA(cudaEventRecordWithFlags(marks[1], s, cudaEventRecordExternal));
@@ -1647,6 +1673,29 @@ int bsgdtv_batch_autotune(bsgdtv_batch_t h, int fgp_iters, int epochs_per_trial,
         h->epoch = epoch;
         return BSGDTV_OK;
     };
+    // lanes per nonzero of each pass: the rule's count (one chunk of 4 * LPN
+    // slices = all of them) and fewer lanes covering the slices in 2 or 4
+    // chunks (more nonzeros per warp step, the nonzeros reread per chunk);
+    // each pass's product time decides, the other pass kept at its choice
+    if (h->lpn < 32 && !h->matrix_free) {
+        for (int pass = 0; pass < 2; ++pass) {
+            int best_l = h->lpn;
+            double best_pk = 1e300;
+            for (int l = h->lpn; l >= std::max(2, h->lpn / 4); l /= 2) {
+                (pass == 0 ? h->lpn_row : h->lpn_col) = l;
+                bdrop_graphs(h);
+                BSG_CHECK(bsgdtv_batch_run(h, 1, fgp_iters));
+                double pk = 0.0, ep = 0.0;
+                BSG_CHECK(bsgdtv_batch_run_timed(h, epochs_per_trial, fgp_iters, &pk, &ep));
+                BSG_CHECK(restore());
+                if (pk < best_pk * 0.99) {   // fewer lanes only when measurably faster
+                    best_pk = pk;
+                    best_l = l;
+                }
+            }
+            (pass == 0 ? h->lpn_row : h->lpn_col) = best_l;
+        }
+    }
     // slices per FGP launch group: half, once and twice the L2-budget size, all
     const int per = fgp_group_by_budget(h);
     std::vector<int> groups;
@@ -1678,6 +1727,31 @@ int bsgdtv_batch_autotune(bsgdtv_batch_t h, int fgp_iters, int epochs_per_trial,
     if (fgp_chunk) *fgp_chunk = best;
     if (fgp_group) *fgp_group = best_g > 0 ? best_g : per;
     if (epoch_ms) *epoch_ms = best_ms / epochs_per_trial;
+    return BSGDTV_OK;
+}
+
+int bsgdtv_batch_get_tuning(bsgdtv_batch_t h, int *fgp_chunk, int *fgp_group, int *lanes_row,
+                            int *lanes_col) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    if (fgp_chunk) *fgp_chunk = h->fgp_chunk;
+    if (fgp_group) *fgp_group = h->fgp_group > 0 ? h->fgp_group : fgp_group_by_budget(h);
+    if (lanes_row) *lanes_row = h->lpn_row ? h->lpn_row : h->lpn;
+    if (lanes_col) *lanes_col = h->lpn_col ? h->lpn_col : h->lpn;
+    return BSGDTV_OK;
+}
+
+int bsgdtv_batch_set_pass_lanes(bsgdtv_batch_t h, int lanes_row, int lanes_col) {
+    if (!h) return fail(BSGDTV_ERR_INVALID_ARG, "null handle");
+    auto ok = [&](int l) {
+        return l == 0 || l == h->lpn ||
+               (l >= 2 && l < h->lpn && (l & (l - 1)) == 0 && h->lpn < 32);
+    };
+    if (!ok(lanes_row) || !ok(lanes_col))
+        return fail(BSGDTV_ERR_INVALID_ARG,
+                    "lanes: 0, the batch's lanes per nonzero, or a smaller power of two >= 2");
+    h->lpn_row = lanes_row;
+    h->lpn_col = lanes_col;
+    bdrop_graphs(h);
     return BSGDTV_OK;
 }
 

@@ -150,14 +150,17 @@ struct FgpLaunch {
 // this region iterates that are a whole launch ahead.  A weight <= 0 makes an
 // image's prox the identity (x = b).
 // TY x V: threads in y x pixels per thread (TY * V = RH, V = 4).
-template <int TY, int V>
+// kMulti: the launch has several parts; with one part the descriptor's
+// fields are read at fixed offsets of the kernel arguments.
+template <int TY, int V, bool kMulti>
 __global__ void __launch_bounds__(RW *TY)
     fgp_kernel(const __grid_constant__ FgpLaunch L, const float *__restrict__ mom, int k0, int iters,
                int HL, int IH, int IW, int first, int last) {
     __shared__ __align__(16) FgpShared<TY, V> sh;
 
     int pi = 0;
-    while (pi + 1 < L.n_parts && (int)blockIdx.x >= L.part[pi + 1].cta_begin) ++pi;
+    if constexpr (kMulti)
+        while (pi + 1 < L.n_parts && (int)blockIdx.x >= L.part[pi + 1].cta_begin) ++pi;
     const FgpPart &P = L.part[pi];
     const int per = P.rx * P.ry, local = (int)blockIdx.x - P.cta_begin;
     const int z = local / per, reg = local - z * per;
@@ -363,8 +366,10 @@ cudaError_t launch_fgp_parts(const FgpImages *parts, int n_parts, int iters, con
     if (single) {
         // one launch, no field traffic (first and last)
         const int ctas = build(0, 0, RH, RW, L);
-        cudaError_t e = launch_kernel(fgp_kernel<TY, V>, dim3(ctas), block, 0, s, pdl, L, mom, 0,
-                                      iters, 0, RH, RW, 1, 1);
+        cudaError_t e = n_parts > 1 ? launch_kernel(fgp_kernel<TY, V, true>, dim3(ctas), block, 0, s, pdl,
+                                                    L, mom, 0, iters, 0, RH, RW, 1, 1)
+                                    : launch_kernel(fgp_kernel<TY, V, false>, dim3(ctas), block, 0, s, pdl,
+                                                    L, mom, 0, iters, 0, RH, RW, 1, 1);
         add_launches(1);
         return e != cudaSuccess ? e : cudaGetLastError();
     }
@@ -375,8 +380,11 @@ cudaError_t launch_fgp_parts(const FgpImages *parts, int n_parts, int iters, con
         const int IH = RH - 2 * HL, IW = RW - 2 * HL;
         const int ctas = build(launch, HL, IH, IW, L);
         const int first = (done == 0), last = (done + chunk == iters);
-        cudaError_t e = launch_kernel(fgp_kernel<TY, V>, dim3(ctas), block, 0, s, pdl || done > 0, L,
-                                      mom, done, chunk, HL, IH, IW, first, last);
+        const bool p = pdl || done > 0;
+        cudaError_t e = n_parts > 1 ? launch_kernel(fgp_kernel<TY, V, true>, dim3(ctas), block, 0, s, p, L,
+                                                    mom, done, chunk, HL, IH, IW, first, last)
+                                    : launch_kernel(fgp_kernel<TY, V, false>, dim3(ctas), block, 0, s, p, L,
+                                                    mom, done, chunk, HL, IH, IW, first, last);
         add_launches(1);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return e;

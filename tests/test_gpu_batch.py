@@ -318,34 +318,55 @@ def test_batch_set_slice_restarts_one_slot(B):
 
 
 def test_batch_autotune_keeps_results(B):
-    """The autotuner times every candidate FGP launch shape on the batch's data,
-    restores the state after each trial and keeps the fastest; the iterates
-    are bit-identical whatever it picks.  130x130 images (several regions)."""
+    """The autotuner times the passes' lanes per nonzero and every candidate
+    FGP launch shape on the batch's data, restores the state after each trial
+    and keeps the fastest; FGP shapes give bit-identical iterates, other
+    lanes per nonzero change only the FP32 summation order (<= 1e-6), and a
+    tuning applied by hand reproduces the tuned run bit for bit.  130x130
+    images (several regions), 16 slices (4 lanes per nonzero; 2 tried)."""
     n, na, nb = 130, 12, 185
     A = synth.parallel_beam_csr(n, na, nb)
-    _, Y = synth.slice_stack(A, n, 8, 6, seed=3)
+    _, Y = synth.slice_stack(A, n, 8, 16, seed=3)
     Y = Y.astype(np.float32)
     u, _ = oracle.power_iteration(A)
-    mu, lam = 0.9 / (2 * u), np.full(6, 0.05)
-    with B.BatchReconstructor(A, (n, n), 6) as bt:
+    mu, lam = 0.9 / (2 * u), np.full(16, 0.05)
+    with B.BatchReconstructor(A, (n, n), 16) as bt:
         bt.set_data(Y, lam, mu)
         bt.run(4, 30)
         X_plain = bt.x().copy()
         bt.set_data(Y, lam, mu)
         bt.run(2, 30)
         chunk, group, ms = bt.autotune(30, 2)
-        assert chunk in (3, 4, 5, 6, 8) and 1 <= group <= 6 and ms > 0
+        assert chunk in (3, 4, 5, 6, 8) and 1 <= group <= 16 and ms > 0
+        tuned = bt.tuning()
         bt.run(2, 30)
         X_tuned = bt.x().copy()
-        bt.set_tuning(3, 2)                  # a tuning applied by hand: same bits
+        bt.set_tuning(3, 2)                  # FGP shape by hand: same bits
+        bt.set_pass_lanes(0, 0)
         bt.set_data(Y, lam, mu)
         bt.run(4, 30)
         X_set = bt.x().copy()
+        bt.set_tuning(tuned[0], tuned[1])    # the tuned choice by hand: the tuned bits
+        bt.set_pass_lanes(tuned[2], tuned[3])
+        bt.set_data(Y, lam, mu)
+        bt.run(4, 30)
+        X_again = bt.x().copy()
+        bt.set_pass_lanes(2, 0)              # other lanes: FP32 rounding only
+        bt.set_data(Y, lam, mu)
+        bt.run(4, 30)
+        X_lanes = bt.x().copy()
         with pytest.raises(B.BsgdtvError) as e:
             bt.set_tuning(9, 0)
         assert e.value.code == -1
-    assert np.array_equal(X_plain, X_tuned)
+        for bad in (3, 1):
+            with pytest.raises(B.BsgdtvError) as e:
+                bt.set_pass_lanes(bad, 0)
+            assert e.value.code == -1
     assert np.array_equal(X_plain, X_set)
+    assert np.array_equal(X_tuned, X_again)
+    for X in (X_tuned, X_lanes):
+        for b in range(16):
+            assert rel(X[b], X_plain[b]) <= 1e-6
 
 
 def test_batches_share_one_operator(B):
