@@ -67,7 +67,9 @@ enum {
     BSGDTV_FMT_BF16_I16 = 3
 };
 
-/* Creates a handle from a host CSR matrix A (rows = rays, cols = pixels).
+/* Creates a handle from a host CSR matrix A (rows = rays, cols = pixels; the
+ * system y = A x of Eq. 1) split into the M x N blocks A_{I_i}^{J_j} of
+ * Sec. 2.1.
  *   rows, cols          size of A; cols must equal img_h*img_w.
  *   row_ptr [rows+1]    int64 offsets, row_ptr[0] = 0, non-decreasing.
  *   col_idx [nnz]       int32 column indices in [0, cols), ascending in a row.
@@ -110,14 +112,16 @@ int bsgdtv_create_csr_ex(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, i
 int bsgdtv_create_parallel_beam(bsgdtv_t *out, int n, int n_angles, int n_bins, int M, int N,
                                 int format, void *stream);
 
-/* Releases every resource of the handle.  NULL is ignored. */
+/* Releases every resource of the handle (API housekeeping: no passage of
+ * the paper).  NULL is ignored. */
 void bsgdtv_destroy(bsgdtv_t h);
 
-/* Copies the partition bounds I_i [M+1] and J_j [N+1] (host arrays). */
+/* Copies the partition bounds I_i [M+1] and J_j [N+1] of Sec. 2.1 (host
+ * arrays, either may be NULL). */
 int bsgdtv_get_partition(bsgdtv_t h, int64_t *row_bounds, int64_t *col_bounds);
 
-/* Sets the projections y [rows] (FP32), the TV weight lambda >= 0 and the step
- * mu.  mu <= 0 selects mu = 0.9/(2 u_max) (Theorem 1 requires mu < 1/(2 u_max)),
+/* Sets the projections y [rows] (FP32; Eq. 1), the TV weight lambda >= 0
+ * (Eq. 1, Algorithm 1's prox weight 2 mu lambda) and the step mu.  mu <= 0 selects mu = 0.9/(2 u_max) (Theorem 1 requires mu < 1/(2 u_max)),
  * estimating u_max first if no estimate exists.  Resets the iteration:
  * x^0 = 0, r^{-1} = y - A x^0 = y, epoch counter 0.  Rejects NaN/Inf in y
  * (BSGDTV_ERR_NONFINITE); once y is being copied, a failure leaves the handle
@@ -126,7 +130,8 @@ int bsgdtv_get_partition(bsgdtv_t h, int64_t *row_bounds, int64_t *col_bounds);
  * not (the call waits for the handle's earlier work and the copy). */
 int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, double mu);
 
-/* Largest eigenvalue u_max of A^T A by power iteration in FP64 on the device
+/* Largest eigenvalue u_max of A^T A (Theorem 1: the epoch recurrence
+ * converges for mu < 1/(2 u_max)) by power iteration in FP64 on the device
  * (A as stored, i.e. FP32 weights widened to FP64), from the all-ones vector,
  * stopping when the Rayleigh quotient changes by <= rel_tol relatively or after
  * max_iters iterations.  Writes u_max and the iteration count (may be NULL). */
@@ -135,8 +140,10 @@ int bsgdtv_estimate_umax(bsgdtv_t h, int max_iters, double rel_tol, double *u_ma
 /* Current step mu (after set_data) and the stored u_max estimate (0 if none). */
 int bsgdtv_get_params(bsgdtv_t h, double *mu, double *lambda, double *u_max);
 
-/* Runs `epochs` epochs of Algorithm 1 with `fgp_iters` FGP iterations for
- * the TV prox (lambda = 0 or fgp_iters = 0 makes the prox the identity).  Asynchronous
+/* Runs `epochs` epochs of Algorithm 1 (Sec. 2.1: block products, residual
+ * and gradient sums, step, TV prox; the gradient uses the previous epoch's
+ * residual, Eq. 3) with `fgp_iters` FGP iterations for the TV prox (lambda =
+ * 0 or fgp_iters = 0 makes the prox the identity).  Asynchronous
  * on the handle's stream; resumes from the current state. */
 int bsgdtv_run(bsgdtv_t h, int epochs, int fgp_iters);
 
@@ -170,16 +177,19 @@ int bsgdtv_run_subsets_timed(bsgdtv_t h, int iters, int fgp_iters, const uint8_t
 int bsgdtv_run_timed(bsgdtv_t h, int epochs, int fgp_iters, double *products_ms,
                      double *epoch_ms);
 
-/* Copies x [cols] (FP32).  To the host: synchronises the stream. */
-int bsgdtv_get_x(bsgdtv_t h, float *out, int out_on_device);
+/* Copies the current iterate x^k of Algorithm 1, [cols] FP32, row-major
+ * image, into out (n floats: BSGDTV_ERR_INVALID_ARG if n < cols).  To the
+ * host: synchronises the stream. */
+int bsgdtv_get_x(bsgdtv_t h, float *out, int out_on_device, int64_t n);
 
 /* Checkpoint: x^k [cols], r^{k-1} [rows] (the residual the next epoch's
- * gradient uses) and k.  set_state restores them (requires set_data first). */
+ * gradient uses: Eq. 3 makes it part of the state) and k.  set_state restores them (requires set_data first). */
 int bsgdtv_get_state(bsgdtv_t h, float *x, float *r, int64_t *epoch, int on_device);
 int bsgdtv_set_state(bsgdtv_t h, const float *x, const float *r, int64_t epoch, int on_device);
 
 /* FP64 monitoring of the current x: data term ||y - A x||^2 and TV(x)
- * (Eq. 1; the function Algorithm 1 with its TV prox as printed minimises is
+ * (Eq. 1, TV of Eq. 2 read as isotropic forward differences with a Neumann
+ * border; the function Algorithm 1 with its TV prox as printed minimises is
  * data + lambda*TV).
  * Synchronises. */
 int bsgdtv_objective(bsgdtv_t h, double *data_term, double *tv);
@@ -196,7 +206,8 @@ int bsgdtv_objective(bsgdtv_t h, double *data_term, double *tv);
 int bsgdtv_run_until(bsgdtv_t h, int max_epochs, int fgp_iters, int check_every, double rel_tol,
                      int *epochs_run, double *objective);
 
-/* Test hook: the block products of Algorithm 1 for given x [cols] and r [rows]
+/* Test hook: the block products z^j_{I_i} and g-hat^i_{J_j} of Algorithm 1
+ * (Sec. 2.1) for given x [cols] and r [rows]
  * (device pointers), computed by the same fused kernel the epoch uses.
  *   z_blocks [N*rows]:  z_blocks[j*rows + k] = (A_{I_i}^{J_j} x_{J_j})_k for row
  *                       k of block I_i (i.e. z^j stacked over i).

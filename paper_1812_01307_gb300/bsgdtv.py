@@ -51,7 +51,7 @@ def load(path: str | None = None):
         "bsgdtv_run_subsets_timed": (I32, [P, I32, I32, P, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "bsgdtv_fp32_fma_peak": (I32, [ctypes.POINTER(D), ctypes.POINTER(D)]),
         "bsgdtv_run_until": (I32, [P, I32, I32, I32, D, ctypes.POINTER(I32), ctypes.POINTER(D)]),
-        "bsgdtv_get_x": (I32, [P, P, I32]),
+        "bsgdtv_get_x": (I32, [P, P, I32, I64]),
         "bsgdtv_get_state": (I32, [P, P, P, ctypes.POINTER(I64), I32]),
         "bsgdtv_set_state": (I32, [P, P, P, I64, I32]),
         "bsgdtv_objective": (I32, [P, ctypes.POINTER(D), ctypes.POINTER(D)]),
@@ -326,9 +326,9 @@ def bsgdtv_get_x(h, out):
     lib = load()
     if _is_tensor(out):
         import torch
-        rc = lib.bsgdtv_get_x(h, _dev_ptr(out, torch.float32), 1)
+        rc = lib.bsgdtv_get_x(h, _dev_ptr(out, torch.float32), 1, int(out.numel()))
     else:
-        rc = lib.bsgdtv_get_x(h, _host_ptr(out, np.float32), 0)
+        rc = lib.bsgdtv_get_x(h, _host_ptr(out, np.float32), 0, int(out.size))
     _check(rc, "bsgdtv_get_x")
     return out
 

@@ -849,9 +849,10 @@ int bsgdtv_run_subsets_timed(bsgdtv_t h, int iters, int fgp_iters, const uint8_t
     return rc;
 }
 
-int bsgdtv_get_x(bsgdtv_t h, float *out, int out_on_device) {
+int bsgdtv_get_x(bsgdtv_t h, float *out, int out_on_device, int64_t n) {
     BSG_TRACE();
     if (!h || !out) return fail(BSGDTV_ERR_INVALID_ARG, "null handle or out");
+    if (n < h->dl.cols) return fail(BSGDTV_ERR_INVALID_ARG, "out holds fewer than cols floats");
     BSG_CHECK(set_device(h));
     const size_t bytes = h->dl.cols * sizeof(float);
     BSG_CUDA(cudaMemcpyAsync(out, h->x, bytes,
