@@ -98,6 +98,27 @@ class ClockSampler:
         except (OSError, FileNotFoundError):
             self.proc = None
 
+    def samples(self):
+        """Rows written so far (0 if the sampler is not running)."""
+        if self.proc is None or not self.path:
+            return 0
+        try:
+            self.f.flush()
+            with open(self.path) as f:
+                return sum(1 for line in f if line.count(",") >= 8)
+        except OSError:
+            return 0
+
+    def wait_samples(self, n, limit_s, work=None):
+        """Until at least n rows exist (at most limit_s seconds), calling
+        work() meanwhile (e.g. untimed epochs that keep the GPU loaded)."""
+        t0 = time.perf_counter()
+        while self.proc is not None and self.samples() < n and time.perf_counter() - t0 < limit_s:
+            if work is not None:
+                work()
+            else:
+                time.sleep(0.02)
+
     def stop(self):
         if self.proc is None:
             return None
@@ -449,6 +470,13 @@ def run_ours(args):
     sampler.start()
     rec.run(W, wl.fgp_iters)
     torch.cuda.synchronize()
+
+    def untimed():   # more warm-up epochs while the clock sampler starts
+        rec.run(20, wl.fgp_iters)
+        torch.cuda.synchronize()
+
+    sampler.wait_samples(1, 5.0, untimed)
+    n_before = sampler.samples()
     launches0 = B.bsgdtv_launch_count()
     D.barrier()
     torch.cuda.synchronize()
@@ -459,8 +487,11 @@ def run_ours(args):
     ev1.record()
     torch.cuda.synchronize()
     D.barrier()
-    clocks = sampler.stop()
+    # a short timed region may fall between two samples: keep the GPU loaded
+    # with untimed epochs until the sampler has recorded one more
     launches = B.bsgdtv_launch_count() - launches0
+    sampler.wait_samples(n_before + 1, 5.0, untimed)
+    clocks = sampler.stop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     elapsed_max = D.max_over_ranks(elapsed, dev)
     value = world * K / elapsed_max
