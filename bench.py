@@ -579,6 +579,9 @@ def run_ours(args):
         lam_b = np.random.default_rng(wl.seed + 3).uniform(0.01, 0.05, Bs)
         Kfb = 30   # FGP iterations of the batched-volume configuration
     for kind, bfmt in (batch_kinds if not args.no_variants and args.batch_slices > 0 else []):
+        # an NVTX range per variant lets a profiler select its launches
+        # (ncu --nvtx --nvtx-include batch/ ...)
+        torch.cuda.nvtx.range_push(kind)
         bt = B.BatchReconstructor(P.A, (wl.n, wl.n), Bs, fmt=bfmt)
         bt.set_data(Ys_dev, lam_b, mu)
         if args.batch_tuning:   # a known tuning: no timing trials (e.g. under a profiler)
@@ -600,6 +603,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         dt = D.max_over_ranks(b0.elapsed_time(b1) / 1e3, dev)
         bt.close()
+        torch.cuda.nvtx.range_pop()
         nnz_b = int(P.A.row_ptr[-1])
         # both passes: A once each (4 B index + 4 B FP32 or 2 B FP16 weight per
         # nonzero), and y, x, r, x^ of every slice once per pass they appear in
@@ -633,6 +637,7 @@ def run_ours(args):
     # large and matrix free: 2048x2048, 60 ellipses, 1440 angles x 2897 bins, 16 slices
     if not args.no_variants and "matrix_free" in args.variants.split(","):
         import math
+        torch.cuda.nvtx.range_push("matrix_free")
         n5 = args.mf_n
         na5, nb5, S5, K5 = int(round(1440 * n5 / 2048)), int(math.ceil(math.sqrt(2) * n5)), 16, 50
         X5 = np.stack([synth.phantom(n5, 60, s).ravel() for s in range(S5)]).astype(np.float32)
@@ -657,6 +662,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         dt5 = D.max_over_ranks(m0.elapsed_time(m1) / 1e3, dev)
         mf.close()
+        torch.cuda.nvtx.range_pop()
         # the operator's nonzeros (no stored A): 4 flops per nonzero and slice at
         # least (one FMA in each pass), at the measured FP32 peak
         nnz5 = synth.parallel_beam_nnz(n5, na5, nb5)

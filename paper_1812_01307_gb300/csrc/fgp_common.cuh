@@ -50,6 +50,20 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// 1 / sqrt(max(a, 1)) (a NaN a gives 1, as fmaxf would).  The argument of
+// the approximate reciprocal square root is >= 1, never subnormal, so its
+// flush-to-zero form returns the same value as the plain one, without the
+// instructions the plain form spends on subnormal arguments.
+__device__ __forceinline__ float rsqrt_max1(float a) {
+    float r;
+    asm("{\n\t.reg .f32 m;\n\t"
+        "max.f32 m, %1, 0f3F800000;\n\t"
+        "rsqrt.approx.ftz.f32 %0, m;\n\t}"
+        : "=f"(r)
+        : "f"(a));
+    return r;
+}
+
 // A thread's 4 pixels as two pairs: pixels (0, 1) and (2, 3) of the strip.
 struct Strip {
     float2 h[2];
@@ -71,7 +85,7 @@ struct Strip {
 // throughout, because its dual step (cp or cq: 1/(8 tau) where the component
 // exists, else 0) keeps it there, and the joint projection then equals the
 // single-component clip t/max(1,|t|); outside the image b, p and q are all 0.
-// rsqrtf(max(n2, 1)) is the scale 1/max(1, sqrt(n2)).
+// rsqrt_max1(n2) is the scale 1/max(1, sqrt(n2)).
 template <int TY, int V>
 __device__ __forceinline__ void fgp_step(Strip &p, Strip &pp, Strip &q, Strip &qp,
                                          const Strip &bb, const Strip &cp, const Strip &cq,
@@ -114,7 +128,7 @@ __device__ __forceinline__ void fgp_step(Strip &p, Strip &pp, Strip &q, Strip &q
         const float2 pt = fma2(sub2(uu.h[k], udn[k]), cp.h[k], rr.h[k]);
         const float2 qt = fma2(sub2(uu.h[k], urt[k]), cq.h[k], ss.h[k]);
         const float2 n2 = fma2(pt, pt, mul2(qt, qt));
-        const float2 inv = make_float2(rsqrtf(fmaxf(n2.x, 1.f)), rsqrtf(fmaxf(n2.y, 1.f)));
+        const float2 inv = make_float2(rsqrt_max1(n2.x), rsqrt_max1(n2.y));
         pp.h[k] = mul2(pt, inv);
         qp.h[k] = mul2(qt, inv);
     }
