@@ -52,8 +52,8 @@ int fgp_chunk_for(int h, int w, int iters, int n_sms) {
     int best = kMaxChunk;
     long long best_cost = -1;
     for (int c = 4; c <= 12; ++c) {
-        const int inner = RW - 2 * (c + 1);
-        const long long grid = (long long)((w + inner - 1) / inner) * ((h + inner - 1) / inner);
+        const long long grid =
+            (long long)fgp_regions_along(w, RW, c + 1) * fgp_regions_along(h, RH, c + 1);
         const long long waves = (grid + std::max(n_sms, 1) - 1) / std::max(n_sms, 1);
         const long long cost = (long long)((iters + c - 1) / c) * (waves * c + 2);
         if (best_cost < 0 || cost <= best_cost) {

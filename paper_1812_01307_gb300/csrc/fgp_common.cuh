@@ -134,6 +134,34 @@ __device__ __forceinline__ void fgp_step(Strip &p, Strip &pp, Strip &q, Strip &q
     }
 }
 
+// Regions along one image dimension of `len` pixels for regions of R pixels
+// with a halo of HL: a region at the image's edge needs no halo on that side
+// (outside the image every iterate is exactly zero, as the region's zero
+// borders and masks make it), so the first and the last region's interiors
+// reach R - HL pixels and only the others' are R - 2 HL wide.
+__host__ __device__ inline int fgp_regions_along(int len, int R, int HL) {
+    if (len <= R) return 1;
+    const int rest = len - 2 * (R - HL);
+    return 2 + (rest > 0 ? (rest + R - 2 * HL - 1) / (R - 2 * HL) : 0);
+}
+// Region b of n along that dimension: its first pixel and its interior [lo, hi)
+// in region-local coordinates.
+__device__ __forceinline__ void fgp_place(int b, int n, int len, int R, int HL, int &first, int &lo,
+                                          int &hi) {
+    if (n == 1) {
+        first = 0;
+        lo = 0;
+        hi = len;
+        return;
+    }
+    const int inner = R - 2 * HL;
+    const int start = (b == 0) ? 0 : (R - HL) + (b - 1) * inner;
+    const int end = (b == n - 1) ? len : (R - HL) + b * inner;
+    first = (b == 0) ? 0 : start - HL;
+    lo = start - first;
+    hi = end - first;
+}
+
 // One launch of the FGP covers the images of up to kMaxFgpParts parts (a
 // part: `slices` images of H x W, `plane` floats apart, with their own
 // weights).  CTA blockIdx.x belongs to the last part whose cta_begin it has
@@ -169,7 +197,7 @@ struct FgpLaunch {
 template <int TY, int V, bool kMulti>
 __global__ void __launch_bounds__(RW *TY)
     fgp_kernel(const __grid_constant__ FgpLaunch L, const float *__restrict__ mom, int k0, int iters,
-               int HL, int IH, int IW, int first, int last) {
+               int HL, int first, int last) {
     __shared__ __align__(16) FgpShared<TY, V> sh;
 
     int pi = 0;
@@ -195,7 +223,9 @@ __global__ void __launch_bounds__(RW *TY)
     const float c8 = 1.0f / (8.0f * tau);
 
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int R0 = by * IH - HL, C0 = bx * IW - HL;
+    int R0, C0, rlo, rhi, clo, chi;
+    fgp_place(by, P.ry, H, RH, HL, R0, rlo, rhi);
+    fgp_place(bx, P.rx, W, RW, HL, C0, clo, chi);
     const int j = C0 + tx;
     const bool col_in = (j >= 0 && j < W);
 
@@ -237,7 +267,7 @@ __global__ void __launch_bounds__(RW *TY)
         for (int v = 0; v < V; ++v) {
             const int rr_ = ty * V + v;
             const int i = R0 + rr_;
-            const bool interior = rr_ >= HL && rr_ < HL + IH && tx >= HL && tx < HL + IW;
+            const bool interior = rr_ >= rlo && rr_ < rhi && tx >= clo && tx < chi;
             if (interior && col_in && i >= 0 && i < H) x_out[(int64_t)i * W + j] = b[(int64_t)i * W + j];
         }
         return;
@@ -295,7 +325,7 @@ __global__ void __launch_bounds__(RW *TY)
         for (int v = 0; v < V; ++v) {
             const int rr_ = ty * V + v;
             const int i = R0 + rr_;
-            const bool interior = rr_ >= HL && rr_ < HL + IH && tx >= HL && tx < HL + IW;
+            const bool interior = rr_ >= rlo && rr_ < rhi && tx >= clo && tx < chi;
             if (!(interior && col_in && i >= 0 && i < H)) continue;
             const float p_up = (v > 0) ? pa.get(v - 1) : sh.r_edge[ty][tx];
             const float q_left = sh.s[tx][rr_];
@@ -306,7 +336,7 @@ __global__ void __launch_bounds__(RW *TY)
         for (int v = 0; v < V; ++v) {
             const int rr_ = ty * V + v;
             const int i = R0 + rr_;
-            const bool interior = rr_ >= HL && rr_ < HL + IH && tx >= HL && tx < HL + IW;
+            const bool interior = rr_ >= rlo && rr_ < rhi && tx >= clo && tx < chi;
             if (!(interior && col_in && i >= 0 && i < H)) continue;
             const int64_t o = (int64_t)i * W + j;
             p_out[o] = pa.get(v);
@@ -354,7 +384,7 @@ cudaError_t launch_fgp_parts(const FgpImages *parts, int n_parts, int iters, con
     const dim3 block(RW, TY);
     bool single = true;
     for (int k = 0; k < n_parts; ++k) single = single && fits_one_region(parts[k].h, parts[k].w);
-    auto build = [&](int launch, int HL, int IH, int IW, FgpLaunch &L) -> int {
+    auto build = [&](int launch, int HL, FgpLaunch &L) -> int {
         int ctas = 0;
         L.n_parts = n_parts;
         for (int k = 0; k < n_parts; ++k) {
@@ -369,8 +399,8 @@ cudaError_t launch_fgp_parts(const FgpImages *parts, int n_parts, int iters, con
             P.plane = q.plane;
             P.H = q.h;
             P.W = q.w;
-            P.rx = (q.w + IW - 1) / IW;
-            P.ry = (q.h + IH - 1) / IH;
+            P.rx = fgp_regions_along(q.w, RW, HL);
+            P.ry = fgp_regions_along(q.h, RH, HL);
             P.cta_begin = ctas;
             ctas += P.rx * P.ry * q.slices;
         }
@@ -379,11 +409,11 @@ cudaError_t launch_fgp_parts(const FgpImages *parts, int n_parts, int iters, con
     FgpLaunch L = {};
     if (single) {
         // one launch, no field traffic (first and last)
-        const int ctas = build(0, 0, RH, RW, L);
+        const int ctas = build(0, 0, L);
         cudaError_t e = n_parts > 1 ? launch_kernel(fgp_kernel<TY, V, true>, dim3(ctas), block, 0, s, pdl,
-                                                    L, mom, 0, iters, 0, RH, RW, 1, 1)
+                                                    L, mom, 0, iters, 0, 1, 1)
                                     : launch_kernel(fgp_kernel<TY, V, false>, dim3(ctas), block, 0, s, pdl,
-                                                    L, mom, 0, iters, 0, RH, RW, 1, 1);
+                                                    L, mom, 0, iters, 0, 1, 1);
         add_launches(1);
         return e != cudaSuccess ? e : cudaGetLastError();
     }
@@ -391,14 +421,13 @@ cudaError_t launch_fgp_parts(const FgpImages *parts, int n_parts, int iters, con
     for (int launch = 0; done < iters; ++launch) {
         const int chunk = std::min(max_chunk, iters - done);
         const int HL = chunk + 1;
-        const int IH = RH - 2 * HL, IW = RW - 2 * HL;
-        const int ctas = build(launch, HL, IH, IW, L);
+        const int ctas = build(launch, HL, L);
         const int first = (done == 0), last = (done + chunk == iters);
         const bool p = pdl || done > 0;
         cudaError_t e = n_parts > 1 ? launch_kernel(fgp_kernel<TY, V, true>, dim3(ctas), block, 0, s, p, L,
-                                                    mom, done, chunk, HL, IH, IW, first, last)
+                                                    mom, done, chunk, HL, first, last)
                                     : launch_kernel(fgp_kernel<TY, V, false>, dim3(ctas), block, 0, s, p, L,
-                                                    mom, done, chunk, HL, IH, IW, first, last);
+                                                    mom, done, chunk, HL, first, last);
         add_launches(1);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return e;
