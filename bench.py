@@ -504,16 +504,27 @@ def run_ours(args):
     y_np, x_np = y_pin.numpy(), x_pin.numpy()
     torch.cuda.synchronize()
     D.barrier()
+    # the one-call form: y in, one epoch, x out, one synchronisation
+    t0 = time.perf_counter()
+    for _ in range(E):
+        B.bsgdtv_reconstruct(rec.h, y_np, wl.lam, mu, 1, wl.fgp_iters, x_np)
+    torch.cuda.synchronize()
+    e2e_dt = D.max_over_ranks(time.perf_counter() - t0, dev)
+    # the same through the three calls (a synchronisation after y and after x)
+    D.barrier()
     t0 = time.perf_counter()
     for _ in range(E):
         B.bsgdtv_set_data(rec.h, y_np, wl.lam, mu)
         rec.run(1, wl.fgp_iters)
         B.bsgdtv_get_x(rec.h, x_np)
     torch.cuda.synchronize()
-    e2e_dt = D.max_over_ranks(time.perf_counter() - t0, dev)
+    e2e3_dt = D.max_over_ranks(time.perf_counter() - t0, dev)
     e2e = {"value": world * E / e2e_dt, "unit": "epochs/s", "h2d_bytes_per_step": 4 * P.A.rows,
            "d2h_bytes_per_step": 4 * P.A.cols_n, "steps": E,
-           "note": "per step: bsgdtv_set_data(host y) + bsgdtv_run(1 epoch) + bsgdtv_get_x(host x)"}
+           "three_calls_value": world * E / e2e3_dt,
+           "note": "per step: bsgdtv_reconstruct(host y, 1 epoch, host x) from pinned buffers, "
+                   "one synchronisation; three_calls_value: bsgdtv_set_data(host y) + "
+                   "bsgdtv_run(1 epoch) + bsgdtv_get_x(host x)"}
     rec.close()
     peak, peak_kind = hbm_peak()
     fp32_scalar, fp32_packed = B.bsgdtv_fp32_fma_peak()

@@ -182,6 +182,18 @@ int bsgdtv_run_timed(bsgdtv_t h, int epochs, int fgp_iters, double *products_ms,
  * host: synchronises the stream. */
 int bsgdtv_get_x(bsgdtv_t h, float *out, int out_on_device, int64_t n);
 
+/* One reconstruction in one call: bsgdtv_set_data(y, lambda, mu), then
+ * bsgdtv_run(epochs, fgp_iters) (Algorithm 1, Sec. 2.1), then bsgdtv_get_x
+ * into x_out (n_x floats, at least cols), queued on the handle's stream and
+ * synchronised once at the end instead of after the copy of y and again after
+ * the copy of x.  Same iterates as the three calls.  The check of y for
+ * NaN/Inf is read back with x: non-finite y gives BSGDTV_ERR_NONFINITE after
+ * the epochs have run (x_out then holds no meaningful result) and leaves the
+ * handle without data, as a failed set_data does.  A host y and x_out may be
+ * reused as soon as the call returns. */
+int bsgdtv_reconstruct(bsgdtv_t h, const float *y, int y_on_device, double lambda, double mu,
+                       int epochs, int fgp_iters, float *x_out, int x_on_device, int64_t n_x);
+
 /* Checkpoint: x^k [cols], r^{k-1} [rows] (the residual the next epoch's
  * gradient uses: Eq. 3 makes it part of the state) and k.  set_state restores them (requires set_data first). */
 int bsgdtv_get_state(bsgdtv_t h, float *x, float *r, int64_t *epoch, int on_device);

@@ -52,6 +52,7 @@ def load(path: str | None = None):
         "bsgdtv_fp32_fma_peak": (I32, [ctypes.POINTER(D), ctypes.POINTER(D)]),
         "bsgdtv_run_until": (I32, [P, I32, I32, I32, D, ctypes.POINTER(I32), ctypes.POINTER(D)]),
         "bsgdtv_get_x": (I32, [P, P, I32, I64]),
+        "bsgdtv_reconstruct": (I32, [P, P, I32, D, D, I32, I32, P, I32, I64]),
         "bsgdtv_get_state": (I32, [P, P, P, ctypes.POINTER(I64), I32]),
         "bsgdtv_set_state": (I32, [P, P, P, I64, I32]),
         "bsgdtv_objective": (I32, [P, ctypes.POINTER(D), ctypes.POINTER(D)]),
@@ -115,7 +116,7 @@ def exported_symbols():
     """Names the binding expects the library to export."""
     return ["bsgdtv_create_csr", "bsgdtv_create_csr_ex", "bsgdtv_create_parallel_beam", "bsgdtv_stored_weight", "bsgdtv_destroy", "bsgdtv_get_partition", "bsgdtv_set_data",
             "bsgdtv_estimate_umax", "bsgdtv_get_params", "bsgdtv_run", "bsgdtv_run_timed",
-            "bsgdtv_run_until", "bsgdtv_get_x",
+            "bsgdtv_run_until", "bsgdtv_get_x", "bsgdtv_reconstruct",
             "bsgdtv_get_state", "bsgdtv_set_state", "bsgdtv_objective", "bsgdtv_block_products",
             "bsgdtv_get_info", "bsgdtv_tv_prox", "bsgdtv_tv_prox_static", "bsgdtv_partition_bounds",
             "bsgdtv_layout_check", "bsgdtv_run_subsets", "bsgdtv_run_subsets_timed",
@@ -330,6 +331,24 @@ def bsgdtv_get_x(h, out):
     else:
         rc = lib.bsgdtv_get_x(h, _host_ptr(out, np.float32), 0, int(out.size))
     _check(rc, "bsgdtv_get_x")
+    return out
+
+
+def bsgdtv_reconstruct(h, y, lam, mu, epochs, fgp_iters, out):
+    """set_data + run + get_x in one call with one synchronisation; y and
+    out are both CUDA float32 tensors or both float32 numpy arrays."""
+    lib = load()
+    if _is_tensor(y) != _is_tensor(out):
+        raise TypeError("y and out must both be CUDA tensors or both numpy arrays")
+    if _is_tensor(y):
+        import torch
+        rc = lib.bsgdtv_reconstruct(h, _dev_ptr(y, torch.float32), 1, float(lam), float(mu), int(epochs),
+                                    int(fgp_iters), _dev_ptr(out, torch.float32), 1, int(out.numel()))
+    else:
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        rc = lib.bsgdtv_reconstruct(h, _host_ptr(y, np.float32), 0, float(lam), float(mu), int(epochs),
+                                    int(fgp_iters), _host_ptr(out, np.float32), 0, int(out.size))
+    _check(rc, "bsgdtv_reconstruct")
     return out
 
 
@@ -747,6 +766,16 @@ class Reconstructor:
         if out is None:
             out = np.empty(self.cols, dtype=np.float32)
         return bsgdtv_get_x(self.h, out)
+
+    def reconstruct(self, y, lam, mu, epochs, fgp_iters, out=None):
+        """set_data + run + x in one call (one synchronisation)."""
+        if out is None:
+            if _is_tensor(y):
+                import torch
+                out = torch.empty(self.cols, dtype=torch.float32, device=y.device)
+            else:
+                out = np.empty(self.cols, dtype=np.float32)
+        return bsgdtv_reconstruct(self.h, y, lam, mu, epochs, fgp_iters, out)
 
     def objective(self):
         return bsgdtv_objective(self.h)

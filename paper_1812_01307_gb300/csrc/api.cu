@@ -59,7 +59,7 @@ struct bsgdtv_ctx {
     float *mom = nullptr;
     int mom_len = 0;
     int *flag = nullptr;
-    float *rmax = nullptr;   // [3] max |r| of r[0], r[1] and of a test-hook r
+    float *rmax = nullptr;   // [4] max |r| of r[0], r[1] and of a test-hook r; max |y| kept by reconstruct
     int cur = 0;   // r[cur] holds r^{k-1}
     bool z_stale = true;   // z partials not yet A x^0 = 0 or computed by an epoch
     bool has_data = false;
@@ -436,7 +436,7 @@ int bsgdtv_create_csr_ex(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, i
         (rc = dalloc(hp, &h->xhat, cols)) || (rc = dalloc(hp, &h->z_part, d.n_slabs * kSlab)) ||
         (rc = dalloc(hp, &h->g_part, (size_t)d.n_groups * cols)) || (rc = dalloc(hp, &h->fgp, (size_t)kFgpFieldPlanes * cols)) ||
         (rc = dalloc(hp, &h->flag, 1)) ||
-        (rc = dalloc(hp, &d.item_ctr, 2)) || (rc = dalloc(hp, &h->rmax, 3))) {
+        (rc = dalloc(hp, &d.item_ctr, 2)) || (rc = dalloc(hp, &h->rmax, 4))) {
         bsgdtv_destroy(h.release());
         return rc;
     }
@@ -859,6 +859,58 @@ int bsgdtv_get_x(bsgdtv_t h, float *out, int out_on_device, int64_t n) {
                              out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              h->stream));
     if (!out_on_device) BSG_CUDA(cudaStreamSynchronize(h->stream));
+    return BSGDTV_OK;
+}
+
+int bsgdtv_reconstruct(bsgdtv_t h, const float *y, int y_on_device, double lambda, double mu,
+                       int epochs, int fgp_iters, float *x_out, int x_on_device, int64_t n_x) {
+    BSG_TRACE();
+    if (!h || !y || !x_out) return fail(BSGDTV_ERR_INVALID_ARG, "null handle, y or x_out");
+    if (!(lambda >= 0.0) || !std::isfinite(lambda) || !std::isfinite(mu))
+        return fail(BSGDTV_ERR_INVALID_ARG, "lambda must be finite and >= 0, mu finite");
+    if (epochs < 0 || fgp_iters < 0) return fail(BSGDTV_ERR_INVALID_ARG, "negative epochs / fgp_iters");
+    if (n_x < h->dl.cols) return fail(BSGDTV_ERR_INVALID_ARG, "x_out holds fewer than cols floats");
+    BSG_CHECK(set_device(h));
+    if (mu <= 0.0) {
+        if (h->u_max <= 0.0) {
+            double u;
+            BSG_CHECK(bsgdtv_estimate_umax(h, 5000, 1e-12, &u, nullptr));
+        }
+        if (h->u_max <= 0.0) return fail(BSGDTV_ERR_INVALID_ARG, "A is zero: u_max = 0");
+        mu = 0.9 / (2.0 * h->u_max);
+    }
+    if (h->mu != mu || h->lambda != lambda) drop_graphs(h);
+    h->lambda = lambda;
+    h->mu = mu;
+    if (epochs > 0 && (!h->gexec[0] || h->graph_fgp_iters != fgp_iters || h->graph_mu != h->mu ||
+                       h->graph_lambda != h->lambda))
+        BSG_CHECK(build_graphs(h, fgp_iters));
+    cudaStream_t s = h->stream;
+    const int64_t R = h->dl.rows, c = h->dl.cols;
+    h->has_data = false;
+    // set_data's copy and initialisation, with max |y| kept aside for the
+    // check; then the epochs; then x and the check value, read back together
+    BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float),
+                             y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    BSG_CUDA(launch_init_state(h->y, h->r[0], h->x, R, c, h->rmax, s));
+    BSG_CUDA(cudaMemcpyAsync(h->rmax + 3, h->rmax, sizeof(float), cudaMemcpyDeviceToDevice, s));
+    h->cur = 0;
+    h->z_stale = true;
+    h->epoch = 0;
+    for (int e = 0; e < epochs; ++e) {
+        BSG_CUDA(cudaGraphLaunch(h->gexec[h->cur], s));
+        add_launches(h->graph_kernels);
+        h->cur ^= 1;
+        h->z_stale = false;
+        h->epoch++;
+    }
+    BSG_CUDA(cudaMemcpyAsync(x_out, h->x, c * sizeof(float),
+                             x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    float ymax = 0.f;
+    BSG_CUDA(cudaMemcpyAsync(&ymax, h->rmax + 3, sizeof(float), cudaMemcpyDeviceToHost, s));
+    BSG_CUDA(cudaStreamSynchronize(s));
+    if (!std::isfinite(ymax)) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+    h->has_data = true;
     return BSGDTV_OK;
 }
 

@@ -415,6 +415,48 @@ def test_host_y_is_read_before_set_data_returns(B):
         assert e.value.code == -4
 
 
+def test_reconstruct_is_set_data_run_get_x(B):
+    """bsgdtv_reconstruct (one call, one synchronisation) gives the iterates of
+    set_data + run + get_x bit for bit, from host and from device buffers; a
+    pinned y may be reused at once; non-finite y gives BSGDTV_ERR_NONFINITE
+    and leaves no data; a short x_out is rejected."""
+    A, _, y, n, na, nb, M, N = _problem("wide130")
+    y32 = y.astype(np.float32)
+    with B.Reconstructor(A, (n, n), M, N, row_unit=nb, col_unit=n) as rec:
+        u, _ = rec.estimate_umax(500, 1e-10)
+        mu = 0.9 / (2 * u)
+        rec.set_data(y32, 0.05, mu)
+        rec.run(7, 10)
+        x_ref = rec.x().copy()
+        rec.run(2, 10)                         # move the state on, then start over
+        pinned = torch.empty(A.rows, dtype=torch.float32).pin_memory()
+        yp = pinned.numpy()
+        yp[:] = y32
+        out = np.full(A.cols_n + 3, -1.0, dtype=np.float32)
+        rec.reconstruct(yp, 0.05, mu, 7, 10, out)
+        yp[:] = np.nan
+        assert np.array_equal(out[:A.cols_n], x_ref) and np.all(out[A.cols_n:] == -1.0)
+        xd = rec.reconstruct(torch.from_numpy(y32).cuda(), 0.05, mu, 7, 10)
+        assert np.array_equal(xd.cpu().numpy(), x_ref)
+        rec.run(3, 10)                         # the handle holds the data: run continues
+        rec.set_data(y32, 0.05, mu)
+        rec.run(10, 10)
+        x10 = rec.x().copy()
+        assert np.array_equal(rec.reconstruct(y32, 0.05, mu, 10, 10), x10)
+        assert np.array_equal(rec.reconstruct(y32, 0.05, 0.0, 0, 10), np.zeros(A.cols_n, np.float32))
+        bad = y32.copy()
+        bad[5] = np.inf
+        with pytest.raises(B.BsgdtvError) as e:
+            rec.reconstruct(bad, 0.05, mu, 3, 10)
+        assert e.value.code == -6
+        with pytest.raises(B.BsgdtvError) as e:
+            rec.run(1, 10)
+        assert e.value.code == -4
+        with pytest.raises(B.BsgdtvError) as e:
+            rec.reconstruct(y32, 0.05, mu, 3, 10, np.empty(A.cols_n - 1, np.float32))
+        assert e.value.code == -1
+
+
 def test_ellipse512_full_size_epochs(B):
     """The 512x512 workload (360 angles x 727 bins, M = N = 8, lambda 0.02, 50 FGP
     iterations) in the launch configuration bench.py times: 3 epochs vs the oracle."""
