@@ -59,7 +59,10 @@ struct bsgdtv_ctx {
     float *mom = nullptr;
     int mom_len = 0;
     int *flag = nullptr;
-    float *rmax = nullptr;   // [4] max |r| of r[0], r[1] and of a test-hook r; max |y| kept by reconstruct
+    float *rmax = nullptr;   // [3] max |r| of r[0], r[1] and of a test-hook r
+    int *init_part = nullptr;   // [kInitBlocks + 1] block maxima and counter of the init kernel
+    float *check_host = nullptr;   // page-locked word: max |y| of the last initialisation
+    float *check_dev = nullptr;    // its device address
     int cur = 0;   // r[cur] holds r^{k-1}
     bool z_stale = true;   // z partials not yet A x^0 = 0 or computed by an epoch
     bool has_data = false;
@@ -436,11 +439,15 @@ int bsgdtv_create_csr_ex(bsgdtv_t *out, int64_t rows, int64_t cols, int img_h, i
         (rc = dalloc(hp, &h->xhat, cols)) || (rc = dalloc(hp, &h->z_part, d.n_slabs * kSlab)) ||
         (rc = dalloc(hp, &h->g_part, (size_t)d.n_groups * cols)) || (rc = dalloc(hp, &h->fgp, (size_t)kFgpFieldPlanes * cols)) ||
         (rc = dalloc(hp, &h->flag, 1)) ||
-        (rc = dalloc(hp, &d.item_ctr, 2)) || (rc = dalloc(hp, &h->rmax, 4))) {
+        (rc = dalloc(hp, &d.item_ctr, 2)) || (rc = dalloc(hp, &h->rmax, 3)) ||
+        (rc = dalloc(hp, &h->init_part, kInitBlocks + 1))) {
         bsgdtv_destroy(h.release());
         return rc;
     }
     cudaError_t e = cudaMemsetAsync(d.item_ctr, 0, 2 * sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->init_part, 0, (kInitBlocks + 1) * sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaHostAlloc(&h->check_host, sizeof(float), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&h->check_dev, h->check_host, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         bsgdtv_destroy(h.release());
@@ -491,6 +498,7 @@ void bsgdtv_destroy(bsgdtv_t h) {
     for (cudaEvent_t ev : h->tmark)
         if (ev) cudaEventDestroy(ev);
     for (void *p : h->allocs) cudaFree(p);
+    if (h->check_host) cudaFreeHost(h->check_host);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
@@ -561,6 +569,35 @@ int bsgdtv_estimate_umax(bsgdtv_t h, int max_iters, double rel_tol, double *u_ma
     return BSGDTV_OK;
 }
 
+// The address at which the GPU reads or writes a caller's buffer directly:
+// device memory as given, page-locked (pinned or registered) host memory
+// through its device address; null for pageable host memory, which goes
+// through a copy.
+static float *device_view(const float *p, int on_device) {
+    if (on_device) return const_cast<float *>(p);
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? static_cast<float *>(a.devicePointer) : nullptr;
+}
+
+// y into the handle and the initial state (x^0 = 0, r^{-1} = y, max |y| into
+// rmax[0] and the check word) on the handle's stream: one kernel reading y
+// where it lies when the GPU can, else a copy first.
+static int enqueue_init(bsgdtv_ctx *h, const float *y, int y_on_device) {
+    cudaStream_t s = h->stream;
+    const int64_t R = h->dl.rows, c = h->dl.cols;
+    const float *src = device_view(y, y_on_device);
+    if (!src) {
+        BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float), cudaMemcpyHostToDevice, s));
+        src = h->y;
+    }
+    BSG_CUDA(launch_init_from(src, h->y, h->r[0], h->x, R, c, h->rmax, h->check_dev, h->init_part, s));
+    return BSGDTV_OK;
+}
+
 int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, double mu) {
     BSG_TRACE();
     if (!h || !y) return fail(BSGDTV_ERR_INVALID_ARG, "null handle or y");
@@ -568,20 +605,15 @@ int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, 
         return fail(BSGDTV_ERR_INVALID_ARG, "lambda must be finite and >= 0, mu finite");
     BSG_CHECK(set_device(h));
     cudaStream_t s = h->stream;
-    const int64_t R = h->dl.rows, c = h->dl.cols;
     h->has_data = false;   // y is overwritten from here on: a failure leaves no data
     // copy y, then in one launch r^{-1} = y - A x^0 = y, x^0 = 0 and max |y|
     // (which is Inf or NaN exactly when y is not finite: the check); the
     // read-back of max |y| returns after the copy has read y, so a host y may
     // be reused at once, pageable or pinned.  The last block products are
     // A x^0 = 0 (cleared when the stochastic iteration first needs them).
-    BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float),
-                             y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    BSG_CUDA(launch_init_state(h->y, h->r[0], h->x, R, c, h->rmax, s));
-    float ymax = 0.f;
-    BSG_CUDA(cudaMemcpyAsync(&ymax, h->rmax, sizeof(float), cudaMemcpyDeviceToHost, s));
+    BSG_CHECK(enqueue_init(h, y, y_on_device));
     BSG_CUDA(cudaStreamSynchronize(s));
-    if (!std::isfinite(ymax)) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+    if (!std::isfinite(*h->check_host)) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
     h->cur = 0;
     h->z_stale = true;
     if (mu <= 0.0) {
@@ -849,15 +881,27 @@ int bsgdtv_run_subsets_timed(bsgdtv_t h, int iters, int fgp_iters, const uint8_t
     return rc;
 }
 
+// x into a caller's buffer on the handle's stream: a copy on the device, or a
+// kernel writing page-locked host memory through its device address, or a
+// copy to pageable host memory.
+static int enqueue_x_out(bsgdtv_ctx *h, float *out, int out_on_device) {
+    const int64_t c = h->dl.cols;
+    if (out_on_device) {
+        BSG_CUDA(cudaMemcpyAsync(out, h->x, c * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+        return BSGDTV_OK;
+    }
+    float *dst = device_view(out, 0);
+    if (dst) BSG_CUDA(launch_copy_out(h->x, dst, c, h->stream));
+    else BSG_CUDA(cudaMemcpyAsync(out, h->x, c * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    return BSGDTV_OK;
+}
+
 int bsgdtv_get_x(bsgdtv_t h, float *out, int out_on_device, int64_t n) {
     BSG_TRACE();
     if (!h || !out) return fail(BSGDTV_ERR_INVALID_ARG, "null handle or out");
     if (n < h->dl.cols) return fail(BSGDTV_ERR_INVALID_ARG, "out holds fewer than cols floats");
     BSG_CHECK(set_device(h));
-    const size_t bytes = h->dl.cols * sizeof(float);
-    BSG_CUDA(cudaMemcpyAsync(out, h->x, bytes,
-                             out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                             h->stream));
+    BSG_CHECK(enqueue_x_out(h, out, out_on_device));
     if (!out_on_device) BSG_CUDA(cudaStreamSynchronize(h->stream));
     return BSGDTV_OK;
 }
@@ -886,14 +930,10 @@ int bsgdtv_reconstruct(bsgdtv_t h, const float *y, int y_on_device, double lambd
                        h->graph_lambda != h->lambda))
         BSG_CHECK(build_graphs(h, fgp_iters));
     cudaStream_t s = h->stream;
-    const int64_t R = h->dl.rows, c = h->dl.cols;
     h->has_data = false;
-    // set_data's copy and initialisation, with max |y| kept aside for the
-    // check; then the epochs; then x and the check value, read back together
-    BSG_CUDA(cudaMemcpyAsync(h->y, y, R * sizeof(float),
-                             y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    BSG_CUDA(launch_init_state(h->y, h->r[0], h->x, R, c, h->rmax, s));
-    BSG_CUDA(cudaMemcpyAsync(h->rmax + 3, h->rmax, sizeof(float), cudaMemcpyDeviceToDevice, s));
+    // set_data's initialisation (max |y| into the check word), the epochs,
+    // x out; the check word is read after the one synchronisation
+    BSG_CHECK(enqueue_init(h, y, y_on_device));
     h->cur = 0;
     h->z_stale = true;
     h->epoch = 0;
@@ -904,12 +944,9 @@ int bsgdtv_reconstruct(bsgdtv_t h, const float *y, int y_on_device, double lambd
         h->z_stale = false;
         h->epoch++;
     }
-    BSG_CUDA(cudaMemcpyAsync(x_out, h->x, c * sizeof(float),
-                             x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-    float ymax = 0.f;
-    BSG_CUDA(cudaMemcpyAsync(&ymax, h->rmax + 3, sizeof(float), cudaMemcpyDeviceToHost, s));
+    BSG_CHECK(enqueue_x_out(h, x_out, x_on_device));
     BSG_CUDA(cudaStreamSynchronize(s));
-    if (!std::isfinite(ymax)) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
+    if (!std::isfinite(*h->check_host)) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
     h->has_data = true;
     return BSGDTV_OK;
 }

@@ -149,8 +149,14 @@ cudaError_t launch_check_finite(const float *v, int64_t n, int *flag, cudaStream
 // Start of an iteration: r0 = y [rows], x = 0 [cols] and *rmax = max |y|,
 // which is Inf or NaN exactly when y holds a NaN or +-Inf (a memset and one
 // launch).
-cudaError_t launch_init_state(const float *y, float *r0, float *x, int64_t rows, int64_t cols,
-                              float *rmax, cudaStream_t s);
+// One launch: y_dst = y (y may be page-locked host memory through its device
+// address), r0 = y, x = 0, max |y| into *rmax and *check; part: kInitBlocks + 1
+// ints, the last one 0 between launches.
+constexpr int kInitBlocks = 512;
+cudaError_t launch_init_from(const float *y, float *y_dst, float *r0, float *x, int64_t rows,
+                             int64_t cols, float *rmax, float *check, int *part, cudaStream_t s);
+// dst = src (dst may be page-locked host memory through its device address).
+cudaError_t launch_copy_out(const float *src, float *dst, int64_t n, cudaStream_t s);
 constexpr int kDotPartials = 1024;
 
 // fgp.cu: K FGP iterations on an h x w image.  `mom` holds the K momentum

@@ -362,18 +362,27 @@ cudaError_t launch_block_sums(const DevLayout &d, const float *z_part, const int
     return cudaGetLastError();
 }
 
-// r^{-1} = y, x^0 = 0 and *rmax = the largest |y| bit pattern with the sign
-// cleared (rmax zeroed beforehand).  Patterns order like the magnitudes, and
-// NaN / +-Inf are exactly those >= 0x7f800000, so *rmax is max |y| when y is
-// finite and reads as Inf or NaN when it is not.
-__global__ void init_state_kernel(const float *__restrict__ y, float *__restrict__ r0,
-                                  float *__restrict__ x, int64_t rows, int64_t cols, float *rmax) {
+// The initial state of Algorithm 1 in one launch, from y wherever the GPU
+// can read it (device memory, or page-locked host memory through its device
+// address): y_dst = y (skipped when y is y_dst), r^{-1} = y, x^0 = 0, and
+// max |y| as the largest bit pattern with the sign cleared.  Patterns order
+// like the magnitudes, and NaN / +-Inf are exactly those >= 0x7f800000, so it
+// is max |y| when y is finite and reads as Inf or NaN when it is not.  The
+// last block to finish reduces the blocks' maxima, writes the result to
+// rmax[0] and to *check (a word the host reads after synchronising) and puts
+// the block counter back to 0.  part: kInitBlocks partial maxima and the
+// counter.
+__global__ void __launch_bounds__(kThreads)
+    init_from_kernel(const float *__restrict__ y, float *y_dst, float *__restrict__ r0,
+                     float *__restrict__ x, int64_t rows, int64_t cols, float *rmax, float *check,
+                     int *part) {
     const int64_t n = rows > cols ? rows : cols;
     int m = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (i < rows) {
             const float v = y[i];
+            if (y_dst) y_dst[i] = v;
             r0[i] = v;
             m = max(m, __float_as_int(v) & 0x7fffffff);
         }
@@ -381,20 +390,54 @@ __global__ void init_state_kernel(const float *__restrict__ y, float *__restrict
     }
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     __shared__ int wmax[kThreads / 32];
+    __shared__ bool last;
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        m = (threadIdx.x < (int)(blockDim.x >> 5)) ? wmax[threadIdx.x] : 0;
-        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (threadIdx.x == 0) atomicMax(reinterpret_cast<int *>(rmax), m);
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < kThreads / 32; ++k) m = max(m, wmax[k]);
+        part[blockIdx.x] = m;
+        __threadfence();
+        last = atomicAdd(part + kInitBlocks, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    m = 0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x)
+        m = max(m, reinterpret_cast<volatile int *>(part)[k]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < kThreads / 32; ++k) m = max(m, wmax[k]);
+        *rmax = __int_as_float(m);
+        *check = __int_as_float(m);
+        part[kInitBlocks] = 0;
     }
 }
 
-cudaError_t launch_init_state(const float *y, float *r0, float *x, int64_t rows, int64_t cols,
-                              float *rmax, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(rmax, 0, sizeof(float), s);
-    if (e != cudaSuccess) return e;
-    init_state_kernel<<<grid_for(std::max(rows, cols)), kThreads, 0, s>>>(y, r0, x, rows, cols, rmax);
+cudaError_t launch_init_from(const float *y, float *y_dst, float *r0, float *x, int64_t rows,
+                             int64_t cols, float *rmax, float *check, int *part, cudaStream_t s) {
+    const int grid = (int)std::min<int64_t>(kInitBlocks, std::max<int64_t>(1, (std::max(rows, cols) + kThreads - 1) / kThreads));
+    init_from_kernel<<<grid, kThreads, 0, s>>>(y, y == y_dst ? nullptr : y_dst, r0, x, rows, cols, rmax,
+                                               check, part);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+// dst[0 .. n) = src (dst: device memory, or page-locked host memory through
+// its device address).
+__global__ void __launch_bounds__(kThreads) copy_out_kernel(const float *__restrict__ src,
+                                                            float *__restrict__ dst, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+cudaError_t launch_copy_out(const float *src, float *dst, int64_t n, cudaStream_t s) {
+    const int grid = (int)std::min<int64_t>(kInitBlocks, std::max<int64_t>(1, (n + kThreads - 1) / kThreads));
+    copy_out_kernel<<<grid, kThreads, 0, s>>>(src, dst, n);
     add_launches(1);
     return cudaGetLastError();
 }

@@ -438,6 +438,11 @@ def test_reconstruct_is_set_data_run_get_x(B):
         assert np.array_equal(out[:A.cols_n], x_ref) and np.all(out[A.cols_n:] == -1.0)
         xd = rec.reconstruct(torch.from_numpy(y32).cuda(), 0.05, mu, 7, 10)
         assert np.array_equal(xd.cpu().numpy(), x_ref)
+        xo = torch.full((A.cols_n,), -1.0, dtype=torch.float32).pin_memory().numpy()
+        rec.reconstruct(y32, 0.05, mu, 7, 10, xo)      # pinned x out: written by a kernel
+        assert np.array_equal(xo, x_ref)
+        xg = torch.zeros(A.cols_n, dtype=torch.float32).pin_memory().numpy()
+        assert np.array_equal(B.bsgdtv_get_x(rec.h, xg), x_ref)
         rec.run(3, 10)                         # the handle holds the data: run continues
         rec.set_data(y32, 0.05, mu)
         rec.run(10, 10)
