@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--served-pack-ratio", type=float, default=4.0,
                     help="largest ratio of nonzeros between geometries packed into one group")
     ap.add_argument("--served-tick", type=int, default=10, help="max epochs between admissions")
+    ap.add_argument("--served-slots", type=int, default=0,
+                    help="slots per group for every geometry (0: the L2 rule, 32 at most)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip every variant (stored formats and the batch)")
     ap.add_argument("--variants", default="f32_i16,f16_i16,bf16_i16,batch,batch_f16,matrix_free,stochastic",
@@ -210,9 +212,17 @@ def served_stream(args, B, synth):
     budget = int(args.served_budget_gb * 2 ** 30)
     t_setup = time.perf_counter()
     geoms = {}
+    slots_of = {}
 
-    def slot_cap(n):
-        return 32
+    def slot_cap(n, rows):
+        # slots per group: the server's own rule (0) unless --served-slots
+        # fixes the number; the rule's value, for the report
+        if args.served_slots > 0:
+            return args.served_slots, args.served_slots
+        slots = 32
+        while slots > 1 and slots * max(rows, n * n) * 4 > 64 * 2 ** 20:
+            slots //= 2
+        return 0, slots
 
     srv = B.Server(budget, K, args.served_tick)
     pack = getattr(args, "served_pack", 1)
@@ -225,7 +235,8 @@ def served_stream(args, B, synth):
         # on-the-fly projector (no second stored copy of A)
         with B.BatchReconstructor(None, (n, n), 1, parallel_beam=(na, nb)) as one:
             u, _ = one.estimate_umax(300, 1e-9)
-        gid = srv.add_geometry(A, (n, n), 0.9 / (2 * u), slots=slot_cap(n), fmt=B.FMT_F16_I16,
+        ask, slots_of[n] = slot_cap(n, A.rows)
+        gid = srv.add_geometry(A, (n, n), 0.9 / (2 * u), slots=ask, fmt=B.FMT_F16_I16,
                                prewarm=0)
         ys = [synth.noisy_projections(A, synth.phantom(n, ellipses[n], s), s).astype(np.float32)
               for s in range(pool)]
@@ -272,7 +283,7 @@ def served_stream(args, B, synth):
     return {"requests": N, "stream": ("the first %d requests of the 2000-request served stream" % N
                                        if full else "%d requests without the 1024x1024 ones" % N),
             "mix": mix, "fgp_iters": K, "epochs": "U{100..300}", "lambda": "U(0.01,0.1)",
-            "weights": "f16", "slots_per_group": 32,
+            "weights": "f16", "slots_per_group": {str(n): slots_of[n] for n in sizes},
             "hbm_budget_gb": args.served_budget_gb, "packing_max_parts": pack,
             "packed_groups": st2["packed_groups"], "max_parts_per_group": st2["max_parts"],
             "launches_per_epoch_of_a_packed_group": st2["packed_launches"] or None,

@@ -551,7 +551,10 @@ void bsgdtv_server_destroy(bsgdtv_server_t s);
 
 /* Registers a geometry: host CSR A as for bsgdtv_create_csr (validated and
  * uploaded once as an operator), the batch weight format
- * (bsgdtv_batch_create_csr_ex), the largest number of slots per group, the
+ * (bsgdtv_batch_create_csr_ex), the largest number of slots per group (0:
+ * the largest power of two up to 32 for which a group's x and r, slots x
+ * max(rows, cols) floats, fit in 64 MiB, so that the batch passes' gathers stay
+ * in L2), the
  * step mu > 0 for this A (Theorem 1: mu < 1/(2 u_max), e.g. from
  * bsgdtv_estimate_umax) and how many groups of that size to create now
  * (prewarm, as far as the budget allows; the rest are made on demand).

@@ -113,6 +113,18 @@ def test_server_alone_equals_mixed_and_oracle(B):
         assert rel(mixed[i], x_ref) <= 1e-4, i
 
 
+def test_server_slots_by_l2_rule(B):
+    """slots = 0 lets the server size groups by its L2 rule (32 for these small
+    images): the mix runs and matches the oracle."""
+    out, st = _serve(B, MIX[:6], slots=0)
+    assert st["completed"] == 6
+    for i in (0, 1, 4):
+        name, seed, lam, ep = MIX[i]
+        A, n, _, mu = geometry(name)
+        x_ref, _ = oracle.run(A, request(name, seed).astype(np.float64), (n, n), 1, 1, lam, mu, ep, K)
+        assert rel(out[i], x_ref) <= 1e-4, i
+
+
 def _op_bytes(B, A):
     return (B.bsgdtv_batch_device_bytes(A.rows, A.cols_n, A.nnz, 1)
             - B.bsgdtv_batch_device_bytes(A.rows, A.cols_n, 0, 1))
