@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--served-pack-ratio", type=float, default=4.0,
                     help="largest ratio of nonzeros between geometries packed into one group")
     ap.add_argument("--served-tick", type=int, default=10, help="max epochs between admissions")
+    ap.add_argument("--served-priority", type=int, default=1,
+                    help="1: groups of smaller geometries on higher-priority streams; 0: all equal")
     ap.add_argument("--served-slots", type=int, default=0,
                     help="slots per group for every geometry (0: the L2 rule, 32 at most)")
     ap.add_argument("--no-variants", action="store_true",
@@ -225,6 +227,7 @@ def served_stream(args, B, synth):
         return 0, slots
 
     srv = B.Server(budget, K, args.served_tick)
+    srv.set_priority(args.served_priority)
     pack = getattr(args, "served_pack", 1)
     if pack > 1:
         srv.set_packing(pack, getattr(args, "served_pack_ratio", 4.0))
@@ -280,11 +283,19 @@ def served_stream(args, B, synth):
     srv.close()
     slice_epochs = sum(r[3] for r in reqs)
     mix = {str(n): int(sum(1 for r in reqs if r[0] == n)) for n in sizes}
+    by_size = {}
+    for n in sizes:   # Poisson-phase latency of each image size
+        ln = lat[[i for i, r in enumerate(reqs) if r[0] == n]]
+        if len(ln):
+            by_size[str(n)] = {"p50_ms": 1e3 * float(np.percentile(ln, 50)),
+                               "p99_ms": 1e3 * float(np.percentile(ln, 99))}
     return {"requests": N, "stream": ("the first %d requests of the 2000-request served stream" % N
                                        if full else "%d requests without the 1024x1024 ones" % N),
             "mix": mix, "fgp_iters": K, "epochs": "U{100..300}", "lambda": "U(0.01,0.1)",
             "weights": "f16", "slots_per_group": {str(n): slots_of[n] for n in sizes},
             "hbm_budget_gb": args.served_budget_gb, "packing_max_parts": pack,
+            "stream_priority_by_size": bool(args.served_priority),
+            "latency_by_size": by_size,
             "packed_groups": st2["packed_groups"], "max_parts_per_group": st2["max_parts"],
             "launches_per_epoch_of_a_packed_group": st2["packed_launches"] or None,
             "max_tick_epochs": args.served_tick,

@@ -615,6 +615,16 @@ int bsgdtv_server_hold(bsgdtv_server_t s, int hold);
  * (the default) packs nothing.  Applies to groups made afterwards. */
 int bsgdtv_server_set_packing(bsgdtv_server_t s, int max_parts, double cost_ratio);
 
+/* by_size != 0 (the default): each group runs on a stream whose priority is
+ * one step higher for every factor of 16 by which its operator has fewer
+ * nonzeros than the largest registered one, within the device's priority
+ * range, so that when SMs free up the short kernels of much smaller images are
+ * scheduled before the long kernels of large ones (running kernels are not
+ * preempted; results do not change); geometries within a factor of 16 of each
+ * other share a priority.  0: every group at the default priority.  Applies to
+ * groups made afterwards. */
+int bsgdtv_server_set_priority(bsgdtv_server_t s, int by_size);
+
 /* stats [18]: submitted, completed, failed, queued, running, groups, device
  * bytes in use (operators and groups), most requests running at once, runs
  * of epochs launched, epochs run by groups, slice-epochs of requests, groups

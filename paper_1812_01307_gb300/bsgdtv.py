@@ -99,6 +99,7 @@ def load(path: str | None = None):
         "bsgdtv_server_stats": (I32, [P, P]),
         "bsgdtv_server_arm": (I32, [P, I32, D]),
         "bsgdtv_server_set_packing": (I32, [P, I32, D]),
+        "bsgdtv_server_set_priority": (I32, [P, I32]),
         "bsgdtv_server_hold": (I32, [P, I32]),
         "bsgdtv_launch_count": (I64, []),
         "bsgdtv_last_error": (ctypes.c_char_p, []),
@@ -126,7 +127,8 @@ def exported_symbols():
             "bsgdtv_batch_get_slice_x", "bsgdtv_batch_device_bytes", "bsgdtv_server_create",
             "bsgdtv_server_destroy", "bsgdtv_server_add_geometry", "bsgdtv_server_submit",
             "bsgdtv_server_poll", "bsgdtv_server_cancel", "bsgdtv_server_wait", "bsgdtv_server_stats",
-            "bsgdtv_server_arm", "bsgdtv_server_set_packing", "bsgdtv_server_hold",
+            "bsgdtv_server_arm", "bsgdtv_server_set_packing", "bsgdtv_server_set_priority",
+            "bsgdtv_server_hold",
             "bsgdtv_batch_create_parallel_beam", "bsgdtv_mf_ray_weights", "bsgdtv_batch_estimate_umax",
             "bsgdtv_batch_project", "bsgdtv_batch_autotune", "bsgdtv_batch_set_tuning",
             "bsgdtv_batch_get_tuning", "bsgdtv_batch_set_pass_lanes", "bsgdtv_operator_create_csr",
@@ -1001,6 +1003,10 @@ class Server:
     def set_packing(self, max_parts, cost_ratio=4.0):
         _check(load().bsgdtv_server_set_packing(self.h, int(max_parts), float(cost_ratio)),
                "bsgdtv_server_set_packing")
+
+    def set_priority(self, by_size):
+        _check(load().bsgdtv_server_set_priority(self.h, int(bool(by_size))),
+               "bsgdtv_server_set_priority")
 
     def arm(self, geom_id, wait_s):
         """Arms an idle group of the geometry for wait_s seconds (device-side

@@ -165,6 +165,7 @@ struct bsgdtv_server_ctx {
     bool hold = false;   // admissions held (bsgdtv_server_hold)
     int pack_max_parts = 1;
     double pack_cost_ratio = 4.0;
+    bool priority_by_size = true;   // smaller geometries' groups on higher-priority streams
     int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, ticks = 0, epochs_run = 0, groups_made = 0,
             groups_freed = 0, max_running = 0, slice_epochs = 0, wait_timeouts = 0, armed_epochs = 0,
             packed_groups = 0, max_parts = 0, packed_launches = 0;
@@ -244,7 +245,26 @@ int make_group(bsgdtv_server_ctx *s, const std::vector<int> &gis, int slots, Gro
         ops.push_back(s->geoms[gi]->op);
     }
     g->bytes = bytes;
-    BSG_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+    // stream priority: one step up for every factor of 16 by which the
+    // group's largest operator has fewer nonzeros than the largest registered
+    // one, within the device's range.  The short kernels of much smaller
+    // images are then scheduled ahead of the long ones of large images
+    // whenever SMs free up (nothing is preempted), which costs the large ones
+    // little: the small ones are a small share of the work.  Geometries within
+    // a factor of 16 of each other share a priority.
+    int prio = 0;
+    if (s->priority_by_size) {
+        int least = 0, greatest = 0;
+        BSG_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        int64_t own = 1, top = 1;
+        for (int gi : gis) own = std::max(own, s->geoms[gi]->nnz);
+        for (const auto &G : s->geoms)
+            if (G) top = std::max(top, G->nnz);
+        int steps = 0;
+        for (int64_t v = own; v * 16 <= top; v *= 16) ++steps;
+        prio = std::max(greatest, least - steps);
+    }
+    BSG_CUDA(cudaStreamCreateWithPriority(&g->stream, cudaStreamNonBlocking, prio));
     int rc = BSGDTV_OK;
     for (cudaEvent_t &ev : g->run_ev)
         if (rc == BSGDTV_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
@@ -901,6 +921,13 @@ int bsgdtv_server_set_packing(bsgdtv_server_t s, int max_parts, double cost_rati
     std::lock_guard<std::mutex> lock(s->mu);
     s->pack_max_parts = max_parts;
     s->pack_cost_ratio = cost_ratio;
+    return BSGDTV_OK;
+}
+
+int bsgdtv_server_set_priority(bsgdtv_server_t s, int by_size) {
+    if (!s) return fail(BSGDTV_ERR_INVALID_ARG, "null argument");
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->priority_by_size = by_size != 0;
     return BSGDTV_OK;
 }
 
