@@ -61,11 +61,12 @@ MIX = [("g64", 1, 0.05, 14), ("g37", 2, 0.02, 9), ("g64", 3, 0.1, 23), ("g64", 4
        ("g64", 9, 0.02, 8), ("g37", 10, 0.06, 12)]
 
 
-def _serve(B, reqs, slots=3, max_tick=4, budget=1 << 34, stagger=0, pack=1):
+def _serve(B, reqs, slots=3, max_tick=4, budget=1 << 34, stagger=0, pack=1, priority=1):
     """Runs the requests through one server; submits `stagger` at a time from
     a second thread while the first ones run; pack > 1 lets groups take that
     many geometries.  Returns {index: x}."""
     with B.Server(budget, K, max_tick) as srv:
+        srv.set_priority(priority)
         if pack > 1:
             srv.set_packing(pack, 1e9)
             srv.hold(True)   # the whole burst is queued before the first group is made
@@ -123,6 +124,15 @@ def test_server_slots_by_l2_rule(B):
         A, n, _, mu = geometry(name)
         x_ref, _ = oracle.run(A, request(name, seed).astype(np.float64), (n, n), 1, 1, lam, mu, ep, K)
         assert rel(out[i], x_ref) <= 1e-4, i
+
+
+def test_server_priority_changes_no_result(B):
+    """Stream priorities by size (the default) and equal priorities give the
+    same results bit for bit (two geometries of different sizes)."""
+    with_prio, _ = _serve(B, MIX[:6], stagger=3)
+    equal, _ = _serve(B, MIX[:6], stagger=3, priority=0)
+    for i in range(6):
+        assert np.array_equal(with_prio[i], equal[i]), i
 
 
 def _op_bytes(B, A):
