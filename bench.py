@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--served-pack-ratio", type=float, default=4.0,
                     help="largest ratio of nonzeros between geometries packed into one group")
     ap.add_argument("--served-tick", type=int, default=10, help="max epochs between admissions")
+    ap.add_argument("--served-rate", type=float, default=0.0,
+                    help="Poisson arrival rate of the served stream, requests/s (0: 0.7x the saturated rate)")
     ap.add_argument("--served-priority", type=int, default=1,
                     help="1: groups of smaller geometries on higher-priority streams; 0: all equal")
     ap.add_argument("--served-slots", type=int, default=0,
@@ -275,7 +277,7 @@ def served_stream(args, B, synth):
     st0 = srv.stats()
     lat_sat, span_sat = run(np.zeros(N))
     sat_rps = N / span_sat
-    rate = 0.7 * sat_rps
+    rate = args.served_rate if args.served_rate > 0 else 0.7 * sat_rps
     arrivals = np.cumsum(rng.exponential(1.0 / rate, N))
     st1 = srv.stats()
     lat, span = run(arrivals)
@@ -309,7 +311,8 @@ def served_stream(args, B, synth):
             "max_running": st2["max_running"], "groups_made": st2["groups_made"],
             "ticks": st2["ticks"] - st1["ticks"], "setup_s": t_setup,
             "note": "latency = submit to x in host memory; inputs drawn from a pool of %d seeded "
-                    "phantoms per size; phase 1 all at once, phase 2 Poisson at 0.7x phase 1" % pool}
+                    "phantoms per size; phase 1 all at once, phase 2 Poisson at %s" % (
+                        pool, "%.3g requests/s (given)" % rate if args.served_rate > 0 else "0.7x phase 1")}
 
 
 # ------------------------------------------------------------- CPU oracle
