@@ -263,6 +263,16 @@ int bsgdtv_tv_prox(const float *b, float *x, int img_h, int img_w, double tau, i
 int bsgdtv_tv_prox_static(const float *b, float *x, int img_h, int img_w, double tau, int iters,
                           void *stream);
 
+/* Host only (no GPU needed): how the TV prox (Beck-Teboulle FGP, the prox of
+ * Algorithm 1's last step) tiles one image dimension of len pixels into
+ * regions of 64 pixels that overlap by `halo` (iterations per launch + 1):
+ * the region count, and for the first max_regions regions k their first
+ * pixel first[k] and their interior [lo[k], hi[k]) in region coordinates
+ * (first, lo, hi may be NULL).  The regions at the image's edges keep no halo
+ * on the outer side.  This is the placement the prox kernel computes. */
+int bsgdtv_fgp_tiling(int len, int halo, int max_regions, int *n_regions, int *first, int *lo,
+                      int *hi);
+
 /* Host only (no GPU needed): the partition bounds bsgdtv_create_csr uses when
  * row_bounds / col_bounds are NULL, written to row_bounds [M+1] and
  * col_bounds [N+1]. */

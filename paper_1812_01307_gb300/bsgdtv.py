@@ -61,6 +61,7 @@ def load(path: str | None = None):
         "bsgdtv_tv_prox": (I32, [P, P, I32, I32, D, I32, P]),
         "bsgdtv_tv_prox_static": (I32, [P, P, I32, I32, D, I32, P]),
         "bsgdtv_partition_bounds": (I32, [I64, I64, I32, I32, I64, I64, P, P]),
+        "bsgdtv_fgp_tiling": (I32, [I32, I32, I32, P, P, P, P]),
         "bsgdtv_layout_check": (I32, [I64, I64, I32, I32, P, P, P, I32, I32, I64, I64, P, P, I32, I32, P]),
         "bsgdtv_batch_create_csr": (I32, [ctypes.POINTER(P), I64, I64, I32, I32, P, P, P, I32, P]),
         "bsgdtv_batch_create_csr_ex": (I32, [ctypes.POINTER(P), I64, I64, I32, I32, P, P, P, I32, I32, P]),
@@ -120,6 +121,7 @@ def exported_symbols():
             "bsgdtv_run_until", "bsgdtv_get_x", "bsgdtv_reconstruct",
             "bsgdtv_get_state", "bsgdtv_set_state", "bsgdtv_objective", "bsgdtv_block_products",
             "bsgdtv_get_info", "bsgdtv_tv_prox", "bsgdtv_tv_prox_static", "bsgdtv_partition_bounds",
+            "bsgdtv_fgp_tiling",
             "bsgdtv_layout_check", "bsgdtv_run_subsets", "bsgdtv_run_subsets_timed",
             "bsgdtv_fp32_fma_peak", "bsgdtv_batch_create_csr", "bsgdtv_batch_destroy",
             "bsgdtv_batch_set_data", "bsgdtv_batch_run", "bsgdtv_batch_run_timed",
@@ -417,6 +419,18 @@ def bsgdtv_tv_prox_static(b, x, tau, iters, stream=None):
                                         int(b.shape[0]), int(b.shape[1]), float(tau), int(iters),
                                         stream if stream is not None else current_stream()),
            "bsgdtv_tv_prox_static")
+
+
+def bsgdtv_fgp_tiling(length, halo):
+    """The prox's regions along one dimension: list of (first, lo, hi)."""
+    lib = load()
+    n = ctypes.c_int()
+    _check(lib.bsgdtv_fgp_tiling(int(length), int(halo), 0, ctypes.byref(n), None, None, None),
+           "bsgdtv_fgp_tiling")
+    f, lo, hi = (np.zeros(max(n.value, 1), np.int32) for _ in range(3))
+    _check(lib.bsgdtv_fgp_tiling(int(length), int(halo), n.value, ctypes.byref(n), _host_ptr(f, np.int32),
+                                 _host_ptr(lo, np.int32), _host_ptr(hi, np.int32)), "bsgdtv_fgp_tiling")
+    return [(int(f[k]), int(lo[k]), int(hi[k])) for k in range(n.value)]
 
 
 def bsgdtv_partition_bounds(rows, cols, M, N, row_unit=1, col_unit=1):

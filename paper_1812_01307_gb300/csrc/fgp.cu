@@ -77,3 +77,21 @@ cudaError_t launch_fgp(const float *b, float *x, int h, int w, float tau, int it
 }
 
 }  // namespace bsgdtv
+
+using namespace bsgdtv;
+
+extern "C" int bsgdtv_fgp_tiling(int len, int halo, int max_regions, int *n_regions, int *first,
+                                 int *lo, int *hi) {
+    if (len < 1 || halo < 1 || 2 * halo >= fgpk::RW || max_regions < 0 || !n_regions)
+        return fail(BSGDTV_ERR_INVALID_ARG, "need len >= 1, 1 <= halo < 32, max_regions >= 0, n_regions");
+    const int n = fgpk::fgp_regions_along(len, fgpk::RW, halo);
+    *n_regions = n;
+    for (int k = 0; k < n && k < max_regions; ++k) {
+        int f = 0, l = 0, h = 0;
+        fgpk::fgp_place(k, n, len, fgpk::RW, halo, f, l, h);
+        if (first) first[k] = f;
+        if (lo) lo[k] = l;
+        if (hi) hi[k] = h;
+    }
+    return BSGDTV_OK;
+}

@@ -146,8 +146,8 @@ __host__ __device__ inline int fgp_regions_along(int len, int R, int HL) {
 }
 // Region b of n along that dimension: its first pixel and its interior [lo, hi)
 // in region-local coordinates.
-__device__ __forceinline__ void fgp_place(int b, int n, int len, int R, int HL, int &first, int &lo,
-                                          int &hi) {
+__host__ __device__ __forceinline__ void fgp_place(int b, int n, int len, int R, int HL, int &first,
+                                                   int &lo, int &hi) {
     if (n == 1) {
         first = 0;
         lo = 0;
