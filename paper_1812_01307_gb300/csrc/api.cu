@@ -606,11 +606,12 @@ int bsgdtv_set_data(bsgdtv_t h, const float *y, int y_on_device, double lambda, 
     BSG_CHECK(set_device(h));
     cudaStream_t s = h->stream;
     h->has_data = false;   // y is overwritten from here on: a failure leaves no data
-    // copy y, then in one launch r^{-1} = y - A x^0 = y, x^0 = 0 and max |y|
-    // (which is Inf or NaN exactly when y is not finite: the check); the
-    // read-back of max |y| returns after the copy has read y, so a host y may
-    // be reused at once, pageable or pinned.  The last block products are
-    // A x^0 = 0 (cleared when the stochastic iteration first needs them).
+    // one launch (after a copy when y is pageable host memory) stores y and
+    // sets r^{-1} = y - A x^0 = y, x^0 = 0 and the check word max |y| (Inf or
+    // NaN exactly when y is not finite); the synchronisation returns after
+    // y has been read, so a host y may be reused at once, pageable or
+    // pinned.  The last block products are A x^0 = 0 (cleared when the
+    // stochastic iteration first needs them).
     BSG_CHECK(enqueue_init(h, y, y_on_device));
     BSG_CUDA(cudaStreamSynchronize(s));
     if (!std::isfinite(*h->check_host)) return fail(BSGDTV_ERR_NONFINITE, "non-finite value in y");
