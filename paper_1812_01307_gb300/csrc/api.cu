@@ -1,6 +1,7 @@
 // C ABI of the BSGD-TV library: handle lifetime, data, the epoch loop of
 // Algorithm 1 (captured once per configuration into CUDA graphs), the FP64
 // step-size estimate (Theorem 1) and monitoring (Eq. 1).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -882,6 +883,28 @@ int bsgdtv_run_subsets_timed(bsgdtv_t h, int iters, int fgp_iters, const uint8_t
     return rc;
 }
 
+// Whether the GPU may write page-locked host memory at p through its device
+// address (memory registered read-only may not be written by the device),
+// asked through the driver's entry point; false when that cannot be asked.
+static bool device_writable(const void *p) {
+    using Fn = CUresult (*)(void *, CUpointer_attribute, CUdeviceptr);
+    static const Fn fn = []() -> Fn {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<Fn>(f);
+    }();
+    if (!fn) return false;
+    unsigned int flags = 0;
+    if (fn(&flags, CU_POINTER_ATTRIBUTE_ACCESS_FLAGS, (CUdeviceptr)(uintptr_t)p) != CUDA_SUCCESS) return false;
+    return flags == CU_POINTER_ATTRIBUTE_ACCESS_FLAG_READWRITE;
+}
+
 // x into a caller's buffer on the handle's stream: a copy on the device, or a
 // kernel writing page-locked host memory through its device address, or a
 // copy to pageable host memory.
@@ -892,7 +915,7 @@ static int enqueue_x_out(bsgdtv_ctx *h, float *out, int out_on_device) {
         return BSGDTV_OK;
     }
     float *dst = device_view(out, 0);
-    if (dst) BSG_CUDA(launch_copy_out(h->x, dst, c, h->stream));
+    if (dst && device_writable(out)) BSG_CUDA(launch_copy_out(h->x, dst, c, h->stream));
     else BSG_CUDA(cudaMemcpyAsync(out, h->x, c * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     return BSGDTV_OK;
 }
